@@ -1,0 +1,84 @@
+"""ctypes wrapper of oracle/direct.c: the NUDFT by its definition (eq. (1.2)).
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).  ``build()`` compiles the C
+file with gcc into ``oracle/_direct.so`` next to it; it is called lazily on first
+use and by ``__graft_entry__.build()``.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "direct.c")
+_LIB = os.path.join(_HERE, "_direct.so")
+_lib = None
+
+
+def build(force=False):
+    """Compile direct.c (plain C, OpenMP, no fast-math, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".%d.tmp" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC",
+                               "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        i64, p = ctypes.c_int64, ctypes.c_void_p
+        for name in ("nudft2", "nudft2h", "nudft2d"):
+            getattr(lib, name).argtypes = [i64, i64, p, p, p]
+            getattr(lib, name).restype = None
+        lib.nudft2_2d.argtypes = [i64, i64, i64, p, p, p, p]
+        lib.nudft2_2d.restype = None
+        _lib = lib
+    return _lib
+
+
+def _c128(a):
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def nudft2(x, c):
+    """f_j = sum_{k<N} c_k exp(-2 pi i x_j k)  (eq. (1.2))."""
+    x, c = _f64(x), _c128(c)
+    f = np.empty(x.size, dtype=np.complex128)
+    _load().nudft2(c.size, x.size, x.ctypes.data, c.ctypes.data, f.ctypes.data)
+    return f
+
+
+def nudft2_adjoint(x, g, N):
+    """c_k = sum_j g_j exp(+2 pi i x_j k), k < N: the conjugate transpose of nudft2."""
+    x, g = _f64(x), _c128(g)
+    c = np.empty(int(N), dtype=np.complex128)
+    _load().nudft2h(int(N), x.size, x.ctypes.data, g.ctypes.data, c.ctypes.data)
+    return c
+
+
+def nudft2_deriv(x, c):
+    """f'_j = sum_k (-2 pi i k) c_k exp(-2 pi i x_j k) = d f_j / d x_j."""
+    x, c = _f64(x), _c128(c)
+    f = np.empty(x.size, dtype=np.complex128)
+    _load().nudft2d(c.size, x.size, x.ctypes.data, c.ctypes.data, f.ctypes.data)
+    return f
+
+
+def nudft2_2d(x, y, C):
+    """f_j = sum_{k1<m, k2<n} C[k1, k2] exp(-2 pi i (k1 x_j + k2 y_j))  (eq. (4.1))."""
+    x, y, C = _f64(x), _f64(y), _c128(C)
+    m, n = C.shape
+    f = np.empty(x.size, dtype=np.complex128)
+    _load().nudft2_2d(m, n, x.size, x.ctypes.data, y.ctypes.data, C.ctypes.data, f.ctypes.data)
+    return f

@@ -1,0 +1,282 @@
+"""Pins for the low-rank oracle against what the paper and the mathematics fix.
+
+* Table 2.1's ranks (golden fixture) and the bound of eq. (2.7).
+* Fig. 2.1's rounding example (golden fixture).
+* Theorem A.2: ||A - A_K||_max <= eps, by brute force against the dense A.
+* Section 2.4's error bounds against the direct sum (an independent oracle).
+* gamma = 0 reduces to the FFT (section 2.1.2); the worst grid of section 2.4 has a
+  closed form through a library FFT.
+* A^H is the adjoint; the type-I transform of section 3.1 is the transpose.
+* The x-derivative against finite differences and torch autograd of a direct sum.
+* Planted mistakes (phase sign, primes, the i^r factor) fail the brute-force pin.
+"""
+
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import direct, lowrank
+from paper_1701_04492_gb300 import workloads as wl
+
+
+def _load(golden_dir, name):
+    with open(os.path.join(golden_dir, name)) as fh:
+        return json.load(fh)
+
+
+# --- K -----------------------------------------------------------------------
+
+@pytest.mark.parametrize("row", ["single", "half"])
+def test_table_2_1_rows_reproduced(golden_dir, row):
+    tab = _load(golden_dir, "table_2_1.json")
+    edges = tab["gamma_band_upper_edges"]
+    want = tab["rows"][row]["K"]
+    got = [lowrank.choose_K(tab["rows"][row]["eps"], g) for g in edges]
+    assert got == want
+
+
+def test_table_2_1_double_row_is_the_cap(golden_dir):
+    tab = _load(golden_dir, "table_2_1.json")
+    edges = tab["gamma_band_upper_edges"]
+    want = tab["rows"]["double"]["K"]
+    got = [lowrank.choose_K(tab["rows"]["double"]["eps"], g) for g in edges]
+    assert got == want
+    # Strictly inside a band the rank never exceeds the band's table entry.
+    for lo, hi, K in zip(edges[:-1], edges[1:], want[1:]):
+        assert lowrank.choose_K(1e-300 + 2.2e-16, 0.5 * (lo + hi)) <= K
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-4, 1e-7, 1e-9, 1e-12, 1e-14])
+@pytest.mark.parametrize("gamma", [1 / 64, 1 / 8, 0.3, 0.5])
+def test_rank_within_eq_2_7(eps, gamma):
+    # Eq. (2.7) is a sufficient rank; the tail rule picks the smallest rank that
+    # satisfies the same triangle-inequality bound, so it can only be smaller.
+    assert lowrank.choose_K(eps, gamma) <= lowrank.lambert_w_rank(eps, gamma)
+
+
+def test_rank_at_the_metric_workload():
+    # gamma -> 1/2, eps = 1e-9: K = 12, and 11 does not suffice.
+    assert lowrank.choose_K(1e-9, 0.5) == 12
+    assert lowrank.tail_bound(11, 0.5) > 1e-9
+
+
+def test_rank_monotone_in_gamma_and_eps():
+    gs = np.linspace(1e-3, 0.5, 40)
+    for eps in (1e-4, 1e-9, 1e-14):
+        Ks = [lowrank.choose_K(eps, g) for g in gs]
+        assert all(a <= b for a, b in zip(Ks, Ks[1:]))
+    for g in (0.1, 0.5):
+        Ks = [lowrank.choose_K(e, g) for e in (1e-2, 1e-4, 1e-8, 1e-12)]
+        assert all(a <= b for a, b in zip(Ks, Ks[1:]))
+
+
+# --- rounding (eqs. (2.8)-(2.9)) ------------------------------------------------
+
+def test_fig_2_1_example(golden_dir):
+    fig = _load(golden_dir, "fig_2_1.json")
+    N = fig["N"]
+    x = np.array(fig["x_times_N_as_drawn"]) / N
+    s, t, delta = lowrank.round_to_grid(x, N)
+    assert s.tolist() == fig["s_arrow_targets_as_drawn"]
+    assert t.tolist() == fig["t_from_eq_2_9"]
+    assert np.all(np.abs(delta) <= 0.5)
+
+
+def test_rounding_ties_wrap_and_negative():
+    L = 16
+    x = np.array([0.5 / L, 1.5 / L, 1.0, -0.25 / L, -3.0 - 1.0 / L, 15.5 / L, 7.0 + 3.0 / L])
+    s, t, delta = lowrank.round_to_grid(x, L)
+    assert s.tolist() == [0, 2, 16, 0, -49, 16, 115]     # ties to even
+    assert t.tolist() == [0, 2, 0, 0, 15, 0, 3]          # Euclidean mod
+    assert np.all(np.abs(delta) <= 0.5)
+    assert np.all(L * x == s + delta)
+
+
+# --- Theorem A.2 by brute force ------------------------------------------------
+
+SAMPLE_SETS = {
+    "uniform": lambda n, L: wl.samples_uniform(n, 21),
+    "perturbed": lambda n, L: wl.samples_perturbed(n, 22, 0.5),
+    "perturbed_1/8": lambda n, L: wl.samples_perturbed(n, 23, 0.125),
+    "worst_1/32": lambda n, L: wl.samples_worst(n, 1 / 32),
+    "wide": lambda n, L: 10.0 * wl.samples_uniform(n, 24) - 5.0,
+}
+
+
+@pytest.mark.parametrize("name", sorted(SAMPLE_SETS))
+@pytest.mark.parametrize("eps", [1e-4, 1e-9, 1e-12])
+@pytest.mark.parametrize("N,L", [(256, 256), (200, 256), (128, 256), (97, 97)])
+def test_low_rank_approximation_bound(name, eps, N, L):
+    x = SAMPLE_SETS[name](N, L)
+    P = lowrank.plan(N, x, eps, L)
+    err = np.max(np.abs(lowrank.dense_A(P) - lowrank.dense_AK(P)))
+    assert err <= eps
+    assert err <= lowrank.tail_bound(P.K, P.gamma) + 1e-14
+    assert P.gamma <= N / (2 * L) + 1e-15
+
+
+def test_oversampling_lowers_the_rank():
+    # Section 2.3: on a grid of 2N points gamma <= 1/4, so double precision needs
+    # 13 FFTs of length 2N instead of 16 of length N (Table 2.1).
+    N = 1024
+    x = wl.samples_uniform(N, 25)
+    assert lowrank.plan(N, x, 2.2e-16).K == 16
+    assert lowrank.plan(N, x, 2.2e-16, 2 * N).K == 13
+
+
+def _plant(monkeypatch, what):
+    if what == "phase_sign":
+        monkeypatch.setattr(lowrank, "phase", lambda d: np.exp(1j * math.pi * np.asarray(d)))
+    elif what == "no_primes":
+        monkeypatch.setattr(lowrank, "prime_weights", lambda K: np.ones(K))
+    elif what == "no_i_power":
+        orig = lowrank.bessel_coefficients
+        monkeypatch.setattr(lowrank, "bessel_coefficients",
+                            lambda K, g: np.abs(orig(K, g)) * np.sign(orig(K, g).real + orig(K, g).imag))
+    elif what == "bessel_sign":
+        orig = lowrank.bessel_coefficients
+
+        def flipped(K, g):
+            return orig(K, -g)
+        monkeypatch.setattr(lowrank, "bessel_coefficients", flipped)
+
+
+@pytest.mark.parametrize("what", ["phase_sign", "no_primes", "no_i_power", "bessel_sign"])
+def test_planted_mistakes_break_the_bound(monkeypatch, what):
+    N = 128
+    x = wl.samples_uniform(N, 26)
+    _plant(monkeypatch, what)
+    P = lowrank.plan(N, x, 1e-9)
+    err = np.max(np.abs(lowrank.dense_A(P) - lowrank.dense_AK(P)))
+    assert err > 1e-3
+
+
+# --- the whole method against the direct sum (section 2.4) ---------------------
+
+@pytest.mark.parametrize("eps", [1e-4, 1e-9, 1e-12])
+@pytest.mark.parametrize("name", ["uniform", "perturbed", "wide"])
+@pytest.mark.parametrize("N,L", [(4096, 4096), (3000, 4096), (1000, 1000)])
+def test_error_bound_against_direct(eps, name, N, L):
+    x = SAMPLE_SETS[name](N, L)
+    c = wl.coeffs_cn(N, 31)
+    P = lowrank.plan(N, x, eps, L)
+    f = lowrank.nufft2(P, c)
+    fd = direct.nudft2(x, c)
+    rounding = 1e-15 * N * math.log2(L)
+    # infinity norm: |((A - A_K) o F(t,:)) c|_j <= ||A - A_K||_max ||c||_1
+    assert np.max(np.abs(f - fd)) <= (eps + rounding) * np.sum(np.abs(c))
+    # 2-norm bound of section 2.4: N eps ||c||_2
+    assert np.linalg.norm(f - fd) <= N * (eps + rounding) * np.linalg.norm(c)
+
+
+def test_gamma_zero_is_one_fft():
+    N = 2048
+    c = wl.coeffs_cn(N, 32)
+    P = lowrank.plan(N, wl.samples_equispaced(N), 1e-12)
+    assert P.K == 1 and P.gamma == 0.0
+    assert np.array_equal(lowrank.nufft2(P, c), np.fft.fft(c)[P.t])
+
+
+@pytest.mark.parametrize("N,gamma", [(4096, 0.5), (4096, 1 / 8), (1 << 16, 1 / 32), (1 << 16, 0.5)])
+def test_worst_grid_closed_form(N, gamma):
+    # Section 2.4's worst grid: each half is a shifted uniform grid, so
+    # f_j = FFT(c o exp(-+2 pi i gamma k / N))_j exactly.
+    x = wl.samples_worst(N, gamma)
+    c = wl.coeffs_cn(N, 33)
+    k = np.arange(N)
+    plus = np.fft.fft(c * np.exp(-2j * math.pi * gamma * k / N))
+    minus = np.fft.fft(c * np.exp(2j * math.pi * gamma * k / N))
+    ref = np.where(np.arange(N) <= N // 2, plus, minus)
+    for eps in (1e-9, 1e-14):
+        P = lowrank.plan(N, x, eps)
+        f = lowrank.nufft2(P, c)
+        assert np.max(np.abs(f - ref)) <= (eps + 1e-15 * N) * np.sum(np.abs(c))
+
+
+def test_error_growth_decaying_coefficients():
+    # Section 2.4: with c ~ randn / k^2 the error is far below the Gaussian case.
+    N = 2048
+    x = wl.samples_uniform(N, 34)
+    P = lowrank.plan(N, x, 1e-7)
+    e_gauss = np.linalg.norm(lowrank.nufft2(P, wl.coeffs_cn(N, 34)) - direct.nudft2(x, wl.coeffs_cn(N, 34)))
+    cd = wl.coeffs_decay(N, 34)
+    e_decay = np.linalg.norm(lowrank.nufft2(P, cd) - direct.nudft2(x, cd))
+    assert e_decay < e_gauss
+
+
+# --- adjoint, transpose and derivative ----------------------------------------
+
+@pytest.mark.parametrize("N,L,M", [(4096, 4096, 4096), (1000, 1024, 1500), (64, 64, 10)])
+def test_adjoint_identity(N, L, M):
+    x = wl.samples_uniform(M, 41)
+    c = wl.coeffs_cn(N, 41)
+    g = wl.cotangent_cn(M, 41)
+    P = lowrank.plan(N, x, 1e-9, L)
+    lhs = np.vdot(g, lowrank.nufft2(P, c))
+    rhs = np.vdot(lowrank.nufft2_adjoint(P, g), c)
+    scale = np.linalg.norm(lowrank.nufft2(P, c)) * np.linalg.norm(g)
+    assert abs(lhs - rhs) <= 1e-13 * scale
+
+
+@pytest.mark.parametrize("eps", [1e-6, 1e-12])
+def test_adjoint_against_direct(eps):
+    N, M = 2048, 3000
+    x = wl.samples_uniform(M, 42)
+    g = wl.cotangent_cn(M, 42)
+    P = lowrank.plan(N, x, eps, 2048)
+    c = lowrank.nufft2_adjoint(P, g)
+    ref = direct.nudft2_adjoint(x, g, N)
+    assert np.max(np.abs(c - ref)) <= (eps + 1e-15 * M) * np.sum(np.abs(g))
+
+
+def test_type1_is_the_transpose():
+    # Section 3.1: F~1 c with (F~1)_jk = exp(-2 pi i (j/N) w_k) equals F~2^T c for
+    # samples w_k / N.
+    N = 512
+    w = N * wl.samples_uniform(N, 43)
+    g = wl.cotangent_cn(N, 43)
+    P = lowrank.plan(N, w / N, 1e-12)
+    f1 = lowrank.nufft1(P, g)
+    j = np.arange(N)
+    ref = np.exp(-2j * math.pi * np.outer(j, w) / N) @ g
+    assert np.max(np.abs(f1 - ref)) <= 1e-11 * np.sum(np.abs(g))
+
+
+def test_x_derivative_against_direct_and_finite_differences():
+    N, M = 200, 120
+    x = wl.samples_uniform(M, 44)
+    c = wl.coeffs_cn(N, 44)
+    g = wl.cotangent_cn(M, 44)
+    P = lowrank.plan(N, x, 1e-12, 256)
+    gx = lowrank.nufft2_dx(P, c, g)
+    ref = np.real(np.conj(g) * direct.nudft2_deriv(x, c))
+    assert np.max(np.abs(gx - ref)) <= 1e-9 * np.sum(np.abs(c)) * 2 * math.pi * N
+    # central differences of Re<f, g> = Re sum_j conj(g_j) f_j, h = 1e-6 (FP64);
+    # truncation (2 pi N h)^2 / 6 ~ 3e-7 relative at N = 200.
+    h = 1e-6
+    fp = direct.nudft2(x + h, c)
+    fm = direct.nudft2(x - h, c)
+    fd = np.real(np.conj(g) * (fp - fm)) / (2 * h)
+    assert np.max(np.abs(gx - fd)) <= 1e-5 * np.max(np.abs(ref))
+
+
+def test_x_derivative_against_torch_autograd():
+    torch = pytest.importorskip("torch")
+    N, M = 96, 50
+    x = wl.samples_uniform(M, 45)
+    c = wl.coeffs_cn(N, 45)
+    g = wl.cotangent_cn(M, 45)
+    xt = torch.tensor(x, dtype=torch.float64, requires_grad=True)
+    ct = torch.tensor(c, dtype=torch.complex128, requires_grad=True)
+    k = torch.arange(N, dtype=torch.float64)
+    f = (torch.exp(-2j * math.pi * xt[:, None] * k[None, :]) * ct[None, :]).sum(1)
+    loss = (torch.conj(torch.tensor(g)) * f).real.sum()
+    loss.backward()
+    P = lowrank.plan(N, x, 1e-13, 128)
+    assert np.max(np.abs(lowrank.nufft2_dx(P, c, g) - xt.grad.numpy())) <= 1e-8 * N * N
+    # d loss / d c in torch's convention (conjugate Wirtinger, x2) is A^H g.
+    gc = ct.grad.numpy()
+    assert np.max(np.abs(lowrank.nufft2_adjoint(P, g) - gc)) <= 1e-11 * np.sum(np.abs(g))
