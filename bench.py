@@ -1,0 +1,401 @@
+#!/usr/bin/env python
+"""Benchmark of the low-rank NUFFT-II on one GB300: N = M = 2^20, eps = 1e-9.
+
+One step = the whole online hot path on one batch of synthetic input: the forward
+NUFFT-II f = A c (pass 1 + pass 2), then the backward of a loss through it: the
+adjoint A^H g (pass A + pass B) and the x-derivative (pass 1 + pass 2 on
+(-2 pi i k) c).  The plan (rounding, rank, coefficients, bucketing) is built once
+before the timed region, as the paper's planning stage is (section 2.3); its time
+is reported separately.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Inputs: x_j = j/N + 0.5 u_j / N with u_j ~ U[-1, 1] (the perturbed grid), c, g ~ CN(0,1)
+complex64, all seeded (paper_1701_04492_gb300.workloads).  L2 is flushed (a 512 MiB
+write) before every timed step; only the step itself is inside the CUDA events.
+Rank 0 prints one JSON line.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "NUFFT-II Gpts/s at N=2^20, ε=1e-9 (fwd, fwd+bwd); % HBM roofline vs plain"
+N_LOG2 = 20
+EPS = 1e-9
+SEED = 2024
+FLUSH_BYTES = 512 << 20
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP32 ALU peak: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2070 MHz (maximum SM clock)
+SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _workload():
+    from paper_1701_04492_gb300 import workloads as wl
+    N = 1 << N_LOG2
+    x = wl.samples_perturbed(N, SEED, 0.5)
+    c = wl.coeffs_cn(N, SEED).astype(np.complex64)
+    g = wl.cotangent_cn(N, SEED).astype(np.complex64)
+    return N, x, c, g
+
+
+# ---------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.uuid, "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) != 6:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[2:]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------
+# traffic from the committed ncu summary (null when the kernels changed since)
+# ---------------------------------------------------------------------------------
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1701_04492_gb300", "csrc")
+    for name in ("fft_team.cuh", "passes.cuh"):
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(kernel):
+    path = os.path.join(ROOT, "profiles", "ncu_traffic_n2e20.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"source_hash:\s*(\w+)", txt)
+    if not m or m.group(1) != kernel_source_hash():
+        return None
+    m = re.search(r"^\|\s*%s\s*\|[^|]*\|\s*([0-9.eE+]+)\s*\|" % re.escape(kernel), txt, re.M)
+    return float(m.group(1)) if m else None
+
+
+# ---------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1701_04492_gb300 import api
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    N, x, c_np, g_np = _workload()
+    M = x.size
+    stream = torch.cuda.current_stream(dev)
+    c = torch.tensor(c_np, device=dev)
+    g = torch.tensor(g_np, device=dev)
+    f = torch.empty(M, dtype=torch.complex64, device=dev)
+    gc = torch.empty(N, dtype=torch.complex64, device=dev)
+    gx = torch.empty(M, dtype=torch.float32, device=dev)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    plan = api.Plan(N, x, EPS, "f32", device=dev)
+    torch.cuda.synchronize(dev)
+    plan_ms = (time.perf_counter() - t0) * 1e3
+
+    def step():
+        plan.forward(c, f)
+        plan.adjoint(f, gc)          # the loss cotangent is taken as f itself
+        plan.dx(c, g, gx)
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize(dev)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in evs:
+            flush.fill_(1.0)
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize(dev)
+        return [a.elapsed_time(b) for a, b in evs]
+
+    uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(uuid) as clk:
+        step_ms = timed(step, args.steps, args.warmup)
+    if ws > 1:
+        dist.barrier()
+    tot = torch.tensor([sum(step_ms)], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+    total_ms = float(tot.item())
+    value = ws * M * args.steps / (total_ms * 1e-3) / 1e9
+
+    extra = {}
+    if rank == 0:
+        # forward only, and the uniform-x forward
+        fwd_ms = timed(lambda: plan.forward(c, f), args.steps, args.warmup)
+        extra["fwd_gpts"] = M * len(fwd_ms) / (sum(fwd_ms) * 1e-3) / 1e9
+        extra["fwd_ms"] = float(np.mean(fwd_ms))
+        from paper_1701_04492_gb300 import workloads as wl
+        xu = wl.samples_uniform(M, SEED)
+        plan_u = api.Plan(N, xu, EPS, "f32", device=dev)
+        fu_ms = timed(lambda: plan_u.forward(c, f), args.steps, args.warmup)
+        extra["fwd_uniform_x_gpts"] = M * len(fu_ms) / (sum(fu_ms) * 1e-3) / 1e9
+        del plan_u
+        # the plain unfused FP64 form of the method, and the fused FP64 path
+        c64 = c.to(torch.complex128)
+        f64 = torch.empty(M, dtype=torch.complex128, device=dev)
+        plan64 = api.Plan(N, x, EPS, "f64", unfused=True, device=dev)
+        st = max(3, args.steps // 4)
+        pl_ms = timed(lambda: plan64.forward_unfused(c64, f64), st, 2)
+        fu64_ms = timed(lambda: plan64.forward(c64, f64), st, 2)
+        extra["plain_unfused_fp64_fwd_gpts"] = M * st / (sum(pl_ms) * 1e-3) / 1e9
+        extra["fused_fp64_fwd_gpts"] = M * st / (sum(fu64_ms) * 1e-3) / 1e9
+        extra["fused_fp32_vs_plain_fp64_fwd_speedup"] = extra["fwd_gpts"] / extra["plain_unfused_fp64_fwd_gpts"]
+        del plan64
+        # per-kernel device time from events around each launch
+        tplan = api.Plan(N, x, EPS, "f32", timing=True, device=dev)
+        kt = {"pass1": [], "pass2": [], "passA": [], "passB": [], "pass1_dx": [], "pass2_dx": []}
+        for i in range(args.warmup + args.steps):
+            flush.fill_(1.0)
+            tplan.forward(c, f)
+            a1, a2 = tplan.kernel_times()
+            flush.fill_(1.0)
+            tplan.adjoint(f, gc)
+            b1, b2 = tplan.kernel_times()
+            flush.fill_(1.0)
+            tplan.dx(c, g, gx)
+            d1, d2 = tplan.kernel_times()
+            if i >= args.warmup:
+                for k, v in zip(kt, (a1, a2, b1, b2, d1, d2)):
+                    kt[k].append(v)
+        kavg = {k: float(np.mean(v)) for k, v in kt.items()}
+        extra["kernel_ms"] = kavg
+        K, L = tplan.K, tplan.L
+        L1 = 1 << ((N_LOG2 + 1) // 2)
+        L2 = L // L1
+        flops = {
+            "pass1": 5.0 * K * L * np.log2(L2) + 2.0 * K * N,
+            "pass2": 5.0 * K * L * np.log2(L1) + 8.0 * K * M,
+        }
+        flops["passA"], flops["passB"] = flops["pass2"], flops["pass1"]
+        flops["pass1_dx"], flops["pass2_dx"] = flops["pass1"], flops["pass2"]
+        dom = max(("pass1", "pass2", "passA", "passB"), key=lambda k: kavg[k])
+        peak_tf = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        ach = flops[dom] / (kavg[dom] * 1e-3) / 1e12
+        traffic = committed_traffic(dom)
+        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s",
+                "frac": ach / peak_tf, "traffic": traffic,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                "flops_per_launch": flops[dom]}
+        hbm = json.load(open(PEAKS_PATH))["hbm_gbs"] if os.path.exists(PEAKS_PATH) else 6800.0
+        fwd_s = extra["fwd_ms"] * 1e-3
+        extra["hbm_algorithmic"] = {
+            "bytes_per_point": 24, "fwd_GBps": 24.0 * M / fwd_s / 1e9,
+            "frac_of_measured_hbm": 24.0 * M / fwd_s / 1e9 / hbm, "hbm_peak_GBps": hbm}
+        del tplan
+
+        # end to end through the API with host buffers: H2D c, g; fwd + bwd; D2H f, gc, gx
+        ch = torch.tensor(c_np).pin_memory()
+        ghost = torch.tensor(g_np).pin_memory()
+        fh = torch.empty(M, dtype=torch.complex64).pin_memory()
+        gch = torch.empty(N, dtype=torch.complex64).pin_memory()
+        gxh = torch.empty(M, dtype=torch.float32).pin_memory()
+
+        def e2e_step():
+            c.copy_(ch, non_blocking=True)
+            g.copy_(ghost, non_blocking=True)
+            step()
+            fh.copy_(f, non_blocking=True)
+            gch.copy_(gc, non_blocking=True)
+            gxh.copy_(gx, non_blocking=True)
+        e_ms = timed(e2e_step, args.steps, args.warmup)
+        torch.cuda.synchronize(dev)
+        e2e = {"value": M * len(e_ms) / (sum(e_ms) * 1e-3) / 1e9, "unit": "Gpts/s",
+               "h2d_bytes_per_step": ch.numel() * 8 + ghost.numel() * 8,
+               "d2h_bytes_per_step": fh.numel() * 8 + gch.numel() * 8 + gxh.numel() * 4}
+
+        line = {
+            "metric": METRIC, "value": value, "unit": "Gpts/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "1D NUFFT-II fwd+bwd (fwd, adjoint A^H, d/dx), N=M=2^20, eps=1e-9, "
+                                   "perturbed grid x_j=j/N+0.5u_j/N, c,g~CN(0,1) complex64",
+                       "N": N, "M": M, "eps": EPS, "K": K, "gamma": plan.gamma, "L": L,
+                       "parallelism": "replicas" if ws > 1 else "single-gpu",
+                       "l2": "flushed before every timed step (512 MiB write)"},
+            "plan_ms": plan_ms,
+            "roofline": roof,
+            "e2e": e2e,
+            "gpu_launches": 6 * args.steps,
+            "clocks": clk.summary(),
+        }
+        line.update(extra)
+        if ws == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(plan, c_np, g_np, x, f)
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def cpu_baseline(plan, c_np, g_np, x, f_gpu):
+    """The oracle as it stands, one FP64 fwd+bwd step at a time on this host, for
+    about 10-20 s; also the GPU result's error against it."""
+    from oracle import lowrank
+    N = c_np.size
+    c = c_np.astype(np.complex128)
+    g = g_np.astype(np.complex128)
+    P = lowrank.plan(N, x, EPS, plan.L)
+    f_cpu = None
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        f_cpu = lowrank.nufft2(P, c)
+        lowrank.nufft2_adjoint(P, f_cpu)
+        lowrank.nufft2_dx(P, c, g)
+        n += 1
+        if time.perf_counter() - t0 > 10.0 or n >= 3:
+            break
+    dt = time.perf_counter() - t0
+    fg = f_gpu.cpu().numpy().astype(np.complex128)
+    err2 = float(np.linalg.norm(fg - f_cpu) / np.linalg.norm(f_cpu))
+    errinf = float(np.max(np.abs(fg - f_cpu)) / np.sum(np.abs(c)))
+    return {"value": x.size * n / dt / 1e9, "unit": "Gpts/s", "cores": 1, "kind": "oracle",
+            "sample": "%d full fwd+bwd step(s) of the same workload (N=M=2^20, K=%d) in numpy FP64 "
+                      "(single-threaded FFT), plan excluded" % (n, P.K),
+            "gpu_f32_fwd_rel2_err_vs_oracle": err2, "gpu_f32_fwd_inf_err_over_c1": errinf}
+
+
+# ---------------------------------------------------------------------------------
+# reference arm: the oracle, on this host's cores
+# ---------------------------------------------------------------------------------
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    from oracle import lowrank
+    N, x, c_np, g_np = _workload()
+    c = c_np.astype(np.complex128)
+    g = g_np.astype(np.complex128)
+    P = lowrank.plan(N, x, EPS, None if N >= 1024 else 1024)
+
+    def step():
+        f = lowrank.nufft2(P, c)
+        lowrank.nufft2_adjoint(P, f)
+        lowrank.nufft2_dx(P, c, g)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    v = x.size * args.steps / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Gpts/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "1D NUFFT-II fwd+bwd (fwd, adjoint A^H, d/dx), N=M=2^20, eps=1e-9, "
+                                   "perturbed grid x_j=j/N+0.5u_j/N, c,g~CN(0,1)", "N": N, "M": x.size,
+                       "eps": EPS, "K": P.K},
+            "cpu_baseline": {"value": v, "unit": "Gpts/s", "cores": 1, "kind": "oracle",
+                             "sample": "full fwd+bwd steps of the workload in numpy FP64, plan excluded"},
+            "e2e": {"value": v, "unit": "Gpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,162 @@
+/* nufft.h -- C ABI of the GB300 low-rank NUFFT library (libnufft.so).
+ *
+ * The transform is the nonuniform DFT of type II of Ruiz-Antolin and Townsend,
+ * "A nonuniform fast Fourier transform based on low rank approximation"
+ * (arXiv:1701.04492), eq. (1.2):
+ *
+ *     f_j = sum_{k=0}^{N-1} c_k exp(-2 pi i x_j k),      j = 0..M-1,
+ *
+ * computed by the method of section 2.2: each sample is rounded to the nearest of
+ * L grid points (eqs. (2.8)-(2.9)), the perturbation matrix is replaced by its
+ * rank-K Chebyshev/Bessel approximation (eq. (2.6), Theorem A.2), and f is the
+ * sum of K diagonally scaled FFTs of length L (eq. (2.11), section 2.3).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Complex arrays are interleaved (re, im), contiguous: float2 for NUFFT_F32
+ *   (torch.complex64), double2 for NUFFT_F64 (torch.complex128), as the plan's
+ *   precision says.  Real arrays (x, gx) are double for the plan, and of the
+ *   plan's precision for gx.
+ * - Pointers named *_dev are device pointers owned by the caller; *_host are
+ *   host pointers (pinned memory gives the fastest copies).  The library keeps no
+ *   reference to any caller pointer after a call returns.
+ * - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *   stream).  Exec calls are asynchronous on that stream: they enqueue kernels,
+ *   allocate nothing and do not synchronise.
+ * - Frequencies are k = 0..N-1 (not centred), with the negative exponent, as in
+ *   the paper.  Samples x_j may be any finite reals; they are wrapped by
+ *   periodicity (section 2.2 allows samples outside [0, 1)).
+ * - Return value: NUFFT_OK (0) or a negative NUFFT_E* code; nufft_strerror()
+ *   names it.  No C++ exception crosses this boundary.  A plan stays valid after
+ *   an exec call fails.
+ * - A plan may be used from one stream at a time: its work buffer is shared by
+ *   all exec calls on it.
+ */
+#ifndef NUFFT_H
+#define NUFFT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nufft_plan_s *nufft_plan;
+
+enum nufft_prec { NUFFT_F32 = 0, NUFFT_F64 = 1 };
+
+enum nufft_status {
+    NUFFT_OK = 0,
+    NUFFT_EINVAL = -1,        /* bad argument: size, eps, null pointer, non-finite x */
+    NUFFT_ENOMEM = -2,        /* device or host allocation failed */
+    NUFFT_ECUDA = -3,         /* a CUDA call failed (no device, launch error, ...) */
+    NUFFT_EUNSUPPORTED = -4,  /* size beyond what this build handles */
+    NUFFT_ESTATE = -5         /* call needs a plan option that was not set */
+};
+
+/* Plan flags. */
+#define NUFFT_PLAN_UNFUSED 1u  /* also build the materialised factors U (M x K) and
+                                  V (N x K) used by nufft2_exec_unfused */
+#define NUFFT_PLAN_TIMING 2u   /* record a CUDA event around every kernel the exec
+                                  calls launch (see nufft_kernel_times) */
+
+/* Planning stage (section 2.3, "Planning the transform").
+ *
+ * Computes s = rint(L x), t = s mod L, delta = L x - s (eqs. (2.8)-(2.9)) and the
+ * scaled perturbation d = delta * N / L in FP64 on the device, then
+ * gamma = max |d| (section 2.1.2 "always compute gamma"), the rank K (the smallest
+ * rank whose dropped Chebyshev/Bessel terms sum to <= eps, capped by Table 2.1's
+ * double-precision row), the coefficients a_pr of eq. (2.6), a bucketing of the
+ * samples by grid point, and twiddle tables.
+ *
+ *   out    receives the plan handle (set to NULL on failure).
+ *   N      number of frequencies, 1 <= N <= 2^22.
+ *   M      number of samples, 0 <= M < 2^31.
+ *   x_dev  M doubles on the device; read during the call only.  Must be finite
+ *          with |L x| < 2^52.
+ *   eps    working accuracy, 0 < eps < 1.
+ *   prec   NUFFT_F32 or NUFFT_F64: the arithmetic of the exec calls.
+ *   L      grid size: 0 picks the smallest power of two >= max(N, 1024); a
+ *          nonzero value must be a power of two with max(N, 1024) <= L <= 2^22
+ *          (L > N is the oversampling variant of section 2.3 and lowers K).
+ *   flags  0 or a combination of NUFFT_PLAN_UNFUSED and NUFFT_PLAN_TIMING.
+ *
+ * Allocates all device memory the exec calls need.  Synchronises `stream` once
+ * (to read gamma and validate x).  Errors: NUFFT_EINVAL, NUFFT_EUNSUPPORTED,
+ * NUFFT_ENOMEM, NUFFT_ECUDA.
+ */
+int nufft2_plan(nufft_plan *out, int64_t N, int64_t M, const double *x_dev, double eps,
+                int prec, int64_t L, unsigned flags, void *stream);
+
+/* Plan facts.  Any output pointer may be NULL.  K = rank, gamma = max |d_j|,
+ * L = grid size, work_bytes = device memory the plan owns. */
+int nufft2_plan_info(nufft_plan p, int *K, double *gamma, int64_t *L, int64_t *work_bytes);
+
+/* Copy the plan's FP64 rounding results and coefficients out (for checking).
+ *   t_dev      M int32 on the device: t_j = mod(rint(L x_j), L)     (eq. (2.9)); may be NULL
+ *   d_dev      M doubles on the device: d_j = (L x_j - s_j) N / L   (the scaled
+ *              perturbation of eq. (2.10)); may be NULL
+ *   alpha_host K*K doubles on the host, [p*K + r] = alpha_pr with the eq. (2.6)
+ *              coefficient a_pr = i^r alpha_pr; may be NULL
+ * Synchronises `stream`. */
+int nufft2_plan_export(nufft_plan p, int32_t *t_dev, double *d_dev, double *alpha_host, void *stream);
+
+/* Release the plan and all device memory it owns.  Safe on NULL.  The caller must
+ * make sure no exec on the plan is still running (synchronise its stream). */
+int nufft_destroy(nufft_plan p);
+
+/* Online stage, forward (eq. (2.11); the two-step form of section 2.3):
+ * f = sum_r D_{u_r} I_L(t,:) F_L D_{v_r} c.
+ *   c_dev  N complex coefficients.   f_dev  M complex values (written).
+ * c and f must not overlap.  Error bound: |f - f_exact|_inf <= eps ||c||_1 plus
+ * rounding of the plan's precision. */
+int nufft2_exec(nufft_plan p, const void *c_dev, void *f_dev, void *stream);
+
+/* Adjoint: c = A^H g, the conjugate transpose of nufft2_exec's operator, i.e.
+ * c_k = sum_j g_j exp(+2 pi i x_j k).  Section 3.1 gives the transpose (the
+ * paper's NUFFT-I) as the same factors with F^T in place of F; the adjoint is
+ * its complex conjugate: F~2^T g = conj(A^H conj(g)).
+ *   g_dev  M complex values.   c_dev  N complex coefficients (written). */
+int nufft1_exec(nufft_plan p, const void *g_dev, void *c_dev, void *stream);
+
+/* Derivative with respect to the samples (not in the paper; the chain rule of
+ * eq. (1.2)): gx_j (+)= Re(conj(g_j) f'_j) with f'_j = sum_k (-2 pi i k) c_k
+ * exp(-2 pi i x_j k), computed as a second NUFFT-II of (-2 pi i k) o c on the same
+ * plan.  This is d/dx_j of Re(sum_j conj(g_j) f_j).
+ *   c_dev   N complex, g_dev M complex, gx_dev M reals of the plan's precision.
+ *   accumulate  0: gx = ..., 1: gx += ... */
+int nufft2_exec_dx(nufft_plan p, const void *c_dev, const void *g_dev, void *gx_dev,
+                   int accumulate, void *stream);
+
+/* B independent transforms sharing the plan: f_b = A c_b, b = 0..B-1, with
+ * c_b at c_dev + b*ldc elements and f_b at f_dev + b*ldf elements
+ * (ldc >= N, ldf >= M). */
+int nufft2_exec_batch(nufft_plan p, int64_t B, const void *c_dev, int64_t ldc,
+                      void *f_dev, int64_t ldf, void *stream);
+
+/* The same as nufft2_exec with HOST buffers: copies c host->device into a
+ * plan-owned staging buffer, runs the transform, copies f device->host and
+ * synchronises `stream`. */
+int nufft2_exec_host(nufft_plan p, const void *c_host, void *f_host, void *stream);
+
+/* The unfused form of the same method, the section 2.3 one-liner run step by
+ * step: W = D_v c for all ranks, K plain FFTs of length L, row gather X(t,:),
+ * then f = (U .* X) 1 with the materialised factors.  Needs a plan made with
+ * NUFFT_PLAN_UNFUSED (else NUFFT_ESTATE).  A comparator, not the fast path. */
+int nufft2_exec_unfused(nufft_plan p, const void *c_dev, void *f_dev, void *stream);
+
+/* Device time of each kernel launched by the plan's most recent exec call, in
+ * launch order (forward and dx: pass 1, pass 2; adjoint: pass A, pass B), from
+ * CUDA events recorded on the exec's stream.  Needs NUFFT_PLAN_TIMING (else
+ * NUFFT_ESTATE).  Writes min(cap, count) values to ms_out and the count to
+ * *count.  Waits for the last event. */
+int nufft_kernel_times(nufft_plan p, float *ms_out, int cap, int *count);
+
+/* Human-readable name of a status code. */
+const char *nufft_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NUFFT_H */

@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import platform
 import subprocess
 
 import numpy as np
@@ -21,11 +22,16 @@ _lib = None
 
 def build(force=False):
     """Compile direct.c (plain C, OpenMP, no fast-math, no FMA contraction)."""
+    stamp = _LIB + ".machine"
+    if not os.path.exists(stamp) or open(stamp).read().strip() != platform.machine():
+        force = True
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".%d.tmp" % os.getpid()
         subprocess.check_call(["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC",
                                "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
+        with open(stamp, "w") as fh:
+            fh.write(platform.machine())
     return _LIB
 
 

@@ -1,0 +1,231 @@
+"""Python binding of libnufft: plan objects over torch CUDA tensors, and autograd.
+
+PyTorch provides device memory and streams only; every step of the transform runs
+in the library's CUDA kernels.  All calls are enqueued on the current torch stream
+of the tensors' device.
+"""
+
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import NUFFT_F32, NUFFT_F64, NUFFT_PLAN_TIMING, NUFFT_PLAN_UNFUSED, NufftError, check
+
+_CDTYPE = {NUFFT_F32: torch.complex64, NUFFT_F64: torch.complex128}
+_RDTYPE = {NUFFT_F32: torch.float32, NUFFT_F64: torch.float64}
+
+
+def _prec(precision):
+    if precision in ("f32", "float32", torch.float32, torch.complex64, NUFFT_F32):
+        return NUFFT_F32
+    if precision in ("f64", "float64", torch.float64, torch.complex128, NUFFT_F64):
+        return NUFFT_F64
+    raise ValueError("precision must be 'f32' or 'f64'")
+
+
+def _stream(device):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """A planned NUFFT-II on a fixed set of samples x (the planning stage, section 2.3).
+
+    Parameters
+    ----------
+    N : number of frequencies k = 0..N-1
+    x : samples, a 1-D tensor or array (moved to the current CUDA device as float64)
+    eps : working accuracy
+    precision : 'f32' (complex64 exec) or 'f64' (complex128 exec)
+    L : grid size (0 = smallest power of two >= max(N, 1024); L > N oversamples)
+    unfused : also build the materialised factors for :meth:`forward_unfused`
+    """
+
+    def __init__(self, N, x, eps, precision="f32", L=0, unfused=False, timing=False, device=None):
+        lib = _lib.load()
+        device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        if not isinstance(x, torch.Tensor):
+            x = torch.as_tensor(x)
+        x = x.detach().to(device=device, dtype=torch.float64).contiguous()
+        self.device = device
+        self.N, self.M = int(N), int(x.numel())
+        self.prec = _prec(precision)
+        self.cdtype, self.rdtype = _CDTYPE[self.prec], _RDTYPE[self.prec]
+        h = ctypes.c_void_p()
+        with torch.cuda.device(device):
+            rc = lib.nufft2_plan(ctypes.byref(h), self.N, self.M, _ptr(x) if self.M else None,
+                                 float(eps), self.prec, int(L),
+                                 (NUFFT_PLAN_UNFUSED if unfused else 0) | (NUFFT_PLAN_TIMING if timing else 0),
+                                 _stream(device))
+        check(rc, "nufft2_plan")
+        self._h = h
+        self.eps = float(eps)
+        K, g, Lo, wb = ctypes.c_int(), ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
+        check(lib.nufft2_plan_info(h, ctypes.byref(K), ctypes.byref(g), ctypes.byref(Lo), ctypes.byref(wb)),
+              "nufft2_plan_info")
+        self.K, self.gamma, self.L, self.work_bytes = K.value, g.value, Lo.value, wb.value
+
+    # -- lifetime -----------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            torch.cuda.synchronize(self.device)
+            _lib.load().nufft_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- helpers ----------------------------------------------------------------------
+    def _cx(self, t, n, name):
+        if t.device != self.device or t.dtype != self.cdtype or not t.is_contiguous() or t.numel() != n:
+            raise ValueError("%s must be a contiguous %s tensor of %d elements on %s"
+                             % (name, self.cdtype, n, self.device))
+        return t
+
+    def export(self):
+        """(t, d, alpha): grid indices, scaled perturbations (FP64) and a_pr = i^r alpha_pr."""
+        t = torch.empty(self.M, dtype=torch.int32, device=self.device)
+        d = torch.empty(self.M, dtype=torch.float64, device=self.device)
+        alpha = (ctypes.c_double * (self.K * self.K))()
+        with torch.cuda.device(self.device):
+            check(_lib.load().nufft2_plan_export(self._h, _ptr(t) if self.M else None,
+                                                 _ptr(d) if self.M else None, alpha, _stream(self.device)),
+                  "nufft2_plan_export")
+        import numpy as np
+        return t, d, np.array(alpha[:], dtype=np.float64).reshape(self.K, self.K)
+
+    def kernel_times(self):
+        """Device milliseconds of each kernel of the last exec call (plan built with timing=True)."""
+        buf = (ctypes.c_float * 8)()
+        n = ctypes.c_int()
+        check(_lib.load().nufft_kernel_times(self._h, buf, 8, ctypes.byref(n)), "nufft_kernel_times")
+        return list(buf[: n.value])
+
+    # -- online stage -------------------------------------------------------------------
+    def forward(self, c, out=None):
+        """f = A c (the NUFFT-II, eq. (2.11))."""
+        self._cx(c, self.N, "c")
+        f = out if out is not None else torch.empty(self.M, dtype=self.cdtype, device=self.device)
+        self._cx(f, self.M, "f")
+        with torch.cuda.device(self.device):
+            check(_lib.load().nufft2_exec(self._h, _ptr(c), _ptr(f), _stream(self.device)), "nufft2_exec")
+        return f
+
+    def adjoint(self, g, out=None):
+        """c = A^H g (the conjugate transpose of forward)."""
+        self._cx(g, self.M, "g")
+        c = out if out is not None else torch.empty(self.N, dtype=self.cdtype, device=self.device)
+        self._cx(c, self.N, "c")
+        with torch.cuda.device(self.device):
+            check(_lib.load().nufft1_exec(self._h, _ptr(g), _ptr(c), _stream(self.device)), "nufft1_exec")
+        return c
+
+    def transpose(self, g):
+        """The paper's NUFFT-I (section 3.1): A^T g = conj(A^H conj(g))."""
+        return torch.conj(self.adjoint(torch.conj(g).resolve_conj().contiguous())).resolve_conj()
+
+    def dx(self, c, g, out=None, accumulate=False):
+        """gx_j (+)= Re(conj(g_j) d f_j / d x_j)."""
+        self._cx(c, self.N, "c")
+        self._cx(g, self.M, "g")
+        gx = out if out is not None else torch.empty(self.M, dtype=self.rdtype, device=self.device)
+        if gx.dtype != self.rdtype or gx.numel() != self.M or not gx.is_contiguous():
+            raise ValueError("gx must be a contiguous %s tensor of %d elements" % (self.rdtype, self.M))
+        with torch.cuda.device(self.device):
+            check(_lib.load().nufft2_exec_dx(self._h, _ptr(c), _ptr(g), _ptr(gx), int(bool(accumulate)),
+                                             _stream(self.device)), "nufft2_exec_dx")
+        return gx
+
+    def forward_batch(self, c, out=None):
+        """f[b] = A c[b] for a (B, N) batch."""
+        if c.dim() != 2 or c.shape[1] != self.N or c.dtype != self.cdtype or c.stride(1) != 1:
+            raise ValueError("c must be (B, N) %s with unit inner stride" % self.cdtype)
+        B = c.shape[0]
+        f = out if out is not None else torch.empty(B, self.M, dtype=self.cdtype, device=self.device)
+        with torch.cuda.device(self.device):
+            check(_lib.load().nufft2_exec_batch(self._h, B, _ptr(c), c.stride(0), _ptr(f), f.stride(0),
+                                                _stream(self.device)), "nufft2_exec_batch")
+        return f
+
+    def forward_host(self, c_host, f_host):
+        """f_host = A c_host with host (ideally pinned) tensors; synchronises."""
+        if c_host.device.type != "cpu" or f_host.device.type != "cpu":
+            raise ValueError("forward_host takes CPU tensors")
+        if c_host.dtype != self.cdtype or f_host.dtype != self.cdtype:
+            raise ValueError("dtype must be %s" % self.cdtype)
+        with torch.cuda.device(self.device):
+            check(_lib.load().nufft2_exec_host(self._h, _ptr(c_host), _ptr(f_host), _stream(self.device)),
+                  "nufft2_exec_host")
+        return f_host
+
+    def forward_unfused(self, c, out=None):
+        """The unfused comparator (plan must be built with unfused=True)."""
+        self._cx(c, self.N, "c")
+        f = out if out is not None else torch.empty(self.M, dtype=self.cdtype, device=self.device)
+        with torch.cuda.device(self.device):
+            check(_lib.load().nufft2_exec_unfused(self._h, _ptr(c), _ptr(f), _stream(self.device)),
+                  "nufft2_exec_unfused")
+        return f
+
+
+class _Nufft2(torch.autograd.Function):
+    """f = A(x) c with a hand-written backward: dL/dc = A^H g, dL/dx = Re(conj(g) A((-2 pi i k) c))."""
+
+    @staticmethod
+    def forward(ctx, c, x, plan):
+        ctx.plan = plan
+        ctx.save_for_backward(c)
+        cc = c.detach().contiguous()
+        if cc.dim() == 1:
+            return plan.forward(cc)
+        return plan.forward_batch(cc)
+
+    @staticmethod
+    def backward(ctx, g):
+        (c,) = ctx.saved_tensors
+        plan = ctx.plan
+        g = g.contiguous()
+        gc = gx = None
+        batched = c.dim() == 2
+        if ctx.needs_input_grad[0]:
+            if batched:
+                gc = torch.stack([plan.adjoint(g[b].contiguous()) for b in range(g.shape[0])])
+            else:
+                gc = plan.adjoint(g)
+        if ctx.needs_input_grad[1]:
+            gx = torch.empty(plan.M, dtype=plan.rdtype, device=plan.device)
+            if batched:
+                for b in range(g.shape[0]):
+                    plan.dx(c[b].detach().contiguous(), g[b].contiguous(), gx, accumulate=b > 0)
+            else:
+                plan.dx(c.detach().contiguous(), g, gx)
+            gx = gx.to(torch.float64)
+        return gc, gx, None
+
+
+def nufft2(c, x, eps=1e-9, plan=None, L=0):
+    """Differentiable NUFFT-II: f_j = sum_k c_k exp(-2 pi i x_j k) for c of shape (N,)
+    or (B, N) (complex64 -> FP32 exec, complex128 -> FP64 exec) and samples x (float64).
+    Gradients flow to c and x.  Pass a prebuilt ``plan`` to reuse it (it must have
+    been built on the same x)."""
+    if plan is None:
+        plan = Plan(c.shape[-1], x.detach(), eps, precision=c.dtype, L=L, device=c.device)
+    return _Nufft2.apply(c, x, plan)
+
+
+__all__ = ["Plan", "nufft2", "NufftError", "NUFFT_F32", "NUFFT_F64"]

@@ -1,0 +1,363 @@
+// exec.cu -- the online stage: launch geometry, the exec entry points of the C ABI,
+// and the unfused comparator (the section 2.3 one-liner run step by step).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "passes.cuh"
+
+namespace nufft {
+
+NUFFT_DECLARE_ROWS(float, 4)
+NUFFT_DECLARE_ROWS(float, 8)
+NUFFT_DECLARE_ROWS(float, 12)
+NUFFT_DECLARE_ROWS(float, 16)
+NUFFT_DECLARE_ROWS(double, 4)
+NUFFT_DECLARE_ROWS(double, 8)
+NUFFT_DECLARE_ROWS(double, 12)
+NUFFT_DECLARE_ROWS(double, 16)
+NUFFT_DECLARE_COLS(float)
+NUFFT_DECLARE_COLS(double)
+
+namespace {
+
+// Complex elements per 128-byte shared-memory wavefront.
+template <typename T> constexpr int nbank() { return 128 / (2 * (int)sizeof(T)); }
+
+// Slot stride (elements) for a team slot of a length-P FFT: padded length, then
+// nudged so that the q teams sharing a wavefront land on disjoint banks.
+template <typename T>
+int slot_stride(int P, int E, int q) {
+    const int base = P + P / E;
+    const int nb = nbank<T>();
+    if (q <= 1) return base;
+    const int target = nb / std::min(q, nb);
+    return base + (((target - base % nb) % nb) + nb) % nb;
+}
+
+int clamp_pow2(int v, int lo, int hi) { return std::max(lo, std::min(hi, v)); }
+
+}  // namespace
+
+template <typename T>
+int plan_geometry(nufft_plan p) {
+    constexpr int EM = EmaxT<T>::v;
+    const int E1 = std::min(EM, p->L1), TT1 = p->L1 / E1;
+    const int E2 = std::min(EM, p->L2), TT2 = p->L2 / E2;
+    const size_t cxs = 2 * sizeof(T);
+    // column passes: C columns per CTA, columns fastest across the lanes
+    p->C1 = clamp_pow2(256 / TT2, 1, p->L1);
+    p->CB = clamp_pow2(128 / TT2, 1, p->L1);
+    p->S1 = slot_stride<T>(p->L2, E2, p->C1);
+    p->SB = slot_stride<T>(p->L2, E2, p->CB);
+    p->smem1 = (size_t)p->C1 * p->S1 * cxs;
+    p->smemB = ((size_t)p->CB * p->SB + (size_t)p->CB * p->L2) * cxs;   // slots + accumulators
+    // row passes: buckets of B2 rows, nt2 teams, G ranks staged at once
+    p->B2 = clamp_pow2(1024 / p->L1, 1, p->L2);
+    p->NB = p->L2 / p->B2;
+    p->nt2 = std::max(1, 128 / TT1);
+    p->S2 = slot_stride<T>(p->L1, E1, std::max(1, nbank<T>() / TT1));
+    auto slots = [&](int G) { return ((G * p->B2 + p->nt2 - 1) / p->nt2) * p->nt2; };
+    int G = p->K;
+    while (G > 1 && (size_t)slots(G) * p->S2 * cxs > SMEM_BUDGET) --G;
+    if ((size_t)slots(G) * p->S2 * cxs > SMEM_BUDGET) return NUFFT_EUNSUPPORTED;
+    p->G = G;
+    p->smem2 = (size_t)slots(G) * p->S2 * cxs;
+    if (p->smem1 > SMEM_BUDGET || p->smemB > SMEM_BUDGET) return NUFFT_EUNSUPPORTED;
+    return NUFFT_OK;
+}
+
+namespace {
+
+template <typename T>
+PassArgs<T> base_args(nufft_plan p) {
+    PassArgs<T> a{};
+    a.Y = (cx<T> *)p->Y;
+    a.fscr = (cx<T> *)p->fscr;
+    a.tsorted = p->tsorted;
+    a.perm = p->perm;
+    a.bstart = p->bstart;
+    a.dsorted = (const T *)p->dsorted;
+    a.tw = (const cx<T> *)p->tw4096;
+    a.twhi = (const cx<T> *)p->twhi;
+    a.twlo = (const cx<T> *)p->twlo;
+    a.N = p->N;
+    a.M = p->M;
+    a.L = p->L;
+    a.L1 = p->L1;
+    a.L2 = p->L2;
+    a.lg1 = p->lg1;
+    a.lg2 = p->lg2;
+    a.K = p->K;
+    a.G = p->G;
+    a.B2 = p->B2;
+    a.inv_gamma = p->gamma > 0.0 ? (T)(1.0 / p->gamma) : T(0);
+    return a;
+}
+
+template <typename T>
+int run_rows(nufft_plan p, const PassArgs<T> &a, bool adjoint, cudaStream_t s) {
+    switch (p->kmax) {
+        case 4: return launch_rows<T, 4>(p, a, adjoint, s);
+        case 8: return launch_rows<T, 8>(p, a, adjoint, s);
+        case 12: return launch_rows<T, 12>(p, a, adjoint, s);
+        case 16: return launch_rows<T, 16>(p, a, adjoint, s);
+        default: return NUFFT_EUNSUPPORTED;
+    }
+}
+
+// ---- unfused comparator kernels ----------------------------------------------------
+
+// U[j][r] = sum'_p a_pr exp(-i pi d_j) T_p(d_j / gamma), FP64 (eq. (2.6)).
+template <typename T>
+__global__ void k_uf_U(const double *__restrict__ d, int64_t M, int K, double inv_gamma,
+                       int trivial, const Beta<double, KMAX_ALL> aw, cx<T> *__restrict__ U) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < M;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        if (trivial) { U[j * K] = mk<T>(1, 0); continue; }
+        const double xi = d[j] * inv_gamma;
+        double Tp[KMAX_ALL];
+        Tp[0] = 1.0;
+        Tp[1] = xi;
+        for (int q = 2; q < K; ++q) Tp[q] = 2.0 * xi * Tp[q - 1] - Tp[q - 2];
+        double sn, cs;
+        sincospi(d[j], &sn, &cs);
+        for (int r = 0; r < K; ++r) {
+            double s = 0.0;
+            for (int q = 0; q < K; ++q) s += aw.b[r][q] * Tp[q];
+            // i^r exp(-i pi d) s
+            cx<double> u = mk<double>(cs * s, -sn * s);
+            u = mul_ipow<double>(u, r);
+            U[j * K + r] = mk<T>((T)u.x, (T)u.y);
+        }
+    }
+}
+
+// V[k][r] = T_r(2k/N - 1), V[k][0] = 1/2 (eq. (2.6)), FP64.
+template <typename T>
+__global__ void k_uf_V(int64_t N, int K, int trivial, T *__restrict__ V) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        if (trivial) { V[k * K] = T(1); continue; }
+        const double z = double(2 * k - N) / double(N);
+        double a = 1.0, b = z;
+        V[k * K] = T(0.5);
+        if (K > 1) V[k * K + 1] = (T)z;
+        for (int r = 2; r < K; ++r) {
+            const double c = 2.0 * z * b - a;
+            a = b;
+            b = c;
+            V[k * K + r] = (T)c;
+        }
+    }
+}
+
+// W[r][k] = V[k][r] c_k for k < N, 0 for N <= k < L.
+template <typename T>
+__global__ void k_uf_vscale(const cx<T> *__restrict__ c, const T *__restrict__ V, int64_t N,
+                            int64_t L, int K, cx<T> *__restrict__ W) {
+    const int64_t tot = (int64_t)K * L;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(idx / L);
+        const int64_t k = idx - (int64_t)r * L;
+        cx<T> w = mk<T>(0, 0);
+        if (k < N) {
+            const T v = V[k * K + r];
+            const cx<T> cc = c[k];
+            w = mk<T>(v * cc.x, v * cc.y);
+        }
+        W[idx] = w;
+    }
+}
+
+// Xg[r][j] = X[r][t_j]  (the row gather I_L(t,:))
+template <typename T>
+__global__ void k_uf_gather(const cx<T> *__restrict__ X, const int32_t *__restrict__ t, int64_t M,
+                            int64_t L, int K, cx<T> *__restrict__ Xg) {
+    const int64_t tot = (int64_t)K * M;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(idx / M);
+        const int64_t j = idx - (int64_t)r * M;
+        Xg[idx] = X[(int64_t)r * L + t[j]];
+    }
+}
+
+// f_j = sum_r U[j][r] Xg[r][j]  ((U .* X) * ones(K))
+template <typename T>
+__global__ void k_uf_ranksum(const cx<T> *__restrict__ U, const cx<T> *__restrict__ Xg, int64_t M,
+                             int K, cx<T> *__restrict__ f) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < M;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        cx<T> acc = mk<T>(0, 0);
+        for (int r = 0; r < K; ++r) acc = cadd<T>(acc, cmul<T>(U[j * K + r], Xg[(int64_t)r * M + j]));
+        f[j] = acc;
+    }
+}
+
+int grid1d(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 32)); }
+
+}  // namespace
+
+template <typename T>
+int plan_unfused_factors(nufft_plan p, cudaStream_t s) {
+    const size_t cxs = 2 * sizeof(T);
+    const int64_t M = std::max<int64_t>(p->M, 1);
+    NUFFT_CUDA_TRY(cudaMalloc(&p->U, (size_t)M * p->K * cxs));
+    NUFFT_CUDA_TRY(cudaMalloc(&p->V, (size_t)p->N * p->K * sizeof(T)));
+    NUFFT_CUDA_TRY(cudaMalloc(&p->Xg, (size_t)p->K * p->L * cxs));
+    p->work_bytes += (int64_t)((size_t)M * p->K * cxs + (size_t)p->N * p->K * sizeof(T) +
+                               (size_t)p->K * p->L * cxs);
+    if (p->M > (int64_t)p->L) {   // the gathered K x M block reuses Y
+        cudaFree(p->Y);
+        p->Y = nullptr;
+        NUFFT_CUDA_TRY(cudaMalloc(&p->Y, (size_t)p->K * p->M * cxs));
+        p->work_bytes += (int64_t)((size_t)p->K * (p->M - p->L) * cxs);
+    }
+    Beta<double, KMAX_ALL> aw{};
+    for (int r = 0; r < p->K; ++r)
+        for (int q = 0; q < p->K; ++q) aw.b[r][q] = (q == 0 ? 0.5 : 1.0) * p->alpha[q][r];
+    const int trivial = p->gamma == 0.0;
+    const double inv_gamma = trivial ? 0.0 : 1.0 / p->gamma;
+    if (p->M > 0)
+        k_uf_U<T><<<grid1d(p->M), 256, 0, s>>>(p->d_j, p->M, p->K, inv_gamma, trivial, aw, (cx<T> *)p->U);
+    k_uf_V<T><<<grid1d(p->N), 256, 0, s>>>(p->N, p->K, trivial, (T *)p->V);
+    NUFFT_CUDA_TRY(cudaGetLastError());
+    return NUFFT_OK;
+}
+
+template <typename T>
+int exec_forward(nufft_plan p, const void *c, void *f, cudaStream_t s) {
+    if (p->M == 0) return NUFFT_OK;
+    PassArgs<T> a = base_args<T>(p);
+    a.in = (const cx<T> *)c;
+    a.out = (cx<T> *)f;
+    if (int rc = mark(p, s, true)) return rc;
+    if (int rc = launch_cols<T>(p, a, false, s)) return rc;
+    if (int rc = mark(p, s, false)) return rc;
+    if (int rc = run_rows<T>(p, a, false, s)) return rc;
+    return mark(p, s, false);
+}
+
+template <typename T>
+int exec_adjoint(nufft_plan p, const void *g, void *c, cudaStream_t s) {
+    if (p->M == 0) {
+        NUFFT_CUDA_TRY(cudaMemsetAsync(c, 0, (size_t)p->N * 2 * sizeof(T), s));
+        return NUFFT_OK;
+    }
+    PassArgs<T> a = base_args<T>(p);
+    a.in = (const cx<T> *)g;
+    a.out = (cx<T> *)c;
+    if (int rc = mark(p, s, true)) return rc;
+    if (int rc = run_rows<T>(p, a, true, s)) return rc;
+    if (int rc = mark(p, s, false)) return rc;
+    if (int rc = launch_cols<T>(p, a, true, s)) return rc;
+    return mark(p, s, false);
+}
+
+template <typename T>
+int exec_dx(nufft_plan p, const void *c, const void *g, void *gx, int acc, cudaStream_t s) {
+    if (p->M == 0) return NUFFT_OK;
+    PassArgs<T> a = base_args<T>(p);
+    a.in = (const cx<T> *)c;
+    a.g = (const cx<T> *)g;
+    a.gx = (T *)gx;
+    a.mode = MODE_DX;
+    a.accumulate = acc;
+    if (int rc = mark(p, s, true)) return rc;
+    if (int rc = launch_cols<T>(p, a, false, s)) return rc;
+    if (int rc = mark(p, s, false)) return rc;
+    if (int rc = run_rows<T>(p, a, false, s)) return rc;
+    return mark(p, s, false);
+}
+
+template <typename T>
+int exec_unfused(nufft_plan p, const void *c, void *f, cudaStream_t s) {
+    if (!(p->flags & NUFFT_PLAN_UNFUSED)) return NUFFT_ESTATE;
+    if (p->M == 0) return NUFFT_OK;
+    cx<T> *W = (cx<T> *)p->Xg;   // K x L: scaled columns, later the FFT outputs X
+    k_uf_vscale<T><<<grid1d((int64_t)p->K * p->L), 256, 0, s>>>((const cx<T> *)c, (const T *)p->V,
+                                                                p->N, p->L, p->K, W);
+    NUFFT_CUDA_TRY(cudaGetLastError());
+    PassArgs<T> a = base_args<T>(p);
+    a.in = W;
+    a.out = W;
+    a.mode = MODE_PLAIN_IN | MODE_PLAIN_OUT;
+    if (int rc = launch_cols<T>(p, a, false, s)) return rc;   // W -> Y
+    if (int rc = run_rows<T>(p, a, false, s)) return rc;      // Y -> X (in W)
+    cx<T> *Xg = (cx<T> *)p->Y;
+    k_uf_gather<T><<<grid1d((int64_t)p->K * p->M), 256, 0, s>>>(W, p->t_j, p->M, p->L, p->K, Xg);
+    k_uf_ranksum<T><<<grid1d(p->M), 256, 0, s>>>((const cx<T> *)p->U, Xg, p->M, p->K, (cx<T> *)f);
+    NUFFT_CUDA_TRY(cudaGetLastError());
+    return NUFFT_OK;
+}
+
+template int plan_geometry<float>(nufft_plan);
+template int plan_geometry<double>(nufft_plan);
+template int plan_unfused_factors<float>(nufft_plan, cudaStream_t);
+template int plan_unfused_factors<double>(nufft_plan, cudaStream_t);
+
+}  // namespace nufft
+
+// ---- C ABI --------------------------------------------------------------------------
+
+using nufft::exec_adjoint;
+using nufft::exec_dx;
+using nufft::exec_forward;
+using nufft::exec_unfused;
+
+extern "C" int nufft2_exec(nufft_plan p, const void *c_dev, void *f_dev, void *stream) {
+    if (!p || !c_dev || (p->M > 0 && !f_dev)) return NUFFT_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    return p->prec == NUFFT_F32 ? exec_forward<float>(p, c_dev, f_dev, s)
+                                : exec_forward<double>(p, c_dev, f_dev, s);
+}
+
+extern "C" int nufft1_exec(nufft_plan p, const void *g_dev, void *c_dev, void *stream) {
+    if (!p || !c_dev || (p->M > 0 && !g_dev)) return NUFFT_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    return p->prec == NUFFT_F32 ? exec_adjoint<float>(p, g_dev, c_dev, s)
+                                : exec_adjoint<double>(p, g_dev, c_dev, s);
+}
+
+extern "C" int nufft2_exec_dx(nufft_plan p, const void *c_dev, const void *g_dev, void *gx_dev,
+                              int accumulate, void *stream) {
+    if (!p || !c_dev || (p->M > 0 && (!g_dev || !gx_dev))) return NUFFT_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    return p->prec == NUFFT_F32 ? exec_dx<float>(p, c_dev, g_dev, gx_dev, accumulate, s)
+                                : exec_dx<double>(p, c_dev, g_dev, gx_dev, accumulate, s);
+}
+
+extern "C" int nufft2_exec_batch(nufft_plan p, int64_t B, const void *c_dev, int64_t ldc,
+                                 void *f_dev, int64_t ldf, void *stream) {
+    if (!p || B < 0 || ldc < p->N || ldf < p->M) return NUFFT_EINVAL;
+    if (B > 0 && (!c_dev || (p->M > 0 && !f_dev))) return NUFFT_EINVAL;
+    const size_t cxs = p->prec == NUFFT_F32 ? 8 : 16;
+    for (int64_t b = 0; b < B; ++b) {
+        const void *cb = (const char *)c_dev + (size_t)(b * ldc) * cxs;
+        void *fb = (char *)f_dev + (size_t)(b * ldf) * cxs;
+        if (int rc = nufft2_exec(p, cb, fb, stream)) return rc;
+    }
+    return NUFFT_OK;
+}
+
+extern "C" int nufft2_exec_host(nufft_plan p, const void *c_host, void *f_host, void *stream) {
+    if (!p || !c_host || (p->M > 0 && !f_host)) return NUFFT_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t cxs = p->prec == NUFFT_F32 ? 8 : 16;
+    NUFFT_CUDA_TRY(cudaMemcpyAsync(p->cstage, c_host, (size_t)p->N * cxs, cudaMemcpyHostToDevice, s));
+    if (int rc = nufft2_exec(p, p->cstage, p->fstage, stream)) return rc;
+    if (p->M > 0)
+        NUFFT_CUDA_TRY(cudaMemcpyAsync(f_host, p->fstage, (size_t)p->M * cxs, cudaMemcpyDeviceToHost, s));
+    NUFFT_CUDA_TRY(cudaStreamSynchronize(s));
+    return NUFFT_OK;
+}
+
+extern "C" int nufft2_exec_unfused(nufft_plan p, const void *c_dev, void *f_dev, void *stream) {
+    if (!p || !c_dev || (p->M > 0 && !f_dev)) return NUFFT_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    return p->prec == NUFFT_F32 ? exec_unfused<float>(p, c_dev, f_dev, s)
+                                : exec_unfused<double>(p, c_dev, f_dev, s);
+}

@@ -1,0 +1,201 @@
+// fft_team.cuh -- in-register DFTs and a Stockham FFT executed by a team of threads.
+//
+// A length-P transform (P a power of two, P <= E^3) is done by TT = P/E threads,
+// each holding E complex values in registers.  Stage s applies radix R_s
+// butterflies (R_0 = E, then E or the remainder); between stages the data moves
+// through the team's shared-memory slot.  The formulation is the self-sorting
+// (Stockham) one: virtual butterfly v of a stage with radix R, after NS points
+// of sub-transforms, reads x[v + (P/R) i], multiplies input i by w_{NS R}^{i (v mod NS)}
+// and writes output i to (v / NS) NS R + (v mod NS) + NS i.  Input and output are in
+// natural order.
+//
+//   input layout : thread tt holds x[tt + TT m], m = 0..E-1      (strided by TT)
+//   output layout: register e holds X[out_index(tt, e)]
+//
+// Every thread of the CTA must call run() the same number of times (it uses
+// __syncthreads between stages); teams with no work run on a scratch slot.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace nufft {
+
+template <typename T> struct CxT;
+template <> struct CxT<float> { using type = float2; };
+template <> struct CxT<double> { using type = double2; };
+template <typename T> using cx = typename CxT<T>::type;
+
+template <typename T> __device__ __forceinline__ cx<T> mk(T a, T b) { cx<T> r; r.x = a; r.y = b; return r; }
+template <typename T> __device__ __forceinline__ cx<T> cadd(cx<T> a, cx<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
+template <typename T> __device__ __forceinline__ cx<T> csub(cx<T> a, cx<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
+// a * b
+template <typename T> __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
+    return mk<T>(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+template <typename T> __device__ __forceinline__ cx<T> cmulc(cx<T> a, cx<T> b) {
+    return mk<T>(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y));
+}
+// a * i^q  (q mod 4)
+template <typename T> __device__ __forceinline__ cx<T> mul_ipow(cx<T> a, int q) {
+    switch (q & 3) {
+        case 0: return a;
+        case 1: return mk<T>(-a.y, a.x);
+        case 2: return mk<T>(-a.x, -a.y);
+        default: return mk<T>(a.y, -a.x);
+    }
+}
+
+// cos(2 pi m / 32) for m in [0, 8], from the half-angle values of pi/16.
+__host__ __device__ constexpr double cos32_oct(int m) {
+    return m == 0 ? 1.0
+         : m == 1 ? 0.98078528040323044912618223613424
+         : m == 2 ? 0.92387953251128675612818318939679
+         : m == 3 ? 0.83146961230254523707878837761791
+         : m == 4 ? 0.70710678118654752440084436210485
+         : m == 5 ? 0.55557023301960222474283081394853
+         : m == 6 ? 0.38268343236508977172845998403040
+         : m == 7 ? 0.19509032201612826784828486847702
+                  : 0.0;
+}
+__host__ __device__ constexpr double cos32(int m) {
+    return (m & 31) <= 8  ? cos32_oct(m & 31)
+         : (m & 31) <= 16 ? -cos32_oct(16 - (m & 31))
+         : (m & 31) <= 24 ? -cos32_oct((m & 31) - 16)
+                          : cos32_oct(32 - (m & 31));
+}
+__host__ __device__ constexpr double sin32(int m) { return cos32(m - 8); }
+
+// a * exp(-+ 2 pi i m / 32): forward (INV = false) uses the negative exponent.
+template <bool INV, typename T>
+__device__ __forceinline__ cx<T> mul_w32(cx<T> a, int m) {
+    m &= 31;
+    if (m == 0) return a;
+    if (m == 16) return mk<T>(-a.x, -a.y);
+    if (m == 8) return INV ? mk<T>(-a.y, a.x) : mk<T>(a.y, -a.x);
+    if (m == 24) return INV ? mk<T>(a.y, -a.x) : mk<T>(-a.y, a.x);
+    const T c = (T)cos32(m);
+    const T s = (T)(INV ? sin32(m) : -sin32(m));   // exp(i s') with s' = -+ angle
+    if (m == 4 || m == 12 || m == 20 || m == 28) {
+        // |c| = |s| = 1/sqrt(2): (c a.x - s a.y, c a.y + s a.x) with shared products
+        return mk<T>(c * a.x - s * a.y, c * a.y + s * a.x);
+    }
+    return mk<T>(fma(c, a.x, -s * a.y), fma(c, a.y, s * a.x));
+}
+
+// In-place DFT of R points held in registers, natural order in and out,
+// radix-2 decimation in time, fully unrolled.
+template <int R, bool INV, typename T>
+struct Dft {
+    __device__ __forceinline__ static void run(cx<T> (&s)[R]) {
+        cx<T> ev[R / 2], od[R / 2];
+#pragma unroll
+        for (int k = 0; k < R / 2; ++k) { ev[k] = s[2 * k]; od[k] = s[2 * k + 1]; }
+        Dft<R / 2, INV, T>::run(ev);
+        Dft<R / 2, INV, T>::run(od);
+#pragma unroll
+        for (int k = 0; k < R / 2; ++k) {
+            cx<T> o = mul_w32<INV, T>(od[k], k * (32 / R));
+            s[k] = cadd<T>(ev[k], o);
+            s[k + R / 2] = csub<T>(ev[k], o);
+        }
+    }
+};
+template <bool INV, typename T>
+struct Dft<1, INV, T> { __device__ __forceinline__ static void run(cx<T> (&)[1]) {} };
+template <bool INV, typename T>
+struct Dft<2, INV, T> {
+    __device__ __forceinline__ static void run(cx<T> (&s)[2]) {
+        cx<T> a = s[0], b = s[1];
+        s[0] = cadd<T>(a, b);
+        s[1] = csub<T>(a, b);
+    }
+};
+
+__host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v / 2); }
+
+// Shared-memory index with one pad element per E elements (bank-conflict relief).
+template <int E> __device__ __forceinline__ int padi(int o) { return o + (o >> ilog2c(E)); }
+template <int E> __host__ __device__ constexpr int padded_len(int P) { return P + P / E; }
+
+template <typename T, int P, int E, bool INV>
+struct TeamFft {
+    static_assert(P % E == 0, "P must be a multiple of E");
+    static constexpr int TT = P / E;
+    static constexpr int R0 = E;
+    static constexpr int REM1 = TT;
+    static constexpr int R1 = REM1 > E ? E : REM1;
+    static constexpr int R2 = REM1 / R1;
+    static_assert(R2 <= E, "P too large for E");
+    static constexpr int RL = R2 > 1 ? R2 : (R1 > 1 ? R1 : R0);  // last radix
+    static constexpr int NSL = P / RL;                            // sub-transform size before it
+
+    // Output index of register e after run().
+    __device__ __forceinline__ static int out_index(int tt, int e) {
+        const int b = e / RL, i = e % RL;
+        return tt + TT * b + NSL * i;
+    }
+
+    template <int R, int NS>
+    __device__ __forceinline__ static void stage(cx<T> (&a)[E], int tt, const cx<T>* __restrict__ tw) {
+#pragma unroll
+        for (int b = 0; b < E / R; ++b) {
+            cx<T> s[R];
+#pragma unroll
+            for (int i = 0; i < R; ++i) s[i] = a[b * R + i];
+            if (NS > 1) {
+                const int v = tt + TT * b;
+                const int j = v & (NS - 1);
+#pragma unroll
+                for (int i = 1; i < R; ++i) {
+                    const cx<T> w = __ldg(&tw[i * j * (4096 / (NS * R))]);
+                    s[i] = INV ? cmulc<T>(s[i], w) : cmul<T>(s[i], w);
+                }
+            }
+            Dft<R, INV, T>::run(s);
+#pragma unroll
+            for (int i = 0; i < R; ++i) a[b * R + i] = s[i];
+        }
+    }
+
+    // Write the outputs of a stage (radix R after NS) to sm; read the inputs of the
+    // next stage (radix Rn).
+    template <int R, int NS, int Rn>
+    __device__ __forceinline__ static void exchange(cx<T> (&a)[E], int tt, cx<T>* sm) {
+#pragma unroll
+        for (int b = 0; b < E / R; ++b) {
+            const int v = tt + TT * b;
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                const int o = (v / NS) * NS * R + (v % NS) + NS * i;
+                sm[padi<E>(o)] = a[b * R + i];
+            }
+        }
+        __syncthreads();
+        constexpr int Vn = P / Rn;
+#pragma unroll
+        for (int b = 0; b < E / Rn; ++b) {
+            const int v = tt + TT * b;
+#pragma unroll
+            for (int i = 0; i < Rn; ++i) a[b * Rn + i] = sm[padi<E>(v + Vn * i)];
+        }
+        __syncthreads();
+    }
+
+    // tw: the table w_4096^m = exp(-2 pi i m / 4096), m < 4096.
+    __device__ __forceinline__ static void run(cx<T> (&a)[E], int tt, cx<T>* sm,
+                                               const cx<T>* __restrict__ tw) {
+        stage<R0, 1>(a, tt, tw);
+        if constexpr (R1 > 1) {
+            exchange<R0, 1, R1>(a, tt, sm);
+            stage<R1, R0>(a, tt, tw);
+            if constexpr (R2 > 1) {
+                exchange<R1, R0, R2>(a, tt, sm);
+                stage<R2, R0 * R1>(a, tt, tw);
+            }
+        }
+    }
+};
+
+}  // namespace nufft

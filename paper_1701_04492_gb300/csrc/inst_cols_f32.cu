@@ -1,0 +1,6 @@
+// Explicit instantiation of the column-pass launchers (pass 1 and pass B).
+#include "passes.cuh"
+
+namespace nufft {
+template int launch_cols<float>(nufft_plan, const PassArgs<float> &, bool, cudaStream_t);
+}

@@ -1,0 +1,107 @@
+// nufft_internal.h -- the plan object and helpers shared by the library's sources.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/nufft.h"
+
+namespace nufft {
+
+constexpr int KMAX_ALL = 16;       // Table 2.1's double row caps the rank at 16
+constexpr int TW_BASE = 4096;      // in-pass twiddle table w_4096^m
+constexpr int LOG2_L_MIN = 10;     // grids are at least 1024 points (two passes of 32)
+constexpr int LOG2_L_MAX = 22;     // two passes of at most 2048
+constexpr size_t SMEM_BUDGET = 200 * 1024;
+
+// Real coefficient table: beta[r][p] multiplies T_p(xi) in the r-th sample factor.
+template <typename T, int KM>
+struct Beta { T b[KM][KM]; };
+
+}  // namespace nufft
+
+// The plan.  Index conventions: the grid has L = L1 * L2 points; a grid index
+// t = L2 n1 + n2 (n1 < L1, n2 < L2).  Pass 1 / B transform columns of length L2
+// (over k2 of k = k1 + L1 k2), pass 2 / A transform rows of length L1.
+// Samples are sorted by the key (bucket, n1, row) with n2 = bucket*B2 + row.
+struct nufft_plan_s {
+    int64_t N = 0, M = 0, L = 0;
+    int L1 = 0, L2 = 0, lg1 = 0, lg2 = 0;
+    int prec = 0;
+    int K = 1;
+    int kmax = 4;          // rank rounded up to 4, 8, 12 or 16 (kernel template)
+    double gamma = 0.0, eps = 0.0;
+    unsigned flags = 0;
+    int device = 0;
+
+    // execution geometry (fixed at plan time)
+    int B2 = 1;            // grid rows per pass-2 bucket
+    int NB = 1;            // number of buckets = L2 / B2
+    int G = 1;             // ranks staged together in pass 2 / pass A
+    int nt2 = 1;           // teams per pass-2 / pass-A CTA
+    int C1 = 1;            // columns per pass-1 CTA
+    int CB = 1;            // columns per pass-B CTA
+    size_t smem2 = 0;      // dynamic shared memory of pass 2 / A
+    size_t smem1 = 0;      // of pass 1
+    size_t smemB = 0;      // of pass B
+    int S1 = 0, SB = 0, S2 = 0;   // slot strides (elements)
+
+    double beta[nufft::KMAX_ALL][nufft::KMAX_ALL] = {};   // [r][p] = w_r w_p alpha_pr
+    double alpha[nufft::KMAX_ALL][nufft::KMAX_ALL] = {};  // a_pr = i^r alpha_pr
+
+    // device memory owned by the plan
+    int32_t *tsorted = nullptr, *perm = nullptr, *bstart = nullptr, *t_j = nullptr;
+    void *dsorted = nullptr;   // d in sorted order, plan precision
+    double *d_j = nullptr;     // d in sample order, FP64 (unfused factors)
+    void *tw4096 = nullptr, *twhi = nullptr, *twlo = nullptr;
+    void *Y = nullptr;         // K * L complex: intermediate between the passes
+    void *fscr = nullptr;      // M complex: partial sums when G < K
+    void *cstage = nullptr, *fstage = nullptr;   // exec_host staging
+    void *U = nullptr, *V = nullptr, *Xg = nullptr;   // unfused comparator
+    int64_t work_bytes = 0;
+
+    // NUFFT_PLAN_TIMING: events around each launch of the last exec call
+    cudaEvent_t ev[8] = {};
+    int nev = 0;       // events recorded by the last exec call
+};
+
+namespace nufft {
+// Record the next timing event (no-op without NUFFT_PLAN_TIMING).
+inline int mark(nufft_plan p, cudaStream_t s, bool first) {
+    if (!(p->flags & NUFFT_PLAN_TIMING)) return NUFFT_OK;
+    if (first) p->nev = 0;
+    if (p->nev >= 8) return NUFFT_OK;
+    if (cudaEventRecord(p->ev[p->nev], s) != cudaSuccess) { (void)cudaGetLastError(); return NUFFT_ECUDA; }
+    ++p->nev;
+    return NUFFT_OK;
+}
+}  // namespace nufft
+
+namespace nufft {
+
+// host_math.cpp
+double bessel_j_int(int n, double z);
+void chebyshev_alpha(int K, double gamma, double *alpha /* K*K, [p*K + r] */);
+double tail_bound(int K, double gamma);
+int choose_rank(double eps, double gamma);
+void twiddle(int64_t n, int64_t m, double *c, double *s);   // exp(-2 pi i m / n)
+
+// exec_*.cu
+template <typename T> int exec_forward(nufft_plan p, const void *c, void *f, cudaStream_t s);
+template <typename T> int exec_adjoint(nufft_plan p, const void *g, void *c, cudaStream_t s);
+template <typename T> int exec_dx(nufft_plan p, const void *c, const void *g, void *gx, int acc,
+                                  cudaStream_t s);
+template <typename T> int exec_unfused(nufft_plan p, const void *c, void *f, cudaStream_t s);
+template <typename T> int plan_geometry(nufft_plan p);
+template <typename T> int plan_unfused_factors(nufft_plan p, cudaStream_t s);
+
+}  // namespace nufft
+
+#define NUFFT_CUDA_TRY(expr)                                   \
+    do {                                                       \
+        cudaError_t e_ = (expr);                               \
+        if (e_ != cudaSuccess) {                               \
+            (void)cudaGetLastError();                          \
+            return e_ == cudaErrorMemoryAllocation ? NUFFT_ENOMEM : NUFFT_ECUDA; \
+        }                                                      \
+    } while (0)

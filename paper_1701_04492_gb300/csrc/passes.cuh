@@ -1,0 +1,434 @@
+// passes.cuh -- the exec kernels of the low-rank NUFFT (section 2.3, two-step form).
+//
+// Forward, f = sum_r D_{u_r} I_L(t,:) F_L D_{v_r} c (eq. (2.11)), with the L-point
+// FFT split four-step as L = L1 * L2, input index k = k1 + L1 k2, output index
+// n = L2 n1 + n2:
+//   pass 1  (one CTA per block of C columns k1 and one rank r):
+//           x_k = i^r T_r(2k/N - 1) c_k          V-scale, fused into the load
+//           Y_r[n2][k1] = w_L^{n2 k1} sum_{k2} x_{k1 + L1 k2} w_{L2}^{n2 k2}
+//   pass 2  (one CTA per bucket of B2 rows n2, all ranks):
+//           X_r[L2 n1 + n2] = sum_{k1} Y_r[n2][k1] w_{L1}^{n1 k1}   into shared memory
+//           f_j = exp(-i pi d_j) sum_r mu_r(xi_j) X_r[t_j]          gather, U-scale, rank-sum
+//           for the samples j whose grid point t_j lies in the bucket.
+// With the primes of eq. (2.6) folded into beta, u_r(j) v_r(k) =
+// exp(-i pi d_j) mu_r(j) i^r T_r(2k/N - 1), mu_r = sum_p beta_rp T_p(d_j / gamma).
+//
+// Adjoint, c = A^H g, the same steps conjugated and reversed:
+//   pass A  Z_r[t] = sum_{j: t_j = t} mu_r(j) exp(+i pi d_j) g_j    (segmented over
+//           the sorted samples, no atomics), inverse row DFTs, conj twiddle -> Y_r
+//   pass B  inverse column DFTs, c_k = sum_r (-i)^r T_r(2k/N - 1) (...)_k
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fft_team.cuh"
+#include "nufft_internal.h"
+
+namespace nufft {
+
+enum PassMode : int {
+    MODE_PLAIN_IN = 1,    // pass 1 reads a pre-scaled W_r instead of c
+    MODE_PLAIN_OUT = 2,   // pass 2 writes X_r in natural order instead of gathering
+    MODE_DX = 4           // pass 1 scales by -2 pi i k; pass 2 forms Re(conj(g) f')
+};
+
+template <typename T> struct EmaxT;
+template <> struct EmaxT<float> { static constexpr int v = 32; };
+template <> struct EmaxT<double> { static constexpr int v = 16; };
+template <typename T, int P> __host__ __device__ constexpr int e_of() { return P < EmaxT<T>::v ? P : EmaxT<T>::v; }
+
+template <typename T>
+struct PassArgs {
+    const cx<T> *in;      // pass 1: c (or W);  pass A: g
+    cx<T> *Y;             // intermediate, K x L2 x L1
+    cx<T> *out;           // pass 2: f (or X);  pass B: c
+    const cx<T> *g;       // dx cotangent
+    T *gx;                // dx output
+    cx<T> *fscr;          // partial sums over rank groups (sorted order)
+    const int32_t *tsorted, *perm, *bstart;
+    const T *dsorted;
+    const cx<T> *tw, *twhi, *twlo;
+    int64_t N, M, L;
+    int L1, L2, lg1, lg2;
+    int K, G, B2, C, lgC, S;
+    int mode, accumulate;
+    T inv_gamma;
+};
+
+// T_r(z) by the three-term recurrence (NIST 18.9.1).
+template <typename T>
+__device__ __forceinline__ T cheb_T(int r, T z) {
+    if (r == 0) return T(1);
+    T a = T(1), b = z;
+    for (int q = 1; q < r; ++q) {
+        const T c = fma(T(2) * z, b, -a);
+        a = b;
+        b = c;
+    }
+    return b;
+}
+
+template <typename T>
+__device__ __forceinline__ void sincospi_t(T x, T *s, T *c);
+template <>
+__device__ __forceinline__ void sincospi_t<float>(float x, float *s, float *c) { sincospif(x, s, c); }
+template <>
+__device__ __forceinline__ void sincospi_t<double>(double x, double *s, double *c) { sincospi(x, s, c); }
+
+// The four-step twiddle w_L^m, m = n2 k1 < L, from two tables.
+template <typename T>
+__device__ __forceinline__ cx<T> twiddle_L(const PassArgs<T> &a, int m) {
+    const cx<T> hi = __ldg(&a.twhi[m >> 12]);
+    const cx<T> lo = __ldg(&a.twlo[m & 4095]);
+    return cmul<T>(hi, lo);
+}
+
+template <typename T>
+__device__ __forceinline__ cx<T> *smem_base() {
+    extern __shared__ __align__(16) unsigned char nufft_smem_raw[];
+    return reinterpret_cast<cx<T> *>(nufft_smem_raw);
+}
+
+// ---- pass 1: V-scale + column FFTs (length L2) + four-step twiddle ----------------
+template <typename T, int P2>
+__global__ void __launch_bounds__(256) k_pass1(const PassArgs<T> a) {
+    constexpr int E = e_of<T, P2>();
+    using TF = TeamFft<T, P2, E, false>;
+    constexpr int TT = TF::TT;
+    cx<T> *smem = smem_base<T>();
+    const int cc = threadIdx.x & (a.C - 1);
+    const int tt = threadIdx.x >> a.lgC;
+    const int k1 = blockIdx.x * a.C + cc;
+    const int r = blockIdx.y;
+    cx<T> v[E];
+    if (a.mode & MODE_PLAIN_IN) {
+        const cx<T> *W = a.in + (int64_t)r * a.L;
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = W[k1 + (int64_t)a.L1 * (tt + TT * m)];
+    } else {
+        const T invN = T(1) / T(a.N);
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const int64_t k = k1 + (int64_t)a.L1 * (tt + TT * m);
+            cx<T> cv = mk<T>(0, 0);
+            if (k < a.N) {
+                cv = a.in[k];
+                if (a.mode & MODE_DX) {   // (-2 pi i k) c_k
+                    const T w = T(6.283185307179586476925286766559) * T(k);
+                    cv = mk<T>(w * cv.y, -w * cv.x);
+                }
+                const T z = T(2 * k - a.N) * invN;
+                const T tr = cheb_T<T>(r, z);
+                cv = mk<T>(tr * cv.x, tr * cv.y);
+            }
+            v[m] = mul_ipow<T>(cv, r);
+        }
+    }
+    TF::run(v, tt, smem + cc * a.S, a.tw);
+    cx<T> *Yr = a.Y + (int64_t)r * a.L;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int n2 = TF::out_index(tt, e);
+        const cx<T> w = twiddle_L<T>(a, n2 * k1);
+        Yr[(int64_t)n2 * a.L1 + k1] = cmul<T>(v[e], w);
+    }
+}
+
+// ---- pass 2: row FFTs (length L1) into shared memory, then gather/U-scale/rank-sum --
+template <typename T, int P1, int KM>
+__global__ void __launch_bounds__(256) k_pass2(const PassArgs<T> a, const Beta<T, KM> beta) {
+    constexpr int E = e_of<T, P1>();
+    using TF = TeamFft<T, P1, E, false>;
+    constexpr int TT = TF::TT;
+    cx<T> *smem = smem_base<T>();
+    const int nt = blockDim.x / TT;
+    const int team = threadIdx.x / TT, tt = threadIdx.x % TT;
+    const int b = blockIdx.x;
+    const int i0 = a.bstart[b], i1 = a.bstart[b + 1];
+    const int L2m = a.L2 - 1;
+    for (int g0 = 0; g0 < a.K; g0 += a.G) {
+        const int gc = min(a.G, a.K - g0);
+        const int njobs = gc * a.B2;
+        for (int j0 = 0; j0 < njobs; j0 += nt) {
+            const int job = j0 + team;
+            const bool act = job < njobs;
+            const int rl = act ? job / a.B2 : 0, row = act ? job % a.B2 : 0;
+            const int n2 = b * a.B2 + row;
+            const cx<T> *src = a.Y + ((int64_t)(g0 + rl) * a.L2 + n2) * a.L1;
+            cx<T> *sm = smem + job * a.S;
+            cx<T> v[E];
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[m] = act ? src[tt + TT * m] : mk<T>(0, 0);
+            TF::run(v, tt, sm, a.tw);
+#pragma unroll
+            for (int e = 0; e < E; ++e) sm[padi<E>(TF::out_index(tt, e))] = v[e];
+        }
+        __syncthreads();
+        if (a.mode & MODE_PLAIN_OUT) {
+            // X_r[L2 n1 + n2] in natural order, rows fastest for coalescing
+            const int tot = njobs * a.L1;
+            for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+                const int row = idx % a.B2;
+                const int rest = idx / a.B2;
+                const int n1 = rest % a.L1;
+                const int rl = rest / a.L1;
+                a.out[(int64_t)(g0 + rl) * a.L + (int64_t)a.L2 * n1 + b * a.B2 + row] =
+                    smem[(rl * a.B2 + row) * a.S + padi<E>(n1)];
+            }
+        } else {
+            for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+                const int t = a.tsorted[i];
+                const int row = (t & L2m) - b * a.B2;
+                const int n1 = t >> a.lg2;
+                const T d = a.dsorted[i];
+                const T xi = d * a.inv_gamma;
+                T Tp[KM];
+                Tp[0] = T(1);
+                if (KM > 1) Tp[1] = xi;
+#pragma unroll
+                for (int q = 2; q < KM; ++q) Tp[q] = fma(T(2) * xi, Tp[q - 1], -Tp[q - 2]);
+                cx<T> acc = g0 == 0 ? mk<T>(0, 0) : a.fscr[i];
+#pragma unroll
+                for (int r = 0; r < KM; ++r) {
+                    if (r >= g0 && r < g0 + gc) {
+                        T mu = T(0);
+#pragma unroll
+                        for (int q = (r & 1); q < KM; q += 2) mu = fma(beta.b[r][q], Tp[q], mu);
+                        const cx<T> x = smem[((r - g0) * a.B2 + row) * a.S + padi<E>(n1)];
+                        acc.x = fma(mu, x.x, acc.x);
+                        acc.y = fma(mu, x.y, acc.y);
+                    }
+                }
+                if (g0 + gc < a.K) {
+                    a.fscr[i] = acc;
+                } else {
+                    T sn, cs;
+                    sincospi_t<T>(d, &sn, &cs);
+                    const cx<T> val = mk<T>(fma(acc.x, cs, acc.y * sn), fma(acc.y, cs, -acc.x * sn));
+                    const int j = a.perm[i];
+                    if (a.mode & MODE_DX) {
+                        const cx<T> gg = a.g[j];
+                        const T re = fma(gg.x, val.x, gg.y * val.y);
+                        a.gx[j] = a.accumulate ? a.gx[j] + re : re;
+                    } else {
+                        a.out[j] = val;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---- pass A (adjoint): segmented scatter into shared memory, inverse row FFTs -----
+template <typename T, int P1, int KM>
+__global__ void __launch_bounds__(256) k_passA(const PassArgs<T> a, const Beta<T, KM> beta) {
+    constexpr int E = e_of<T, P1>();
+    using TF = TeamFft<T, P1, E, true>;
+    constexpr int TT = TF::TT;
+    cx<T> *smem = smem_base<T>();
+    const int nt = blockDim.x / TT;
+    const int team = threadIdx.x / TT, tt = threadIdx.x % TT;
+    const int b = blockIdx.x;
+    const int i0 = a.bstart[b], i1 = a.bstart[b + 1];
+    const int L2m = a.L2 - 1;
+    for (int g0 = 0; g0 < a.K; g0 += a.G) {
+        const int gc = min(a.G, a.K - g0);
+        const int njobs = gc * a.B2;
+        const int nslots = ((njobs + nt - 1) / nt) * nt;
+        for (int idx = threadIdx.x; idx < nslots * a.S; idx += blockDim.x) smem[idx] = mk<T>(0, 0);
+        __syncthreads();
+        for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+            const int t = a.tsorted[i];
+            if (i > i0 && a.tsorted[i - 1] == t) continue;   // not the first of its grid point
+            cx<T> acc[KM];
+#pragma unroll
+            for (int r = 0; r < KM; ++r) acc[r] = mk<T>(0, 0);
+            for (int i2 = i; i2 < i1 && a.tsorted[i2] == t; ++i2) {
+                const T d = a.dsorted[i2];
+                const T xi = d * a.inv_gamma;
+                T Tp[KM];
+                Tp[0] = T(1);
+                if (KM > 1) Tp[1] = xi;
+#pragma unroll
+                for (int q = 2; q < KM; ++q) Tp[q] = fma(T(2) * xi, Tp[q - 1], -Tp[q - 2]);
+                T sn, cs;
+                sincospi_t<T>(d, &sn, &cs);
+                const cx<T> gg = a.in[a.perm[i2]];
+                const cx<T> h = mk<T>(fma(gg.x, cs, -gg.y * sn), fma(gg.y, cs, gg.x * sn));  // g e^{+i pi d}
+#pragma unroll
+                for (int r = 0; r < KM; ++r) {
+                    if (r >= g0 && r < g0 + gc) {
+                        T mu = T(0);
+#pragma unroll
+                        for (int q = (r & 1); q < KM; q += 2) mu = fma(beta.b[r][q], Tp[q], mu);
+                        acc[r].x = fma(mu, h.x, acc[r].x);
+                        acc[r].y = fma(mu, h.y, acc[r].y);
+                    }
+                }
+            }
+            const int row = (t & L2m) - b * a.B2;
+            const int n1 = t >> a.lg2;
+#pragma unroll
+            for (int r = 0; r < KM; ++r)
+                if (r >= g0 && r < g0 + gc) smem[((r - g0) * a.B2 + row) * a.S + padi<E>(n1)] = acc[r];
+        }
+        __syncthreads();
+        for (int j0 = 0; j0 < njobs; j0 += nt) {
+            const int job = j0 + team;
+            const bool act = job < njobs;
+            const int rl = act ? job / a.B2 : 0, row = act ? job % a.B2 : 0;
+            const int n2 = b * a.B2 + row;
+            cx<T> *sm = smem + job * a.S;
+            cx<T> v[E];
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[m] = sm[padi<E>(tt + TT * m)];
+            __syncthreads();
+            TF::run(v, tt, sm, a.tw);
+            if (act) {
+                cx<T> *dst = a.Y + ((int64_t)(g0 + rl) * a.L2 + n2) * a.L1;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int k1 = TF::out_index(tt, e);
+                    dst[k1] = cmulc<T>(v[e], twiddle_L<T>(a, n2 * k1));
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---- pass B (adjoint): inverse column FFTs, V-scale and rank-sum -----------------
+// The rank-sum accumulators live in shared memory after the C exchange slots, at
+// ((e TT + tt) C + cc): consecutive lanes hit consecutive elements.
+template <typename T, int P2>
+__global__ void __launch_bounds__(256) k_passB(const PassArgs<T> a) {
+    constexpr int E = e_of<T, P2>();
+    using TF = TeamFft<T, P2, E, true>;
+    constexpr int TT = TF::TT;
+    cx<T> *smem = smem_base<T>();
+    const int cc = threadIdx.x & (a.C - 1);
+    const int tt = threadIdx.x >> a.lgC;
+    const int k1 = blockIdx.x * a.C + cc;
+    const T invN = T(1) / T(a.N);
+    cx<T> *acc = smem + a.C * a.S;
+#pragma unroll
+    for (int e = 0; e < E; ++e) acc[(e * TT + tt) * a.C + cc] = mk<T>(0, 0);
+    for (int r = 0; r < a.K; ++r) {
+        const cx<T> *Yr = a.Y + (int64_t)r * a.L;
+        cx<T> v[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = Yr[(int64_t)(tt + TT * m) * a.L1 + k1];
+        TF::run(v, tt, smem + cc * a.S, a.tw);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int64_t k = k1 + (int64_t)a.L1 * TF::out_index(tt, e);
+            const T z = T(2 * k - a.N) * invN;
+            const T tr = cheb_T<T>(r, z);
+            const cx<T> y = mul_ipow<T>(v[e], -r);
+            cx<T> &s = acc[(e * TT + tt) * a.C + cc];
+            s.x = fma(tr, y.x, s.x);
+            s.y = fma(tr, y.y, s.y);
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int64_t k = k1 + (int64_t)a.L1 * TF::out_index(tt, e);
+        if (k < a.N) a.out[k] = acc[(e * TT + tt) * a.C + cc];
+    }
+}
+
+// ---- launchers ------------------------------------------------------------------
+
+template <typename F>
+int dispatch_P(int P, F &&f) {
+    switch (P) {
+        case 32: return f(std::integral_constant<int, 32>{});
+        case 64: return f(std::integral_constant<int, 64>{});
+        case 128: return f(std::integral_constant<int, 128>{});
+        case 256: return f(std::integral_constant<int, 256>{});
+        case 512: return f(std::integral_constant<int, 512>{});
+        case 1024: return f(std::integral_constant<int, 1024>{});
+        case 2048: return f(std::integral_constant<int, 2048>{});
+        default: return NUFFT_EUNSUPPORTED;
+    }
+}
+
+// Opt a kernel into more than 48 KB of dynamic shared memory, once per device.
+template <typename K>
+inline int set_smem(K kern, size_t bytes, int device, int *done) {
+    if (bytes > 48 * 1024 && device >= 0 && device < 64 && !done[device]) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(SMEM_BUDGET + 16 * 1024)) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return NUFFT_ECUDA;
+        }
+        done[device] = 1;
+    }
+    return NUFFT_OK;
+}
+
+inline int launch_status() {
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;
+}
+
+template <typename T>
+int launch_cols(nufft_plan p, const PassArgs<T> &a0, bool adjoint, cudaStream_t s) {
+    return dispatch_P(p->L2, [&](auto PC) -> int {
+        constexpr int P = decltype(PC)::value;
+        constexpr int TT = P / e_of<T, P>();
+        PassArgs<T> a = a0;
+        a.C = adjoint ? p->CB : p->C1;
+        a.lgC = 0;
+        while ((1 << a.lgC) < a.C) ++a.lgC;
+        a.S = adjoint ? p->SB : p->S1;
+        const size_t smem = adjoint ? p->smemB : p->smem1;
+        const dim3 block(a.C * TT);
+        static int done_b[64] = {}, done_1[64] = {};
+        if (adjoint) {
+            auto kern = k_passB<T, P>;
+            if (int rc = set_smem(kern, smem, p->device, done_b)) return rc;
+            kern<<<dim3(p->L1 / a.C), block, smem, s>>>(a);
+        } else {
+            auto kern = k_pass1<T, P>;
+            if (int rc = set_smem(kern, smem, p->device, done_1)) return rc;
+            kern<<<dim3(p->L1 / a.C, p->K), block, smem, s>>>(a);
+        }
+        return launch_status();
+    });
+}
+
+template <typename T, int KM>
+int launch_rows(nufft_plan p, const PassArgs<T> &a0, bool adjoint, cudaStream_t s) {
+    Beta<T, KM> beta;
+    for (int r = 0; r < KM; ++r)
+        for (int q = 0; q < KM; ++q) beta.b[r][q] = (T)p->beta[r][q];
+    return dispatch_P(p->L1, [&](auto PC) -> int {
+        constexpr int P = decltype(PC)::value;
+        constexpr int TT = P / e_of<T, P>();
+        PassArgs<T> a = a0;
+        a.S = p->S2;
+        const dim3 block(p->nt2 * TT);
+        static int done_a[64] = {}, done_2[64] = {};
+        if (adjoint) {
+            auto kern = k_passA<T, P, KM>;
+            if (int rc = set_smem(kern, p->smem2, p->device, done_a)) return rc;
+            kern<<<dim3(p->NB), block, p->smem2, s>>>(a, beta);
+        } else {
+            auto kern = k_pass2<T, P, KM>;
+            if (int rc = set_smem(kern, p->smem2, p->device, done_2)) return rc;
+            kern<<<dim3(p->NB), block, p->smem2, s>>>(a, beta);
+        }
+        return launch_status();
+    });
+}
+
+// explicit instantiation declarations (defined in the inst_*.cu files)
+#define NUFFT_DECLARE_ROWS(T, KM) \
+    extern template int launch_rows<T, KM>(nufft_plan, const PassArgs<T> &, bool, cudaStream_t);
+#define NUFFT_DECLARE_COLS(T) \
+    extern template int launch_cols<T>(nufft_plan, const PassArgs<T> &, bool, cudaStream_t);
+
+}  // namespace nufft

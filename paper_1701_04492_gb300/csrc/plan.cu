@@ -1,0 +1,440 @@
+// plan.cu -- the planning stage (section 2.3 "Planning the transform").
+//
+// Device work, FP64: s = rint(L x), t = s mod L, delta = L x - s (eqs. (2.8)-(2.9)),
+// d = delta N / L and gamma = max |d| (section 2.1.2).  Host work, FP64: the rank K
+// and the coefficients a_pr of eq. (2.6).  Then a stable LSD radix sort groups the
+// samples by the pass-2 tile that holds their grid point, and the twiddle tables
+// are built.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "fft_team.cuh"
+#include "nufft_internal.h"
+
+namespace nufft {
+namespace {
+
+constexpr int SORT_THREADS = 256;
+constexpr int SORT_CHUNK = 4096;          // elements per CTA
+constexpr int SORT_BITS = 8;
+constexpr int SORT_BINS = 1 << SORT_BITS;
+
+// ---- eqs. (2.8)-(2.9) ---------------------------------------------------------
+
+__global__ void k_round(const double *__restrict__ x, int64_t M, double Ld, int64_t L,
+                        double ratio, int32_t *__restrict__ t_out, double *__restrict__ d_out,
+                        unsigned long long *__restrict__ gamma_bits, int *__restrict__ bad) {
+    unsigned long long local = 0;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < M;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const double xj = x[j];
+        const double Lx = Ld * xj;                     // exact: L is a power of two
+        if (!isfinite(Lx) || fabs(Lx) >= 4503599627370496.0) {   // 2^52
+            atomicOr(bad, 1);
+            t_out[j] = 0;
+            d_out[j] = 0.0;
+            continue;
+        }
+        const double s = rint(Lx);                      // nearest, ties to even
+        const double q = floor(s / Ld);                 // exact quotient of a power of two
+        const double t = s - q * Ld;                    // Euclidean: t in [0, L)
+        const double delta = Lx - s;                    // exact, |delta| <= 1/2
+        const double d = delta * ratio;
+        t_out[j] = (int32_t)t;
+        d_out[j] = d;
+        const unsigned long long bits = (unsigned long long)__double_as_longlong(fabs(d));
+        local = bits > local ? bits : local;
+    }
+    // warp max, then one atomic per warp
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long v = __shfl_down_sync(0xffffffffu, local, o);
+        local = v > local ? v : local;
+    }
+    if ((threadIdx.x & 31) == 0 && local) atomicMax(gamma_bits, local);
+}
+
+// ---- stable LSD radix sort of (key, index) ---------------------------------------
+
+__device__ __forceinline__ int32_t sort_key(int32_t t, int lg1, int lg2, int B2) {
+    const int32_t n2 = t & ((1 << lg2) - 1);
+    const int32_t n1 = t >> lg2;
+    const int32_t bucket = n2 / B2;
+    const int32_t row = n2 - bucket * B2;
+    return (bucket << lg1) * B2 + n1 * B2 + row;
+}
+
+__global__ void k_keys(const int32_t *__restrict__ t, int64_t M, int lg1, int lg2, int B2,
+                       int32_t *__restrict__ key, int32_t *__restrict__ val) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < M;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        key[j] = sort_key(t[j], lg1, lg2, B2);
+        val[j] = (int32_t)j;
+    }
+}
+
+__global__ void __launch_bounds__(SORT_THREADS) k_hist(const int32_t *__restrict__ key, int64_t M,
+                                                      int shift, int nchunks,
+                                                      int32_t *__restrict__ counts) {
+    __shared__ int h[SORT_BINS];
+    for (int i = threadIdx.x; i < SORT_BINS; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * SORT_CHUNK;
+    for (int i = threadIdx.x; i < SORT_CHUNK; i += blockDim.x) {
+        const int64_t j = base + i;
+        if (j < M) atomicAdd(&h[(key[j] >> shift) & (SORT_BINS - 1)], 1);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < SORT_BINS; i += blockDim.x)
+        counts[(int64_t)i * nchunks + blockIdx.x] = h[i];
+}
+
+// Exclusive scan of n counts by one CTA of 1024 threads.
+__global__ void __launch_bounds__(1024) k_scan(int32_t *__restrict__ counts, int64_t n) {
+    __shared__ int64_t part[1024];
+    const int64_t seg = (n + 1023) / 1024;
+    const int64_t lo = threadIdx.x * seg, hi = min(n, lo + seg);
+    int64_t s = 0;
+    for (int64_t i = lo; i < hi; ++i) s += counts[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const int64_t v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int64_t run = part[threadIdx.x] - s;   // exclusive prefix of this segment
+    for (int64_t i = lo; i < hi; ++i) {
+        const int32_t c = counts[i];
+        counts[i] = (int32_t)run;
+        run += c;
+    }
+}
+
+__global__ void __launch_bounds__(SORT_THREADS) k_scatter(const int32_t *__restrict__ kin,
+                                                         const int32_t *__restrict__ vin, int64_t M,
+                                                         int shift, int nchunks,
+                                                         const int32_t *__restrict__ offsets,
+                                                         int32_t *__restrict__ kout,
+                                                         int32_t *__restrict__ vout) {
+    constexpr int NW = SORT_THREADS / 32;
+    constexpr int PER_WARP = SORT_CHUNK / NW;
+    __shared__ int wc[NW][SORT_BINS];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < NW * SORT_BINS; i += blockDim.x) (&wc[0][0])[i] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * SORT_CHUNK + w * PER_WARP;
+    const unsigned lt = (1u << lane) - 1u;
+    // 1) per-warp digit counts
+    for (int s = 0; s < PER_WARP; s += 32) {
+        const int64_t j = base + s + lane;
+        const int dg = j < M ? ((kin[j] >> shift) & (SORT_BINS - 1)) : SORT_BINS;
+        const unsigned peers = __match_any_sync(0xffffffffu, dg);
+        if (dg < SORT_BINS && (peers & lt) == 0) wc[w][dg] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // 2) turn counts into start positions: chunk offset + earlier warps of this chunk
+    for (int dg = threadIdx.x; dg < SORT_BINS; dg += blockDim.x) {
+        int run = offsets[(int64_t)dg * nchunks + blockIdx.x];
+        for (int ww = 0; ww < NW; ++ww) {
+            const int c = wc[ww][dg];
+            wc[ww][dg] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    // 3) stable placement, in input order within each warp
+    for (int s = 0; s < PER_WARP; s += 32) {
+        const int64_t j = base + s + lane;
+        const int dg = j < M ? ((kin[j] >> shift) & (SORT_BINS - 1)) : SORT_BINS;
+        const unsigned peers = __match_any_sync(0xffffffffu, dg);
+        if (dg < SORT_BINS) {
+            const int pos = wc[w][dg] + __popc(peers & lt);
+            kout[pos] = kin[j];
+            vout[pos] = vin[j];
+        }
+        __syncwarp();
+        if (dg < SORT_BINS && (peers & lt) == 0) wc[w][dg] += __popc(peers);
+        __syncwarp();
+    }
+}
+
+template <typename T>
+__global__ void k_build(const int32_t *__restrict__ perm, const int32_t *__restrict__ t_j,
+                        const double *__restrict__ d_j, int64_t M, int32_t *__restrict__ tsorted,
+                        T *__restrict__ dsorted) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t j = perm[i];
+        tsorted[i] = t_j[j];
+        dsorted[i] = (T)d_j[j];
+    }
+}
+
+// bstart[b] = first sorted position whose bucket is >= b, b = 0..NB.
+__global__ void k_bstart(const int32_t *__restrict__ keys, int64_t M, int bucket_shift, int NB,
+                         int32_t *__restrict__ bstart) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= M;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int prev = i == 0 ? -1 : (keys[i - 1] >> bucket_shift);
+        const int cur = i == M ? NB : (keys[i] >> bucket_shift);
+        for (int b = prev + 1; b <= cur; ++b) bstart[b] = (int32_t)i;
+    }
+}
+
+int grid_for(int64_t n, int threads) {
+    int64_t g = (n + threads - 1) / threads;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 16));
+}
+
+template <typename T>
+int upload_table(void **dst, const std::vector<double> &re, const std::vector<double> &im,
+                 cudaStream_t s, int64_t *bytes) {
+    const size_t n = re.size();
+    std::vector<T> h(2 * n);
+    for (size_t i = 0; i < n; ++i) { h[2 * i] = (T)re[i]; h[2 * i + 1] = (T)im[i]; }
+    NUFFT_CUDA_TRY(cudaMalloc(dst, h.size() * sizeof(T)));
+    *bytes += (int64_t)(h.size() * sizeof(T));
+    NUFFT_CUDA_TRY(cudaMemcpyAsync(*dst, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    NUFFT_CUDA_TRY(cudaStreamSynchronize(s));   // h goes out of scope
+    return NUFFT_OK;
+}
+
+template <typename T>
+int build_tables(nufft_plan p, cudaStream_t s) {
+    std::vector<double> re(TW_BASE), im(TW_BASE);
+    for (int m = 0; m < TW_BASE; ++m) twiddle(TW_BASE, m, &re[m], &im[m]);
+    int rc = upload_table<T>(&p->tw4096, re, im, s, &p->work_bytes);
+    if (rc) return rc;
+    // four-step twiddle w_L^m = w_L^(4096 m_hi) * w_L^(m_lo), m = 4096 m_hi + m_lo
+    const int64_t nlo = std::min<int64_t>(p->L, TW_BASE);
+    const int64_t nhi = std::max<int64_t>(1, p->L / TW_BASE);
+    re.assign(nlo, 0.0); im.assign(nlo, 0.0);
+    for (int64_t m = 0; m < nlo; ++m) twiddle(p->L, m, &re[m], &im[m]);
+    if ((rc = upload_table<T>(&p->twlo, re, im, s, &p->work_bytes))) return rc;
+    re.assign(nhi, 0.0); im.assign(nhi, 0.0);
+    for (int64_t m = 0; m < nhi; ++m) twiddle(p->L, m * TW_BASE, &re[m], &im[m]);
+    return upload_table<T>(&p->twhi, re, im, s, &p->work_bytes);
+}
+
+template <typename T>
+int plan_device(nufft_plan p, const double *x, cudaStream_t s) {
+    const int64_t M = p->M;
+    struct Scratch {
+        unsigned long long *gbits = nullptr;
+        int *bad = nullptr;
+        int32_t *ka = nullptr, *va = nullptr, *kb = nullptr, *vb = nullptr, *cnt = nullptr;
+        ~Scratch() {
+            cudaFree(gbits); cudaFree(bad); cudaFree(ka); cudaFree(va);
+            cudaFree(kb); cudaFree(vb); cudaFree(cnt);
+        }
+    } sc;
+    const size_t Mi = (size_t)std::max<int64_t>(M, 1);
+    NUFFT_CUDA_TRY(cudaMalloc(&sc.gbits, sizeof(unsigned long long)));
+    NUFFT_CUDA_TRY(cudaMalloc(&sc.bad, sizeof(int)));
+    NUFFT_CUDA_TRY(cudaMalloc(&p->t_j, Mi * sizeof(int32_t)));
+    NUFFT_CUDA_TRY(cudaMalloc(&p->d_j, Mi * sizeof(double)));
+    p->work_bytes += (int64_t)(Mi * (sizeof(int32_t) + sizeof(double)));
+    NUFFT_CUDA_TRY(cudaMemsetAsync(sc.gbits, 0, sizeof(unsigned long long), s));
+    NUFFT_CUDA_TRY(cudaMemsetAsync(sc.bad, 0, sizeof(int), s));
+    if (M > 0) {
+        k_round<<<grid_for(M, 256), 256, 0, s>>>(x, M, (double)p->L, p->L,
+                                                 (double)p->N / (double)p->L, p->t_j, p->d_j,
+                                                 sc.gbits, sc.bad);
+        NUFFT_CUDA_TRY(cudaGetLastError());
+    }
+    unsigned long long gb = 0;
+    int bad = 0;
+    NUFFT_CUDA_TRY(cudaMemcpyAsync(&gb, sc.gbits, sizeof(gb), cudaMemcpyDeviceToHost, s));
+    NUFFT_CUDA_TRY(cudaMemcpyAsync(&bad, sc.bad, sizeof(bad), cudaMemcpyDeviceToHost, s));
+    NUFFT_CUDA_TRY(cudaStreamSynchronize(s));
+    if (bad) return NUFFT_EINVAL;
+    double gamma;
+    std::memcpy(&gamma, &gb, sizeof(gamma));
+    p->gamma = gamma;
+
+    // rank and coefficients (eq. (2.6)); beta folds the primes of both sums
+    p->K = choose_rank(p->eps, gamma);
+    p->kmax = std::min(KMAX_ALL, ((p->K + 3) / 4) * 4);
+    std::memset(p->beta, 0, sizeof(p->beta));
+    std::memset(p->alpha, 0, sizeof(p->alpha));
+    if (gamma == 0.0) {
+        p->beta[0][0] = 1.0;   // u = v = 1: one FFT
+        p->alpha[0][0] = 1.0;
+    } else {
+        std::vector<double> al(p->K * p->K);
+        chebyshev_alpha(p->K, gamma, al.data());
+        for (int r = 0; r < p->K; ++r)
+            for (int q = 0; q < p->K; ++q) {
+                const double w = (r == 0 ? 0.5 : 1.0) * (q == 0 ? 0.5 : 1.0);
+                p->alpha[q][r] = al[q * p->K + r];
+                p->beta[r][q] = w * al[q * p->K + r];
+            }
+    }
+
+    int rc = plan_geometry<T>(p);
+    if (rc) return rc;
+
+    // bucket the samples: stable sort by (bucket, n1, row)
+    NUFFT_CUDA_TRY(cudaMalloc(&p->tsorted, Mi * sizeof(int32_t)));
+    NUFFT_CUDA_TRY(cudaMalloc(&p->perm, Mi * sizeof(int32_t)));
+    NUFFT_CUDA_TRY(cudaMalloc(&p->dsorted, Mi * sizeof(T)));
+    NUFFT_CUDA_TRY(cudaMalloc(&p->bstart, (size_t)(p->NB + 1) * sizeof(int32_t)));
+    p->work_bytes += (int64_t)(Mi * (2 * sizeof(int32_t) + sizeof(T)) + (p->NB + 1) * sizeof(int32_t));
+    NUFFT_CUDA_TRY(cudaMalloc(&sc.ka, Mi * sizeof(int32_t)));
+    NUFFT_CUDA_TRY(cudaMalloc(&sc.va, Mi * sizeof(int32_t)));
+    NUFFT_CUDA_TRY(cudaMalloc(&sc.kb, Mi * sizeof(int32_t)));
+    const int nchunks = (int)std::max<int64_t>(1, (M + SORT_CHUNK - 1) / SORT_CHUNK);
+    NUFFT_CUDA_TRY(cudaMalloc(&sc.cnt, (size_t)SORT_BINS * nchunks * sizeof(int32_t)));
+    int32_t *kin = sc.ka, *vin = sc.va, *kout = sc.kb, *vout = p->perm;
+    if (M > 0) {
+        k_keys<<<grid_for(M, 256), 256, 0, s>>>(p->t_j, M, p->lg1, p->lg2, p->B2, kin, vin);
+        NUFFT_CUDA_TRY(cudaGetLastError());
+        const int lgL = p->lg1 + p->lg2;
+        const int passes = (lgL + SORT_BITS - 1) / SORT_BITS;
+        NUFFT_CUDA_TRY(cudaMalloc(&sc.vb, Mi * sizeof(int32_t)));
+        for (int ps = 0; ps < passes; ++ps) {
+            // the last pass lands in perm
+            vout = (ps == passes - 1) ? p->perm : (vin == sc.va ? sc.vb : sc.va);
+            kout = (kin == sc.ka) ? sc.kb : sc.ka;
+            const int shift = ps * SORT_BITS;
+            k_hist<<<nchunks, SORT_THREADS, 0, s>>>(kin, M, shift, nchunks, sc.cnt);
+            k_scan<<<1, 1024, 0, s>>>(sc.cnt, (int64_t)SORT_BINS * nchunks);
+            k_scatter<<<nchunks, SORT_THREADS, 0, s>>>(kin, vin, M, shift, nchunks, sc.cnt, kout, vout);
+            NUFFT_CUDA_TRY(cudaGetLastError());
+            kin = kout;
+            vin = vout;
+        }
+        k_build<T><<<grid_for(M, 256), 256, 0, s>>>(p->perm, p->t_j, p->d_j, M, p->tsorted,
+                                                    (T *)p->dsorted);
+        NUFFT_CUDA_TRY(cudaGetLastError());
+    }
+    // bucket = key >> (lg1 + log2 B2)
+    int lgB2 = 0;
+    while ((1 << lgB2) < p->B2) ++lgB2;
+    k_bstart<<<grid_for(M + 1, 256), 256, 0, s>>>(kin, M, p->lg1 + lgB2, p->NB, p->bstart);
+    NUFFT_CUDA_TRY(cudaGetLastError());
+
+    if ((rc = build_tables<T>(p, s))) return rc;
+
+    // work buffers
+    const size_t cxs = 2 * sizeof(T);
+    NUFFT_CUDA_TRY(cudaMalloc(&p->Y, (size_t)p->K * p->L * cxs));
+    NUFFT_CUDA_TRY(cudaMalloc(&p->fscr, Mi * cxs));
+    NUFFT_CUDA_TRY(cudaMalloc(&p->cstage, (size_t)p->N * cxs));
+    NUFFT_CUDA_TRY(cudaMalloc(&p->fstage, Mi * cxs));
+    p->work_bytes += (int64_t)(((size_t)p->K * p->L + 2 * Mi + p->N) * cxs);
+    if (p->flags & NUFFT_PLAN_UNFUSED) {
+        if ((rc = plan_unfused_factors<T>(p, s))) return rc;
+    }
+    NUFFT_CUDA_TRY(cudaStreamSynchronize(s));
+    return NUFFT_OK;
+}
+
+void free_plan(nufft_plan p) {
+    if (!p) return;
+    void *bufs[] = {p->tsorted, p->perm, p->bstart, p->t_j, p->dsorted, p->d_j, p->tw4096,
+                    p->twhi, p->twlo, p->Y, p->fscr, p->cstage, p->fstage, p->U, p->V, p->Xg};
+    for (void *b : bufs) if (b) cudaFree(b);
+    for (cudaEvent_t e : p->ev) if (e) cudaEventDestroy(e);
+    delete p;
+}
+
+}  // namespace
+}  // namespace nufft
+
+extern "C" int nufft2_plan(nufft_plan *out, int64_t N, int64_t M, const double *x_dev, double eps,
+                           int prec, int64_t L, unsigned flags, void *stream) {
+    using namespace nufft;
+    if (!out) return NUFFT_EINVAL;
+    *out = nullptr;
+    if (N < 1 || M < 0 || M >= ((int64_t)1 << 31) || !(eps > 0.0 && eps < 1.0)) return NUFFT_EINVAL;
+    if (prec != NUFFT_F32 && prec != NUFFT_F64) return NUFFT_EINVAL;
+    if (M > 0 && !x_dev) return NUFFT_EINVAL;
+    if (flags & ~(NUFFT_PLAN_UNFUSED | NUFFT_PLAN_TIMING)) return NUFFT_EINVAL;
+    if (N > ((int64_t)1 << LOG2_L_MAX)) return NUFFT_EUNSUPPORTED;
+    if (L == 0) {
+        L = (int64_t)1 << LOG2_L_MIN;
+        while (L < N) L <<= 1;
+    } else {
+        if (L < N || (L & (L - 1)) != 0) return NUFFT_EINVAL;
+        if (L < ((int64_t)1 << LOG2_L_MIN) || L > ((int64_t)1 << LOG2_L_MAX)) return NUFFT_EUNSUPPORTED;
+    }
+    nufft_plan p = new (std::nothrow) nufft_plan_s();
+    if (!p) return NUFFT_ENOMEM;
+    p->N = N; p->M = M; p->L = L; p->eps = eps; p->prec = prec; p->flags = flags;
+    int lg = 0;
+    while (((int64_t)1 << lg) < L) ++lg;
+    p->lg1 = (lg + 1) / 2;
+    p->lg2 = lg / 2;
+    p->L1 = 1 << p->lg1;
+    p->L2 = 1 << p->lg2;
+    if (cudaGetDevice(&p->device) != cudaSuccess) { free_plan(p); return NUFFT_ECUDA; }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (flags & NUFFT_PLAN_TIMING)
+        for (cudaEvent_t &e : p->ev)
+            if (cudaEventCreate(&e) != cudaSuccess) { (void)cudaGetLastError(); free_plan(p); return NUFFT_ECUDA; }
+    const int rc = prec == NUFFT_F32 ? plan_device<float>(p, x_dev, s) : plan_device<double>(p, x_dev, s);
+    if (rc != NUFFT_OK) { free_plan(p); return rc; }
+    *out = p;
+    return NUFFT_OK;
+}
+
+extern "C" int nufft2_plan_info(nufft_plan p, int *K, double *gamma, int64_t *L, int64_t *work_bytes) {
+    if (!p) return NUFFT_EINVAL;
+    if (K) *K = p->K;
+    if (gamma) *gamma = p->gamma;
+    if (L) *L = p->L;
+    if (work_bytes) *work_bytes = p->work_bytes;
+    return NUFFT_OK;
+}
+
+extern "C" int nufft2_plan_export(nufft_plan p, int32_t *t_dev, double *d_dev, double *alpha_host,
+                                  void *stream) {
+    if (!p) return NUFFT_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (p->M > 0 && t_dev)
+        NUFFT_CUDA_TRY(cudaMemcpyAsync(t_dev, p->t_j, (size_t)p->M * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    if (p->M > 0 && d_dev)
+        NUFFT_CUDA_TRY(cudaMemcpyAsync(d_dev, p->d_j, (size_t)p->M * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (alpha_host)
+        for (int q = 0; q < p->K; ++q)
+            for (int r = 0; r < p->K; ++r) alpha_host[q * p->K + r] = p->alpha[q][r];
+    NUFFT_CUDA_TRY(cudaStreamSynchronize(s));
+    return NUFFT_OK;
+}
+
+extern "C" int nufft_kernel_times(nufft_plan p, float *ms_out, int cap, int *count) {
+    if (!p || (cap > 0 && !ms_out)) return NUFFT_EINVAL;
+    if (!(p->flags & NUFFT_PLAN_TIMING)) return NUFFT_ESTATE;
+    const int n = p->nev > 0 ? p->nev - 1 : 0;
+    if (count) *count = n;
+    if (n == 0) return NUFFT_OK;
+    NUFFT_CUDA_TRY(cudaEventSynchronize(p->ev[p->nev - 1]));
+    for (int i = 0; i < n && i < cap; ++i) NUFFT_CUDA_TRY(cudaEventElapsedTime(&ms_out[i], p->ev[i], p->ev[i + 1]));
+    return NUFFT_OK;
+}
+
+extern "C" int nufft_destroy(nufft_plan p) {
+    nufft::free_plan(p);
+    return NUFFT_OK;
+}
+
+extern "C" const char *nufft_strerror(int code) {
+    switch (code) {
+        case NUFFT_OK: return "ok";
+        case NUFFT_EINVAL: return "invalid argument";
+        case NUFFT_ENOMEM: return "out of memory";
+        case NUFFT_ECUDA: return "CUDA error";
+        case NUFFT_EUNSUPPORTED: return "unsupported size";
+        case NUFFT_ESTATE: return "plan lacks the option this call needs";
+        default: return "unknown status";
+    }
+}

@@ -1,0 +1,59 @@
+"""The C ABI library builds, loads and exports every entry point include/nufft.h
+declares; argument checks that need no GPU return the documented codes."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1701_04492_gb300 import _lib, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "nufft.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(nufft\w*)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return _lib.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert "nufft2_plan" in names and "nufft2_exec" in names and "nufft1_exec" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    # and the binding's signature table covers exactly the header
+    assert sorted(_lib.SIGNATURES) == names
+
+
+def test_argument_errors_without_gpu(lib):
+    h = ctypes.c_void_p()
+    plan = lib.nufft2_plan
+    assert plan(ctypes.byref(h), 0, 4, None, 1e-9, 0, 0, 0, None) == -1          # N < 1
+    assert plan(ctypes.byref(h), 16, -1, None, 1e-9, 0, 0, 0, None) == -1        # M < 0
+    assert plan(ctypes.byref(h), 16, 4, None, 1e-9, 0, 0, 0, None) == -1         # x NULL
+    assert plan(ctypes.byref(h), 16, 0, None, 0.0, 0, 0, 0, None) == -1          # eps
+    assert plan(ctypes.byref(h), 16, 0, None, 1.0, 0, 0, 0, None) == -1
+    assert plan(ctypes.byref(h), 16, 0, None, 1e-9, 2, 0, 0, None) == -1         # precision
+    assert plan(ctypes.byref(h), 16, 0, None, 1e-9, 0, 3000, 0, None) == -1      # L not 2^n
+    assert plan(ctypes.byref(h), 4096, 0, None, 1e-9, 0, 2048, 0, None) == -1    # L < N
+    assert plan(ctypes.byref(h), 16, 0, None, 1e-9, 0, 512, 0, None) == -4       # L < 1024
+    assert plan(ctypes.byref(h), 1 << 23, 0, None, 1e-9, 0, 0, 0, None) == -4    # N too large
+    assert plan(ctypes.byref(h), 16, 0, None, 1e-9, 0, 0, 8, None) == -1         # unknown flag
+    assert plan(None, 16, 0, None, 1e-9, 0, 0, 0, None) == -1
+    assert h.value is None
+    for fn in ("nufft2_exec", "nufft1_exec", "nufft2_exec_host", "nufft2_exec_unfused"):
+        assert getattr(lib, fn)(None, None, None, None) == -1
+    assert lib.nufft2_exec_dx(None, None, None, None, 0, None) == -1
+    assert lib.nufft2_exec_batch(None, 1, None, 1, None, 1, None) == -1
+    assert lib.nufft2_plan_info(None, None, None, None, None) == -1
+    assert lib.nufft_destroy(None) == 0
+    for code in (0, -1, -2, -3, -4, -5):
+        assert lib.nufft_strerror(code)

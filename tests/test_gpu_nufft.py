@@ -1,0 +1,249 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Tolerances (derived in DESIGN.md, "Tolerances"):
+  FP64 exec  vs the low-rank oracle: ||df||_2 / ||f||_2 <= 1e-13 (same method,
+             rounding only); vs the direct sum: |df|_inf <= (eps + 1e-13) ||c||_1.
+  FP32 exec  vs the low-rank oracle: ||df||_2 / ||f||_2 <= 1e-5 (FP32 FFT rounding,
+             ~u log2 L); vs the direct sum: |df|_inf <= max(eps, 5e-6) ||c||_1.
+  Integer plan results (t) and the FP64 perturbations d: bit-exact.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import direct, lowrank  # noqa: E402
+from paper_1701_04492_gb300 import workloads as wl  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_1701_04492_gb300 import api as a
+    return a
+
+
+def _dev(a, dtype):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def _rel2(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _cdt(prec):
+    return torch.complex64 if prec == "f32" else torch.complex128
+
+
+def _cast(c, prec):
+    """The coefficients the GPU sees (FP32 runs round them; the oracle uses the same values)."""
+    return c.astype(np.complex64).astype(np.complex128) if prec == "f32" else c
+
+
+TOL_REL = {"f32": 1e-5, "f64": 1e-13}
+
+
+def _samples(kind, n, seed):
+    return {"uniform": lambda: wl.samples_uniform(n, seed),
+            "perturbed": lambda: wl.samples_perturbed(n, seed, 0.5),
+            "equispaced": lambda: wl.samples_equispaced(n),
+            "wide": lambda: 20.0 * wl.samples_uniform(n, seed) - 10.0,
+            "worst": lambda: wl.samples_worst(n, 1 / 8)}[kind]()
+
+
+# ---- plan: eqs. (2.8)-(2.9), gamma, K, a_pr -------------------------------------
+
+@pytest.mark.parametrize("kind", ["uniform", "perturbed", "wide", "equispaced"])
+@pytest.mark.parametrize("N,L,M", [(4096, 0, 4096), (3000, 0, 5000), (1000, 2048, 777)])
+def test_plan_matches_oracle(api, kind, N, L, M):
+    x = _samples(kind, M, 3)
+    if kind == "equispaced":
+        x = wl.samples_equispaced(N)[: M] if M <= N else np.arange(M) / N
+    plan = api.Plan(N, x, 1e-9, "f64", L=L)
+    P = lowrank.plan(N, x, 1e-9, plan.L)
+    t, d, alpha = plan.export()
+    assert np.array_equal(t.cpu().numpy(), P.t.astype(np.int32))
+    assert np.array_equal(d.cpu().numpy(), P.d)             # bit-exact FP64
+    assert plan.gamma == P.gamma
+    assert plan.K == P.K
+    if P.gamma > 0:
+        ipow = (1j) ** np.arange(P.K)
+        assert np.max(np.abs(alpha * ipow[None, :] - P.a)) <= 1e-15
+
+
+def test_plan_rejects_nonfinite(api):
+    x = wl.samples_uniform(100, 4)
+    x[17] = np.nan
+    with pytest.raises(api.NufftError) as e:
+        api.Plan(128, x, 1e-9, "f32")
+    assert e.value.code == -1
+    x[17] = 1e300
+    with pytest.raises(api.NufftError):
+        api.Plan(128, x, 1e-9, "f32")
+
+
+# ---- forward -----------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("kind", ["uniform", "equispaced"])
+def test_c1_against_direct(api, prec, kind):
+    # 1D NUFFT-II at N = 4096, eps = 1e-12: full comparison with the direct sum.
+    N, eps = 4096, 1e-12
+    x = wl.samples_uniform(N, 1) if kind == "uniform" else wl.samples_equispaced(N)
+    c = _cast(wl.coeffs_cn(N, 1), prec)
+    plan = api.Plan(N, x, eps, prec)
+    f = plan.forward(_dev(c, _cdt(prec))).cpu().numpy()
+    fd = direct.nudft2(x, c)
+    tol = (eps + 1e-13) if prec == "f64" else max(eps, 5e-6)
+    assert np.max(np.abs(f - fd)) <= tol * np.sum(np.abs(c))
+    if kind == "equispaced":
+        assert plan.K == 1
+        assert _rel2(f, np.fft.fft(c)) <= TOL_REL[prec]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("kind", ["uniform", "perturbed", "wide", "worst"])
+@pytest.mark.parametrize("N,L,M,eps", [(4096, 0, 4096, 1e-9), (3000, 0, 4100, 1e-4),
+                                       (1000, 1024, 777, 1e-12), (2048, 4096, 3000, 1e-14),
+                                       (50000, 0, 65536, 1e-9), (1, 0, 5, 1e-9), (17, 0, 1, 1e-6)])
+def test_forward_against_oracle(api, prec, kind, N, L, M, eps):
+    x = _samples(kind, M, 5)
+    c = _cast(wl.coeffs_cn(N, 5), prec)
+    plan = api.Plan(N, x, eps, prec, L=L)
+    f = plan.forward(_dev(c, _cdt(prec))).cpu().numpy()
+    P = lowrank.plan(N, x, eps, plan.L)
+    assert plan.K == P.K
+    fo = lowrank.nufft2(P, c)
+    assert _rel2(f, fo) <= TOL_REL[prec]
+
+
+def test_zero_samples(api):
+    plan = api.Plan(64, np.zeros(0), 1e-9, "f32")
+    c = _dev(wl.coeffs_cn(64, 6), torch.complex64)
+    assert plan.forward(c).numel() == 0
+    g = torch.zeros(0, dtype=torch.complex64, device="cuda")
+    assert torch.count_nonzero(plan.adjoint(g)).item() == 0
+
+
+# ---- adjoint (A^H) and the paper's type I (A^T) ----------------------------------------
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("N,L,M,eps", [(4096, 0, 4096, 1e-9), (3000, 0, 5000, 1e-12),
+                                       (1000, 2048, 777, 1e-6), (65536, 0, 65536, 1e-9)])
+def test_adjoint_against_oracle(api, prec, N, L, M, eps):
+    x = wl.samples_uniform(M, 7)
+    g = _cast(wl.cotangent_cn(M, 7), prec)
+    plan = api.Plan(N, x, eps, prec, L=L)
+    c = plan.adjoint(_dev(g, _cdt(prec))).cpu().numpy()
+    P = lowrank.plan(N, x, eps, plan.L)
+    assert _rel2(c, lowrank.nufft2_adjoint(P, g)) <= TOL_REL[prec]
+
+
+def test_adjoint_against_direct_and_inner_product(api):
+    N, M, eps = 2048, 3000, 1e-12
+    x = wl.samples_uniform(M, 8)
+    c = wl.coeffs_cn(N, 8)
+    g = wl.cotangent_cn(M, 8)
+    plan = api.Plan(N, x, eps, "f64")
+    f = plan.forward(_dev(c, torch.complex128)).cpu().numpy()
+    ah = plan.adjoint(_dev(g, torch.complex128)).cpu().numpy()
+    assert np.max(np.abs(ah - direct.nudft2_adjoint(x, g, N))) <= (eps + 1e-13) * np.sum(np.abs(g))
+    lhs, rhs = np.vdot(g, f), np.vdot(ah, c)
+    assert abs(lhs - rhs) <= 1e-13 * np.linalg.norm(f) * np.linalg.norm(g)
+    # section 3.1: F~1 = F~2^T, conj(A^H conj(g))
+    at = plan.transpose(_dev(g, torch.complex128)).cpu().numpy()
+    assert _rel2(at, lowrank.nufft1(lowrank.plan(N, x, eps), g)) <= 1e-13
+
+
+# ---- derivative with respect to x ----------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_dx_against_oracle(api, prec):
+    N, M, eps = 4096, 3000, 1e-10
+    x = wl.samples_uniform(M, 9)
+    c = _cast(wl.coeffs_cn(N, 9), prec)
+    g = _cast(wl.cotangent_cn(M, 9), prec)
+    plan = api.Plan(N, x, eps, prec)
+    gx = plan.dx(_dev(c, _cdt(prec)), _dev(g, _cdt(prec))).cpu().numpy().astype(np.float64)
+    ref = lowrank.nufft2_dx(lowrank.plan(N, x, eps), c, g)
+    assert _rel2(gx, ref) <= TOL_REL[prec] * 10
+    exact = np.real(np.conj(g) * direct.nudft2_deriv(x, c))
+    assert np.max(np.abs(gx - exact)) <= max(eps, 5e-6 if prec == "f32" else 1e-13) * \
+        2 * math.pi * N * np.sum(np.abs(c)) * np.max(np.abs(g))
+    # accumulate flag
+    gx2 = torch.full((M,), 1.5, dtype=plan.rdtype, device="cuda")
+    plan.dx(_dev(c, _cdt(prec)), _dev(g, _cdt(prec)), gx2, accumulate=True)
+    assert np.allclose(gx2.cpu().numpy() - 1.5, gx, rtol=1e-5, atol=1e-3 * np.max(np.abs(gx)) * TOL_REL[prec])
+
+
+# ---- full-size workload: N = M = 2^20, eps = 1e-9 ----------------------------------------
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("kind", ["perturbed", "uniform"])
+def test_full_size_against_oracle(api, prec, kind):
+    N = 1 << 20
+    x = _samples(kind, N, 10)
+    c = _cast(wl.coeffs_cn(N, 10), prec)
+    plan = api.Plan(N, x, 1e-9, prec)
+    assert plan.K == 12
+    f = plan.forward(_dev(c, _cdt(prec))).cpu().numpy()
+    P = lowrank.plan(N, x, 1e-9, plan.L)
+    assert _rel2(f, lowrank.nufft2(P, c)) <= TOL_REL[prec]
+    rows = np.random.default_rng(10).choice(N, 256, replace=False)
+    fd = direct.nudft2(x[rows], c)
+    tol = (1e-9 + 1e-13) if prec == "f64" else 5e-6
+    assert np.max(np.abs(f[rows] - fd)) <= tol * np.sum(np.abs(c))
+    # adjoint at full size
+    g = _cast(wl.cotangent_cn(N, 10), prec)
+    ah = plan.adjoint(_dev(g, _cdt(prec))).cpu().numpy()
+    assert _rel2(ah, lowrank.nufft2_adjoint(P, g)) <= TOL_REL[prec]
+
+
+# ---- unfused comparator, host path, batch, determinism -------------------------------------
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_unfused_equals_fused(api, prec):
+    N, M = 8192, 10000
+    x = wl.samples_uniform(M, 11)
+    c = _cast(wl.coeffs_cn(N, 11), prec)
+    plan = api.Plan(N, x, 1e-9, prec, unfused=True)
+    cd = _dev(c, _cdt(prec))
+    fu = plan.forward_unfused(cd).cpu().numpy()
+    ff = plan.forward(cd).cpu().numpy()
+    assert _rel2(fu, ff) <= TOL_REL[prec] * 2
+    plan2 = api.Plan(N, x, 1e-9, prec)
+    with pytest.raises(api.NufftError) as e:
+        plan2.forward_unfused(cd)
+    assert e.value.code == -5
+
+
+def test_host_path_and_batch(api):
+    N, M, B = 4096, 5000, 5
+    x = wl.samples_uniform(M, 12)
+    plan = api.Plan(N, x, 1e-9, "f32")
+    cs = np.stack([wl.coeffs_cn(N, 100 + b) for b in range(B)]).astype(np.complex64)
+    cd = _dev(cs, torch.complex64)
+    fb = plan.forward_batch(cd).cpu().numpy()
+    for b in range(B):
+        assert np.array_equal(fb[b], plan.forward(cd[b].contiguous()).cpu().numpy())
+    ch = torch.tensor(cs[0]).pin_memory()
+    fh = torch.empty(M, dtype=torch.complex64).pin_memory()
+    plan.forward_host(ch, fh)
+    assert np.array_equal(fh.numpy(), fb[0])
+
+
+def test_deterministic(api):
+    N, M = 65536, 70000
+    x = wl.samples_uniform(M, 13)
+    plan = api.Plan(N, x, 1e-9, "f32")
+    c = _dev(wl.coeffs_cn(N, 13), torch.complex64)
+    g = _dev(wl.cotangent_cn(M, 13), torch.complex64)
+    assert torch.equal(plan.forward(c), plan.forward(c))
+    assert torch.equal(plan.adjoint(g), plan.adjoint(g))
+    # a second plan on the same samples gives the same bits
+    plan2 = api.Plan(N, x, 1e-9, "f32")
+    assert torch.equal(plan.forward(c), plan2.forward(c))
