@@ -17,6 +17,7 @@ from . import workloads  # noqa: F401
 def __getattr__(name):
     # the torch binding is imported on first use, so `workloads` stays light
     if name in ("Plan", "nufft2", "NufftError", "api"):
-        from . import api
+        import importlib
+        api = importlib.import_module(__name__ + ".api")
         return api if name == "api" else getattr(api, name)
     raise AttributeError(name)
