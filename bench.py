@@ -178,6 +178,17 @@ def run_ours(args):
         plan.adjoint(f, gc)          # the loss cotangent is taken as f itself
         plan.dx(c, g, gx)
 
+    if args.only:
+        # profiling mode: only the named operation, no extra measurements
+        op = {"step": step, "fwd": lambda: plan.forward(c, f), "adj": lambda: plan.adjoint(f, gc),
+              "dx": lambda: plan.dx(c, g, gx)}[args.only]
+        for _ in range(args.warmup + args.steps):
+            op()
+        torch.cuda.synchronize(dev)
+        if rank == 0:
+            print(json.dumps({"only": args.only, "steps": args.steps, "warmup": args.warmup, "K": plan.K}))
+        return
+
     def timed(fn, steps, warmup):
         for _ in range(warmup):
             fn()
@@ -388,8 +399,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", choices=["step", "fwd", "adj", "dx"], default=None,
+                    help="profiling mode: run only this operation warmup+steps times, untimed")
     args = ap.parse_args()
-    if args.warmup < 3:
+    if args.warmup < 3 and not args.only:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)

@@ -51,19 +51,34 @@ int plan_geometry(nufft_plan p) {
     p->CB = clamp_pow2(128 / TT2, 1, p->L1);
     p->S1 = slot_stride<T>(p->L2, E2, p->C1);
     p->SB = slot_stride<T>(p->L2, E2, p->CB);
-    p->smem1 = (size_t)p->C1 * p->S1 * cxs;
+    p->smem1 = ((size_t)p->C1 * p->S1 + (size_t)p->C1 * E2) * cxs;   // slots + four-step table
     p->smemB = ((size_t)p->CB * p->SB + (size_t)p->CB * p->L2) * cxs;   // slots + accumulators
     // row passes: buckets of B2 rows, nt2 teams, G ranks staged at once
     p->B2 = clamp_pow2(1024 / p->L1, 1, p->L2);
     p->NB = p->L2 / p->B2;
-    p->nt2 = std::max(1, 128 / TT1);
     p->S2 = slot_stride<T>(p->L1, E1, std::max(1, nbank<T>() / TT1));
-    auto slots = [&](int G) { return ((G * p->B2 + p->nt2 - 1) / p->nt2) * p->nt2; };
+    const int maxt = std::max(1, 256 / TT1);
+    auto bytes = [&](int G, int nt) {
+        const size_t slots = (size_t)((G * p->B2 + nt - 1) / nt) * nt;
+        return (slots * p->S2 + (size_t)nt * E1) * cxs;   // slots + four-step tables
+    };
+    // the largest group that fits, then the team count: the largest <= 256 threads
+    // dividing the group's B2 G row FFTs (no idle team), at least 64 threads
     int G = p->K;
-    while (G > 1 && (size_t)slots(G) * p->S2 * cxs > SMEM_BUDGET) --G;
-    if ((size_t)slots(G) * p->S2 * cxs > SMEM_BUDGET) return NUFFT_EUNSUPPORTED;
+    while (G > 1 && bytes(G, 1) > SMEM_BUDGET) --G;
+    int nt = 1;
+    for (;;) {
+        nt = 1;
+        for (int d = 1; d <= maxt; ++d)
+            if ((G * p->B2) % d == 0) nt = d;
+        if (nt * TT1 < 64) nt = std::min(maxt, std::max(nt, 64 / TT1));
+        if (bytes(G, nt) <= SMEM_BUDGET || G == 1) break;
+        --G;
+    }
+    if (bytes(G, nt) > SMEM_BUDGET) return NUFFT_EUNSUPPORTED;
     p->G = G;
-    p->smem2 = (size_t)slots(G) * p->S2 * cxs;
+    p->nt2 = nt;
+    p->smem2 = bytes(G, nt);
     if (p->smem1 > SMEM_BUDGET || p->smemB > SMEM_BUDGET) return NUFFT_EUNSUPPORTED;
     return NUFFT_OK;
 }
@@ -79,7 +94,8 @@ PassArgs<T> base_args(nufft_plan p) {
     a.perm = p->perm;
     a.bstart = p->bstart;
     a.dsorted = (const T *)p->dsorted;
-    a.tw = (const cx<T> *)p->tw4096;
+    a.twc = (const cx<T> *)p->twst2;
+    a.twr = (const cx<T> *)p->twst1;
     a.twhi = (const cx<T> *)p->twhi;
     a.twlo = (const cx<T> *)p->twlo;
     a.N = p->N;

@@ -19,6 +19,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 namespace nufft {
 
 template <typename T> struct CxT;
@@ -84,32 +86,50 @@ __device__ __forceinline__ cx<T> mul_w32(cx<T> a, int m) {
     return mk<T>(fma(c, a.x, -s * a.y), fma(c, a.y, s * a.x));
 }
 
-// In-place DFT of R points held in registers, natural order in and out,
-// radix-2 decimation in time, fully unrolled.
+__host__ __device__ constexpr int bitrev_c(int i, int bits) {
+    int r = 0;
+    for (int b = 0; b < bits; ++b) r |= ((i >> b) & 1) << (bits - 1 - b);
+    return r;
+}
+
+// f(std::integral_constant<int, i>) for i = 0..N-1, indices known to the compiler.
+template <typename F, int... I>
+__device__ __forceinline__ void static_for_impl(F &&f, std::integer_sequence<int, I...>) {
+    (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, typename F>
+__device__ __forceinline__ void static_for(F &&f) {
+    static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
+
+// In-place DFT of R points held in registers, natural order in and out:
+// radix-2 decimation in time on the bit-reversed renaming of the inputs, fully
+// unrolled, so at most R + 2 complex values are live.
 template <int R, bool INV, typename T>
 struct Dft {
     __device__ __forceinline__ static void run(cx<T> (&s)[R]) {
-        cx<T> ev[R / 2], od[R / 2];
+        constexpr int LG = R == 1 ? 0 : R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : R == 16 ? 4 : 5;
+        cx<T> t[R];
+        static_for<R>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            constexpr int j = bitrev_c(i, LG);
+            t[i] = s[j];
+        });
 #pragma unroll
-        for (int k = 0; k < R / 2; ++k) { ev[k] = s[2 * k]; od[k] = s[2 * k + 1]; }
-        Dft<R / 2, INV, T>::run(ev);
-        Dft<R / 2, INV, T>::run(od);
+        for (int h = 1; h < R; h *= 2) {
 #pragma unroll
-        for (int k = 0; k < R / 2; ++k) {
-            cx<T> o = mul_w32<INV, T>(od[k], k * (32 / R));
-            s[k] = cadd<T>(ev[k], o);
-            s[k + R / 2] = csub<T>(ev[k], o);
+            for (int g = 0; g < R; g += 2 * h) {
+#pragma unroll
+                for (int k = 0; k < h; ++k) {
+                    const cx<T> a = t[g + k];
+                    const cx<T> b = mul_w32<INV, T>(t[g + k + h], k * (16 / h));   // w_{2h}^k
+                    t[g + k] = cadd<T>(a, b);
+                    t[g + k + h] = csub<T>(a, b);
+                }
+            }
         }
-    }
-};
-template <bool INV, typename T>
-struct Dft<1, INV, T> { __device__ __forceinline__ static void run(cx<T> (&)[1]) {} };
-template <bool INV, typename T>
-struct Dft<2, INV, T> {
-    __device__ __forceinline__ static void run(cx<T> (&s)[2]) {
-        cx<T> a = s[0], b = s[1];
-        s[0] = cadd<T>(a, b);
-        s[1] = csub<T>(a, b);
+#pragma unroll
+        for (int i = 0; i < R; ++i) s[i] = t[i];
     }
 };
 
@@ -131,13 +151,21 @@ struct TeamFft {
     static constexpr int RL = R2 > 1 ? R2 : (R1 > 1 ? R1 : R0);  // last radix
     static constexpr int NSL = P / RL;                            // sub-transform size before it
 
-    // Output index of register e after run().
+    // Output index of register e after run(): tt + TT q(e).
     __device__ __forceinline__ static int out_index(int tt, int e) {
         const int b = e / RL, i = e % RL;
         return tt + TT * b + NSL * i;
     }
+    __host__ __device__ static constexpr int out_q(int e) { return e / RL + (E / RL) * (e % RL); }
 
-    template <int R, int NS>
+    // Stage twiddles w_{NS R}^{i j} live in one table per FFT length, stage s >= 1
+    // at offset TW_OFF_s, entry (i - 1) NS + j: lanes with consecutive j read
+    // consecutive entries.
+    static constexpr int TW_OFF1 = 0;
+    static constexpr int TW_OFF2 = (R1 - 1) * R0;
+    static constexpr int TW_SIZE = (R1 - 1) * R0 + (R2 > 1 ? (R2 - 1) * R0 * R1 : 0);
+
+    template <int R, int NS, int OFF>
     __device__ __forceinline__ static void stage(cx<T> (&a)[E], int tt, const cx<T>* __restrict__ tw) {
 #pragma unroll
         for (int b = 0; b < E / R; ++b) {
@@ -149,7 +177,7 @@ struct TeamFft {
                 const int j = v & (NS - 1);
 #pragma unroll
                 for (int i = 1; i < R; ++i) {
-                    const cx<T> w = __ldg(&tw[i * j * (4096 / (NS * R))]);
+                    const cx<T> w = __ldg(&tw[OFF + (i - 1) * NS + j]);
                     s[i] = INV ? cmulc<T>(s[i], w) : cmul<T>(s[i], w);
                 }
             }
@@ -183,16 +211,16 @@ struct TeamFft {
         __syncthreads();
     }
 
-    // tw: the table w_4096^m = exp(-2 pi i m / 4096), m < 4096.
+    // tw: this length's stage table (TW_SIZE entries, forward exponent).
     __device__ __forceinline__ static void run(cx<T> (&a)[E], int tt, cx<T>* sm,
                                                const cx<T>* __restrict__ tw) {
-        stage<R0, 1>(a, tt, tw);
+        stage<R0, 1, 0>(a, tt, tw);
         if constexpr (R1 > 1) {
             exchange<R0, 1, R1>(a, tt, sm);
-            stage<R1, R0>(a, tt, tw);
+            stage<R1, R0, TW_OFF1>(a, tt, tw);
             if constexpr (R2 > 1) {
                 exchange<R1, R0, R2>(a, tt, sm);
-                stage<R2, R0 * R1>(a, tt, tw);
+                stage<R2, R0 * R1, TW_OFF2>(a, tt, tw);
             }
         }
     }

@@ -9,7 +9,7 @@
 namespace nufft {
 
 constexpr int KMAX_ALL = 16;       // Table 2.1's double row caps the rank at 16
-constexpr int TW_BASE = 4096;      // in-pass twiddle table w_4096^m
+constexpr int TW_BASE = 4096;      // low level of the two-level four-step twiddle table
 constexpr int LOG2_L_MIN = 10;     // grids are at least 1024 points (two passes of 32)
 constexpr int LOG2_L_MAX = 22;     // two passes of at most 2048
 constexpr size_t SMEM_BUDGET = 200 * 1024;
@@ -53,7 +53,8 @@ struct nufft_plan_s {
     int32_t *tsorted = nullptr, *perm = nullptr, *bstart = nullptr, *t_j = nullptr;
     void *dsorted = nullptr;   // d in sorted order, plan precision
     double *d_j = nullptr;     // d in sample order, FP64 (unfused factors)
-    void *tw4096 = nullptr, *twhi = nullptr, *twlo = nullptr;
+    void *twst1 = nullptr, *twst2 = nullptr;   // stage twiddle tables for lengths L1, L2
+    void *twhi = nullptr, *twlo = nullptr;     // four-step twiddle, two levels
     void *Y = nullptr;         // K * L complex: intermediate between the passes
     void *fscr = nullptr;      // M complex: partial sums when G < K
     void *cstage = nullptr, *fstage = nullptr;   // exec_host staging

@@ -48,7 +48,8 @@ struct PassArgs {
     cx<T> *fscr;          // partial sums over rank groups (sorted order)
     const int32_t *tsorted, *perm, *bstart;
     const T *dsorted;
-    const cx<T> *tw, *twhi, *twlo;
+    const cx<T> *twc, *twr;     // stage twiddle tables: column FFTs (L2), row FFTs (L1)
+    const cx<T> *twhi, *twlo;   // four-step twiddle w_L^m = twhi[m >> 12] twlo[m & 4095]
     int64_t N, M, L;
     int L1, L2, lg1, lg2;
     int K, G, B2, C, lgC, S;
@@ -76,12 +77,21 @@ __device__ __forceinline__ void sincospi_t<float>(float x, float *s, float *c) {
 template <>
 __device__ __forceinline__ void sincospi_t<double>(double x, double *s, double *c) { sincospi(x, s, c); }
 
-// The four-step twiddle w_L^m, m = n2 k1 < L, from two tables.
+// w_L^m for 0 <= m < L from the two-level table (two roundings, ~1.5 ulp).
 template <typename T>
 __device__ __forceinline__ cx<T> twiddle_L(const PassArgs<T> &a, int m) {
     const cx<T> hi = __ldg(&a.twhi[m >> 12]);
     const cx<T> lo = __ldg(&a.twlo[m & 4095]);
     return cmul<T>(hi, lo);
+}
+
+// The four-step twiddle w_L^{n k} of an FFT output with index n = tt + TT q (q < E)
+// splits as w_L^{tt k} w_L^{TT q k}: a per-thread base times a per-(team, q)
+// table that the team fills in shared memory.  Entries: tab[q * ld].
+template <typename T, int E, int TT>
+__device__ __forceinline__ void fill_fourstep(const PassArgs<T> &a, int k, int tt, cx<T> *tab, int ld) {
+#pragma unroll
+    for (int q = tt; q < E; q += TT) tab[q * ld] = twiddle_L<T>(a, TT * q * k);
 }
 
 template <typename T>
@@ -91,8 +101,9 @@ __device__ __forceinline__ cx<T> *smem_base() {
 }
 
 // ---- pass 1: V-scale + column FFTs (length L2) + four-step twiddle ----------------
+// Shared memory: C exchange slots of S elements, then the four-step table [q][cc].
 template <typename T, int P2>
-__global__ void __launch_bounds__(256) k_pass1(const PassArgs<T> a) {
+__global__ void __launch_bounds__(256, 2) k_pass1(const PassArgs<T> a) {
     constexpr int E = e_of<T, P2>();
     using TF = TeamFft<T, P2, E, false>;
     constexpr int TT = TF::TT;
@@ -101,37 +112,68 @@ __global__ void __launch_bounds__(256) k_pass1(const PassArgs<T> a) {
     const int tt = threadIdx.x >> a.lgC;
     const int k1 = blockIdx.x * a.C + cc;
     const int r = blockIdx.y;
+    cx<T> *ftab = smem + a.C * a.S;
+    fill_fourstep<T, E, TT>(a, k1, tt, ftab + cc, a.C);
     cx<T> v[E];
     if (a.mode & MODE_PLAIN_IN) {
-        const cx<T> *W = a.in + (int64_t)r * a.L;
+        const cx<T> *W = a.in + (int64_t)r * a.L + k1 + a.L1 * tt;
 #pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = W[k1 + (int64_t)a.L1 * (tt + TT * m)];
+        for (int m = 0; m < E; ++m) v[m] = W[m * (a.L1 * TT)];
     } else {
-        const T invN = T(1) / T(a.N);
+        const int k0 = k1 + a.L1 * tt, kstride = a.L1 * TT;
+        const cx<T> *cb = a.in + k0;
 #pragma unroll
-        for (int m = 0; m < E; ++m) {
-            const int64_t k = k1 + (int64_t)a.L1 * (tt + TT * m);
-            cx<T> cv = mk<T>(0, 0);
-            if (k < a.N) {
-                cv = a.in[k];
+        for (int m = 0; m < E; ++m) v[m] = k0 + m * kstride < a.N ? cb[m * kstride] : mk<T>(0, 0);
+        // v_r(k) = T_r(z_k), z_k = (2k - N)/N, by the three-term recurrence run
+        // across the elements (element-innermost for independent FMAs)
+        const T invN = T(1) / T(a.N);
+        constexpr int H = E < 8 ? E : 8;
+#pragma unroll
+        for (int h0 = 0; h0 < E; h0 += H) {
+            T z2[H], ta[H], tb[H];
+#pragma unroll
+            for (int m = 0; m < H; ++m) {
+                const int k = k1 + a.L1 * (tt + TT * (h0 + m));
+                const T z = T(2 * k - a.N) * invN;
+                z2[m] = T(2) * z;
+                ta[m] = T(1);
+                tb[m] = z;
+            }
+            int q = 1;
+            for (; q + 1 < r; q += 2) {
+#pragma unroll
+                for (int m = 0; m < H; ++m) {
+                    ta[m] = fma(z2[m], tb[m], -ta[m]);
+                    tb[m] = fma(z2[m], ta[m], -tb[m]);
+                }
+            }
+            const bool odd = q < r;
+#pragma unroll
+            for (int m = 0; m < H; ++m) {
+                T tr = r == 0 ? T(1) : tb[m];
+                if (odd) tr = fma(z2[m], tb[m], -ta[m]);
+                cx<T> cv = v[h0 + m];
                 if (a.mode & MODE_DX) {   // (-2 pi i k) c_k
+                    const int k = k1 + a.L1 * (tt + TT * (h0 + m));
                     const T w = T(6.283185307179586476925286766559) * T(k);
                     cv = mk<T>(w * cv.y, -w * cv.x);
                 }
-                const T z = T(2 * k - a.N) * invN;
-                const T tr = cheb_T<T>(r, z);
-                cv = mk<T>(tr * cv.x, tr * cv.y);
+                v[h0 + m] = mul_ipow<T>(mk<T>(tr * cv.x, tr * cv.y), r);
             }
-            v[m] = mul_ipow<T>(cv, r);
         }
     }
-    TF::run(v, tt, smem + cc * a.S, a.tw);
-    cx<T> *Yr = a.Y + (int64_t)r * a.L;
+    TF::run(v, tt, smem + cc * a.S, a.twc);
+    __syncthreads();   // the four-step table is complete
+    const cx<T> base = twiddle_L<T>(a, tt * k1);
+    // output n2 = tt + TT q(e) goes to Y_r[n2][k1]
+    cx<T> *yb = a.Y + (int64_t)r * a.L + tt * a.L1 + k1;
+    const int ystride = TT * a.L1;
+    const cx<T> *fb = ftab + cc;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-        const int n2 = TF::out_index(tt, e);
-        const cx<T> w = twiddle_L<T>(a, n2 * k1);
-        Yr[(int64_t)n2 * a.L1 + k1] = cmul<T>(v[e], w);
+        const int q = TF::out_q(e);
+        const cx<T> w = cmul<T>(base, fb[q * a.C]);
+        yb[q * ystride] = cmul<T>(v[e], w);
     }
 }
 
@@ -160,7 +202,7 @@ __global__ void __launch_bounds__(256) k_pass2(const PassArgs<T> a, const Beta<T
             cx<T> v[E];
 #pragma unroll
             for (int m = 0; m < E; ++m) v[m] = act ? src[tt + TT * m] : mk<T>(0, 0);
-            TF::run(v, tt, sm, a.tw);
+            TF::run(v, tt, sm, a.twr);
 #pragma unroll
             for (int e = 0; e < E; ++e) sm[padi<E>(TF::out_index(tt, e))] = v[e];
         }
@@ -275,6 +317,7 @@ __global__ void __launch_bounds__(256) k_passA(const PassArgs<T> a, const Beta<T
                 if (r >= g0 && r < g0 + gc) smem[((r - g0) * a.B2 + row) * a.S + padi<E>(n1)] = acc[r];
         }
         __syncthreads();
+        cx<T> *ftab = smem + nslots * a.S + team * E;   // this team's four-step table
         for (int j0 = 0; j0 < njobs; j0 += nt) {
             const int job = j0 + team;
             const bool act = job < njobs;
@@ -284,16 +327,19 @@ __global__ void __launch_bounds__(256) k_passA(const PassArgs<T> a, const Beta<T
             cx<T> v[E];
 #pragma unroll
             for (int m = 0; m < E; ++m) v[m] = sm[padi<E>(tt + TT * m)];
+            fill_fourstep<T, E, TT>(a, n2, tt, ftab, 1);
             __syncthreads();
-            TF::run(v, tt, sm, a.tw);
+            TF::run(v, tt, sm, a.twr);
             if (act) {
+                const cx<T> base = twiddle_L<T>(a, n2 * tt);
                 cx<T> *dst = a.Y + ((int64_t)(g0 + rl) * a.L2 + n2) * a.L1;
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                     const int k1 = TF::out_index(tt, e);
-                    dst[k1] = cmulc<T>(v[e], twiddle_L<T>(a, n2 * k1));
+                    dst[k1] = cmulc<T>(v[e], cmul<T>(base, ftab[TF::out_q(e)]));
                 }
             }
+            __syncthreads();   // the next job refills ftab
         }
         __syncthreads();
     }
@@ -319,8 +365,8 @@ __global__ void __launch_bounds__(256) k_passB(const PassArgs<T> a) {
         const cx<T> *Yr = a.Y + (int64_t)r * a.L;
         cx<T> v[E];
 #pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = Yr[(int64_t)(tt + TT * m) * a.L1 + k1];
-        TF::run(v, tt, smem + cc * a.S, a.tw);
+        for (int m = 0; m < E; ++m) v[m] = Yr[(tt + TT * m) * a.L1 + k1];
+        TF::run(v, tt, smem + cc * a.S, a.twc);
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int64_t k = k1 + (int64_t)a.L1 * TF::out_index(tt, e);

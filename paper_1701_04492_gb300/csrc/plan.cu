@@ -207,12 +207,36 @@ int upload_table(void **dst, const std::vector<double> &re, const std::vector<do
     return NUFFT_OK;
 }
 
+// Stage twiddles of a length-P team FFT (the schedule of TeamFft in fft_team.cuh:
+// radices E, then min(E, P/E), then the rest): stage s >= 1 with radix R after NS
+// points holds w_{NS R}^{i j} at offset + (i - 1) NS + j.
+template <typename T>
+int stage_table(int P, void **dst, cudaStream_t s, int64_t *bytes) {
+    const int EM = sizeof(T) == 4 ? 32 : 16;
+    const int E = std::min(EM, P), TT = P / E;
+    const int R0 = E, R1 = TT > 1 ? std::min(E, TT) : 1, R2 = TT / R1;
+    std::vector<double> re, im;
+    auto add_stage = [&](int R, int NS) {
+        for (int i = 1; i < R; ++i)
+            for (int j = 0; j < NS; ++j) {
+                double c, sn;
+                twiddle((int64_t)NS * R, (int64_t)i * j, &c, &sn);
+                re.push_back(c);
+                im.push_back(sn);
+            }
+    };
+    if (R1 > 1) add_stage(R1, R0);
+    if (R2 > 1) add_stage(R2, R0 * R1);
+    if (re.empty()) { re.push_back(1.0); im.push_back(0.0); }
+    return upload_table<T>(dst, re, im, s, bytes);
+}
+
 template <typename T>
 int build_tables(nufft_plan p, cudaStream_t s) {
-    std::vector<double> re(TW_BASE), im(TW_BASE);
-    for (int m = 0; m < TW_BASE; ++m) twiddle(TW_BASE, m, &re[m], &im[m]);
-    int rc = upload_table<T>(&p->tw4096, re, im, s, &p->work_bytes);
+    int rc = stage_table<T>(p->L1, &p->twst1, s, &p->work_bytes);
     if (rc) return rc;
+    if ((rc = stage_table<T>(p->L2, &p->twst2, s, &p->work_bytes))) return rc;
+    std::vector<double> re, im;
     // four-step twiddle w_L^m = w_L^(4096 m_hi) * w_L^(m_lo), m = 4096 m_hi + m_lo
     const int64_t nlo = std::min<int64_t>(p->L, TW_BASE);
     const int64_t nhi = std::max<int64_t>(1, p->L / TW_BASE);
@@ -340,8 +364,8 @@ int plan_device(nufft_plan p, const double *x, cudaStream_t s) {
 
 void free_plan(nufft_plan p) {
     if (!p) return;
-    void *bufs[] = {p->tsorted, p->perm, p->bstart, p->t_j, p->dsorted, p->d_j, p->tw4096,
-                    p->twhi, p->twlo, p->Y, p->fscr, p->cstage, p->fstage, p->U, p->V, p->Xg};
+    void *bufs[] = {p->tsorted, p->perm, p->bstart, p->t_j, p->dsorted, p->d_j, p->twst1,
+                    p->twst2, p->twhi, p->twlo, p->Y, p->fscr, p->cstage, p->fstage, p->U, p->V, p->Xg};
     for (void *b : bufs) if (b) cudaFree(b);
     for (cudaEvent_t e : p->ev) if (e) cudaEventDestroy(e);
     delete p;
