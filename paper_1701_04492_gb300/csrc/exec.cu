@@ -53,14 +53,19 @@ int plan_geometry(nufft_plan p) {
     p->SB = slot_stride<T>(p->L2, E2, p->CB);
     p->smem1 = ((size_t)p->C1 * p->S1 + (size_t)p->C1 * E2) * cxs;   // slots + four-step table
     p->smemB = ((size_t)p->CB * p->SB + (size_t)p->CB * p->L2) * cxs;   // slots + accumulators
+    // rank splits of pass B: enough CTAs for about four per SM, at most one rank each
+    p->SBsplit = std::max(1, std::min(p->K, (4 * 152 + p->L1 / p->CB - 1) / (p->L1 / p->CB)));
     // row passes: buckets of B2 rows, nt2 teams, G ranks staged at once
     p->B2 = clamp_pow2(1024 / p->L1, 1, p->L2);
     p->NB = p->L2 / p->B2;
     p->S2 = slot_stride<T>(p->L1, E1, std::max(1, nbank<T>() / TT1));
     const int maxt = std::max(1, 256 / TT1);
+    p->chunkA = 512;
+    const size_t staging = (size_t)p->chunkA * (sizeof(int32_t) + sizeof(T)) + (size_t)p->chunkA * cxs;
     auto bytes = [&](int G, int nt) {
         const size_t slots = (size_t)((G * p->B2 + nt - 1) / nt) * nt;
-        return (slots * p->S2 + (size_t)nt * E1) * cxs;   // slots + four-step tables
+        // slots + four-step tables + pass A's staged samples
+        return (slots * p->S2 + (size_t)nt * E1) * cxs + staging;
     };
     // the largest group that fits, then the team count: the largest <= 256 threads
     // dividing the group's B2 G row FFTs (no idle team), at least 64 threads
@@ -97,6 +102,8 @@ PassArgs<T> base_args(nufft_plan p) {
     a.twc = (const cx<T> *)p->twst2;
     a.twr = (const cx<T> *)p->twst1;
     a.twhi = (const cx<T> *)p->twhi;
+    a.part = (cx<T> *)p->part;
+    a.counters = p->counters;
     a.twlo = (const cx<T> *)p->twlo;
     a.N = p->N;
     a.M = p->M;

@@ -41,6 +41,8 @@ struct nufft_plan_s {
     int nt2 = 1;           // teams per pass-2 / pass-A CTA
     int C1 = 1;            // columns per pass-1 CTA
     int CB = 1;            // columns per pass-B CTA
+    int SBsplit = 1;       // rank splits of pass B (CTAs per column block)
+    int chunkA = 512;      // samples staged per chunk in pass A
     size_t smem2 = 0;      // dynamic shared memory of pass 2 / A
     size_t smem1 = 0;      // of pass 1
     size_t smemB = 0;      // of pass B
@@ -59,6 +61,8 @@ struct nufft_plan_s {
     void *fscr = nullptr;      // M complex: partial sums when G < K
     void *cstage = nullptr, *fstage = nullptr;   // exec_host staging
     void *U = nullptr, *V = nullptr, *Xg = nullptr;   // unfused comparator
+    void *part = nullptr;      // pass B partial sums, SBsplit x L complex
+    int *counters = nullptr;   // pass B tickets, one per column block
     int64_t work_bytes = 0;
 
     // NUFFT_PLAN_TIMING: events around each launch of the last exec call

@@ -46,6 +46,8 @@ struct PassArgs {
     const cx<T> *g;       // dx cotangent
     T *gx;                // dx output
     cx<T> *fscr;          // partial sums over rank groups (sorted order)
+    cx<T> *part;          // pass B: per-split partial sums, SB x L
+    int *counters;        // pass B: per-column-block tickets (zero between calls)
     const int32_t *tsorted, *perm, *bstart;
     const T *dsorted;
     const cx<T> *twc, *twr;     // stage twiddle tables: column FFTs (L2), row FFTs (L1)
@@ -54,6 +56,7 @@ struct PassArgs {
     int L1, L2, lg1, lg2;
     int K, G, B2, C, lgC, S;
     int mode, accumulate;
+    int chunk;            // pass A: samples staged per chunk
     T inv_gamma;
 };
 
@@ -219,6 +222,7 @@ __global__ void __launch_bounds__(256) k_pass2(const PassArgs<T> a, const Beta<T
                     smem[(rl * a.B2 + row) * a.S + padi<E>(n1)];
             }
         } else {
+#pragma unroll 2
             for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
                 const int t = a.tsorted[i];
                 const int row = (t & L2m) - b * a.B2;
@@ -281,40 +285,65 @@ __global__ void __launch_bounds__(256) k_passA(const PassArgs<T> a, const Beta<T
         const int nslots = ((njobs + nt - 1) / nt) * nt;
         for (int idx = threadIdx.x; idx < nslots * a.S; idx += blockDim.x) smem[idx] = mk<T>(0, 0);
         __syncthreads();
-        for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-            const int t = a.tsorted[i];
-            if (i > i0 && a.tsorted[i - 1] == t) continue;   // not the first of its grid point
-            cx<T> acc[KM];
+        // the bucket's samples, staged chunk by chunk: t, d and the gathered g
+        int32_t *st_t = reinterpret_cast<int32_t *>(smem + nslots * a.S + nt * E);
+        T *st_d = reinterpret_cast<T *>(st_t + a.chunk);
+        cx<T> *st_g = reinterpret_cast<cx<T> *>(st_d + a.chunk);
+        for (int c0 = i0; c0 < i1; c0 += a.chunk) {
+            const int n = min(a.chunk, i1 - c0);
+            __syncthreads();   // the previous chunk is consumed
+#pragma unroll 4
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                st_t[i] = a.tsorted[c0 + i];
+                st_d[i] = a.dsorted[c0 + i];
+                st_g[i] = a.in[a.perm[c0 + i]];
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                const int t = st_t[i];
+                if (c0 + i > i0 && (i > 0 ? st_t[i - 1] : a.tsorted[c0 - 1]) == t) continue;
+                cx<T> acc[KM];
 #pragma unroll
-            for (int r = 0; r < KM; ++r) acc[r] = mk<T>(0, 0);
-            for (int i2 = i; i2 < i1 && a.tsorted[i2] == t; ++i2) {
-                const T d = a.dsorted[i2];
-                const T xi = d * a.inv_gamma;
-                T Tp[KM];
-                Tp[0] = T(1);
-                if (KM > 1) Tp[1] = xi;
+                for (int r = 0; r < KM; ++r) acc[r] = mk<T>(0, 0);
+                // every sample of this grid point, possibly running into the next chunk
+                for (int i2 = i; c0 + i2 < i1; ++i2) {
+                    T d;
+                    cx<T> gg;
+                    if (i2 < n) {
+                        if (st_t[i2] != t) break;
+                        d = st_d[i2];
+                        gg = st_g[i2];
+                    } else {
+                        if (a.tsorted[c0 + i2] != t) break;
+                        d = a.dsorted[c0 + i2];
+                        gg = a.in[a.perm[c0 + i2]];
+                    }
+                    const T xi = d * a.inv_gamma;
+                    T Tp[KM];
+                    Tp[0] = T(1);
+                    if (KM > 1) Tp[1] = xi;
 #pragma unroll
-                for (int q = 2; q < KM; ++q) Tp[q] = fma(T(2) * xi, Tp[q - 1], -Tp[q - 2]);
-                T sn, cs;
-                sincospi_t<T>(d, &sn, &cs);
-                const cx<T> gg = a.in[a.perm[i2]];
-                const cx<T> h = mk<T>(fma(gg.x, cs, -gg.y * sn), fma(gg.y, cs, gg.x * sn));  // g e^{+i pi d}
+                    for (int q = 2; q < KM; ++q) Tp[q] = fma(T(2) * xi, Tp[q - 1], -Tp[q - 2]);
+                    T sn, cs;
+                    sincospi_t<T>(d, &sn, &cs);
+                    const cx<T> h = mk<T>(fma(gg.x, cs, -gg.y * sn), fma(gg.y, cs, gg.x * sn));  // g e^{+i pi d}
 #pragma unroll
-                for (int r = 0; r < KM; ++r) {
-                    if (r >= g0 && r < g0 + gc) {
-                        T mu = T(0);
+                    for (int r = 0; r < KM; ++r) {
+                        if (r >= g0 && r < g0 + gc) {
+                            T mu = T(0);
 #pragma unroll
-                        for (int q = (r & 1); q < KM; q += 2) mu = fma(beta.b[r][q], Tp[q], mu);
-                        acc[r].x = fma(mu, h.x, acc[r].x);
-                        acc[r].y = fma(mu, h.y, acc[r].y);
+                            for (int q = (r & 1); q < KM; q += 2) mu = fma(beta.b[r][q], Tp[q], mu);
+                            acc[r].x = fma(mu, h.x, acc[r].x);
+                            acc[r].y = fma(mu, h.y, acc[r].y);
+                        }
                     }
                 }
-            }
-            const int row = (t & L2m) - b * a.B2;
-            const int n1 = t >> a.lg2;
+                const int row = (t & L2m) - b * a.B2;
+                const int n1 = t >> a.lg2;
 #pragma unroll
-            for (int r = 0; r < KM; ++r)
-                if (r >= g0 && r < g0 + gc) smem[((r - g0) * a.B2 + row) * a.S + padi<E>(n1)] = acc[r];
+                for (int r = 0; r < KM; ++r)
+                    if (r >= g0 && r < g0 + gc) smem[((r - g0) * a.B2 + row) * a.S + padi<E>(n1)] = acc[r];
+            }
         }
         __syncthreads();
         cx<T> *ftab = smem + nslots * a.S + team * E;   // this team's four-step table
@@ -346,8 +375,11 @@ __global__ void __launch_bounds__(256) k_passA(const PassArgs<T> a, const Beta<T
 }
 
 // ---- pass B (adjoint): inverse column FFTs, V-scale and rank-sum -----------------
-// The rank-sum accumulators live in shared memory after the C exchange slots, at
-// ((e TT + tt) C + cc): consecutive lanes hit consecutive elements.
+// Grid (L1 / C, SB): CTA (x, s) sums the ranks r = s, s + SB, s + 2 SB, ... of its C
+// columns in shared memory, at ((e TT + tt) C + cc).  With SB > 1 each CTA stores
+// its partial sum to part[s], and the last CTA of the column block (an atomic
+// ticket, no waiting) adds the SB partials in the fixed order s = 0..SB-1, so the
+// result does not depend on which CTA finishes last.
 template <typename T, int P2>
 __global__ void __launch_bounds__(256) k_passB(const PassArgs<T> a) {
     constexpr int E = e_of<T, P2>();
@@ -357,32 +389,84 @@ __global__ void __launch_bounds__(256) k_passB(const PassArgs<T> a) {
     const int cc = threadIdx.x & (a.C - 1);
     const int tt = threadIdx.x >> a.lgC;
     const int k1 = blockIdx.x * a.C + cc;
+    const int s = blockIdx.y, SB = gridDim.y;
     const T invN = T(1) / T(a.N);
     cx<T> *acc = smem + a.C * a.S;
 #pragma unroll
     for (int e = 0; e < E; ++e) acc[(e * TT + tt) * a.C + cc] = mk<T>(0, 0);
-    for (int r = 0; r < a.K; ++r) {
-        const cx<T> *Yr = a.Y + (int64_t)r * a.L;
+    for (int r = s; r < a.K; r += SB) {
+        const cx<T> *Yb = a.Y + (int64_t)r * a.L + tt * a.L1 + k1;
         cx<T> v[E];
 #pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = Yr[(tt + TT * m) * a.L1 + k1];
+        for (int m = 0; m < E; ++m) v[m] = Yb[m * (TT * a.L1)];
         TF::run(v, tt, smem + cc * a.S, a.twc);
+        // (-i)^r T_r(z_k) v, the recurrence run element-innermost in chunks of H
+        constexpr int H = E < 8 ? E : 8;
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const int64_t k = k1 + (int64_t)a.L1 * TF::out_index(tt, e);
-            const T z = T(2 * k - a.N) * invN;
-            const T tr = cheb_T<T>(r, z);
-            const cx<T> y = mul_ipow<T>(v[e], -r);
-            cx<T> &s = acc[(e * TT + tt) * a.C + cc];
-            s.x = fma(tr, y.x, s.x);
-            s.y = fma(tr, y.y, s.y);
+        for (int h0 = 0; h0 < E; h0 += H) {
+            T z2[H], ta[H], tb[H];
+#pragma unroll
+            for (int m = 0; m < H; ++m) {
+                const int k = k1 + a.L1 * TF::out_index(tt, h0 + m);
+                const T z = T(2 * k - a.N) * invN;
+                z2[m] = T(2) * z;
+                ta[m] = T(1);
+                tb[m] = z;
+            }
+            int q = 1;
+            for (; q + 1 < r; q += 2) {
+#pragma unroll
+                for (int m = 0; m < H; ++m) {
+                    ta[m] = fma(z2[m], tb[m], -ta[m]);
+                    tb[m] = fma(z2[m], ta[m], -tb[m]);
+                }
+            }
+            const bool odd = q < r;
+#pragma unroll
+            for (int m = 0; m < H; ++m) {
+                T tr = r == 0 ? T(1) : tb[m];
+                if (odd) tr = fma(z2[m], tb[m], -ta[m]);
+                const cx<T> y = mul_ipow<T>(v[h0 + m], -r);
+                cx<T> &sacc = acc[((h0 + m) * TT + tt) * a.C + cc];
+                sacc.x = fma(tr, y.x, sacc.x);
+                sacc.y = fma(tr, y.y, sacc.y);
+            }
         }
     }
+    if (SB == 1) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int k = k1 + a.L1 * TF::out_index(tt, e);
+            if (k < a.N) a.out[k] = acc[(e * TT + tt) * a.C + cc];
+        }
+        return;
+    }
+    // partial sums -> part[s]; the last CTA of this column block reduces them
+    cx<T> *mine = a.part + (int64_t)s * a.L;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-        const int64_t k = k1 + (int64_t)a.L1 * TF::out_index(tt, e);
-        if (k < a.N) a.out[k] = acc[(e * TT + tt) * a.C + cc];
+        const int k = k1 + a.L1 * TF::out_index(tt, e);
+        mine[k] = acc[(e * TT + tt) * a.C + cc];
     }
+    __threadfence();
+    __syncthreads();
+    __shared__ int ticket;
+    if (threadIdx.x == 0) ticket = atomicAdd(&a.counters[blockIdx.x], 1);
+    __syncthreads();
+    if (ticket != SB - 1) return;
+    __threadfence();
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int k = k1 + a.L1 * TF::out_index(tt, e);
+        cx<T> t = mk<T>(0, 0);
+        for (int s2 = 0; s2 < SB; ++s2) {
+            const cx<T> pv = __ldcg(&a.part[(int64_t)s2 * a.L + k]);
+            t.x += pv.x;
+            t.y += pv.y;
+        }
+        if (k < a.N) a.out[k] = t;
+    }
+    if (threadIdx.x == 0) a.counters[blockIdx.x] = 0;   // ready for the next call
 }
 
 // ---- launchers ------------------------------------------------------------------
@@ -436,7 +520,7 @@ int launch_cols(nufft_plan p, const PassArgs<T> &a0, bool adjoint, cudaStream_t 
         if (adjoint) {
             auto kern = k_passB<T, P>;
             if (int rc = set_smem(kern, smem, p->device, done_b)) return rc;
-            kern<<<dim3(p->L1 / a.C), block, smem, s>>>(a);
+            kern<<<dim3(p->L1 / a.C, p->SBsplit), block, smem, s>>>(a);
         } else {
             auto kern = k_pass1<T, P>;
             if (int rc = set_smem(kern, smem, p->device, done_1)) return rc;

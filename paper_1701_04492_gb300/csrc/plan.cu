@@ -354,6 +354,12 @@ int plan_device(nufft_plan p, const double *x, cudaStream_t s) {
     NUFFT_CUDA_TRY(cudaMalloc(&p->fscr, Mi * cxs));
     NUFFT_CUDA_TRY(cudaMalloc(&p->cstage, (size_t)p->N * cxs));
     NUFFT_CUDA_TRY(cudaMalloc(&p->fstage, Mi * cxs));
+    if (p->SBsplit > 1) {
+        NUFFT_CUDA_TRY(cudaMalloc(&p->part, (size_t)p->SBsplit * p->L * cxs));
+        NUFFT_CUDA_TRY(cudaMalloc(&p->counters, (size_t)(p->L1 / p->CB) * sizeof(int)));
+        NUFFT_CUDA_TRY(cudaMemsetAsync(p->counters, 0, (size_t)(p->L1 / p->CB) * sizeof(int), s));
+        p->work_bytes += (int64_t)((size_t)p->SBsplit * p->L * cxs + (p->L1 / p->CB) * sizeof(int));
+    }
     p->work_bytes += (int64_t)(((size_t)p->K * p->L + 2 * Mi + p->N) * cxs);
     if (p->flags & NUFFT_PLAN_UNFUSED) {
         if ((rc = plan_unfused_factors<T>(p, s))) return rc;
@@ -365,7 +371,8 @@ int plan_device(nufft_plan p, const double *x, cudaStream_t s) {
 void free_plan(nufft_plan p) {
     if (!p) return;
     void *bufs[] = {p->tsorted, p->perm, p->bstart, p->t_j, p->dsorted, p->d_j, p->twst1,
-                    p->twst2, p->twhi, p->twlo, p->Y, p->fscr, p->cstage, p->fstage, p->U, p->V, p->Xg};
+                    p->twst2, p->twhi, p->twlo, p->Y, p->fscr, p->cstage, p->fstage, p->U, p->V, p->Xg,
+                    p->part, p->counters};
     for (void *b : bufs) if (b) cudaFree(b);
     for (cudaEvent_t e : p->ev) if (e) cudaEventDestroy(e);
     delete p;
