@@ -192,8 +192,9 @@ __global__ void __launch_bounds__(256) k_pass2(const PassArgs<T> a, const Beta<T
     const int b = blockIdx.x;
     const int i0 = a.bstart[b], i1 = a.bstart[b + 1];
     const int L2m = a.L2 - 1;
-    for (int g0 = 0; g0 < a.K; g0 += a.G) {
-        const int gc = min(a.G, a.K - g0);
+    const int Gs = a.G > 0 ? a.G : 1;   // never a zero stride
+    for (int g0 = 0; g0 < a.K; g0 += Gs) {
+        const int gc = min(Gs, a.K - g0);
         const int njobs = gc * a.B2;
         for (int j0 = 0; j0 < njobs; j0 += nt) {
             const int job = j0 + team;
@@ -279,8 +280,9 @@ __global__ void __launch_bounds__(256) k_passA(const PassArgs<T> a, const Beta<T
     const int b = blockIdx.x;
     const int i0 = a.bstart[b], i1 = a.bstart[b + 1];
     const int L2m = a.L2 - 1;
-    for (int g0 = 0; g0 < a.K; g0 += a.G) {
-        const int gc = min(a.G, a.K - g0);
+    const int Gs = a.G > 0 ? a.G : 1;   // never a zero stride
+    for (int g0 = 0; g0 < a.K; g0 += Gs) {
+        const int gc = min(Gs, a.K - g0);
         const int njobs = gc * a.B2;
         const int nslots = ((njobs + nt - 1) / nt) * nt;
         for (int idx = threadIdx.x; idx < nslots * a.S; idx += blockDim.x) smem[idx] = mk<T>(0, 0);
@@ -289,8 +291,9 @@ __global__ void __launch_bounds__(256) k_passA(const PassArgs<T> a, const Beta<T
         int32_t *st_t = reinterpret_cast<int32_t *>(smem + nslots * a.S + nt * E);
         T *st_d = reinterpret_cast<T *>(st_t + a.chunk);
         cx<T> *st_g = reinterpret_cast<cx<T> *>(st_d + a.chunk);
-        for (int c0 = i0; c0 < i1; c0 += a.chunk) {
-            const int n = min(a.chunk, i1 - c0);
+        const int chunk = a.chunk > 0 ? a.chunk : 1;   // never a zero stride
+        for (int c0 = i0; c0 < i1; c0 += chunk) {
+            const int n = min(chunk, i1 - c0);
             __syncthreads();   // the previous chunk is consumed
 #pragma unroll 4
             for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -540,6 +543,8 @@ int launch_rows(nufft_plan p, const PassArgs<T> &a0, bool adjoint, cudaStream_t 
         constexpr int TT = P / e_of<T, P>();
         PassArgs<T> a = a0;
         a.S = p->S2;
+        a.chunk = p->chunkA;
+        if (a.chunk <= 0) return NUFFT_EINVAL;
         const dim3 block(p->nt2 * TT);
         static int done_a[64] = {}, done_2[64] = {};
         if (adjoint) {
