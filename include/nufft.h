@@ -51,7 +51,8 @@ enum nufft_status {
     NUFFT_ENOMEM = -2,        /* device or host allocation failed */
     NUFFT_ECUDA = -3,         /* a CUDA call failed (no device, launch error, ...) */
     NUFFT_EUNSUPPORTED = -4,  /* size beyond what this build handles */
-    NUFFT_ESTATE = -5         /* call needs a plan option that was not set */
+    NUFFT_ESTATE = -5,        /* call needs a plan option that was not set */
+    NUFFT_ETIMEOUT = -6       /* a bounded device-side wait gave up (see nufft2_check) */
 };
 
 /* Plan flags. */
@@ -151,6 +152,12 @@ int nufft2_exec_unfused(nufft_plan p, const void *c_dev, void *f_dev, void *stre
  * NUFFT_ESTATE).  Writes min(cap, count) values to ms_out and the count to
  * *count.  Waits for the last event. */
 int nufft_kernel_times(nufft_plan p, float *ms_out, int cap, int *count);
+
+/* Synchronise `stream` and report whether any exec call on this plan since the
+ * last check had a device-side wait give up (a bulk copy that did not complete
+ * within its time limit): NUFFT_ETIMEOUT, and the results of those calls are
+ * invalid; else NUFFT_OK.  Clears the condition. */
+int nufft2_check(nufft_plan p, void *stream);
 
 /* Human-readable name of a status code. */
 const char *nufft_strerror(int code);

@@ -16,7 +16,7 @@ NUFFT_F32, NUFFT_F64 = 0, 1
 NUFFT_PLAN_UNFUSED = 1
 NUFFT_PLAN_TIMING = 2
 STATUS = {0: "NUFFT_OK", -1: "NUFFT_EINVAL", -2: "NUFFT_ENOMEM", -3: "NUFFT_ECUDA",
-          -4: "NUFFT_EUNSUPPORTED", -5: "NUFFT_ESTATE"}
+          -4: "NUFFT_EUNSUPPORTED", -5: "NUFFT_ESTATE", -6: "NUFFT_ETIMEOUT"}
 
 # name -> (restype, argtypes), mirroring include/nufft.h
 _vp, _i64, _i32, _dbl, _u32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_uint
@@ -33,6 +33,7 @@ SIGNATURES = {
     "nufft2_exec_host": (_i32, [_vp, _vp, _vp, _vp]),
     "nufft2_exec_unfused": (_i32, [_vp, _vp, _vp, _vp]),
     "nufft_kernel_times": (_i32, [_vp, ctypes.POINTER(ctypes.c_float), _i32, ctypes.POINTER(_i32)]),
+    "nufft2_check": (_i32, [_vp, _vp]),
     "nufft_strerror": (ctypes.c_char_p, [_i32]),
 }
 

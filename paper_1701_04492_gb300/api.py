@@ -109,6 +109,11 @@ class Plan:
         import numpy as np
         return t, d, np.array(alpha[:], dtype=np.float64).reshape(self.K, self.K)
 
+    def check(self):
+        """Synchronise and raise NufftError(NUFFT_ETIMEOUT) if a device-side wait gave up."""
+        with torch.cuda.device(self.device):
+            check(_lib.load().nufft2_check(self._h, _stream(self.device)), "nufft2_check")
+
     def kernel_times(self):
         """Device milliseconds of each kernel of the last exec call (plan built with timing=True)."""
         buf = (ctypes.c_float * 8)()

@@ -31,9 +31,14 @@ template <typename T>
 int slot_stride(int P, int E, int q) {
     const int base = P + P / E;
     const int nb = nbank<T>();
-    if (q <= 1) return base;
-    const int target = nb / std::min(q, nb);
-    return base + (((target - base % nb) % nb) + nb) % nb;
+    int s = base;
+    if (q > 1) {
+        const int target = nb / std::min(q, nb);
+        s = base + (((target - base % nb) % nb) + nb) % nb;
+    }
+    // slots are bulk-copy destinations: keep every slot 16-byte aligned
+    while ((s * 2 * (int)sizeof(T)) % 16 != 0) ++s;
+    return s;
 }
 
 int clamp_pow2(int v, int lo, int hi) { return std::max(lo, std::min(hi, v)); }
@@ -62,10 +67,14 @@ int plan_geometry(nufft_plan p) {
     const int maxt = std::max(1, 256 / TT1);
     p->chunkA = 512;
     const size_t staging = (size_t)p->chunkA * (sizeof(int32_t) + sizeof(T)) + (size_t)p->chunkA * cxs;
-    auto bytes = [&](int G, int nt) {
+    // slots + four-step tables + pass A's staged samples, then (16-byte aligned)
+    // pass 2's slot mbarriers
+    auto body = [&](int G, int nt) {
         const size_t slots = (size_t)((G * p->B2 + nt - 1) / nt) * nt;
-        // slots + four-step tables + pass A's staged samples
-        return (slots * p->S2 + (size_t)nt * E1) * cxs + staging;
+        return ((slots * p->S2 + (size_t)nt * E1) * cxs + staging + 15) / 16 * 16;
+    };
+    auto bytes = [&](int G, int nt) {
+        return body(G, nt) + (size_t)((G * p->B2 + nt - 1) / nt) * nt * sizeof(uint64_t);
     };
     // the largest group that fits, then the team count: the largest <= 256 threads
     // dividing the group's B2 G row FFTs (no idle team), at least 64 threads
@@ -83,6 +92,7 @@ int plan_geometry(nufft_plan p) {
     if (bytes(G, nt) > SMEM_BUDGET) return NUFFT_EUNSUPPORTED;
     p->G = G;
     p->nt2 = nt;
+    p->mbar_off2 = body(G, nt);
     p->smem2 = bytes(G, nt);
     if (p->smem1 > SMEM_BUDGET || p->smemB > SMEM_BUDGET) return NUFFT_EUNSUPPORTED;
     return NUFFT_OK;
@@ -104,6 +114,7 @@ PassArgs<T> base_args(nufft_plan p) {
     a.twhi = (const cx<T> *)p->twhi;
     a.part = (cx<T> *)p->part;
     a.counters = p->counters;
+    a.err = p->err;
     a.twlo = (const cx<T> *)p->twlo;
     a.N = p->N;
     a.M = p->M;

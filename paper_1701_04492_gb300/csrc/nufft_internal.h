@@ -43,6 +43,7 @@ struct nufft_plan_s {
     int CB = 1;            // columns per pass-B CTA
     int SBsplit = 1;       // rank splits of pass B (CTAs per column block)
     int chunkA = 512;      // samples staged per chunk in pass A
+    size_t mbar_off2 = 0;  // byte offset of pass 2's mbarriers in its shared memory
     size_t smem2 = 0;      // dynamic shared memory of pass 2 / A
     size_t smem1 = 0;      // of pass 1
     size_t smemB = 0;      // of pass B
@@ -63,6 +64,7 @@ struct nufft_plan_s {
     void *U = nullptr, *V = nullptr, *Xg = nullptr;   // unfused comparator
     void *part = nullptr;      // pass B partial sums, SBsplit x L complex
     int *counters = nullptr;   // pass B tickets, one per column block
+    int *err = nullptr;        // device error word: bounded waits that timed out
     int64_t work_bytes = 0;
 
     // NUFFT_PLAN_TIMING: events around each launch of the last exec call

@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "async_copy.cuh"
 #include "fft_team.cuh"
 #include "nufft_internal.h"
 
@@ -57,6 +58,8 @@ struct PassArgs {
     int K, G, B2, C, lgC, S;
     int mode, accumulate;
     int chunk;            // pass A: samples staged per chunk
+    int mbar_off;         // pass 2: byte offset of the slot mbarriers in shared memory
+    int *err;             // device error word (bounded waits that timed out)
     T inv_gamma;
 };
 
@@ -193,19 +196,38 @@ __global__ void __launch_bounds__(256) k_pass2(const PassArgs<T> a, const Beta<T
     const int i0 = a.bstart[b], i1 = a.bstart[b + 1];
     const int L2m = a.L2 - 1;
     const int Gs = a.G > 0 ? a.G : 1;   // never a zero stride
-    for (int g0 = 0; g0 < a.K; g0 += Gs) {
+    // one mbarrier per slot: the rows of a rank group arrive by bulk copy (TMA)
+    // while earlier rows are transformed
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(smem) + a.mbar_off);
+    __shared__ int cta_failed;
+    if (threadIdx.x == 0) {
+        cta_failed = 0;
+        const int nsl = ((Gs * a.B2 + nt - 1) / nt) * nt;
+        for (int q = 0; q < nsl; ++q) mbar_init(&mbar[q], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    constexpr uint32_t ROW_BYTES = P1 * sizeof(cx<T>);
+    int gi = 0;
+    for (int g0 = 0; g0 < a.K; g0 += Gs, ++gi) {
         const int gc = min(Gs, a.K - g0);
         const int njobs = gc * a.B2;
+        if (threadIdx.x == 0) {
+            for (int q = 0; q < njobs; ++q) {
+                const cx<T> *src = a.Y + ((int64_t)(g0 + q / a.B2) * a.L2 + b * a.B2 + q % a.B2) * a.L1;
+                mbar_arrive_expect_tx(&mbar[q], ROW_BYTES);
+                bulk_copy_g2s(smem + q * a.S, src, ROW_BYTES, &mbar[q]);
+            }
+        }
         for (int j0 = 0; j0 < njobs; j0 += nt) {
             const int job = j0 + team;
             const bool act = job < njobs;
-            const int rl = act ? job / a.B2 : 0, row = act ? job % a.B2 : 0;
-            const int n2 = b * a.B2 + row;
-            const cx<T> *src = a.Y + ((int64_t)(g0 + rl) * a.L2 + n2) * a.L1;
             cx<T> *sm = smem + job * a.S;
             cx<T> v[E];
+            if (act) mbar_wait_bounded(&mbar[job], gi & 1, a.err, &cta_failed);
 #pragma unroll
-            for (int m = 0; m < E; ++m) v[m] = act ? src[tt + TT * m] : mk<T>(0, 0);
+            for (int m = 0; m < E; ++m) v[m] = act ? sm[tt + TT * m] : mk<T>(0, 0);   // row as copied
+            __syncthreads();   // the row is read before the transform reuses its slot
             TF::run(v, tt, sm, a.twr);
 #pragma unroll
             for (int e = 0; e < E; ++e) sm[padi<E>(TF::out_index(tt, e))] = v[e];
@@ -264,6 +286,7 @@ __global__ void __launch_bounds__(256) k_pass2(const PassArgs<T> a, const Beta<T
                 }
             }
         }
+        fence_proxy_async_smem();   // these slot accesses precede the next group's copies
         __syncthreads();
     }
 }
@@ -544,6 +567,7 @@ int launch_rows(nufft_plan p, const PassArgs<T> &a0, bool adjoint, cudaStream_t 
         PassArgs<T> a = a0;
         a.S = p->S2;
         a.chunk = p->chunkA;
+        a.mbar_off = (int)p->mbar_off2;
         if (a.chunk <= 0) return NUFFT_EINVAL;
         const dim3 block(p->nt2 * TT);
         static int done_a[64] = {}, done_2[64] = {};

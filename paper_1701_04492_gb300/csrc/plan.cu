@@ -354,6 +354,8 @@ int plan_device(nufft_plan p, const double *x, cudaStream_t s) {
     NUFFT_CUDA_TRY(cudaMalloc(&p->fscr, Mi * cxs));
     NUFFT_CUDA_TRY(cudaMalloc(&p->cstage, (size_t)p->N * cxs));
     NUFFT_CUDA_TRY(cudaMalloc(&p->fstage, Mi * cxs));
+    NUFFT_CUDA_TRY(cudaMalloc(&p->err, sizeof(int)));
+    NUFFT_CUDA_TRY(cudaMemsetAsync(p->err, 0, sizeof(int), s));
     if (p->SBsplit > 1) {
         NUFFT_CUDA_TRY(cudaMalloc(&p->part, (size_t)p->SBsplit * p->L * cxs));
         NUFFT_CUDA_TRY(cudaMalloc(&p->counters, (size_t)(p->L1 / p->CB) * sizeof(int)));
@@ -372,7 +374,7 @@ void free_plan(nufft_plan p) {
     if (!p) return;
     void *bufs[] = {p->tsorted, p->perm, p->bstart, p->t_j, p->dsorted, p->d_j, p->twst1,
                     p->twst2, p->twhi, p->twlo, p->Y, p->fscr, p->cstage, p->fstage, p->U, p->V, p->Xg,
-                    p->part, p->counters};
+                    p->part, p->counters, p->err};
     for (void *b : bufs) if (b) cudaFree(b);
     for (cudaEvent_t e : p->ev) if (e) cudaEventDestroy(e);
     delete p;
@@ -453,6 +455,20 @@ extern "C" int nufft_kernel_times(nufft_plan p, float *ms_out, int cap, int *cou
     return NUFFT_OK;
 }
 
+extern "C" int nufft2_check(nufft_plan p, void *stream) {
+    if (!p) return NUFFT_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    int h = 0;
+    NUFFT_CUDA_TRY(cudaMemcpyAsync(&h, p->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    NUFFT_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h) {
+        NUFFT_CUDA_TRY(cudaMemsetAsync(p->err, 0, sizeof(int), s));
+        NUFFT_CUDA_TRY(cudaStreamSynchronize(s));
+        return NUFFT_ETIMEOUT;
+    }
+    return NUFFT_OK;
+}
+
 extern "C" int nufft_destroy(nufft_plan p) {
     nufft::free_plan(p);
     return NUFFT_OK;
@@ -466,6 +482,7 @@ extern "C" const char *nufft_strerror(int code) {
         case NUFFT_ECUDA: return "CUDA error";
         case NUFFT_EUNSUPPORTED: return "unsupported size";
         case NUFFT_ESTATE: return "plan lacks the option this call needs";
+        case NUFFT_ETIMEOUT: return "a device-side wait timed out; results of the affected calls are invalid";
         default: return "unknown status";
     }
 }
