@@ -153,6 +153,26 @@ int nufft2_exec_unfused(nufft_plan p, const void *c_dev, void *f_dev, void *stre
  * *count.  Waits for the last event. */
 int nufft_kernel_times(nufft_plan p, float *ms_out, int cap, int *count);
 
+/* The forward transform without a plan and without any device allocation, for
+ * callers that cannot call cudaMalloc (code running inside another allocator's
+ * callbacks, plug-ins whose host forbids device allocation, latency-critical
+ * paths).  The paper has no counterpart: it is a packaging of eq. (2.11) (FP32
+ * exec, the same rank rule and factors as nufft2_plan + nufft2_exec) that keeps
+ * every intermediate in one fixed device array compiled into the library
+ * (about 17 MiB, held by each GPU that loads the library until exit).
+ *   N, M   1 <= N <= 65536, 0 <= M <= 65536; larger sizes return
+ *          NUFFT_EUNSUPPORTED (they do not fit the fixed array).
+ *   x_dev  M doubles (device), finite, as for nufft2_plan.
+ *   eps    working accuracy, 0 < eps < 1.
+ *   c_dev  N complex64 (device).   f_dev  M complex64 (device, written).
+ * The first call on a device looks up that array's device address; make it before
+ * any stream capture.  Every call uses the same array, so calls whose GPU work
+ * overlaps (other streams, other threads) race; serialise them.  Synchronises
+ * `stream` once (to read gamma).  Errors: NUFFT_EINVAL, NUFFT_EUNSUPPORTED,
+ * NUFFT_ECUDA. */
+int nufft2_exec_noalloc(int64_t N, int64_t M, const double *x_dev, double eps, const void *c_dev,
+                        void *f_dev, void *stream);
+
 /* Synchronise `stream` and report whether any exec call on this plan since the
  * last check had a device-side wait give up (a bulk copy that did not complete
  * within its time limit): NUFFT_ETIMEOUT, and the results of those calls are

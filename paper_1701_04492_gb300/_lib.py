@@ -34,6 +34,7 @@ SIGNATURES = {
     "nufft2_exec_unfused": (_i32, [_vp, _vp, _vp, _vp]),
     "nufft_kernel_times": (_i32, [_vp, ctypes.POINTER(ctypes.c_float), _i32, ctypes.POINTER(_i32)]),
     "nufft2_check": (_i32, [_vp, _vp]),
+    "nufft2_exec_noalloc": (_i32, [_i64, _i64, _vp, _dbl, _vp, _vp, _vp]),
     "nufft_strerror": (ctypes.c_char_p, [_i32]),
 }
 
