@@ -53,11 +53,12 @@ int plan_geometry(nufft_plan p) {
     const size_t cxs = 2 * sizeof(T);
     // column passes: C columns per CTA, columns fastest across the lanes
     p->C1 = clamp_pow2(256 / TT2, 1, p->L1);
-    p->CB = clamp_pow2(128 / TT2, 1, p->L1);
+    p->CB = clamp_pow2(128 / TT2, 1, p->L1);   // one 32 KiB tile of the adjoint intermediate
     p->S1 = slot_stride<T>(p->L2, E2, p->C1);
     p->SB = slot_stride<T>(p->L2, E2, p->CB);
     p->smem1 = ((size_t)p->C1 * p->S1 + (size_t)p->C1 * E2) * cxs;   // slots + four-step table
-    p->smemB = ((size_t)p->CB * p->SB + (size_t)p->CB * p->L2) * cxs;   // slots + accumulators
+    // two tile buffers (copy landing zone and exchange slots), then two mbarriers
+    p->smemB = ((2 * (size_t)p->CB * p->SB * cxs + 15) / 16) * 16 + 2 * sizeof(uint64_t);
     // rank splits of pass B: enough CTAs for about four per SM, at most one rank each
     p->SBsplit = std::max(1, std::min(p->K, (4 * 152 + p->L1 / p->CB - 1) / (p->L1 / p->CB)));
     // row passes: buckets of B2 rows, nt2 teams, G ranks staged at once

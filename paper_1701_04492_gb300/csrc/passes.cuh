@@ -59,6 +59,7 @@ struct PassArgs {
     int mode, accumulate;
     int chunk;            // pass A: samples staged per chunk
     int mbar_off;         // pass 2: byte offset of the slot mbarriers in shared memory
+    int CQ, lgCQ;         // pass A/B: columns of pass B's tiles (the adjoint intermediate's tiling)
     int *err;             // device error word (bounded waits that timed out)
     T inv_gamma;
 };
@@ -386,12 +387,15 @@ __global__ void __launch_bounds__(256) k_passA(const PassArgs<T> a, const Beta<T
             __syncthreads();
             TF::run(v, tt, sm, a.twr);
             if (act) {
+                // column-tiled layout for pass B: Y'_r[k1 / CQ][n2][k1 % CQ], so each
+                // CQ-column tile of a rank is one contiguous block
                 const cx<T> base = twiddle_L<T>(a, n2 * tt);
-                cx<T> *dst = a.Y + ((int64_t)(g0 + rl) * a.L2 + n2) * a.L1;
+                cx<T> *dst = a.Y + (int64_t)(g0 + rl) * a.L + n2 * a.CQ;
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                     const int k1 = TF::out_index(tt, e);
-                    dst[k1] = cmulc<T>(v[e], cmul<T>(base, ftab[TF::out_q(e)]));
+                    dst[(k1 >> a.lgCQ) * (a.L2 << a.lgCQ) + (k1 & (a.CQ - 1))] =
+                        cmulc<T>(v[e], cmul<T>(base, ftab[TF::out_q(e)]));
                 }
             }
             __syncthreads();   // the next job refills ftab
@@ -402,12 +406,15 @@ __global__ void __launch_bounds__(256) k_passA(const PassArgs<T> a, const Beta<T
 
 // ---- pass B (adjoint): inverse column FFTs, V-scale and rank-sum -----------------
 // Grid (L1 / C, SB): CTA (x, s) sums the ranks r = s, s + SB, s + 2 SB, ... of its C
-// columns in shared memory, at ((e TT + tt) C + cc).  With SB > 1 each CTA stores
-// its partial sum to part[s], and the last CTA of the column block (an atomic
-// ticket, no waiting) adds the SB partials in the fixed order s = 0..SB-1, so the
-// result does not depend on which CTA finishes last.
+// columns.  Each rank's C-column tile of the intermediate is one contiguous block
+// (pass A writes [k1 / C][n2][k1 % C]); it arrives by bulk asynchronous copy into
+// one of two buffers while the other rank is transformed, and the transform then
+// works in that buffer.  The sum over ranks is held in registers.  With SB > 1
+// each CTA stores its partial sum to part[s], and the last CTA of the column block
+// (an atomic ticket, no waiting) adds the SB partials in the fixed order
+// s = 0..SB-1, so the result does not depend on which CTA finishes last.
 template <typename T, int P2>
-__global__ void __launch_bounds__(256) k_passB(const PassArgs<T> a) {
+__global__ void __launch_bounds__(128, 3) k_passB(const PassArgs<T> a) {
     constexpr int E = e_of<T, P2>();
     using TF = TeamFft<T, P2, E, true>;
     constexpr int TT = TF::TT;
@@ -417,15 +424,35 @@ __global__ void __launch_bounds__(256) k_passB(const PassArgs<T> a) {
     const int k1 = blockIdx.x * a.C + cc;
     const int s = blockIdx.y, SB = gridDim.y;
     const T invN = T(1) / T(a.N);
-    cx<T> *acc = smem + a.C * a.S;
+    const int bufsz = a.C * a.S;                        // elements per buffer
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + 2 * bufsz);
+    __shared__ int cta_failed;
+    const uint32_t tile_bytes = (uint32_t)(a.C * P2 * sizeof(cx<T>));
+    const int64_t tile_off = (int64_t)blockIdx.x * a.C * P2;
+    const int nr = s < a.K ? (a.K - s + SB - 1) / SB : 0;   // ranks of this CTA
+    if (threadIdx.x == 0) {
+        cta_failed = 0;
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        fence_mbar_init();
+        for (int i = 0; i < 2 && i < nr; ++i) {
+            mbar_arrive_expect_tx(&mbar[i], tile_bytes);
+            bulk_copy_g2s(smem + i * bufsz, a.Y + (int64_t)(s + i * SB) * a.L + tile_off, tile_bytes, &mbar[i]);
+        }
+    }
+    __syncthreads();
+    cx<T> acc[E];
 #pragma unroll
-    for (int e = 0; e < E; ++e) acc[(e * TT + tt) * a.C + cc] = mk<T>(0, 0);
-    for (int r = s; r < a.K; r += SB) {
-        const cx<T> *Yb = a.Y + (int64_t)r * a.L + tt * a.L1 + k1;
+    for (int e = 0; e < E; ++e) acc[e] = mk<T>(0, 0);
+    for (int i = 0; i < nr; ++i) {
+        const int r = s + i * SB;
+        cx<T> *buf = smem + (i & 1) * bufsz;
+        mbar_wait_bounded(&mbar[i & 1], (i >> 1) & 1, a.err, &cta_failed);
         cx<T> v[E];
 #pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = Yb[m * (TT * a.L1)];
-        TF::run(v, tt, smem + cc * a.S, a.twc);
+        for (int m = 0; m < E; ++m) v[m] = buf[(tt + TT * m) * a.C + cc];   // tile as copied
+        __syncthreads();
+        TF::run(v, tt, buf + cc * a.S, a.twc);
         // (-i)^r T_r(z_k) v, the recurrence run element-innermost in chunks of H
         constexpr int H = E < 8 ? E : 8;
 #pragma unroll
@@ -453,27 +480,30 @@ __global__ void __launch_bounds__(256) k_passB(const PassArgs<T> a) {
                 T tr = r == 0 ? T(1) : tb[m];
                 if (odd) tr = fma(z2[m], tb[m], -ta[m]);
                 const cx<T> y = mul_ipow<T>(v[h0 + m], -r);
-                cx<T> &sacc = acc[((h0 + m) * TT + tt) * a.C + cc];
-                sacc.x = fma(tr, y.x, sacc.x);
-                sacc.y = fma(tr, y.y, sacc.y);
+                acc[h0 + m].x = fma(tr, y.x, acc[h0 + m].x);
+                acc[h0 + m].y = fma(tr, y.y, acc[h0 + m].y);
             }
+        }
+        // this buffer is free again: refill it with the rank after next
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0 && i + 2 < nr) {
+            mbar_arrive_expect_tx(&mbar[i & 1], tile_bytes);
+            bulk_copy_g2s(buf, a.Y + (int64_t)(r + 2 * SB) * a.L + tile_off, tile_bytes, &mbar[i & 1]);
         }
     }
     if (SB == 1) {
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int k = k1 + a.L1 * TF::out_index(tt, e);
-            if (k < a.N) a.out[k] = acc[(e * TT + tt) * a.C + cc];
+            if (k < a.N) a.out[k] = acc[e];
         }
         return;
     }
     // partial sums -> part[s]; the last CTA of this column block reduces them
     cx<T> *mine = a.part + (int64_t)s * a.L;
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int k = k1 + a.L1 * TF::out_index(tt, e);
-        mine[k] = acc[(e * TT + tt) * a.C + cc];
-    }
+    for (int e = 0; e < E; ++e) mine[k1 + a.L1 * TF::out_index(tt, e)] = acc[e];
     __threadfence();
     __syncthreads();
     __shared__ int ticket;
@@ -568,6 +598,9 @@ int launch_rows(nufft_plan p, const PassArgs<T> &a0, bool adjoint, cudaStream_t 
         a.S = p->S2;
         a.chunk = p->chunkA;
         a.mbar_off = (int)p->mbar_off2;
+        a.CQ = p->CB;
+        a.lgCQ = 0;
+        while ((1 << a.lgCQ) < a.CQ) ++a.lgCQ;
         if (a.chunk <= 0) return NUFFT_EINVAL;
         const dim3 block(p->nt2 * TT);
         static int done_a[64] = {}, done_2[64] = {};
