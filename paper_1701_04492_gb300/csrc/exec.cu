@@ -116,6 +116,9 @@ PassArgs<T> base_args(nufft_plan p) {
     a.part = (cx<T> *)p->part;
     a.counters = p->counters;
     a.err = p->err;
+    a.vfac = (const T *)p->Vfac;
+    a.ufac = (const cx<T> *)p->Ufac;
+    a.mode = p->Ufac ? MODE_FACTORS : 0;
     a.twlo = (const cx<T> *)p->twlo;
     a.N = p->N;
     a.M = p->M;
@@ -234,6 +237,75 @@ __global__ void k_uf_ranksum(const cx<T> *__restrict__ U, const cx<T> *__restric
 
 int grid1d(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 32)); }
 
+// Factor tables of the fused path's MODE_FACTORS, FP64 (eq. (2.6)):
+//   Vfac[r][k] = v_r(k) = T_r(2k/N - 1) (v_0 = 1/2), rank-major;
+//   Ufac[i][r] = u_r(perm[i]) = sum'_p a_pr exp(-i pi d) T_p(d / gamma), sorted order.
+template <typename T>
+__global__ void k_fac_V(int64_t N, int K, int trivial, T *__restrict__ V) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        if (trivial) { V[k] = T(1); continue; }
+        const double z = double(2 * k - N) / double(N);
+        double a = 1.0, b = z;
+        V[k] = T(0.5);
+        if (K > 1) V[N + k] = (T)z;
+        for (int r = 2; r < K; ++r) {
+            const double c = 2.0 * z * b - a;
+            a = b;
+            b = c;
+            V[(int64_t)r * N + k] = (T)c;
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_fac_U(const T *__restrict__ dsorted, int64_t M, int K, double inv_gamma, int trivial,
+                        const Beta<double, KMAX_ALL> aw, cx<T> *__restrict__ U) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (trivial) { U[i * K] = mk<T>(1, 0); continue; }
+        const double d = (double)dsorted[i];
+        const double xi = d * inv_gamma;
+        double Tp[KMAX_ALL];
+        Tp[0] = 1.0;
+        Tp[1] = xi;
+        for (int q = 2; q < K; ++q) Tp[q] = 2.0 * xi * Tp[q - 1] - Tp[q - 2];
+        double sn, cs;
+        sincospi(d, &sn, &cs);
+        for (int r = 0; r < K; ++r) {
+            double sum = 0.0;
+            for (int q = 0; q < K; ++q) sum += aw.b[r][q] * Tp[q];
+            const cx<double> u = mul_ipow<double>(mk<double>(cs * sum, -sn * sum), r);
+            U[i * K + r] = mk<T>((T)u.x, (T)u.y);
+        }
+    }
+}
+
+}  // namespace
+
+template <typename T>
+int plan_factor_tables(nufft_plan p, cudaStream_t s) {
+    const size_t cxs = 2 * sizeof(T);
+    const int64_t M = std::max<int64_t>(p->M, 1);
+    NUFFT_CUDA_TRY(cudaMalloc(&p->Ufac, (size_t)M * p->K * cxs));
+    NUFFT_CUDA_TRY(cudaMalloc(&p->Vfac, (size_t)p->N * p->K * sizeof(T)));
+    p->work_bytes += (int64_t)((size_t)M * p->K * cxs + (size_t)p->N * p->K * sizeof(T));
+    Beta<double, KMAX_ALL> aw{};
+    for (int r = 0; r < p->K; ++r)
+        for (int q = 0; q < p->K; ++q) aw.b[r][q] = (q == 0 ? 0.5 : 1.0) * p->alpha[q][r];
+    const int trivial = p->gamma == 0.0;
+    const double inv_gamma = trivial ? 0.0 : 1.0 / p->gamma;
+    if (p->M > 0)
+        k_fac_U<T><<<grid1d(p->M), 256, 0, s>>>((const T *)p->dsorted, p->M, p->K, inv_gamma, trivial, aw,
+                                                (cx<T> *)p->Ufac);
+    k_fac_V<T><<<grid1d(p->N), 256, 0, s>>>(p->N, p->K, trivial, (T *)p->Vfac);
+    NUFFT_CUDA_TRY(cudaGetLastError());
+    return NUFFT_OK;
+}
+
+template int plan_factor_tables<double>(nufft_plan, cudaStream_t);
+
+namespace {
 }  // namespace
 
 template <typename T>
@@ -299,7 +371,7 @@ int exec_dx(nufft_plan p, const void *c, const void *g, void *gx, int acc, cudaS
     a.in = (const cx<T> *)c;
     a.g = (const cx<T> *)g;
     a.gx = (T *)gx;
-    a.mode = MODE_DX;
+    a.mode |= MODE_DX;
     a.accumulate = acc;
     if (int rc = mark(p, s, true)) return rc;
     if (int rc = launch_cols<T>(p, a, false, s)) return rc;
@@ -319,7 +391,7 @@ int exec_unfused(nufft_plan p, const void *c, void *f, cudaStream_t s) {
     PassArgs<T> a = base_args<T>(p);
     a.in = W;
     a.out = W;
-    a.mode = MODE_PLAIN_IN | MODE_PLAIN_OUT;
+    a.mode |= MODE_PLAIN_IN | MODE_PLAIN_OUT;
     if (int rc = launch_cols<T>(p, a, false, s)) return rc;   // W -> Y
     if (int rc = run_rows<T>(p, a, false, s)) return rc;      // Y -> X (in W)
     cx<T> *Xg = (cx<T> *)p->Y;

@@ -65,6 +65,8 @@ struct nufft_plan_s {
     void *part = nullptr;      // pass B partial sums, SBsplit x L complex
     int *counters = nullptr;   // pass B tickets, one per column block
     int *err = nullptr;        // device error word: bounded waits that timed out
+    void *Ufac = nullptr;      // FP64 plans: u_r in sorted order, M x K complex
+    void *Vfac = nullptr;      // FP64 plans: v_r, K x N real
     int64_t work_bytes = 0;
 
     // NUFFT_PLAN_TIMING: events around each launch of the last exec call
@@ -101,6 +103,7 @@ template <typename T> int exec_dx(nufft_plan p, const void *c, const void *g, vo
 template <typename T> int exec_unfused(nufft_plan p, const void *c, void *f, cudaStream_t s);
 template <typename T> int plan_geometry(nufft_plan p);
 template <typename T> int plan_unfused_factors(nufft_plan p, cudaStream_t s);
+template <typename T> int plan_factor_tables(nufft_plan p, cudaStream_t s);
 
 }  // namespace nufft
 

@@ -31,7 +31,9 @@ namespace nufft {
 enum PassMode : int {
     MODE_PLAIN_IN = 1,    // pass 1 reads a pre-scaled W_r instead of c
     MODE_PLAIN_OUT = 2,   // pass 2 writes X_r in natural order instead of gathering
-    MODE_DX = 4           // pass 1 scales by -2 pi i k; pass 2 forms Re(conj(g) f')
+    MODE_DX = 4,          // pass 1 scales by -2 pi i k; pass 2 forms Re(conj(g) f')
+    MODE_FACTORS = 8      // read the plan's materialised U (sorted) and V instead of
+                          // recomputing them (the FP64 plans: FP64 arithmetic is scarce)
 };
 
 template <typename T> struct EmaxT;
@@ -61,6 +63,8 @@ struct PassArgs {
     int mbar_off;         // pass 2: byte offset of the slot mbarriers in shared memory
     int CQ, lgCQ;         // pass A/B: columns of pass B's tiles (the adjoint intermediate's tiling)
     int *err;             // device error word (bounded waits that timed out)
+    const T *vfac;        // MODE_FACTORS: V[r][k] = v_r(k) of eq. (2.6), K x N
+    const cx<T> *ufac;    // MODE_FACTORS: U[i][r] = u_r(perm[i]) of eq. (2.6), sorted order, M x K
     T inv_gamma;
 };
 
@@ -131,6 +135,21 @@ __global__ void __launch_bounds__(256, 2) k_pass1(const PassArgs<T> a) {
         const cx<T> *cb = a.in + k0;
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = k0 + m * kstride < a.N ? cb[m * kstride] : mk<T>(0, 0);
+        if (a.mode & MODE_FACTORS) {
+            // x_k = v_r(k) c_k with the plan's V
+            const T *vr = a.vfac + (int64_t)r * a.N;
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const int k = k0 + m * kstride;
+                const T w = k < a.N ? vr[k] : T(0);
+                cx<T> cv = v[m];
+                if (a.mode & MODE_DX) {
+                    const T wk = T(6.283185307179586476925286766559) * T(k);
+                    cv = mk<T>(wk * cv.y, -wk * cv.x);
+                }
+                v[m] = mk<T>(w * cv.x, w * cv.y);
+            }
+        } else {
         // v_r(k) = T_r(z_k), z_k = (2k - N)/N, by the three-term recurrence run
         // across the elements (element-innermost for independent FMAs)
         const T invN = T(1) / T(a.N);
@@ -167,6 +186,7 @@ __global__ void __launch_bounds__(256, 2) k_pass1(const PassArgs<T> a) {
                 }
                 v[h0 + m] = mul_ipow<T>(mk<T>(tr * cv.x, tr * cv.y), r);
             }
+        }
         }
     }
     TF::run(v, tt, smem + cc * a.S, a.twc);
@@ -252,30 +272,45 @@ __global__ void __launch_bounds__(256) k_pass2(const PassArgs<T> a, const Beta<T
                 const int row = (t & L2m) - b * a.B2;
                 const int n1 = t >> a.lg2;
                 const T d = a.dsorted[i];
-                const T xi = d * a.inv_gamma;
-                T Tp[KM];
-                Tp[0] = T(1);
-                if (KM > 1) Tp[1] = xi;
-#pragma unroll
-                for (int q = 2; q < KM; ++q) Tp[q] = fma(T(2) * xi, Tp[q - 1], -Tp[q - 2]);
                 cx<T> acc = g0 == 0 ? mk<T>(0, 0) : a.fscr[i];
-#pragma unroll
-                for (int r = 0; r < KM; ++r) {
-                    if (r >= g0 && r < g0 + gc) {
-                        T mu = T(0);
-#pragma unroll
-                        for (int q = (r & 1); q < KM; q += 2) mu = fma(beta.b[r][q], Tp[q], mu);
+                const bool fac = (a.mode & MODE_FACTORS) != 0;
+                if (fac) {
+                    // f_j = sum_r u_r(j) X_r[t_j] with the plan's U (phase included)
+                    const cx<T> *ui = a.ufac + (int64_t)i * a.K;
+                    for (int r = g0; r < g0 + gc; ++r) {
                         const cx<T> x = smem[((r - g0) * a.B2 + row) * a.S + padi<E>(n1)];
-                        acc.x = fma(mu, x.x, acc.x);
-                        acc.y = fma(mu, x.y, acc.y);
+                        const cx<T> u = ui[r];
+                        acc.x = fma(u.x, x.x, fma(-u.y, x.y, acc.x));
+                        acc.y = fma(u.x, x.y, fma(u.y, x.x, acc.y));
+                    }
+                } else {
+                    const T xi = d * a.inv_gamma;
+                    T Tp[KM];
+                    Tp[0] = T(1);
+                    if (KM > 1) Tp[1] = xi;
+#pragma unroll
+                    for (int q = 2; q < KM; ++q) Tp[q] = fma(T(2) * xi, Tp[q - 1], -Tp[q - 2]);
+#pragma unroll
+                    for (int r = 0; r < KM; ++r) {
+                        if (r >= g0 && r < g0 + gc) {
+                            T mu = T(0);
+#pragma unroll
+                            for (int q = (r & 1); q < KM; q += 2) mu = fma(beta.b[r][q], Tp[q], mu);
+                            const cx<T> x = smem[((r - g0) * a.B2 + row) * a.S + padi<E>(n1)];
+                            acc.x = fma(mu, x.x, acc.x);
+                            acc.y = fma(mu, x.y, acc.y);
+                        }
                     }
                 }
                 if (g0 + gc < a.K) {
                     a.fscr[i] = acc;
                 } else {
-                    T sn, cs;
-                    sincospi_t<T>(d, &sn, &cs);
-                    const cx<T> val = mk<T>(fma(acc.x, cs, acc.y * sn), fma(acc.y, cs, -acc.x * sn));
+                    cx<T> val = acc;
+                    if (!fac) {
+                        T sn, cs;
+                        sincospi_t<T>(d, &sn, &cs);
+                        val = mk<T>(fma(acc.x, cs, acc.y * sn), fma(acc.y, cs, -acc.x * sn));
+                    }
                     const int j = a.perm[i];
                     if (a.mode & MODE_DX) {
                         const cx<T> gg = a.g[j];
@@ -344,6 +379,19 @@ __global__ void __launch_bounds__(256) k_passA(const PassArgs<T> a, const Beta<T
                         if (a.tsorted[c0 + i2] != t) break;
                         d = a.dsorted[c0 + i2];
                         gg = a.in[a.perm[c0 + i2]];
+                    }
+                    if (a.mode & MODE_FACTORS) {
+                        // Z_r += conj(u_r(j)) g_j with the plan's U
+                        const cx<T> *ui = a.ufac + (int64_t)(c0 + i2) * a.K;
+#pragma unroll
+                        for (int r = 0; r < KM; ++r) {
+                            if (r >= g0 && r < g0 + gc) {
+                                const cx<T> u = ui[r];
+                                acc[r].x = fma(u.x, gg.x, fma(u.y, gg.y, acc[r].x));
+                                acc[r].y = fma(u.x, gg.y, fma(-u.y, gg.x, acc[r].y));
+                            }
+                        }
+                        continue;
                     }
                     const T xi = d * a.inv_gamma;
                     T Tp[KM];
@@ -453,6 +501,16 @@ __global__ void __launch_bounds__(128, 3) k_passB(const PassArgs<T> a) {
         for (int m = 0; m < E; ++m) v[m] = buf[(tt + TT * m) * a.C + cc];   // tile as copied
         __syncthreads();
         TF::run(v, tt, buf + cc * a.S, a.twc);
+        if (a.mode & MODE_FACTORS) {   // the plan's v_r(k) (real), no i^r
+            const T *vr = a.vfac + (int64_t)r * a.N;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int k = k1 + a.L1 * TF::out_index(tt, e);
+                const T w = k < a.N ? vr[k] : T(0);
+                acc[e].x = fma(w, v[e].x, acc[e].x);
+                acc[e].y = fma(w, v[e].y, acc[e].y);
+            }
+        } else {
         // (-i)^r T_r(z_k) v, the recurrence run element-innermost in chunks of H
         constexpr int H = E < 8 ? E : 8;
 #pragma unroll
@@ -483,6 +541,7 @@ __global__ void __launch_bounds__(128, 3) k_passB(const PassArgs<T> a) {
                 acc[h0 + m].x = fma(tr, y.x, acc[h0 + m].x);
                 acc[h0 + m].y = fma(tr, y.y, acc[h0 + m].y);
             }
+        }
         }
         // this buffer is free again: refill it with the rank after next
         fence_proxy_async_smem();

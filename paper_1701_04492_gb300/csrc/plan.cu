@@ -366,6 +366,11 @@ int plan_device(nufft_plan p, const double *x, cudaStream_t s) {
     if (p->flags & NUFFT_PLAN_UNFUSED) {
         if ((rc = plan_unfused_factors<T>(p, s))) return rc;
     }
+    // FP64 plans read materialised factors in the fused kernels: on this GPU FP64
+    // arithmetic is scarce and bandwidth is not
+    if (p->prec == NUFFT_F64) {
+        if ((rc = plan_factor_tables<double>(p, s))) return rc;
+    }
     NUFFT_CUDA_TRY(cudaStreamSynchronize(s));
     return NUFFT_OK;
 }
@@ -374,7 +379,7 @@ void free_plan(nufft_plan p) {
     if (!p) return;
     void *bufs[] = {p->tsorted, p->perm, p->bstart, p->t_j, p->dsorted, p->d_j, p->twst1,
                     p->twst2, p->twhi, p->twlo, p->Y, p->fscr, p->cstage, p->fstage, p->U, p->V, p->Xg,
-                    p->part, p->counters, p->err};
+                    p->part, p->counters, p->err, p->Ufac, p->Vfac};
     for (void *b : bufs) if (b) cudaFree(b);
     for (cudaEvent_t e : p->ev) if (e) cudaEventDestroy(e);
     delete p;
