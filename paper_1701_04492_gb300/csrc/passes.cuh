@@ -22,6 +22,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "async_copy.cuh"
 #include "fft_team.cuh"
 #include "nufft_internal.h"
@@ -35,6 +37,11 @@ enum PassMode : int {
     MODE_FACTORS = 8      // read the plan's materialised U (sorted) and V instead of
                           // recomputing them (the FP64 plans: FP64 arithmetic is scarce)
 };
+
+// The fused kernels of FP64 plans read the plan's materialised factors (MODE_FACTORS);
+// those of FP32 plans recompute them.  Fixed per element type, so the FP32 kernels
+// carry no code for it.
+template <typename T> constexpr bool kFactors = std::is_same<T, double>::value;
 
 template <typename T> struct EmaxT;
 template <> struct EmaxT<float> { static constexpr int v = 32; };
@@ -135,7 +142,7 @@ __global__ void __launch_bounds__(256, 2) k_pass1(const PassArgs<T> a) {
         const cx<T> *cb = a.in + k0;
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = k0 + m * kstride < a.N ? cb[m * kstride] : mk<T>(0, 0);
-        if (a.mode & MODE_FACTORS) {
+        if constexpr (kFactors<T>) {
             // x_k = v_r(k) c_k with the plan's V
             const T *vr = a.vfac + (int64_t)r * a.N;
 #pragma unroll
@@ -273,7 +280,7 @@ __global__ void __launch_bounds__(256) k_pass2(const PassArgs<T> a, const Beta<T
                 const int n1 = t >> a.lg2;
                 const T d = a.dsorted[i];
                 cx<T> acc = g0 == 0 ? mk<T>(0, 0) : a.fscr[i];
-                const bool fac = (a.mode & MODE_FACTORS) != 0;
+                constexpr bool fac = kFactors<T>;
                 if (fac) {
                     // f_j = sum_r u_r(j) X_r[t_j] with the plan's U (phase included)
                     const cx<T> *ui = a.ufac + (int64_t)i * a.K;
@@ -380,7 +387,7 @@ __global__ void __launch_bounds__(256) k_passA(const PassArgs<T> a, const Beta<T
                         d = a.dsorted[c0 + i2];
                         gg = a.in[a.perm[c0 + i2]];
                     }
-                    if (a.mode & MODE_FACTORS) {
+                    if constexpr (kFactors<T>) {
                         // Z_r += conj(u_r(j)) g_j with the plan's U
                         const cx<T> *ui = a.ufac + (int64_t)(c0 + i2) * a.K;
 #pragma unroll
@@ -501,7 +508,7 @@ __global__ void __launch_bounds__(128, 3) k_passB(const PassArgs<T> a) {
         for (int m = 0; m < E; ++m) v[m] = buf[(tt + TT * m) * a.C + cc];   // tile as copied
         __syncthreads();
         TF::run(v, tt, buf + cc * a.S, a.twc);
-        if (a.mode & MODE_FACTORS) {   // the plan's v_r(k) (real), no i^r
+        if constexpr (kFactors<T>) {   // the plan's v_r(k) (real), no i^r
             const T *vr = a.vfac + (int64_t)r * a.N;
 #pragma unroll
             for (int e = 0; e < E; ++e) {
