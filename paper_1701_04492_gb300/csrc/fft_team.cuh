@@ -139,6 +139,19 @@ __host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c
 template <int E> __device__ __forceinline__ int padi(int o) { return o + (o >> ilog2c(E)); }
 template <int E> __host__ __device__ constexpr int padded_len(int P) { return P + P / E; }
 
+// padi(base + STEP * i) = padi(base) + i (STEP + STEP / E) whenever STEP is a
+// multiple of E (adding a multiple of E leaves the low bits of base alone), so a
+// strided run of padded indices is one per-thread base plus compile-time offsets.
+template <int E, int STEP>
+__device__ __forceinline__ int padi_run(int pbase, int i) {
+    if constexpr (STEP % E == 0) {
+        return pbase + i * (STEP + STEP / E);
+    } else {
+        (void)pbase;
+        return -1;   // not used: callers check STEP % E first
+    }
+}
+
 template <typename T, int P, int E, bool INV>
 struct TeamFft {
     static_assert(P % E == 0, "P must be a multiple of E");
@@ -191,24 +204,42 @@ struct TeamFft {
     // next stage (radix Rn).
     template <int R, int NS, int Rn>
     __device__ __forceinline__ static void exchange(cx<T> (&a)[E], int tt, cx<T>* sm) {
+        static_assert(NS == 1 || NS % E == 0, "later stages follow a radix-E stage");
 #pragma unroll
         for (int b = 0; b < E / R; ++b) {
             const int v = tt + TT * b;
+            if constexpr (NS == 1) {
+                // first stage (R = E): o = v E + i, padded v (E + 1) + i
+                static_assert(R == E, "the first stage has radix E");
+                const int pb = v * (E + 1);
 #pragma unroll
-            for (int i = 0; i < R; ++i) {
-                const int o = (v / NS) * NS * R + (v % NS) + NS * i;
-                sm[padi<E>(o)] = a[b * R + i];
+                for (int i = 0; i < R; ++i) sm[pb + i] = a[b * R + i];
+            } else {
+                const int o0 = (v / NS) * NS * R + (v % NS);
+                const int pb = padi<E>(o0);
+#pragma unroll
+                for (int i = 0; i < R; ++i) sm[padi_run<E, NS>(pb, i)] = a[b * R + i];
             }
         }
         __syncthreads();
         constexpr int Vn = P / Rn;
+        static_assert(Vn % E == 0, "exchange strides are multiples of E");
 #pragma unroll
         for (int b = 0; b < E / Rn; ++b) {
             const int v = tt + TT * b;
+            const int pb = padi<E>(v);
 #pragma unroll
-            for (int i = 0; i < Rn; ++i) a[b * Rn + i] = sm[padi<E>(v + Vn * i)];
+            for (int i = 0; i < Rn; ++i) a[b * Rn + i] = sm[padi_run<E, Vn>(pb, i)];
         }
         __syncthreads();
+    }
+
+    // Padded shared index of output e after run() (out_index(tt, e) padded).
+    __device__ __forceinline__ static int out_padded(int tt, int e) {
+        const int b = e / RL, i = e % RL;
+        const int v = tt + TT * b;
+        if constexpr (NSL % E == 0) return padi_run<E, NSL>(padi<E>(v), i);
+        else return padi<E>(v + NSL * i);
     }
 
     // tw: this length's stage table (TW_SIZE entries, forward exponent).

@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(256) k_pass2(const PassArgs<T> a, const Beta<T
             __syncthreads();   // the row is read before the transform reuses its slot
             TF::run(v, tt, sm, a.twr);
 #pragma unroll
-            for (int e = 0; e < E; ++e) sm[padi<E>(TF::out_index(tt, e))] = v[e];
+            for (int e = 0; e < E; ++e) sm[TF::out_padded(tt, e)] = v[e];
         }
         __syncthreads();
         if (a.mode & MODE_PLAIN_OUT) {
@@ -437,7 +437,10 @@ __global__ void __launch_bounds__(256) k_passA(const PassArgs<T> a, const Beta<T
             cx<T> *sm = smem + job * a.S;
             cx<T> v[E];
 #pragma unroll
-            for (int m = 0; m < E; ++m) v[m] = sm[padi<E>(tt + TT * m)];
+            for (int m = 0; m < E; ++m) {
+                if constexpr (TT % E == 0) v[m] = sm[padi_run<E, TT>(padi<E>(tt), m)];
+                else v[m] = sm[padi<E>(tt + TT * m)];
+            }
             fill_fourstep<T, E, TT>(a, n2, tt, ftab, 1);
             __syncthreads();
             TF::run(v, tt, sm, a.twr);
