@@ -159,7 +159,8 @@ __global__ void __launch_bounds__(256, 2) k_pass1(const PassArgs<T> a) {
         } else {
         // v_r(k) = T_r(z_k), z_k = (2k - N)/N, by the three-term recurrence run
         // across the elements (element-innermost for independent FMAs)
-        const T invN = T(1) / T(a.N);
+        const int Ni = (int)a.N;   // N < 2^23: 32-bit conversions (64-bit ones run on the FP64 pipe)
+        const T invN = T(1) / T(Ni);
         constexpr int H = E < 8 ? E : 8;
 #pragma unroll
         for (int h0 = 0; h0 < E; h0 += H) {
@@ -167,7 +168,7 @@ __global__ void __launch_bounds__(256, 2) k_pass1(const PassArgs<T> a) {
 #pragma unroll
             for (int m = 0; m < H; ++m) {
                 const int k = k1 + a.L1 * (tt + TT * (h0 + m));
-                const T z = T(2 * k - a.N) * invN;
+                const T z = T(2 * k - Ni) * invN;
                 z2[m] = T(2) * z;
                 ta[m] = T(1);
                 tb[m] = z;
@@ -481,7 +482,8 @@ __global__ void __launch_bounds__(128, 3) k_passB(const PassArgs<T> a) {
     const int tt = threadIdx.x >> a.lgC;
     const int k1 = blockIdx.x * a.C + cc;
     const int s = blockIdx.y, SB = gridDim.y;
-    const T invN = T(1) / T(a.N);
+    const int Ni = (int)a.N;   // N < 2^23: 32-bit conversions (64-bit ones run on the FP64 pipe)
+        const T invN = T(1) / T(Ni);
     const int bufsz = a.C * a.S;                        // elements per buffer
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + 2 * bufsz);
     __shared__ int cta_failed;
@@ -529,7 +531,7 @@ __global__ void __launch_bounds__(128, 3) k_passB(const PassArgs<T> a) {
 #pragma unroll
             for (int m = 0; m < H; ++m) {
                 const int k = k1 + a.L1 * TF::out_index(tt, h0 + m);
-                const T z = T(2 * k - a.N) * invN;
+                const T z = T(2 * k - Ni) * invN;
                 z2[m] = T(2) * z;
                 ta[m] = T(1);
                 tb[m] = z;
