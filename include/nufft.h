@@ -129,6 +129,21 @@ int nufft1_exec(nufft_plan p, const void *g_dev, void *c_dev, void *stream);
 int nufft2_exec_dx(nufft_plan p, const void *c_dev, const void *g_dev, void *gx_dev,
                    int accumulate, void *stream);
 
+/* The forward transform and its derivative with respect to the samples in one
+ * call: f = A c and fprime_j = d f_j / d x_j = sum_k (-2 pi i k) c_k exp(-2 pi i x_j k).
+ * With k = N (z + 1)/2 and z T_r(z) = (T_{r+1}(z) + T_{r-1}(z))/2 (z = 2k/N - 1),
+ * the rank-r factor of A_K((-2 pi i k) o c) is a combination of ranks r - 1, r and
+ * r + 1 of the forward, so both come from K + 1 FFTs of length L (eq. (2.11) with
+ * one more rank); the result equals nufft2_exec applied to (-2 pi i k) o c.
+ *   c_dev N complex; f_dev and fprime_dev M complex (written). */
+int nufft2_exec_deriv(nufft_plan p, const void *c_dev, void *f_dev, void *fprime_dev, void *stream);
+
+/* gx_j (+)= Re(conj(g_j) fprime_j): the x-gradient of Re(sum_j conj(g_j) f_j) from
+ * the fprime of nufft2_exec_deriv.  g_dev, fprime_dev M complex; gx_dev M reals of
+ * the plan's precision; accumulate 0: gx = ..., 1: gx += ... */
+int nufft2_grad_x(nufft_plan p, const void *g_dev, const void *fprime_dev, void *gx_dev, int accumulate,
+                  void *stream);
+
 /* B independent transforms sharing the plan: f_b = A c_b, b = 0..B-1, with
  * c_b at c_dev + b*ldc elements and f_b at f_dev + b*ldf elements
  * (ldc >= N, ldf >= M). */

@@ -29,6 +29,8 @@ SIGNATURES = {
     "nufft2_exec": (_i32, [_vp, _vp, _vp, _vp]),
     "nufft1_exec": (_i32, [_vp, _vp, _vp, _vp]),
     "nufft2_exec_dx": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp]),
+    "nufft2_exec_deriv": (_i32, [_vp, _vp, _vp, _vp, _vp]),
+    "nufft2_grad_x": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp]),
     "nufft2_exec_batch": (_i32, [_vp, _i64, _vp, _i64, _vp, _i64, _vp]),
     "nufft2_exec_host": (_i32, [_vp, _vp, _vp, _vp]),
     "nufft2_exec_unfused": (_i32, [_vp, _vp, _vp, _vp]),

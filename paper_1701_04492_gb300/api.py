@@ -156,6 +156,28 @@ class Plan:
                                              _stream(self.device)), "nufft2_exec_dx")
         return gx
 
+    def forward_deriv(self, c, out=None, out_deriv=None):
+        """(f, f') with f = A c and f'_j = d f_j / d x_j, from K + 1 FFTs in one exec."""
+        self._cx(c, self.N, "c")
+        f = out if out is not None else torch.empty(self.M, dtype=self.cdtype, device=self.device)
+        fp = out_deriv if out_deriv is not None else torch.empty(self.M, dtype=self.cdtype, device=self.device)
+        self._cx(f, self.M, "f")
+        self._cx(fp, self.M, "fprime")
+        with torch.cuda.device(self.device):
+            check(_lib.load().nufft2_exec_deriv(self._h, _ptr(c), _ptr(f), _ptr(fp), _stream(self.device)),
+                  "nufft2_exec_deriv")
+        return f, fp
+
+    def grad_x(self, g, fprime, out=None, accumulate=False):
+        """gx_j (+)= Re(conj(g_j) fprime_j)."""
+        self._cx(g, self.M, "g")
+        self._cx(fprime, self.M, "fprime")
+        gx = out if out is not None else torch.empty(self.M, dtype=self.rdtype, device=self.device)
+        with torch.cuda.device(self.device):
+            check(_lib.load().nufft2_grad_x(self._h, _ptr(g), _ptr(fprime), _ptr(gx), int(bool(accumulate)),
+                                            _stream(self.device)), "nufft2_grad_x")
+        return gx
+
     def forward_batch(self, c, out=None):
         """f[b] = A c[b] for a (B, N) batch."""
         if c.dim() != 2 or c.shape[1] != self.N or c.dtype != self.cdtype or c.stride(1) != 1:
@@ -189,36 +211,49 @@ class Plan:
 
 
 class _Nufft2(torch.autograd.Function):
-    """f = A(x) c with a hand-written backward: dL/dc = A^H g, dL/dx = Re(conj(g) A((-2 pi i k) c))."""
+    """f = A(x) c with a hand-written backward: dL/dc = A^H g, dL/dx = Re(conj(g) f').
+
+    When x needs a gradient the forward also forms f' = df/dx (nufft2_exec_deriv: the
+    same pass with one more rank) and keeps it for the backward."""
 
     @staticmethod
     def forward(ctx, c, x, plan):
         ctx.plan = plan
-        ctx.save_for_backward(c)
         cc = c.detach().contiguous()
-        if cc.dim() == 1:
-            return plan.forward(cc)
-        return plan.forward_batch(cc)
+        batched = cc.dim() == 2
+        want_dx = ctx.needs_input_grad[1]
+        fp = None
+        if not want_dx:
+            f = plan.forward_batch(cc) if batched else plan.forward(cc)
+        elif batched:
+            f = torch.empty(cc.shape[0], plan.M, dtype=plan.cdtype, device=plan.device)
+            fp = torch.empty_like(f)
+            for b in range(cc.shape[0]):
+                plan.forward_deriv(cc[b], f[b], fp[b])
+        else:
+            f, fp = plan.forward_deriv(cc)
+        ctx.save_for_backward(fp if fp is not None else torch.empty(0, device=plan.device))
+        ctx.batched = batched
+        return f
 
     @staticmethod
     def backward(ctx, g):
-        (c,) = ctx.saved_tensors
+        (fp,) = ctx.saved_tensors
         plan = ctx.plan
         g = g.contiguous()
         gc = gx = None
-        batched = c.dim() == 2
         if ctx.needs_input_grad[0]:
-            if batched:
+            if ctx.batched:
                 gc = torch.stack([plan.adjoint(g[b].contiguous()) for b in range(g.shape[0])])
             else:
                 gc = plan.adjoint(g)
         if ctx.needs_input_grad[1]:
             gx = torch.empty(plan.M, dtype=plan.rdtype, device=plan.device)
-            if batched:
+            if ctx.batched:
                 for b in range(g.shape[0]):
-                    plan.dx(c[b].detach().contiguous(), g[b].contiguous(), gx, accumulate=b > 0)
+                    plan.grad_x(g[b].contiguous(), fp[b], gx, accumulate=b > 0)
             else:
-                plan.dx(c.detach().contiguous(), g, gx)
+                plan.grad_x(g, fp, gx)
             gx = gx.to(torch.float64)
         return gc, gx, None
 

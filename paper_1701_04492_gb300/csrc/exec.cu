@@ -61,40 +61,43 @@ int plan_geometry(nufft_plan p) {
     p->smemB = ((2 * (size_t)p->CB * p->SB * cxs + 15) / 16) * 16 + 2 * sizeof(uint64_t);
     // rank splits of pass B: enough CTAs for about four per SM, at most one rank each
     p->SBsplit = std::max(1, std::min(p->K, (4 * 152 + p->L1 / p->CB - 1) / (p->L1 / p->CB)));
-    // row passes: buckets of B2 rows, nt2 teams, G ranks staged at once
+    // row passes: buckets of B2 rows; G ranks staged at once by nt teams
     p->B2 = clamp_pow2(1024 / p->L1, 1, p->L2);
     p->NB = p->L2 / p->B2;
     p->S2 = slot_stride<T>(p->L1, E1, std::max(1, nbank<T>() / TT1));
     const int maxt = std::max(1, 256 / TT1);
     p->chunkA = 512;
     const size_t staging = (size_t)p->chunkA * (sizeof(int32_t) + sizeof(T)) + (size_t)p->chunkA * cxs;
-    // slots + four-step tables + pass A's staged samples, then (16-byte aligned)
-    // pass 2's slot mbarriers
-    auto body = [&](int G, int nt) {
-        const size_t slots = (size_t)((G * p->B2 + nt - 1) / nt) * nt;
-        return ((slots * p->S2 + (size_t)nt * E1) * cxs + staging + 15) / 16 * 16;
-    };
-    auto bytes = [&](int G, int nt) {
-        return body(G, nt) + (size_t)((G * p->B2 + nt - 1) / nt) * nt * sizeof(uint64_t);
-    };
+    auto nslots = [&](int G, int nt) { return (size_t)((G * p->B2 + nt - 1) / nt) * nt; };
+    // pass 2: slots, then (16-byte aligned) one mbarrier per slot
+    auto body2 = [&](int G, int nt) { return (nslots(G, nt) * p->S2 * cxs + 15) / 16 * 16; };
+    auto bytes2 = [&](int G, int nt) { return body2(G, nt) + nslots(G, nt) * sizeof(uint64_t); };
+    // pass A: slots, four-step tables, staged samples
+    auto bytesA = [&](int G, int nt) { return (nslots(G, nt) * p->S2 + (size_t)nt * E1) * cxs + staging; };
     // the largest group that fits, then the team count: the largest <= 256 threads
     // dividing the group's B2 G row FFTs (no idle team), at least 64 threads
-    int G = p->K;
-    while (G > 1 && bytes(G, 1) > SMEM_BUDGET) --G;
-    int nt = 1;
-    for (;;) {
-        nt = 1;
-        for (int d = 1; d <= maxt; ++d)
-            if ((G * p->B2) % d == 0) nt = d;
-        if (nt * TT1 < 64) nt = std::min(maxt, std::max(nt, 64 / TT1));
-        if (bytes(G, nt) <= SMEM_BUDGET || G == 1) break;
-        --G;
-    }
-    if (bytes(G, nt) > SMEM_BUDGET) return NUFFT_EUNSUPPORTED;
-    p->G = G;
-    p->nt2 = nt;
-    p->mbar_off2 = body(G, nt);
-    p->smem2 = bytes(G, nt);
+    auto choose = [&](int Gmax, auto bytes, int *Gout, int *ntout) -> bool {
+        int G = Gmax;
+        while (G > 1 && bytes(G, 1) > SMEM_BUDGET) --G;
+        int nt = 1;
+        for (;;) {
+            nt = 1;
+            for (int d = 1; d <= maxt; ++d)
+                if ((G * p->B2) % d == 0) nt = d;
+            if (nt * TT1 < 64) nt = std::min(maxt, std::max(nt, 64 / TT1));
+            if (bytes(G, nt) <= SMEM_BUDGET || G == 1) break;
+            --G;
+        }
+        *Gout = G;
+        *ntout = nt;
+        return bytes(G, nt) <= SMEM_BUDGET;
+    };
+    // pass 2 stages up to K + 1 ranks (the derivative mode adds rank K)
+    if (!choose(p->K + 1, bytes2, &p->G, &p->nt2)) return NUFFT_EUNSUPPORTED;
+    p->mbar_off2 = body2(p->G, p->nt2);
+    p->smem2 = bytes2(p->G, p->nt2);
+    if (!choose(p->K, bytesA, &p->GA, &p->ntA)) return NUFFT_EUNSUPPORTED;
+    p->smemA = bytesA(p->GA, p->ntA);
     if (p->smem1 > SMEM_BUDGET || p->smemB > SMEM_BUDGET) return NUFFT_EUNSUPPORTED;
     return NUFFT_OK;
 }
@@ -130,6 +133,8 @@ PassArgs<T> base_args(nufft_plan p) {
     a.K = p->K;
     a.G = p->G;
     a.B2 = p->B2;
+    a.nranks = p->K;
+    a.piN = (T)(3.14159265358979323846 * (double)p->N);
     a.inv_gamma = p->gamma > 0.0 ? (T)(1.0 / p->gamma) : T(0);
     return a;
 }
@@ -317,11 +322,11 @@ int plan_unfused_factors(nufft_plan p, cudaStream_t s) {
     NUFFT_CUDA_TRY(cudaMalloc(&p->Xg, (size_t)p->K * p->L * cxs));
     p->work_bytes += (int64_t)((size_t)M * p->K * cxs + (size_t)p->N * p->K * sizeof(T) +
                                (size_t)p->K * p->L * cxs);
-    if (p->M > (int64_t)p->L) {   // the gathered K x M block reuses Y
+    if ((size_t)p->K * p->M > (size_t)(p->K + 1) * p->L) {   // the gathered K x M block reuses Y
         cudaFree(p->Y);
         p->Y = nullptr;
         NUFFT_CUDA_TRY(cudaMalloc(&p->Y, (size_t)p->K * p->M * cxs));
-        p->work_bytes += (int64_t)((size_t)p->K * (p->M - p->L) * cxs);
+        p->work_bytes += (int64_t)(((size_t)p->K * p->M - (size_t)(p->K + 1) * p->L) * cxs);
     }
     Beta<double, KMAX_ALL> aw{};
     for (int r = 0; r < p->K; ++r)
@@ -371,13 +376,67 @@ int exec_dx(nufft_plan p, const void *c, const void *g, void *gx, int acc, cudaS
     a.in = (const cx<T> *)c;
     a.g = (const cx<T> *)g;
     a.gx = (T *)gx;
-    a.mode |= MODE_DX;
     a.accumulate = acc;
+    if (!kFactors<T> && p->G >= p->K + 1) {
+        a.mode |= MODE_DERIV | MODE_GX;
+        a.nranks = p->K + 1;
+        a.out = nullptr;
+        a.out2 = nullptr;
+    } else {
+        a.mode |= MODE_PRESCALE | MODE_GX;
+    }
     if (int rc = mark(p, s, true)) return rc;
     if (int rc = launch_cols<T>(p, a, false, s)) return rc;
     if (int rc = mark(p, s, false)) return rc;
     if (int rc = run_rows<T>(p, a, false, s)) return rc;
     return mark(p, s, false);
+}
+
+// f = A c and f' = df/dx (the derivative of eq. (1.2) with respect to each x_j).
+template <typename T>
+int exec_deriv(nufft_plan p, const void *c, void *f, void *fprime, cudaStream_t s) {
+    if (p->M == 0) return NUFFT_OK;
+    if (!kFactors<T> && p->G >= p->K + 1) {
+        PassArgs<T> a = base_args<T>(p);
+        a.in = (const cx<T> *)c;
+        a.out = (cx<T> *)f;
+        a.out2 = (cx<T> *)fprime;
+        a.mode |= MODE_DERIV;
+        a.nranks = p->K + 1;
+        if (int rc = mark(p, s, true)) return rc;
+        if (int rc = launch_cols<T>(p, a, false, s)) return rc;
+        if (int rc = mark(p, s, false)) return rc;
+        if (int rc = run_rows<T>(p, a, false, s)) return rc;
+        return mark(p, s, false);
+    }
+    // otherwise: the forward, then A((-2 pi i k) o c)
+    if (int rc = exec_forward<T>(p, c, f, s)) return rc;
+    PassArgs<T> a = base_args<T>(p);
+    a.in = (const cx<T> *)c;
+    a.out = (cx<T> *)fprime;
+    a.mode |= MODE_PRESCALE;
+    if (int rc = launch_cols<T>(p, a, false, s)) return rc;
+    return run_rows<T>(p, a, false, s);
+}
+
+// gx_j (+)= Re(conj(g_j) f'_j)
+template <typename T>
+__global__ void k_grad_x(const cx<T> *__restrict__ g, const cx<T> *__restrict__ fp, int64_t M, int acc,
+                         T *__restrict__ gx) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < M;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const cx<T> a = g[j], b = fp[j];
+        const T re = fma(a.x, b.x, a.y * b.y);
+        gx[j] = acc ? gx[j] + re : re;
+    }
+}
+
+template <typename T>
+int exec_grad_x(nufft_plan p, const void *g, const void *fprime, void *gx, int acc, cudaStream_t s) {
+    if (p->M == 0) return NUFFT_OK;
+    k_grad_x<T><<<grid1d(p->M), 256, 0, s>>>((const cx<T> *)g, (const cx<T> *)fprime, p->M, acc, (T *)gx);
+    NUFFT_CUDA_TRY(cudaGetLastError());
+    return NUFFT_OK;
 }
 
 template <typename T>
@@ -435,6 +494,22 @@ extern "C" int nufft2_exec_dx(nufft_plan p, const void *c_dev, const void *g_dev
     cudaStream_t s = (cudaStream_t)stream;
     return p->prec == NUFFT_F32 ? exec_dx<float>(p, c_dev, g_dev, gx_dev, accumulate, s)
                                 : exec_dx<double>(p, c_dev, g_dev, gx_dev, accumulate, s);
+}
+
+extern "C" int nufft2_exec_deriv(nufft_plan p, const void *c_dev, void *f_dev, void *fprime_dev,
+                                 void *stream) {
+    if (!p || !c_dev || (p->M > 0 && (!f_dev || !fprime_dev))) return NUFFT_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    return p->prec == NUFFT_F32 ? nufft::exec_deriv<float>(p, c_dev, f_dev, fprime_dev, s)
+                                : nufft::exec_deriv<double>(p, c_dev, f_dev, fprime_dev, s);
+}
+
+extern "C" int nufft2_grad_x(nufft_plan p, const void *g_dev, const void *fprime_dev, void *gx_dev,
+                             int accumulate, void *stream) {
+    if (!p || (p->M > 0 && (!g_dev || !fprime_dev || !gx_dev))) return NUFFT_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    return p->prec == NUFFT_F32 ? nufft::exec_grad_x<float>(p, g_dev, fprime_dev, gx_dev, accumulate, s)
+                                : nufft::exec_grad_x<double>(p, g_dev, fprime_dev, gx_dev, accumulate, s);
 }
 
 extern "C" int nufft2_exec_batch(nufft_plan p, int64_t B, const void *c_dev, int64_t ldc,

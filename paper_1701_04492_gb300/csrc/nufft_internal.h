@@ -37,14 +37,17 @@ struct nufft_plan_s {
     // execution geometry (fixed at plan time)
     int B2 = 1;            // grid rows per pass-2 bucket
     int NB = 1;            // number of buckets = L2 / B2
-    int G = 1;             // ranks staged together in pass 2 / pass A
-    int nt2 = 1;           // teams per pass-2 / pass-A CTA
+    int G = 1;             // ranks staged together in pass 2 (up to K + 1)
+    int nt2 = 1;           // teams per pass-2 CTA
+    int GA = 1;            // ranks staged together in pass A
+    int ntA = 1;           // teams per pass-A CTA
     int C1 = 1;            // columns per pass-1 CTA
     int CB = 1;            // columns per pass-B CTA
     int SBsplit = 1;       // rank splits of pass B (CTAs per column block)
     int chunkA = 512;      // samples staged per chunk in pass A
     size_t mbar_off2 = 0;  // byte offset of pass 2's mbarriers in its shared memory
-    size_t smem2 = 0;      // dynamic shared memory of pass 2 / A
+    size_t smem2 = 0;      // dynamic shared memory of pass 2
+    size_t smemA = 0;      // of pass A
     size_t smem1 = 0;      // of pass 1
     size_t smemB = 0;      // of pass B
     int S1 = 0, SB = 0, S2 = 0;   // slot strides (elements)
@@ -58,7 +61,7 @@ struct nufft_plan_s {
     double *d_j = nullptr;     // d in sample order, FP64 (unfused factors)
     void *twst1 = nullptr, *twst2 = nullptr;   // stage twiddle tables for lengths L1, L2
     void *twhi = nullptr, *twlo = nullptr;     // four-step twiddle, two levels
-    void *Y = nullptr;         // K * L complex: intermediate between the passes
+    void *Y = nullptr;         // (K + 1) * L complex: intermediate between the passes
     void *fscr = nullptr;      // M complex: partial sums when G < K
     void *cstage = nullptr, *fstage = nullptr;   // exec_host staging
     void *U = nullptr, *V = nullptr, *Xg = nullptr;   // unfused comparator

@@ -33,7 +33,9 @@ namespace nufft {
 enum PassMode : int {
     MODE_PLAIN_IN = 1,    // pass 1 reads a pre-scaled W_r instead of c
     MODE_PLAIN_OUT = 2,   // pass 2 writes X_r in natural order instead of gathering
-    MODE_DX = 4,          // pass 1 scales by -2 pi i k; pass 2 forms Re(conj(g) f')
+    MODE_PRESCALE = 4,    // pass 1 scales c by -2 pi i k (pass 2 then gathers f')
+    MODE_DERIV = 16,      // K + 1 ranks; pass 2 forms f and f' = df/dx from the same rows
+    MODE_GX = 32,         // pass 2 writes gx (+)= Re(conj(g) f') instead of a value
     MODE_FACTORS = 8      // read the plan's materialised U (sorted) and V instead of
                           // recomputing them (the FP64 plans: FP64 arithmetic is scarce)
 };
@@ -69,6 +71,9 @@ struct PassArgs {
     int chunk;            // pass A: samples staged per chunk
     int mbar_off;         // pass 2: byte offset of the slot mbarriers in shared memory
     int CQ, lgCQ;         // pass A/B: columns of pass B's tiles (the adjoint intermediate's tiling)
+    int nranks;           // ranks transformed: K, or K + 1 for MODE_DERIV
+    cx<T> *out2;          // MODE_DERIV: f' output (may be null)
+    T piN;                // pi N
     int *err;             // device error word (bounded waits that timed out)
     const T *vfac;        // MODE_FACTORS: V[r][k] = v_r(k) of eq. (2.6), K x N
     const cx<T> *ufac;    // MODE_FACTORS: U[i][r] = u_r(perm[i]) of eq. (2.6), sorted order, M x K
@@ -150,7 +155,7 @@ __global__ void __launch_bounds__(256, 2) k_pass1(const PassArgs<T> a) {
                 const int k = k0 + m * kstride;
                 const T w = k < a.N ? vr[k] : T(0);
                 cx<T> cv = v[m];
-                if (a.mode & MODE_DX) {
+                if (a.mode & MODE_PRESCALE) {
                     const T wk = T(6.283185307179586476925286766559) * T(k);
                     cv = mk<T>(wk * cv.y, -wk * cv.x);
                 }
@@ -187,7 +192,7 @@ __global__ void __launch_bounds__(256, 2) k_pass1(const PassArgs<T> a) {
                 T tr = r == 0 ? T(1) : tb[m];
                 if (odd) tr = fma(z2[m], tb[m], -ta[m]);
                 cx<T> cv = v[h0 + m];
-                if (a.mode & MODE_DX) {   // (-2 pi i k) c_k
+                if (a.mode & MODE_PRESCALE) {   // (-2 pi i k) c_k
                     const int k = k1 + a.L1 * (tt + TT * (h0 + m));
                     const T w = T(6.283185307179586476925286766559) * T(k);
                     cv = mk<T>(w * cv.y, -w * cv.x);
@@ -238,8 +243,8 @@ __global__ void __launch_bounds__(256) k_pass2(const PassArgs<T> a, const Beta<T
     __syncthreads();
     constexpr uint32_t ROW_BYTES = P1 * sizeof(cx<T>);
     int gi = 0;
-    for (int g0 = 0; g0 < a.K; g0 += Gs, ++gi) {
-        const int gc = min(Gs, a.K - g0);
+    for (int g0 = 0; g0 < a.nranks; g0 += Gs, ++gi) {
+        const int gc = min(Gs, a.nranks - g0);
         const int njobs = gc * a.B2;
         if (threadIdx.x == 0) {
             for (int q = 0; q < njobs; ++q) {
@@ -272,6 +277,61 @@ __global__ void __launch_bounds__(256) k_pass2(const PassArgs<T> a, const Beta<T
                 const int rl = rest / a.L1;
                 a.out[(int64_t)(g0 + rl) * a.L + (int64_t)a.L2 * n1 + b * a.B2 + row] =
                     smem[(rl * a.B2 + row) * a.S + padi<E>(n1)];
+            }
+        } else if ((a.mode & MODE_DERIV) && !kFactors<T>) {
+            // f and f' = df/dx from the K + 1 staged ranks (one group).  With
+            // k = N (z + 1)/2 and z T_r = (T_{r+1} + T_{r-1})/2, the rank-r term of
+            // A_K((-2 pi i k) o c) is -pi i N (X_r - i X_{r+1}/2 + i X_{r-1}/2) (r >= 1;
+            // X_0 - i X_1 for r = 0), so f'_j = -pi i N e^{-i pi d} sum_{s<=K} rho_s X_s[t_j]
+            // with rho_s = mu_s + i (mu_{s+1}/2 - mu_{s-1}/2 [s >= 2] - mu_0 [s = 1]).
+#pragma unroll 1
+            for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+                const int t = a.tsorted[i];
+                const int row = (t & L2m) - b * a.B2;
+                const int n1 = t >> a.lg2;
+                const T d = a.dsorted[i];
+                const T xi = d * a.inv_gamma;
+                T Tp[KM];
+                Tp[0] = T(1);
+                if (KM > 1) Tp[1] = xi;
+#pragma unroll
+                for (int q = 2; q < KM; ++q) Tp[q] = fma(T(2) * xi, Tp[q - 1], -Tp[q - 2]);
+                T mu[KM];
+#pragma unroll
+                for (int r = 0; r < KM; ++r) {
+                    T m = T(0);
+#pragma unroll
+                    for (int q = (r & 1); q < KM; q += 2) m = fma(beta.b[r][q], Tp[q], m);
+                    mu[r] = m;   // zero for r >= K (beta is zero-padded)
+                }
+                cx<T> S = mk<T>(0, 0), Sp = mk<T>(0, 0);
+#pragma unroll
+                for (int sidx = 0; sidx <= KM; ++sidx) {
+                    if (sidx < a.nranks) {
+                        const cx<T> x = smem[(sidx * a.B2 + row) * a.S + padi<E>(n1)];
+                        const T ms = sidx < KM ? mu[sidx] : T(0);
+                        T ri = sidx + 1 < KM ? T(0.5) * mu[sidx + 1] : T(0);
+                        if (sidx == 1) ri -= mu[0];
+                        if (sidx >= 2 && sidx - 1 < KM) ri -= T(0.5) * mu[sidx - 1];
+                        S.x = fma(ms, x.x, S.x);
+                        S.y = fma(ms, x.y, S.y);
+                        Sp.x = fma(ms, x.x, fma(-ri, x.y, Sp.x));
+                        Sp.y = fma(ms, x.y, fma(ri, x.x, Sp.y));
+                    }
+                }
+                T sn, cs;
+                sincospi_t<T>(d, &sn, &cs);
+                const cx<T> f = mk<T>(fma(S.x, cs, S.y * sn), fma(S.y, cs, -S.x * sn));
+                const cx<T> ph = mk<T>(fma(Sp.x, cs, Sp.y * sn), fma(Sp.y, cs, -Sp.x * sn));
+                const cx<T> fp = mk<T>(a.piN * ph.y, -a.piN * ph.x);   // -i pi N (phase Sp)
+                const int j = a.perm[i];
+                if (a.out) a.out[j] = f;
+                if (a.out2) a.out2[j] = fp;
+                if (a.mode & MODE_GX) {
+                    const cx<T> gg = a.g[j];
+                    const T re = fma(gg.x, fp.x, gg.y * fp.y);
+                    a.gx[j] = a.accumulate ? a.gx[j] + re : re;
+                }
             }
         } else {
 #pragma unroll 2
@@ -310,7 +370,7 @@ __global__ void __launch_bounds__(256) k_pass2(const PassArgs<T> a, const Beta<T
                         }
                     }
                 }
-                if (g0 + gc < a.K) {
+                if (g0 + gc < a.nranks) {
                     a.fscr[i] = acc;
                 } else {
                     cx<T> val = acc;
@@ -320,7 +380,7 @@ __global__ void __launch_bounds__(256) k_pass2(const PassArgs<T> a, const Beta<T
                         val = mk<T>(fma(acc.x, cs, acc.y * sn), fma(acc.y, cs, -acc.x * sn));
                     }
                     const int j = a.perm[i];
-                    if (a.mode & MODE_DX) {
+                    if (a.mode & MODE_GX) {
                         const cx<T> gg = a.g[j];
                         const T re = fma(gg.x, val.x, gg.y * val.y);
                         a.gx[j] = a.accumulate ? a.gx[j] + re : re;
@@ -651,7 +711,7 @@ int launch_cols(nufft_plan p, const PassArgs<T> &a0, bool adjoint, cudaStream_t 
         } else {
             auto kern = k_pass1<T, P>;
             if (int rc = set_smem(kern, smem, p->device, done_1)) return rc;
-            kern<<<dim3(p->L1 / a.C, p->K), block, smem, s>>>(a);
+            kern<<<dim3(p->L1 / a.C, a.nranks), block, smem, s>>>(a);
         }
         return launch_status();
     });
@@ -669,16 +729,17 @@ int launch_rows(nufft_plan p, const PassArgs<T> &a0, bool adjoint, cudaStream_t 
         a.S = p->S2;
         a.chunk = p->chunkA;
         a.mbar_off = (int)p->mbar_off2;
+        a.G = adjoint ? p->GA : p->G;
         a.CQ = p->CB;
         a.lgCQ = 0;
         while ((1 << a.lgCQ) < a.CQ) ++a.lgCQ;
         if (a.chunk <= 0) return NUFFT_EINVAL;
-        const dim3 block(p->nt2 * TT);
+        const dim3 block((adjoint ? p->ntA : p->nt2) * TT);
         static int done_a[64] = {}, done_2[64] = {};
         if (adjoint) {
             auto kern = k_passA<T, P, KM>;
-            if (int rc = set_smem(kern, p->smem2, p->device, done_a)) return rc;
-            kern<<<dim3(p->NB), block, p->smem2, s>>>(a, beta);
+            if (int rc = set_smem(kern, p->smemA, p->device, done_a)) return rc;
+            kern<<<dim3(p->NB), block, p->smemA, s>>>(a, beta);
         } else {
             auto kern = k_pass2<T, P, KM>;
             if (int rc = set_smem(kern, p->smem2, p->device, done_2)) return rc;

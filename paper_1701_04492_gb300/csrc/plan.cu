@@ -350,7 +350,7 @@ int plan_device(nufft_plan p, const double *x, cudaStream_t s) {
 
     // work buffers
     const size_t cxs = 2 * sizeof(T);
-    NUFFT_CUDA_TRY(cudaMalloc(&p->Y, (size_t)p->K * p->L * cxs));
+    NUFFT_CUDA_TRY(cudaMalloc(&p->Y, (size_t)(p->K + 1) * p->L * cxs));   // rank K: the derivative
     NUFFT_CUDA_TRY(cudaMalloc(&p->fscr, Mi * cxs));
     NUFFT_CUDA_TRY(cudaMalloc(&p->cstage, (size_t)p->N * cxs));
     NUFFT_CUDA_TRY(cudaMalloc(&p->fstage, Mi * cxs));
@@ -362,7 +362,7 @@ int plan_device(nufft_plan p, const double *x, cudaStream_t s) {
         NUFFT_CUDA_TRY(cudaMemsetAsync(p->counters, 0, (size_t)(p->L1 / p->CB) * sizeof(int), s));
         p->work_bytes += (int64_t)((size_t)p->SBsplit * p->L * cxs + (p->L1 / p->CB) * sizeof(int));
     }
-    p->work_bytes += (int64_t)(((size_t)p->K * p->L + 2 * Mi + p->N) * cxs);
+    p->work_bytes += (int64_t)(((size_t)(p->K + 1) * p->L + 2 * Mi + p->N) * cxs);
     if (p->flags & NUFFT_PLAN_UNFUSED) {
         if ((rc = plan_unfused_factors<T>(p, s))) return rc;
     }

@@ -247,3 +247,99 @@ def test_deterministic(api):
     # a second plan on the same samples gives the same bits
     plan2 = api.Plan(N, x, 1e-9, "f32")
     assert torch.equal(plan.forward(c), plan2.forward(c))
+
+
+# ---- the forward with its x-derivative in one exec, and autograd ---------------------------
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("N,L,M,kind", [(4096, 0, 4096, "uniform"), (3000, 0, 5000, "perturbed"),
+                                        (1000, 2048, 777, "uniform"), (1 << 20, 0, 1 << 20, "perturbed"),
+                                        (5, 0, 9, "equispaced")])
+def test_forward_deriv_against_oracle(api, prec, N, L, M, kind):
+    x = _samples(kind, M, 21) if kind != "equispaced" else np.arange(M) / N
+    c = _cast(wl.coeffs_cn(N, 21), prec)
+    plan = api.Plan(N, x, 1e-9, prec, L=L)
+    f, fp = plan.forward_deriv(_dev(c, _cdt(prec)))
+    P = lowrank.plan(N, x, 1e-9, plan.L)
+    assert _rel2(f.cpu().numpy(), lowrank.nufft2(P, c)) <= TOL_REL[prec]
+    ref = lowrank.nufft2(P, -2j * math.pi * np.arange(N) * c)
+    assert _rel2(fp.cpu().numpy(), ref) <= TOL_REL[prec] * 10
+    # the plain forward gives the same f
+    assert _rel2(f.cpu().numpy(), plan.forward(_dev(c, _cdt(prec))).cpu().numpy()) <= TOL_REL[prec]
+
+
+def test_grad_x_matches_dx(api):
+    N, M = 4096, 5000
+    x = wl.samples_uniform(M, 22)
+    c = _dev(wl.coeffs_cn(N, 22).astype(np.complex64), torch.complex64)
+    g = _dev(wl.cotangent_cn(M, 22).astype(np.complex64), torch.complex64)
+    plan = api.Plan(N, x, 1e-9, "f32")
+    f, fp = plan.forward_deriv(c)
+    gx = plan.grad_x(g, fp).cpu().numpy()
+    ref = np.real(np.conj(g.cpu().numpy()) * fp.cpu().numpy())
+    assert np.max(np.abs(gx - ref)) <= 1e-6 * np.max(np.abs(ref))
+    gx2 = plan.dx(c, g).cpu().numpy()
+    assert np.linalg.norm(gx - gx2) <= 1e-5 * np.linalg.norm(gx2)
+    acc = torch.full((M,), 2.0, dtype=torch.float32, device="cuda")
+    plan.grad_x(g, fp, acc, accumulate=True)
+    assert np.allclose(acc.cpu().numpy() - 2.0, gx, rtol=1e-5, atol=1e-5 * np.max(np.abs(gx)))
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_autograd_against_oracle(api, prec):
+    # loss = sum |f - f_target|^2 for a batch of coefficient vectors sharing x
+    N, M, B = 4096, 4096, 4
+    x = wl.samples_uniform(M, 23)
+    cs = np.stack([_cast(wl.coeffs_cn(N, 300 + b), prec) for b in range(B)])
+    ct = _cast(wl.coeffs_cn(N, 399), prec)
+    cdt = _cdt(prec)
+    plan = api.Plan(N, x, 1e-10, prec)
+    ftarget = plan.forward(_dev(ct, cdt))
+    xt = torch.tensor(x, dtype=torch.float64, device="cuda", requires_grad=True)
+    c = _dev(cs, cdt).requires_grad_(True)
+    f = api.nufft2(c, xt, plan=plan)
+    loss = ((f - ftarget[None, :]).abs() ** 2).sum()
+    loss.backward()
+    P = lowrank.plan(N, x, 1e-10, plan.L)
+    ftn = lowrank.nufft2(P, ct)
+    gc_ref, gx_ref = [], np.zeros(M)
+    for b in range(B):
+        fb = lowrank.nufft2(P, cs[b])
+        gb = 2.0 * (fb - ftn)                      # torch's gradient of |f - f*|^2 w.r.t. f
+        gc_ref.append(lowrank.nufft2_adjoint(P, gb))
+        gx_ref += lowrank.nufft2_dx(P, cs[b], gb)
+    tol = 1e-4 if prec == "f32" else 1e-10
+    assert _rel2(c.grad.cpu().numpy(), np.stack(gc_ref)) <= tol
+    assert _rel2(xt.grad.cpu().numpy(), gx_ref) <= tol
+
+
+def test_autograd_finite_differences_fp64(api):
+    # central differences of the loss in x (h = 1e-6) and in c, on the FP64 path at N = 200
+    N, M = 200, 150
+    x = wl.samples_uniform(M, 24)
+    c0 = wl.coeffs_cn(N, 24)
+    g0 = wl.cotangent_cn(M, 24)
+
+    def loss_of(xv, cv):
+        plan = api.Plan(N, xv, 1e-13, "f64")
+        f = plan.forward(_dev(cv, torch.complex128)).cpu().numpy()
+        return float(np.real(np.vdot(g0, f)))
+
+    plan = api.Plan(N, x, 1e-13, "f64")
+    xt = torch.tensor(x, dtype=torch.float64, device="cuda", requires_grad=True)
+    c = _dev(c0, torch.complex128).requires_grad_(True)
+    f = api.nufft2(c, xt, plan=plan)
+    (torch.conj(_dev(g0, torch.complex128)) * f).real.sum().backward()
+    h = 1e-6
+    for j in (0, 37, 149):
+        xp, xm = x.copy(), x.copy()
+        xp[j] += h
+        xm[j] -= h
+        fd = (loss_of(xp, c0) - loss_of(xm, c0)) / (2 * h)
+        assert abs(xt.grad[j].item() - fd) <= 1e-5 * max(1.0, abs(fd))
+    for k in (0, 99):
+        e = np.zeros(N, complex)
+        e[k] = 1.0
+        fd_re = (loss_of(x, c0 + h * e) - loss_of(x, c0 - h * e)) / (2 * h)
+        # torch's complex gradient: d loss / d Re c_k = Re(grad_k)
+        assert abs(c.grad[k].real.item() - fd_re) <= 1e-6 * max(1.0, abs(fd_re))
