@@ -266,6 +266,8 @@ extern "C" int nufft2_exec_noalloc(int64_t N, int64_t M, const double *x_dev, do
     a.lg1 = pl.lg1;
     a.lg2 = pl.lg2;
     a.K = pl.K;
+    a.nranks = pl.K;
+    a.piN = (float)(3.14159265358979323846 * (double)N);
     a.G = pl.G;
     a.B2 = pl.B2;
     a.mode = MODE_PLAIN_OUT;
