@@ -68,34 +68,35 @@ int plan_geometry(nufft_plan p) {
     const int maxt = std::max(1, 256 / TT1);
     p->chunkA = 512;
     const size_t staging = (size_t)p->chunkA * (sizeof(int32_t) + sizeof(T)) + (size_t)p->chunkA * cxs;
-    auto nslots = [&](int G, int nt) { return (size_t)((G * p->B2 + nt - 1) / nt) * nt; };
+    // one slot per staged row (idle teams need none)
+    auto nslots = [&](int G) { return (size_t)G * p->B2; };
     // pass 2: slots, then (16-byte aligned) one mbarrier per slot
-    auto body2 = [&](int G, int nt) { return (nslots(G, nt) * p->S2 * cxs + 15) / 16 * 16; };
-    auto bytes2 = [&](int G, int nt) { return body2(G, nt) + nslots(G, nt) * sizeof(uint64_t); };
+    auto body2 = [&](int G) { return (nslots(G) * p->S2 * cxs + 15) / 16 * 16; };
+    auto bytes2 = [&](int G, int nt) { return body2(G) + nslots(G) * sizeof(uint64_t) + 0 * nt; };
     // pass A: slots, four-step tables, staged samples
-    auto bytesA = [&](int G, int nt) { return (nslots(G, nt) * p->S2 + (size_t)nt * E1) * cxs + staging; };
-    // the largest group that fits, then the team count: the largest <= 256 threads
-    // dividing the group's B2 G row FFTs (no idle team), at least 64 threads
+    auto bytesA = [&](int G, int nt) { return (nslots(G) * p->S2 + (size_t)nt * E1) * cxs + staging; };
+    // teams for J row FFTs: the fewest rounds with at most 256 threads, then the
+    // fewest teams that still take that many rounds
+    auto teams = [&](int J) {
+        const int rounds = (J + maxt - 1) / maxt;
+        int nt = (J + rounds - 1) / rounds;
+        if (nt * TT1 < 64) nt = std::min(maxt, std::max(nt, (64 + TT1 - 1) / TT1));
+        return std::max(1, nt);
+    };
     auto choose = [&](int Gmax, auto bytes, int *Gout, int *ntout) -> bool {
         int G = Gmax;
-        while (G > 1 && bytes(G, 1) > SMEM_BUDGET) --G;
-        int nt = 1;
-        for (;;) {
-            nt = 1;
-            for (int d = 1; d <= maxt; ++d)
-                if ((G * p->B2) % d == 0) nt = d;
-            if (nt * TT1 < 64) nt = std::min(maxt, std::max(nt, 64 / TT1));
-            if (bytes(G, nt) <= SMEM_BUDGET || G == 1) break;
-            --G;
-        }
+        while (G > 1 && bytes(G, teams(G * p->B2)) > SMEM_BUDGET) --G;
         *Gout = G;
-        *ntout = nt;
-        return bytes(G, nt) <= SMEM_BUDGET;
+        *ntout = teams(G * p->B2);
+        return bytes(G, *ntout) <= SMEM_BUDGET;
     };
     // pass 2 stages up to K + 1 ranks (the derivative mode adds rank K)
-    if (!choose(p->K + 1, bytes2, &p->G, &p->nt2)) return NUFFT_EUNSUPPORTED;
-    p->mbar_off2 = body2(p->G, p->nt2);
-    p->smem2 = bytes2(p->G, p->nt2);
+    int nt_dummy = 1;
+    if (!choose(p->K + 1, bytes2, &p->G, &nt_dummy)) return NUFFT_EUNSUPPORTED;
+    p->nt2 = teams(std::min(p->G, p->K) * p->B2);   // forward: K ranks
+    p->nt2d = teams(p->G * p->B2);                  // derivative: K + 1 ranks
+    p->mbar_off2 = body2(p->G);
+    p->smem2 = bytes2(p->G, 1);
     if (!choose(p->K, bytesA, &p->GA, &p->ntA)) return NUFFT_EUNSUPPORTED;
     p->smemA = bytesA(p->GA, p->ntA);
     if (p->smem1 > SMEM_BUDGET || p->smemB > SMEM_BUDGET) return NUFFT_EUNSUPPORTED;

@@ -202,8 +202,10 @@ struct TeamFft {
 
     // Write the outputs of a stage (radix R after NS) to sm; read the inputs of the
     // next stage (radix Rn).
+    // act = false: the thread only takes part in the barriers (an idle team), so the
+    // teams of a CTA can differ in work while every thread meets the same barriers.
     template <int R, int NS, int Rn>
-    __device__ __forceinline__ static void exchange(cx<T> (&a)[E], int tt, cx<T>* sm) {
+    __device__ __forceinline__ static void exchange(cx<T> (&a)[E], int tt, cx<T>* sm, bool act) {
         static_assert(NS == 1 || NS % E == 0, "later stages follow a radix-E stage");
 #pragma unroll
         for (int b = 0; b < E / R; ++b) {
@@ -212,13 +214,17 @@ struct TeamFft {
                 // first stage (R = E): o = v E + i, padded v (E + 1) + i
                 static_assert(R == E, "the first stage has radix E");
                 const int pb = v * (E + 1);
+                if (act) {
 #pragma unroll
-                for (int i = 0; i < R; ++i) sm[pb + i] = a[b * R + i];
+                    for (int i = 0; i < R; ++i) sm[pb + i] = a[b * R + i];
+                }
             } else {
                 const int o0 = (v / NS) * NS * R + (v % NS);
                 const int pb = padi<E>(o0);
+                if (act) {
 #pragma unroll
-                for (int i = 0; i < R; ++i) sm[padi_run<E, NS>(pb, i)] = a[b * R + i];
+                    for (int i = 0; i < R; ++i) sm[padi_run<E, NS>(pb, i)] = a[b * R + i];
+                }
             }
         }
         __syncthreads();
@@ -228,8 +234,10 @@ struct TeamFft {
         for (int b = 0; b < E / Rn; ++b) {
             const int v = tt + TT * b;
             const int pb = padi<E>(v);
+            if (act) {
 #pragma unroll
-            for (int i = 0; i < Rn; ++i) a[b * Rn + i] = sm[padi_run<E, Vn>(pb, i)];
+                for (int i = 0; i < Rn; ++i) a[b * Rn + i] = sm[padi_run<E, Vn>(pb, i)];
+            }
         }
         __syncthreads();
     }
@@ -243,14 +251,15 @@ struct TeamFft {
     }
 
     // tw: this length's stage table (TW_SIZE entries, forward exponent).
+    // act = false: an idle team, which only meets the barriers.
     __device__ __forceinline__ static void run(cx<T> (&a)[E], int tt, cx<T>* sm,
-                                               const cx<T>* __restrict__ tw) {
+                                               const cx<T>* __restrict__ tw, bool act = true) {
         stage<R0, 1, 0>(a, tt, tw);
         if constexpr (R1 > 1) {
-            exchange<R0, 1, R1>(a, tt, sm);
+            exchange<R0, 1, R1>(a, tt, sm, act);
             stage<R1, R0, TW_OFF1>(a, tt, tw);
             if constexpr (R2 > 1) {
-                exchange<R1, R0, R2>(a, tt, sm);
+                exchange<R1, R0, R2>(a, tt, sm, act);
                 stage<R2, R0 * R1, TW_OFF2>(a, tt, tw);
             }
         }

@@ -236,8 +236,7 @@ __global__ void __launch_bounds__(256) k_pass2(const PassArgs<T> a, const Beta<T
     __shared__ int cta_failed;
     if (threadIdx.x == 0) {
         cta_failed = 0;
-        const int nsl = ((Gs * a.B2 + nt - 1) / nt) * nt;
-        for (int q = 0; q < nsl; ++q) mbar_init(&mbar[q], 1);
+        for (int q = 0; q < Gs * a.B2; ++q) mbar_init(&mbar[q], 1);
         fence_mbar_init();
     }
     __syncthreads();
@@ -255,16 +254,18 @@ __global__ void __launch_bounds__(256) k_pass2(const PassArgs<T> a, const Beta<T
         }
         for (int j0 = 0; j0 < njobs; j0 += nt) {
             const int job = j0 + team;
-            const bool act = job < njobs;
-            cx<T> *sm = smem + job * a.S;
+            const bool act = job < njobs;   // idle teams only meet the barriers
+            cx<T> *sm = smem + (act ? job : 0) * a.S;
             cx<T> v[E];
             if (act) mbar_wait_bounded(&mbar[job], gi & 1, a.err, &cta_failed);
 #pragma unroll
             for (int m = 0; m < E; ++m) v[m] = act ? sm[tt + TT * m] : mk<T>(0, 0);   // row as copied
             __syncthreads();   // the row is read before the transform reuses its slot
-            TF::run(v, tt, sm, a.twr);
+            TF::run(v, tt, sm, a.twr, act);
+            if (act) {
 #pragma unroll
-            for (int e = 0; e < E; ++e) sm[TF::out_padded(tt, e)] = v[e];
+                for (int e = 0; e < E; ++e) sm[TF::out_padded(tt, e)] = v[e];
+            }
         }
         __syncthreads();
         if (a.mode & MODE_PLAIN_OUT) {
@@ -411,8 +412,8 @@ __global__ void __launch_bounds__(256) k_passA(const PassArgs<T> a, const Beta<T
     for (int g0 = 0; g0 < a.K; g0 += Gs) {
         const int gc = min(Gs, a.K - g0);
         const int njobs = gc * a.B2;
-        const int nslots = ((njobs + nt - 1) / nt) * nt;
-        for (int idx = threadIdx.x; idx < nslots * a.S; idx += blockDim.x) smem[idx] = mk<T>(0, 0);
+        const int nslots = Gs * a.B2;   // fixed offsets for the tables and staging below
+        for (int idx = threadIdx.x; idx < njobs * a.S; idx += blockDim.x) smem[idx] = mk<T>(0, 0);
         __syncthreads();
         // the bucket's samples, staged chunk by chunk: t, d and the gathered g
         int32_t *st_t = reinterpret_cast<int32_t *>(smem + nslots * a.S + nt * E);
@@ -492,19 +493,20 @@ __global__ void __launch_bounds__(256) k_passA(const PassArgs<T> a, const Beta<T
         cx<T> *ftab = smem + nslots * a.S + team * E;   // this team's four-step table
         for (int j0 = 0; j0 < njobs; j0 += nt) {
             const int job = j0 + team;
-            const bool act = job < njobs;
+            const bool act = job < njobs;   // idle teams only meet the barriers
             const int rl = act ? job / a.B2 : 0, row = act ? job % a.B2 : 0;
             const int n2 = b * a.B2 + row;
-            cx<T> *sm = smem + job * a.S;
+            cx<T> *sm = smem + (act ? job : 0) * a.S;
             cx<T> v[E];
 #pragma unroll
             for (int m = 0; m < E; ++m) {
-                if constexpr (TT % E == 0) v[m] = sm[padi_run<E, TT>(padi<E>(tt), m)];
+                if (!act) v[m] = mk<T>(0, 0);
+                else if constexpr (TT % E == 0) v[m] = sm[padi_run<E, TT>(padi<E>(tt), m)];
                 else v[m] = sm[padi<E>(tt + TT * m)];
             }
             fill_fourstep<T, E, TT>(a, n2, tt, ftab, 1);
             __syncthreads();
-            TF::run(v, tt, sm, a.twr);
+            TF::run(v, tt, sm, a.twr, act);
             if (act) {
                 // column-tiled layout for pass B: Y'_r[k1 / CQ][n2][k1 % CQ], so each
                 // CQ-column tile of a rank is one contiguous block
@@ -734,7 +736,8 @@ int launch_rows(nufft_plan p, const PassArgs<T> &a0, bool adjoint, cudaStream_t 
         a.lgCQ = 0;
         while ((1 << a.lgCQ) < a.CQ) ++a.lgCQ;
         if (a.chunk <= 0) return NUFFT_EINVAL;
-        const dim3 block((adjoint ? p->ntA : p->nt2) * TT);
+        const int nt = adjoint ? p->ntA : (a.nranks > p->K ? p->nt2d : p->nt2);
+        const dim3 block(nt * TT);
         static int done_a[64] = {}, done_2[64] = {};
         if (adjoint) {
             auto kern = k_passA<T, P, KM>;
