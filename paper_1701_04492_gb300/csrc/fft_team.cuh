@@ -234,10 +234,10 @@ struct TeamFft {
         for (int b = 0; b < E / Rn; ++b) {
             const int v = tt + TT * b;
             const int pb = padi<E>(v);
-            if (act) {
+            // loads stay unconditional (an idle team reads its in-bounds slot and
+            // discards the values), so independent loads can be scheduled around them
 #pragma unroll
-                for (int i = 0; i < Rn; ++i) a[b * Rn + i] = sm[padi_run<E, Vn>(pb, i)];
-            }
+            for (int i = 0; i < Rn; ++i) a[b * Rn + i] = sm[padi_run<E, Vn>(pb, i)];
         }
         __syncthreads();
     }
