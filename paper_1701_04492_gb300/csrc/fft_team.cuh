@@ -202,9 +202,12 @@ struct TeamFft {
 
     // Write the outputs of a stage (radix R after NS) to sm; read the inputs of the
     // next stage (radix Rn).
-    // act = false: the thread only takes part in the barriers (an idle team), so the
-    // teams of a CTA can differ in work while every thread meets the same barriers.
-    template <int R, int NS, int Rn>
+    // PRED: a round in which some teams are idle.  A thread with act = false (an idle
+    // team) then only takes part in the barriers, so every thread meets the same
+    // barriers.  Full rounds take PRED = false: stores guarded by a branch cost about a
+    // quarter of a row pass's time, since the stage arithmetic can no longer be
+    // scheduled around them.
+    template <int R, int NS, int Rn, bool PRED>
     __device__ __forceinline__ static void exchange(cx<T> (&a)[E], int tt, cx<T>* sm, bool act) {
         static_assert(NS == 1 || NS % E == 0, "later stages follow a radix-E stage");
 #pragma unroll
@@ -214,14 +217,14 @@ struct TeamFft {
                 // first stage (R = E): o = v E + i, padded v (E + 1) + i
                 static_assert(R == E, "the first stage has radix E");
                 const int pb = v * (E + 1);
-                if (act) {
+                if (!PRED || act) {
 #pragma unroll
                     for (int i = 0; i < R; ++i) sm[pb + i] = a[b * R + i];
                 }
             } else {
                 const int o0 = (v / NS) * NS * R + (v % NS);
                 const int pb = padi<E>(o0);
-                if (act) {
+                if (!PRED || act) {
 #pragma unroll
                     for (int i = 0; i < R; ++i) sm[padi_run<E, NS>(pb, i)] = a[b * R + i];
                 }
@@ -251,15 +254,16 @@ struct TeamFft {
     }
 
     // tw: this length's stage table (TW_SIZE entries, forward exponent).
-    // act = false: an idle team, which only meets the barriers.
+    // PRED with act = false: an idle team, which only meets the barriers.
+    template <bool PRED = false>
     __device__ __forceinline__ static void run(cx<T> (&a)[E], int tt, cx<T>* sm,
                                                const cx<T>* __restrict__ tw, bool act = true) {
         stage<R0, 1, 0>(a, tt, tw);
         if constexpr (R1 > 1) {
-            exchange<R0, 1, R1>(a, tt, sm, act);
+            exchange<R0, 1, R1, PRED>(a, tt, sm, act);
             stage<R1, R0, TW_OFF1>(a, tt, tw);
             if constexpr (R2 > 1) {
-                exchange<R1, R0, R2>(a, tt, sm, act);
+                exchange<R1, R0, R2, PRED>(a, tt, sm, act);
                 stage<R2, R0 * R1, TW_OFF2>(a, tt, tw);
             }
         }

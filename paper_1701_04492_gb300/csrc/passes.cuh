@@ -252,20 +252,26 @@ __global__ void __launch_bounds__(256) k_pass2(const PassArgs<T> a, const Beta<T
                 bulk_copy_g2s(smem + q * a.S, src, ROW_BYTES, &mbar[q]);
             }
         }
-        for (int j0 = 0; j0 < njobs; j0 += nt) {
+        // one round of row FFTs, one job per team; PRED: a round with idle teams
+        auto round = [&](const int j0, auto pred) {
+            constexpr bool PRED = decltype(pred)::value;
             const int job = j0 + team;
-            const bool act = job < njobs;   // idle teams only meet the barriers
+            const bool act = !PRED || job < njobs;   // idle teams only meet the barriers
             cx<T> *sm = smem + (act ? job : 0) * a.S;
             cx<T> v[E];
             if (act) mbar_wait_bounded(&mbar[job], gi & 1, a.err, &cta_failed);
 #pragma unroll
             for (int m = 0; m < E; ++m) v[m] = act ? sm[tt + TT * m] : mk<T>(0, 0);   // row as copied
             __syncthreads();   // the row is read before the transform reuses its slot
-            TF::run(v, tt, sm, a.twr, act);
+            TF::template run<PRED>(v, tt, sm, a.twr, act);
             if (act) {
 #pragma unroll
                 for (int e = 0; e < E; ++e) sm[TF::out_padded(tt, e)] = v[e];
             }
+        };
+        for (int j0 = 0; j0 < njobs; j0 += nt) {
+            if (j0 + nt <= njobs) round(j0, std::false_type{});
+            else round(j0, std::true_type{});
         }
         __syncthreads();
         if (a.mode & MODE_PLAIN_OUT) {
@@ -491,9 +497,10 @@ __global__ void __launch_bounds__(256) k_passA(const PassArgs<T> a, const Beta<T
         }
         __syncthreads();
         cx<T> *ftab = smem + nslots * a.S + team * E;   // this team's four-step table
-        for (int j0 = 0; j0 < njobs; j0 += nt) {
+        auto round = [&](const int j0, auto pred) {   // PRED: a round with idle teams
+            constexpr bool PRED = decltype(pred)::value;
             const int job = j0 + team;
-            const bool act = job < njobs;   // idle teams only meet the barriers
+            const bool act = !PRED || job < njobs;   // idle teams only meet the barriers
             const int rl = act ? job / a.B2 : 0, row = act ? job % a.B2 : 0;
             const int n2 = b * a.B2 + row;
             cx<T> *sm = smem + (act ? job : 0) * a.S;
@@ -506,7 +513,7 @@ __global__ void __launch_bounds__(256) k_passA(const PassArgs<T> a, const Beta<T
             }
             fill_fourstep<T, E, TT>(a, n2, tt, ftab, 1);
             __syncthreads();
-            TF::run(v, tt, sm, a.twr, act);
+            TF::template run<PRED>(v, tt, sm, a.twr, act);
             if (act) {
                 // column-tiled layout for pass B: Y'_r[k1 / CQ][n2][k1 % CQ], so each
                 // CQ-column tile of a rank is one contiguous block
@@ -520,6 +527,10 @@ __global__ void __launch_bounds__(256) k_passA(const PassArgs<T> a, const Beta<T
                 }
             }
             __syncthreads();   // the next job refills ftab
+        };
+        for (int j0 = 0; j0 < njobs; j0 += nt) {
+            if (j0 + nt <= njobs) round(j0, std::false_type{});
+            else round(j0, std::true_type{});
         }
         __syncthreads();
     }
