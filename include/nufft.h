@@ -60,6 +60,19 @@ enum nufft_status {
                                   V (N x K) used by nufft2_exec_unfused */
 #define NUFFT_PLAN_TIMING 2u   /* record a CUDA event around every kernel the exec
                                   calls launch (see nufft_kernel_times) */
+#define NUFFT_PLAN_AUTOTUNE 4u /* with L = 0 (and no NUFFT_PLAN_LONG_COLUMNS): time the
+                                  candidate layouts -- the default grid L0 and the
+                                  oversampled 2 L0 (section 2.3), each with either
+                                  four-step split when log2 L is odd -- by one forward
+                                  and one adjoint exec each (CUDA events, best of 3
+                                  after a warm-up), and keep the fastest.  Choices are
+                                  cached per process by (device, N, M rounded up to a
+                                  power of two, eps, prec, K), so a repeated shape
+                                  plans once.  Synchronises `stream` per candidate. */
+#define NUFFT_PLAN_LONG_COLUMNS 16u /* for odd log2 L: the four-step split
+                                  L = L1 L2 takes the longer FFT on the columns
+                                  (L2 = 2 L1) instead of the rows (L1 = 2 L2).
+                                  Results agree to rounding; speeds differ. */
 
 /* Planning stage (section 2.3, "Planning the transform").
  *
@@ -187,6 +200,78 @@ int nufft_kernel_times(nufft_plan p, float *ms_out, int cap, int *count);
  * NUFFT_ECUDA. */
 int nufft2_exec_noalloc(int64_t N, int64_t M, const double *x_dev, double eps, const void *c_dev,
                         void *f_dev, void *stream);
+
+/* ---- Batches: many independent problems of uneven sizes ----------------------
+ *
+ * No counterpart in the paper, which plans and runs one transform at a time.  A
+ * batch is `count` independent NUFFT-II problems (its own N_i, M_i, x_i, eps_i
+ * each), each planned exactly as by nufft2_plan and run together: problems whose
+ * grids have the same length L and whose ranks share a rank bound (4, 8, 12, 16)
+ * form a class, and one kernel launch per pass covers a whole class, so a batch
+ * of 512 problems runs in a few dozen launches instead of 1024.  Batched launches
+ * cover NUFFT_F32 problems on grids of up to 2^18 points; other problems run their
+ * own plan's launches inside the batch calls.  Results are those of each problem's
+ * own plan (the same arithmetic in the same order).
+ *
+ * Packed layout: problem i's coefficients are c[offN_i .. offN_i + N_i) with
+ * offN_i = sum_{j<i} N_j; its samples (x, f, g) are [offM_i .. offM_i + M_i) with
+ * offM_i = sum_{j<i} M_j.  Precision, stream and ownership rules are those of the
+ * single-plan calls. */
+typedef struct nufft_batch_s *nufft_batch;
+
+#define NUFFT_BATCH_GRAPH 8u   /* nufft2_plan_many: a second exec call with the same
+                                  pointers captures the batch's launches as one CUDA
+                                  graph (each class a parallel branch); later calls
+                                  with those pointers replay it.  Other pointers run
+                                  the launches directly. */
+#define NUFFT_BATCH_PER_PROBLEM 32u /* nufft2_plan_many: run every problem with its
+                                  own plan's launches (with NUFFT_BATCH_GRAPH, one
+                                  parallel graph branch per problem) instead of
+                                  batched launches.  Always the case for NUFFT_F64
+                                  batches and for grids longer than 2^18 points. */
+
+/* Plan a batch.
+ *
+ *   out       receives the handle (NULL on failure).
+ *   count     number of problems, 1 <= count <= 65535.
+ *   N_host, M_host, eps_host   count entries each (host): as nufft2_plan's N, M, eps.
+ *   L_host    count grid sizes as nufft2_plan's L, or NULL (all 0: the default grid).
+ *   x_dev     sum M_i doubles on the device, packed; read during the call only.
+ *   prec      NUFFT_F32 or NUFFT_F64 for every problem.
+ *   flags     NUFFT_BATCH_GRAPH, NUFFT_BATCH_PER_PROBLEM, NUFFT_PLAN_AUTOTUNE (applied
+ *             to each problem's plan).
+ *
+ * Synchronises `stream` once per problem (each plan reads its gamma).  Errors: those
+ * of nufft2_plan for any problem (the batch is then not created), NUFFT_EINVAL. */
+int nufft2_plan_many(nufft_batch *out, int64_t count, const int64_t *N_host, const int64_t *M_host,
+                     const int64_t *L_host, const double *x_dev, const double *eps_host, int prec,
+                     unsigned flags, void *stream);
+
+/* Number of classes (= launches per pass), the packed lengths sum N_i and sum M_i,
+ * and per problem its rank K_i and grid size L_i (K_host, L_host: count entries or
+ * NULL).  Any output pointer may be NULL. */
+int nufft_batch_info(nufft_batch b, int64_t *classes, int64_t *total_N, int64_t *total_M, int *K_host,
+                     int64_t *L_host);
+
+/* Forward transform of every problem: f_i = A_i c_i (packed c: sum N_i, f: sum M_i
+ * complex values on the device).  Two launches per class. */
+int nufft2_exec_many(nufft_batch b, const void *c_dev, void *f_dev, void *stream);
+
+/* Adjoint of every problem: c_i = A_i^H g_i (packed g: sum M_i, c: sum N_i). */
+int nufft1_exec_many(nufft_batch b, const void *g_dev, void *c_dev, void *stream);
+
+/* The same transforms with one single-plan exec call per problem, in order (two
+ * launches per problem): the per-problem comparator of nufft2_exec_many /
+ * nufft1_exec_many.  adjoint = 0: c_dev -> f_dev (forward); 1: f_dev holds g and
+ * c_dev receives A^H g. */
+int nufft2_exec_each(nufft_batch b, const void *c_dev, void *f_dev, int adjoint, void *stream);
+
+/* nufft2_check over every problem of the batch (synchronises `stream`). */
+int nufft_batch_check(nufft_batch b, void *stream);
+
+/* Free the batch and its plans.  NULL is accepted.  Must not race with work in
+ * flight on the batch. */
+int nufft_batch_destroy(nufft_batch b);
 
 /* Synchronise `stream` and report whether any exec call on this plan since the
  * last check had a device-side wait give up (a bulk copy that did not complete

@@ -15,6 +15,10 @@ LIB_PATH = os.path.join(_PKG, "libnufft.so")
 NUFFT_F32, NUFFT_F64 = 0, 1
 NUFFT_PLAN_UNFUSED = 1
 NUFFT_PLAN_TIMING = 2
+NUFFT_PLAN_AUTOTUNE = 4
+NUFFT_BATCH_GRAPH = 8
+NUFFT_PLAN_LONG_COLUMNS = 16
+NUFFT_BATCH_PER_PROBLEM = 32
 STATUS = {0: "NUFFT_OK", -1: "NUFFT_EINVAL", -2: "NUFFT_ENOMEM", -3: "NUFFT_ECUDA",
           -4: "NUFFT_EUNSUPPORTED", -5: "NUFFT_ESTATE", -6: "NUFFT_ETIMEOUT"}
 
@@ -38,6 +42,13 @@ SIGNATURES = {
     "nufft2_check": (_i32, [_vp, _vp]),
     "nufft2_exec_noalloc": (_i32, [_i64, _i64, _vp, _dbl, _vp, _vp, _vp]),
     "nufft_strerror": (ctypes.c_char_p, [_i32]),
+    "nufft2_plan_many": (_i32, [ctypes.POINTER(_vp), _i64, _vp, _vp, _vp, _vp, _vp, _i32, _u32, _vp]),
+    "nufft_batch_info": (_i32, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64), _vp, _vp]),
+    "nufft2_exec_many": (_i32, [_vp, _vp, _vp, _vp]),
+    "nufft1_exec_many": (_i32, [_vp, _vp, _vp, _vp]),
+    "nufft2_exec_each": (_i32, [_vp, _vp, _vp, _i32, _vp]),
+    "nufft_batch_check": (_i32, [_vp, _vp]),
+    "nufft_batch_destroy": (_i32, [_vp]),
 }
 
 _lib = None

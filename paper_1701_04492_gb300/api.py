@@ -12,7 +12,8 @@ import ctypes
 import torch
 
 from . import _lib
-from ._lib import NUFFT_F32, NUFFT_F64, NUFFT_PLAN_TIMING, NUFFT_PLAN_UNFUSED, NufftError, check
+from ._lib import (NUFFT_BATCH_GRAPH, NUFFT_BATCH_PER_PROBLEM, NUFFT_F32, NUFFT_F64, NUFFT_PLAN_AUTOTUNE, NUFFT_PLAN_LONG_COLUMNS,
+                   NUFFT_PLAN_TIMING, NUFFT_PLAN_UNFUSED, NufftError, check)
 
 _CDTYPE = {NUFFT_F32: torch.complex64, NUFFT_F64: torch.complex128}
 _RDTYPE = {NUFFT_F32: torch.float32, NUFFT_F64: torch.float64}
@@ -45,9 +46,13 @@ class Plan:
     precision : 'f32' (complex64 exec) or 'f64' (complex128 exec)
     L : grid size (0 = smallest power of two >= max(N, 1024); L > N oversamples)
     unfused : also build the materialised factors for :meth:`forward_unfused`
+    timing : record per-kernel device times (:meth:`kernel_times`)
+    autotune : with L = 0, time the grid L0 against 2 L0 and both four-step splits, keep the fastest
+    long_columns : for odd log2 L, put the longer FFT of the four-step split on the columns
     """
 
-    def __init__(self, N, x, eps, precision="f32", L=0, unfused=False, timing=False, device=None):
+    def __init__(self, N, x, eps, precision="f32", L=0, unfused=False, timing=False, device=None,
+                 autotune=False, long_columns=False):
         lib = _lib.load()
         device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         if not isinstance(x, torch.Tensor):
@@ -61,7 +66,9 @@ class Plan:
         with torch.cuda.device(device):
             rc = lib.nufft2_plan(ctypes.byref(h), self.N, self.M, _ptr(x) if self.M else None,
                                  float(eps), self.prec, int(L),
-                                 (NUFFT_PLAN_UNFUSED if unfused else 0) | (NUFFT_PLAN_TIMING if timing else 0),
+                                 (NUFFT_PLAN_UNFUSED if unfused else 0) | (NUFFT_PLAN_TIMING if timing else 0)
+                                 | (NUFFT_PLAN_AUTOTUNE if autotune else 0)
+                                 | (NUFFT_PLAN_LONG_COLUMNS if long_columns else 0),
                                  _stream(device))
         check(rc, "nufft2_plan")
         self._h = h
@@ -269,3 +276,115 @@ def nufft2(c, x, eps=1e-9, plan=None, L=0):
 
 
 __all__ = ["Plan", "nufft2", "NufftError", "NUFFT_F32", "NUFFT_F64"]
+
+
+class Batch:
+    """Many independent NUFFT-II problems of uneven sizes, run together.
+
+    Problem i has N[i] frequencies, the samples ``xs[i]`` and accuracy ``eps[i]``; each
+    is planned as by :class:`Plan`.  Problems sharing a grid length and rank bound run
+    in one launch per pass.  Data is packed: coefficients are one tensor of sum(N)
+    values, problem i's at ``offN[i]:offN[i+1]``; samples, values and cotangents one of
+    sum(M), problem i's at ``offM[i]:offM[i+1]``.
+
+    graph : replay a CUDA graph of the launches when called again with the same tensors
+    per_problem : each problem runs its own plan's launches (no batched launches)
+    autotune : tune each problem's grid and split (see :class:`Plan`)
+    L : optional per-problem grid sizes (0 = default)
+    """
+
+    def __init__(self, Ns, xs, eps, precision="f32", graph=False, autotune=False, L=None, device=None,
+                 per_problem=False):
+        import numpy as np
+        lib = _lib.load()
+        device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.device = device
+        self.count = len(Ns)
+        xs = [torch.as_tensor(x).detach().to(device=device, dtype=torch.float64).reshape(-1) for x in xs]
+        if len(xs) != self.count:
+            raise ValueError("one sample vector per problem")
+        epsv = np.broadcast_to(np.asarray(eps, dtype=np.float64), (self.count,)).copy()
+        self.N = np.asarray(Ns, dtype=np.int64)
+        self.M = np.asarray([x.numel() for x in xs], dtype=np.int64)
+        self.offN = np.concatenate([[0], np.cumsum(self.N)])
+        self.offM = np.concatenate([[0], np.cumsum(self.M)])
+        self.prec = _prec(precision)
+        self.cdtype = _CDTYPE[self.prec]
+        xp = torch.cat(xs) if self.count else torch.empty(0, dtype=torch.float64, device=device)
+        Lv = np.zeros(self.count, dtype=np.int64) if L is None else np.asarray(L, dtype=np.int64)
+        flags = ((NUFFT_BATCH_GRAPH if graph else 0) | (NUFFT_PLAN_AUTOTUNE if autotune else 0)
+                 | (NUFFT_BATCH_PER_PROBLEM if per_problem else 0))
+        h = ctypes.c_void_p()
+        with torch.cuda.device(device):
+            rc = lib.nufft2_plan_many(ctypes.byref(h), self.count, self.N.ctypes.data, self.M.ctypes.data,
+                                      Lv.ctypes.data, _ptr(xp) if xp.numel() else None, epsv.ctypes.data,
+                                      self.prec, flags, _stream(device))
+        check(rc, "nufft2_plan_many")
+        self._h = h
+        ncls, tn, tm = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        K = np.zeros(self.count, dtype=np.int32)
+        Lo = np.zeros(self.count, dtype=np.int64)
+        check(lib.nufft_batch_info(h, ctypes.byref(ncls), ctypes.byref(tn), ctypes.byref(tm), K.ctypes.data,
+                                   Lo.ctypes.data), "nufft_batch_info")
+        self.classes, self.total_N, self.total_M = ncls.value, tn.value, tm.value
+        self.K, self.L = K, Lo
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            torch.cuda.synchronize(self.device)
+            _lib.load().nufft_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _cx(self, t, n, name):
+        if t.device != self.device or t.dtype != self.cdtype or not t.is_contiguous() or t.numel() != n:
+            raise ValueError("%s must be a contiguous %s tensor of %d elements on %s"
+                             % (name, self.cdtype, n, self.device))
+        return t
+
+    def _run(self, fn, a, na, b, nb, what):
+        self._cx(a, na, "input")
+        self._cx(b, nb, "output")
+        with torch.cuda.device(self.device):
+            check(fn(self._h, _ptr(a), _ptr(b), _stream(self.device)), what)
+        return b
+
+    def forward(self, c, out=None):
+        """f_i = A_i c_i for every problem (packed)."""
+        f = out if out is not None else torch.empty(self.total_M, dtype=self.cdtype, device=self.device)
+        return self._run(_lib.load().nufft2_exec_many, c, self.total_N, f, self.total_M, "nufft2_exec_many")
+
+    def adjoint(self, g, out=None):
+        """c_i = A_i^H g_i for every problem (packed)."""
+        c = out if out is not None else torch.empty(self.total_N, dtype=self.cdtype, device=self.device)
+        return self._run(_lib.load().nufft1_exec_many, g, self.total_M, c, self.total_N, "nufft1_exec_many")
+
+    def forward_each(self, c, out=None):
+        """The forward with one single-plan exec per problem (the per-problem comparator)."""
+        f = out if out is not None else torch.empty(self.total_M, dtype=self.cdtype, device=self.device)
+        self._cx(c, self.total_N, "c")
+        self._cx(f, self.total_M, "f")
+        with torch.cuda.device(self.device):
+            check(_lib.load().nufft2_exec_each(self._h, _ptr(c), _ptr(f), 0, _stream(self.device)),
+                  "nufft2_exec_each")
+        return f
+
+    def adjoint_each(self, g, out=None):
+        """The adjoint with one single-plan exec per problem."""
+        c = out if out is not None else torch.empty(self.total_N, dtype=self.cdtype, device=self.device)
+        self._cx(g, self.total_M, "g")
+        self._cx(c, self.total_N, "c")
+        with torch.cuda.device(self.device):
+            check(_lib.load().nufft2_exec_each(self._h, _ptr(c), _ptr(g), 1, _stream(self.device)),
+                  "nufft2_exec_each")
+        return c
+
+    def check(self):
+        """Synchronise and raise NufftError(NUFFT_ETIMEOUT) if a device-side wait gave up."""
+        with torch.cuda.device(self.device):
+            check(_lib.load().nufft_batch_check(self._h, _stream(self.device)), "nufft_batch_check")

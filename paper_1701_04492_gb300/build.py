@@ -43,7 +43,14 @@ def _headers():
 
 
 def sources():
-    return sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
+    """Translation units, the slowest to compile (the FP32 row and batched passes) first."""
+    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
+    order = ("inst_rows_f32", "inst_many_f32", "inst_cols_f32", "inst_many_cols", "inst_rows_f64")
+
+    def rank(path):
+        name = os.path.basename(path)
+        return next((i for i, pre in enumerate(order) if name.startswith(pre)), len(order))
+    return sorted(srcs, key=rank)
 
 
 def _compile(src, force, hdr_mtime):

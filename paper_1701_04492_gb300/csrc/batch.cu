@@ -1,0 +1,386 @@
+// batch.cu -- many independent NUFFT-II problems of uneven sizes in few launches.
+//
+// Each problem has its own plan (rounding, rank, sort, tables: section 2.3's
+// planning stage, one per problem).  Problems whose grids have the same length L and
+// whose ranks share a rank bound KM form a class; one launch per pass then covers a
+// whole class (blockIdx.z = the problem), reading each problem's arguments from a
+// device array built here once.  Batched launches exist for FP32 problems on grids
+// of up to 2^18 points; a larger problem fills the GPU alone, and an FP64 problem
+// (or any problem with NUFFT_BATCH_PER_PROBLEM) runs with its own plan's launches,
+// a class of its own.  Inputs and outputs are packed: problem i's coefficients
+// start at sum_{j<i} N_j, its samples at sum_{j<i} M_j.
+//
+// With NUFFT_BATCH_GRAPH, a call whose pointers equal the previous call's replays a
+// CUDA graph of all launches, each class a parallel branch; the graph is captured on
+// the first such call (the eager call before it has set every kernel attribute).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <new>
+#include <type_traits>
+#include <vector>
+
+#include "passes.cuh"
+
+namespace nufft {
+NUFFT_DECLARE_COLS_MANY()
+NUFFT_DECLARE_MANY(4)
+NUFFT_DECLARE_MANY(8)
+NUFFT_DECLARE_MANY(12)
+NUFFT_DECLARE_MANY(16)
+}  // namespace nufft
+
+struct nufft_batch_s {
+    struct Class {
+        int64_t L = 0;
+        int KM = 0;
+        bool single = false;    // one large problem: its own plan's launches
+        std::vector<int> idx;   // members (problem indices)
+        int rep = -1;           // member whose launch geometry covers the class
+        int ny1 = 1, nyB = 1;   // grid.y of pass 1 (largest K) and pass B (largest split)
+        void *a1 = nullptr, *a2 = nullptr, *aA = nullptr, *aB = nullptr, *betas = nullptr;
+        cudaStream_t st = nullptr;   // its branch while a graph is captured
+        cudaEvent_t done = nullptr;
+    };
+    int prec = 0;
+    unsigned flags = 0;
+    std::vector<nufft_plan> plans;
+    std::vector<int64_t> offN, offM;   // count + 1 prefix sums
+    std::vector<Class> cls;
+    // graph state, [0] forward, [1] adjoint
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    const void *gin[2] = {nullptr, nullptr};
+    void *gout[2] = {nullptr, nullptr};
+    const void *lastin[2] = {nullptr, nullptr};
+    void *lastout[2] = {nullptr, nullptr};
+    cudaStream_t cap = nullptr;
+    cudaEvent_t fork = nullptr;
+};
+
+namespace nufft {
+namespace {
+
+void free_batch(nufft_batch b) {
+    if (!b) return;
+    for (auto &c : b->cls) {
+        for (void *q : {c.a1, c.a2, c.aA, c.aB, c.betas})
+            if (q) cudaFree(q);
+        if (c.st) cudaStreamDestroy(c.st);
+        if (c.done) cudaEventDestroy(c.done);
+    }
+    for (cudaGraphExec_t g : b->gexec)
+        if (g) cudaGraphExecDestroy(g);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->fork) cudaEventDestroy(b->fork);
+    for (nufft_plan p : b->plans)
+        if (p) nufft_destroy(p);
+    delete b;
+}
+
+template <typename V>
+int upload(void **dst, const std::vector<V> &h) {
+    NUFFT_CUDA_TRY(cudaMalloc(dst, h.size() * sizeof(V)));
+    NUFFT_CUDA_TRY(cudaMemcpy(*dst, h.data(), h.size() * sizeof(V), cudaMemcpyHostToDevice));
+    return NUFFT_OK;
+}
+
+// The four argument arrays and the coefficient tables of one class.
+template <typename T, int KM>
+int build_class(nufft_batch b, nufft_batch_s::Class &c) {
+    std::vector<PassArgs<T>> v1, v2, vA, vB;
+    std::vector<Beta<T, KM>> be;
+    for (int i : c.idx) {
+        nufft_plan p = b->plans[i];
+        const PassArgs<T> a = base_args<T>(p);
+        PassArgs<T> x1 = a, x2 = a, xA = a, xB = a;
+        cols_fields<T>(p, x1, false);
+        if (int rc = rows_fields<T>(p, x2, false)) return rc;
+        if (int rc = rows_fields<T>(p, xA, true)) return rc;
+        cols_fields<T>(p, xB, true);
+        // forward: in = c, out = f; adjoint: in = g, out = c
+        x1.in_off = x2.in_off = b->offN[i];
+        x1.out_off = x2.out_off = b->offM[i];
+        xA.in_off = xB.in_off = b->offM[i];
+        xA.out_off = xB.out_off = b->offN[i];
+        v1.push_back(x1);
+        v2.push_back(x2);
+        vA.push_back(xA);
+        vB.push_back(xB);
+        be.push_back(beta_of<T, KM>(p));
+        c.ny1 = std::max(c.ny1, p->K);
+        c.nyB = std::max(c.nyB, p->SBsplit);
+    }
+    if (int rc = upload(&c.a1, v1)) return rc;
+    if (int rc = upload(&c.a2, v2)) return rc;
+    if (int rc = upload(&c.aA, vA)) return rc;
+    if (int rc = upload(&c.aB, vB)) return rc;
+    return upload(&c.betas, be);
+}
+
+int build_class_f32(nufft_batch b, nufft_batch_s::Class &c) {
+    switch (c.KM) {
+        case 4: return build_class<float, 4>(b, c);
+        case 8: return build_class<float, 8>(b, c);
+        case 12: return build_class<float, 12>(b, c);
+        case 16: return build_class<float, 16>(b, c);
+        default: return NUFFT_EUNSUPPORTED;
+    }
+}
+
+int rows_many(const nufft_batch_s::Class &c, nufft_plan rep, const void *args, bool adjoint,
+              const void *in, void *out, cudaStream_t s) {
+    using T = float;
+    const int n = (int)c.idx.size();
+    const PassArgs<T> *a = (const PassArgs<T> *)args;
+    switch (c.KM) {
+        case 4: return launch_rows_many<T, 4>(rep, a, (const Beta<T, 4> *)c.betas, n, adjoint, in, out, s);
+        case 8: return launch_rows_many<T, 8>(rep, a, (const Beta<T, 8> *)c.betas, n, adjoint, in, out, s);
+        case 12: return launch_rows_many<T, 12>(rep, a, (const Beta<T, 12> *)c.betas, n, adjoint, in, out, s);
+        case 16: return launch_rows_many<T, 16>(rep, a, (const Beta<T, 16> *)c.betas, n, adjoint, in, out, s);
+        default: return NUFFT_EUNSUPPORTED;
+    }
+}
+
+// The launches of one class, in order, on stream s: two batched launches, or a
+// single problem's own exec call.
+template <typename T>
+int class_launches(nufft_batch b, const nufft_batch_s::Class &c, bool adjoint, const void *in,
+                   void *out, cudaStream_t s) {
+    nufft_plan rep = b->plans[c.rep];
+    const int n = (int)c.idx.size();
+    if (c.single) {
+        const size_t cxs = 2 * sizeof(T);
+        const int i = c.idx[0];
+        const char *src = (const char *)in + (size_t)(adjoint ? b->offM[i] : b->offN[i]) * cxs;
+        char *dst = (char *)out + (size_t)(adjoint ? b->offN[i] : b->offM[i]) * cxs;
+        return adjoint ? nufft1_exec(rep, src, dst, s) : nufft2_exec(rep, src, dst, s);
+    }
+    if constexpr (std::is_same<T, float>::value) {
+        if (!adjoint) {
+            if (int rc = launch_cols_many<T>(rep, (const PassArgs<T> *)c.a1, n, c.ny1, false, in, out, s)) return rc;
+            return rows_many(c, rep, c.a2, false, in, out, s);
+        }
+        if (int rc = rows_many(c, rep, c.aA, true, in, out, s)) return rc;
+        return launch_cols_many<T>(rep, (const PassArgs<T> *)c.aB, n, c.nyB, true, in, out, s);
+    } else {
+        return NUFFT_EUNSUPPORTED;   // FP64 classes are single problems
+    }
+}
+
+template <typename T>
+int launch_all(nufft_batch b, bool adjoint, const void *in, void *out, cudaStream_t s) {
+    for (const auto &c : b->cls)
+        if (int rc = class_launches<T>(b, c, adjoint, in, out, s)) return rc;
+    return NUFFT_OK;
+}
+
+// Capture every class as a parallel branch of one graph (fork from b->cap, join back).
+template <typename T>
+int capture(nufft_batch b, int dir, const void *in, void *out) {
+    if (b->gexec[dir]) {
+        cudaGraphExecDestroy(b->gexec[dir]);
+        b->gexec[dir] = nullptr;
+    }
+    NUFFT_CUDA_TRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    int rc = NUFFT_OK;
+    if (cudaEventRecord(b->fork, b->cap) != cudaSuccess) rc = NUFFT_ECUDA;
+    for (auto &c : b->cls) {
+        if (rc) break;
+        if (cudaStreamWaitEvent(c.st, b->fork, 0) != cudaSuccess) { rc = NUFFT_ECUDA; break; }
+        rc = class_launches<T>(b, c, dir == 1, in, out, c.st);
+        if (!rc && (cudaEventRecord(c.done, c.st) != cudaSuccess ||
+                    cudaStreamWaitEvent(b->cap, c.done, 0) != cudaSuccess))
+            rc = NUFFT_ECUDA;
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(b->cap, &g);
+    if (!rc && e != cudaSuccess) rc = NUFFT_ECUDA;
+    if (!rc && cudaGraphInstantiate(&b->gexec[dir], g, 0) != cudaSuccess) {
+        b->gexec[dir] = nullptr;
+        rc = NUFFT_ECUDA;
+    }
+    if (g) cudaGraphDestroy(g);
+    if (rc) (void)cudaGetLastError();
+    b->gin[dir] = in;
+    b->gout[dir] = out;
+    return rc;
+}
+
+template <typename T>
+int exec_many(nufft_batch b, bool adjoint, const void *in, void *out, cudaStream_t s) {
+    const int dir = adjoint ? 1 : 0;
+    if (b->flags & NUFFT_BATCH_GRAPH) {
+        if (b->gexec[dir] && b->gin[dir] == in && b->gout[dir] == out) {
+            NUFFT_CUDA_TRY(cudaGraphLaunch(b->gexec[dir], s));
+            return NUFFT_OK;
+        }
+        if (b->lastin[dir] == in && b->lastout[dir] == out) {   // second call: capture
+            if (int rc = capture<T>(b, dir, in, out)) return rc;
+            NUFFT_CUDA_TRY(cudaGraphLaunch(b->gexec[dir], s));
+            return NUFFT_OK;
+        }
+    }
+    b->lastin[dir] = in;
+    b->lastout[dir] = out;
+    return launch_all<T>(b, adjoint, in, out, s);
+}
+
+}  // namespace
+}  // namespace nufft
+
+using nufft::free_batch;
+
+extern "C" int nufft2_plan_many(nufft_batch *out, int64_t count, const int64_t *N_host,
+                                const int64_t *M_host, const int64_t *L_host, const double *x_dev,
+                                const double *eps_host, int prec, unsigned flags, void *stream) {
+    using namespace nufft;
+    if (!out) return NUFFT_EINVAL;
+    *out = nullptr;
+    if (count < 1 || count > 65535 || !N_host || !M_host || !eps_host) return NUFFT_EINVAL;
+    if (prec != NUFFT_F32 && prec != NUFFT_F64) return NUFFT_EINVAL;
+    if (flags & ~(NUFFT_BATCH_GRAPH | NUFFT_BATCH_PER_PROBLEM | NUFFT_PLAN_AUTOTUNE)) return NUFFT_EINVAL;
+    int64_t totM = 0;
+    for (int64_t i = 0; i < count; ++i) {
+        if (M_host[i] < 0 || M_host[i] >= ((int64_t)1 << 31)) return NUFFT_EINVAL;
+        totM += M_host[i];
+    }
+    if (totM > 0 && !x_dev) return NUFFT_EINVAL;
+    nufft_batch b = new (std::nothrow) nufft_batch_s();
+    if (!b) return NUFFT_ENOMEM;
+    b->prec = prec;
+    b->flags = flags;
+    b->plans.assign((size_t)count, nullptr);
+    b->offN.assign((size_t)count + 1, 0);
+    b->offM.assign((size_t)count + 1, 0);
+    for (int64_t i = 0; i < count; ++i) {
+        b->offN[i + 1] = b->offN[i] + N_host[i];
+        b->offM[i + 1] = b->offM[i] + M_host[i];
+    }
+    const unsigned pflags = flags & NUFFT_PLAN_AUTOTUNE;
+    for (int64_t i = 0; i < count; ++i) {
+        const int rc = nufft2_plan(&b->plans[i], N_host[i], M_host[i], x_dev ? x_dev + b->offM[i] : nullptr,
+                                   eps_host[i], prec, L_host ? L_host[i] : 0, pflags, stream);
+        if (rc) { free_batch(b); return rc; }
+    }
+    // classes: same L and rank bound; the representative has the largest K
+    for (int64_t i = 0; i < count; ++i) {
+        nufft_plan p = b->plans[i];
+        const bool single = prec == NUFFT_F64 || (flags & NUFFT_BATCH_PER_PROBLEM) ||
+                            std::max(p->L1, p->L2) > MANY_P_MAX;
+        auto it = std::find_if(b->cls.begin(), b->cls.end(), [&](const nufft_batch_s::Class &c) {
+            return !single && !c.single && c.L == p->L && c.KM == p->kmax;
+        });
+        if (it == b->cls.end()) {
+            b->cls.emplace_back();
+            it = b->cls.end() - 1;
+            it->L = p->L;
+            it->KM = p->kmax;
+            it->single = single;
+        }
+        it->idx.push_back((int)i);
+        if (it->rep < 0 || b->plans[it->rep]->K < p->K) it->rep = (int)i;
+    }
+    // every member must fit the representative's shared-memory layouts (pass 2: its
+    // own slots and mbarriers; pass A: its slots plus the launch's team tables);
+    // a member that does not becomes a class of its own
+    std::vector<nufft_batch_s::Class> own_classes;
+    for (auto &c : b->cls) {
+        if (c.single) continue;
+        nufft_plan r = b->plans[c.rep];
+        const size_t E1 = (size_t)std::min<int>(EmaxT<float>::v, r->L1);
+        for (size_t q = 0; q < c.idx.size();) {
+            nufft_plan m = b->plans[c.idx[q]];
+            const size_t needA = m->smemA + (size_t)std::max(0, r->ntA - m->ntA) * E1 * 8;
+            if (m->smem2 <= r->smem2 && needA <= r->smemA && m->smem1 <= r->smem1 && m->smemB <= r->smemB) {
+                ++q;
+                continue;
+            }
+            nufft_batch_s::Class own;
+            own.L = m->L;
+            own.KM = m->kmax;
+            own.single = true;
+            own.idx.push_back(c.idx[q]);
+            own.rep = c.idx[q];
+            c.idx.erase(c.idx.begin() + (long)q);
+            own_classes.push_back(own);
+        }
+    }
+    b->cls.insert(b->cls.end(), own_classes.begin(), own_classes.end());
+    for (auto &c : b->cls) {
+        const int rc = c.single ? NUFFT_OK : build_class_f32(b, c);
+        if (rc) { free_batch(b); return rc; }
+        if (flags & NUFFT_BATCH_GRAPH) {
+            if (cudaStreamCreateWithFlags(&c.st, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming) != cudaSuccess) {
+                (void)cudaGetLastError();
+                free_batch(b);
+                return NUFFT_ECUDA;
+            }
+        }
+    }
+    if (flags & NUFFT_BATCH_GRAPH) {
+        if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) {
+            (void)cudaGetLastError();
+            free_batch(b);
+            return NUFFT_ECUDA;
+        }
+    }
+    *out = b;
+    return NUFFT_OK;
+}
+
+extern "C" int nufft_batch_info(nufft_batch b, int64_t *classes, int64_t *total_N, int64_t *total_M,
+                                int *K_host, int64_t *L_host) {
+    if (!b) return NUFFT_EINVAL;
+    if (classes) *classes = (int64_t)b->cls.size();
+    if (total_N) *total_N = b->offN.back();
+    if (total_M) *total_M = b->offM.back();
+    for (size_t i = 0; i < b->plans.size(); ++i) {
+        if (K_host) K_host[i] = b->plans[i]->K;
+        if (L_host) L_host[i] = b->plans[i]->L;
+    }
+    return NUFFT_OK;
+}
+
+extern "C" int nufft2_exec_many(nufft_batch b, const void *c_dev, void *f_dev, void *stream) {
+    if (!b || !c_dev || (b->offM.back() > 0 && !f_dev)) return NUFFT_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    return b->prec == NUFFT_F32 ? nufft::exec_many<float>(b, false, c_dev, f_dev, s)
+                                : nufft::exec_many<double>(b, false, c_dev, f_dev, s);
+}
+
+extern "C" int nufft1_exec_many(nufft_batch b, const void *g_dev, void *c_dev, void *stream) {
+    if (!b || !c_dev || (b->offM.back() > 0 && !g_dev)) return NUFFT_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    return b->prec == NUFFT_F32 ? nufft::exec_many<float>(b, true, g_dev, c_dev, s)
+                                : nufft::exec_many<double>(b, true, g_dev, c_dev, s);
+}
+
+extern "C" int nufft2_exec_each(nufft_batch b, const void *c_dev, void *f_dev, int adjoint, void *stream) {
+    if (!b || !c_dev || (b->offM.back() > 0 && !f_dev)) return NUFFT_EINVAL;
+    const size_t cxs = b->prec == NUFFT_F32 ? 8 : 16;
+    for (size_t i = 0; i < b->plans.size(); ++i) {
+        const char *cb = (const char *)c_dev + (size_t)b->offN[i] * cxs;
+        char *fb = (char *)f_dev + (size_t)b->offM[i] * cxs;
+        const int rc = adjoint ? nufft1_exec(b->plans[i], fb, (void *)cb, stream)
+                               : nufft2_exec(b->plans[i], cb, fb, stream);
+        if (rc) return rc;
+    }
+    return NUFFT_OK;
+}
+
+extern "C" int nufft_batch_check(nufft_batch b, void *stream) {
+    if (!b) return NUFFT_EINVAL;
+    int worst = NUFFT_OK;
+    for (nufft_plan p : b->plans) {
+        const int rc = nufft2_check(p, stream);
+        if (rc && !worst) worst = rc;
+    }
+    return worst;
+}
+
+extern "C" int nufft_batch_destroy(nufft_batch b) {
+    free_batch(b);
+    return NUFFT_OK;
+}

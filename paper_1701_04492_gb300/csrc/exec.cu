@@ -103,8 +103,6 @@ int plan_geometry(nufft_plan p) {
     return NUFFT_OK;
 }
 
-namespace {
-
 template <typename T>
 PassArgs<T> base_args(nufft_plan p) {
     PassArgs<T> a{};
@@ -139,6 +137,11 @@ PassArgs<T> base_args(nufft_plan p) {
     a.inv_gamma = p->gamma > 0.0 ? (T)(1.0 / p->gamma) : T(0);
     return a;
 }
+
+template PassArgs<float> base_args<float>(nufft_plan);
+template PassArgs<double> base_args<double>(nufft_plan);
+
+namespace {
 
 template <typename T>
 int run_rows(nufft_plan p, const PassArgs<T> &a, bool adjoint, cudaStream_t s) {

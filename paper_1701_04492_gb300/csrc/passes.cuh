@@ -78,6 +78,8 @@ struct PassArgs {
     const T *vfac;        // MODE_FACTORS: V[r][k] = v_r(k) of eq. (2.6), K x N
     const cx<T> *ufac;    // MODE_FACTORS: U[i][r] = u_r(perm[i]) of eq. (2.6), sorted order, M x K
     T inv_gamma;
+    int SB;               // pass B: rank splits (CTAs per column block)
+    int64_t in_off, out_off;   // batched launches: this problem's offsets into the packed in / out
 };
 
 // T_r(z) by the three-term recurrence (NIST 18.9.1).
@@ -117,6 +119,19 @@ __device__ __forceinline__ void fill_fourstep(const PassArgs<T> &a, int k, int t
     for (int q = tt; q < E; q += TT) tab[q * ld] = twiddle_L<T>(a, TT * q * k);
 }
 
+// beta_rp as the kernels read it: from the kernel's parameter space (one plan per
+// launch), or from a shared-memory copy (batched launches) read through a volatile
+// pointer, one broadcast load per use, so that the compiler does not hold the KM^2
+// values in registers.
+template <typename T, int KM>
+__device__ __forceinline__ T beta_at(const Beta<T, KM> &b, int r, int q) { return b.b[r][q]; }
+template <typename T, int KM>
+struct BetaShared {
+    const volatile T *p;
+};
+template <typename T, int KM>
+__device__ __forceinline__ T beta_at(const BetaShared<T, KM> &b, int r, int q) { return b.p[r * KM + q]; }
+
 template <typename T>
 __device__ __forceinline__ cx<T> *smem_base() {
     extern __shared__ __align__(16) unsigned char nufft_smem_raw[];
@@ -126,15 +141,15 @@ __device__ __forceinline__ cx<T> *smem_base() {
 // ---- pass 1: V-scale + column FFTs (length L2) + four-step twiddle ----------------
 // Shared memory: C exchange slots of S elements, then the four-step table [q][cc].
 template <typename T, int P2>
-__global__ void __launch_bounds__(256, 2) k_pass1(const PassArgs<T> a) {
+__device__ __forceinline__ void pass1_body(const PassArgs<T> &a, const int bx, const int by) {
     constexpr int E = e_of<T, P2>();
     using TF = TeamFft<T, P2, E, false>;
     constexpr int TT = TF::TT;
     cx<T> *smem = smem_base<T>();
     const int cc = threadIdx.x & (a.C - 1);
     const int tt = threadIdx.x >> a.lgC;
-    const int k1 = blockIdx.x * a.C + cc;
-    const int r = blockIdx.y;
+    const int k1 = bx * a.C + cc;
+    const int r = by;
     cx<T> *ftab = smem + a.C * a.S;
     fill_fourstep<T, E, TT>(a, k1, tt, ftab + cc, a.C);
     cx<T> v[E];
@@ -218,15 +233,15 @@ __global__ void __launch_bounds__(256, 2) k_pass1(const PassArgs<T> a) {
 }
 
 // ---- pass 2: row FFTs (length L1) into shared memory, then gather/U-scale/rank-sum --
-template <typename T, int P1, int KM>
-__global__ void __launch_bounds__(256) k_pass2(const PassArgs<T> a, const Beta<T, KM> beta) {
+template <typename T, int P1, int KM, typename BT>
+__device__ __forceinline__ void pass2_body(const PassArgs<T> &a, const BT &beta, const int bx) {
     constexpr int E = e_of<T, P1>();
     using TF = TeamFft<T, P1, E, false>;
     constexpr int TT = TF::TT;
     cx<T> *smem = smem_base<T>();
     const int nt = blockDim.x / TT;
     const int team = threadIdx.x / TT, tt = threadIdx.x % TT;
-    const int b = blockIdx.x;
+    const int b = bx;
     const int i0 = a.bstart[b], i1 = a.bstart[b + 1];
     const int L2m = a.L2 - 1;
     const int Gs = a.G > 0 ? a.G : 1;   // never a zero stride
@@ -308,7 +323,7 @@ __global__ void __launch_bounds__(256) k_pass2(const PassArgs<T> a, const Beta<T
                 for (int r = 0; r < KM; ++r) {
                     T m = T(0);
 #pragma unroll
-                    for (int q = (r & 1); q < KM; q += 2) m = fma(beta.b[r][q], Tp[q], m);
+                    for (int q = (r & 1); q < KM; q += 2) m = fma(beta_at(beta, r, q), Tp[q], m);
                     mu[r] = m;   // zero for r >= K (beta is zero-padded)
                 }
                 cx<T> S = mk<T>(0, 0), Sp = mk<T>(0, 0);
@@ -370,7 +385,7 @@ __global__ void __launch_bounds__(256) k_pass2(const PassArgs<T> a, const Beta<T
                         if (r >= g0 && r < g0 + gc) {
                             T mu = T(0);
 #pragma unroll
-                            for (int q = (r & 1); q < KM; q += 2) mu = fma(beta.b[r][q], Tp[q], mu);
+                            for (int q = (r & 1); q < KM; q += 2) mu = fma(beta_at(beta, r, q), Tp[q], mu);
                             const cx<T> x = smem[((r - g0) * a.B2 + row) * a.S + padi<E>(n1)];
                             acc.x = fma(mu, x.x, acc.x);
                             acc.y = fma(mu, x.y, acc.y);
@@ -403,15 +418,15 @@ __global__ void __launch_bounds__(256) k_pass2(const PassArgs<T> a, const Beta<T
 }
 
 // ---- pass A (adjoint): segmented scatter into shared memory, inverse row FFTs -----
-template <typename T, int P1, int KM>
-__global__ void __launch_bounds__(256) k_passA(const PassArgs<T> a, const Beta<T, KM> beta) {
+template <typename T, int P1, int KM, typename BT>
+__device__ __forceinline__ void passA_body(const PassArgs<T> &a, const BT &beta, const int bx) {
     constexpr int E = e_of<T, P1>();
     using TF = TeamFft<T, P1, E, true>;
     constexpr int TT = TF::TT;
     cx<T> *smem = smem_base<T>();
     const int nt = blockDim.x / TT;
     const int team = threadIdx.x / TT, tt = threadIdx.x % TT;
-    const int b = blockIdx.x;
+    const int b = bx;
     const int i0 = a.bstart[b], i1 = a.bstart[b + 1];
     const int L2m = a.L2 - 1;
     const int Gs = a.G > 0 ? a.G : 1;   // never a zero stride
@@ -482,7 +497,7 @@ __global__ void __launch_bounds__(256) k_passA(const PassArgs<T> a, const Beta<T
                         if (r >= g0 && r < g0 + gc) {
                             T mu = T(0);
 #pragma unroll
-                            for (int q = (r & 1); q < KM; q += 2) mu = fma(beta.b[r][q], Tp[q], mu);
+                            for (int q = (r & 1); q < KM; q += 2) mu = fma(beta_at(beta, r, q), Tp[q], mu);
                             acc[r].x = fma(mu, h.x, acc[r].x);
                             acc[r].y = fma(mu, h.y, acc[r].y);
                         }
@@ -546,22 +561,22 @@ __global__ void __launch_bounds__(256) k_passA(const PassArgs<T> a, const Beta<T
 // (an atomic ticket, no waiting) adds the SB partials in the fixed order
 // s = 0..SB-1, so the result does not depend on which CTA finishes last.
 template <typename T, int P2>
-__global__ void __launch_bounds__(128, 3) k_passB(const PassArgs<T> a) {
+__device__ __forceinline__ void passB_body(const PassArgs<T> &a, const int bx, const int by) {
     constexpr int E = e_of<T, P2>();
     using TF = TeamFft<T, P2, E, true>;
     constexpr int TT = TF::TT;
     cx<T> *smem = smem_base<T>();
     const int cc = threadIdx.x & (a.C - 1);
     const int tt = threadIdx.x >> a.lgC;
-    const int k1 = blockIdx.x * a.C + cc;
-    const int s = blockIdx.y, SB = gridDim.y;
+    const int k1 = bx * a.C + cc;
+    const int s = by, SB = a.SB;
     const int Ni = (int)a.N;   // N < 2^23: 32-bit conversions (64-bit ones run on the FP64 pipe)
         const T invN = T(1) / T(Ni);
     const int bufsz = a.C * a.S;                        // elements per buffer
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + 2 * bufsz);
     __shared__ int cta_failed;
     const uint32_t tile_bytes = (uint32_t)(a.C * P2 * sizeof(cx<T>));
-    const int64_t tile_off = (int64_t)blockIdx.x * a.C * P2;
+    const int64_t tile_off = (int64_t)bx * a.C * P2;
     const int nr = s < a.K ? (a.K - s + SB - 1) / SB : 0;   // ranks of this CTA
     if (threadIdx.x == 0) {
         cta_failed = 0;
@@ -651,7 +666,7 @@ __global__ void __launch_bounds__(128, 3) k_passB(const PassArgs<T> a) {
     __threadfence();
     __syncthreads();
     __shared__ int ticket;
-    if (threadIdx.x == 0) ticket = atomicAdd(&a.counters[blockIdx.x], 1);
+    if (threadIdx.x == 0) ticket = atomicAdd(&a.counters[bx], 1);
     __syncthreads();
     if (ticket != SB - 1) return;
     __threadfence();
@@ -666,7 +681,91 @@ __global__ void __launch_bounds__(128, 3) k_passB(const PassArgs<T> a) {
         }
         if (k < a.N) a.out[k] = t;
     }
-    if (threadIdx.x == 0) a.counters[blockIdx.x] = 0;   // ready for the next call
+    if (threadIdx.x == 0) a.counters[bx] = 0;   // ready for the next call
+}
+
+// ---- kernels ----------------------------------------------------------------------
+// One plan per launch: the arguments are kernel parameters.
+template <typename T, int P2>
+__global__ void __launch_bounds__(256, 2) k_pass1(const __grid_constant__ PassArgs<T> a) {
+    pass1_body<T, P2>(a, blockIdx.x, blockIdx.y);
+}
+template <typename T, int P1, int KM>
+__global__ void __launch_bounds__(256) k_pass2(const __grid_constant__ PassArgs<T> a,
+                                               const __grid_constant__ Beta<T, KM> beta) {
+    pass2_body<T, P1, KM>(a, beta, blockIdx.x);
+}
+template <typename T, int P1, int KM>
+__global__ void __launch_bounds__(256) k_passA(const __grid_constant__ PassArgs<T> a,
+                                               const __grid_constant__ Beta<T, KM> beta) {
+    passA_body<T, P1, KM>(a, beta, blockIdx.x);
+}
+template <typename T, int P2>
+__global__ void __launch_bounds__(128, 3) k_passB(const __grid_constant__ PassArgs<T> a) {
+    passB_body<T, P2>(a, blockIdx.x, blockIdx.y);
+}
+
+// Many independent plans per launch (a batch of uneven problems): blockIdx.z is the
+// problem.  The problems of one launch share the grid length L, and so every launch
+// dimension but the rank count; each reads its own arguments (buffers, K, M, tables)
+// from args[z], and its input and output at in + in_off, out + out_off.  CTAs beyond a
+// problem's own rank count or rank split return before any barrier.
+// The problem's arguments, copied to shared memory sa (all threads, then a barrier).
+template <typename T>
+__device__ __forceinline__ void many_args(PassArgs<T> &sa, const PassArgs<T> *__restrict__ args,
+                                          const cx<T> *in, cx<T> *out) {
+    static_assert(sizeof(PassArgs<T>) % 8 == 0, "copied in 8-byte words");
+    const unsigned long long *src = reinterpret_cast<const unsigned long long *>(&args[blockIdx.z]);
+    unsigned long long *dst = reinterpret_cast<unsigned long long *>(&sa);
+    for (int i = threadIdx.x; i < (int)(sizeof(PassArgs<T>) / 8); i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        sa.in = in + sa.in_off;
+        sa.out = out + sa.out_off;
+    }
+    __syncthreads();
+}
+template <typename T, int KM>
+__device__ __forceinline__ void stage_beta(Beta<T, KM> &sb, const Beta<T, KM> *__restrict__ betas) {
+    const T *src = &betas[blockIdx.z].b[0][0];
+    for (int i = threadIdx.x; i < KM * KM; i += blockDim.x) (&sb.b[0][0])[i] = src[i];
+    __syncthreads();
+}
+template <typename T, int P2>
+__global__ void __launch_bounds__(256, 2) k_pass1_many(const PassArgs<T> *__restrict__ args,
+                                                       const cx<T> *in, cx<T> *out) {
+    __shared__ PassArgs<T> a;
+    many_args<T>(a, args, in, out);
+    if ((int)blockIdx.y >= a.nranks) return;
+    pass1_body<T, P2>(a, blockIdx.x, blockIdx.y);
+}
+template <typename T, int P1, int KM>
+__global__ void __launch_bounds__(256) k_pass2_many(const PassArgs<T> *__restrict__ args,
+                                                    const Beta<T, KM> *__restrict__ betas,
+                                                    const cx<T> *in, cx<T> *out) {
+    __shared__ Beta<T, KM> sb;
+    stage_beta<T, KM>(sb, betas);
+    __shared__ PassArgs<T> a;
+    many_args<T>(a, args, in, out);
+    pass2_body<T, P1, KM>(a, BetaShared<T, KM>{&sb.b[0][0]}, blockIdx.x);
+}
+template <typename T, int P1, int KM>
+__global__ void __launch_bounds__(256) k_passA_many(const PassArgs<T> *__restrict__ args,
+                                                    const Beta<T, KM> *__restrict__ betas,
+                                                    const cx<T> *in, cx<T> *out) {
+    __shared__ Beta<T, KM> sb;
+    stage_beta<T, KM>(sb, betas);
+    __shared__ PassArgs<T> a;
+    many_args<T>(a, args, in, out);
+    passA_body<T, P1, KM>(a, BetaShared<T, KM>{&sb.b[0][0]}, blockIdx.x);
+}
+template <typename T, int P2>
+__global__ void __launch_bounds__(128, 3) k_passB_many(const PassArgs<T> *__restrict__ args,
+                                                       const cx<T> *in, cx<T> *out) {
+    __shared__ PassArgs<T> a;
+    many_args<T>(a, args, in, out);
+    if ((int)blockIdx.y >= a.SB) return;
+    passB_body<T, P2>(a, blockIdx.x, blockIdx.y);
 }
 
 // ---- launchers ------------------------------------------------------------------
@@ -681,6 +780,22 @@ int dispatch_P(int P, F &&f) {
         case 512: return f(std::integral_constant<int, 512>{});
         case 1024: return f(std::integral_constant<int, 1024>{});
         case 2048: return f(std::integral_constant<int, 2048>{});
+        default: return NUFFT_EUNSUPPORTED;
+    }
+}
+
+// The batched kernels exist for FFT lengths up to MANY_P_MAX (grids up to 2^18
+// points): batching pays for problems too small to fill the GPU alone.
+constexpr int MANY_P_MAX = 512;
+
+template <typename F>
+int dispatch_P_many(int P, F &&f) {
+    switch (P) {
+        case 32: return f(std::integral_constant<int, 32>{});
+        case 64: return f(std::integral_constant<int, 64>{});
+        case 128: return f(std::integral_constant<int, 128>{});
+        case 256: return f(std::integral_constant<int, 256>{});
+        case 512: return f(std::integral_constant<int, 512>{});
         default: return NUFFT_EUNSUPPORTED;
     }
 }
@@ -704,16 +819,36 @@ inline int launch_status() {
     return e == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;
 }
 
+// The fields a column-pass launch adds to base_args (single and batched launches).
+template <typename T>
+void cols_fields(nufft_plan p, PassArgs<T> &a, bool adjoint) {
+    a.C = adjoint ? p->CB : p->C1;
+    a.lgC = 0;
+    while ((1 << a.lgC) < a.C) ++a.lgC;
+    a.S = adjoint ? p->SB : p->S1;
+    a.SB = p->SBsplit;
+}
+
+// The fields a row-pass launch adds to base_args (single and batched launches).
+template <typename T>
+int rows_fields(nufft_plan p, PassArgs<T> &a, bool adjoint) {
+    a.S = p->S2;
+    a.chunk = p->chunkA;
+    a.mbar_off = (int)p->mbar_off2;
+    a.G = adjoint ? p->GA : p->G;
+    a.CQ = p->CB;
+    a.lgCQ = 0;
+    while ((1 << a.lgCQ) < a.CQ) ++a.lgCQ;
+    return a.chunk > 0 ? NUFFT_OK : NUFFT_EINVAL;
+}
+
 template <typename T>
 int launch_cols(nufft_plan p, const PassArgs<T> &a0, bool adjoint, cudaStream_t s) {
     return dispatch_P(p->L2, [&](auto PC) -> int {
         constexpr int P = decltype(PC)::value;
         constexpr int TT = P / e_of<T, P>();
         PassArgs<T> a = a0;
-        a.C = adjoint ? p->CB : p->C1;
-        a.lgC = 0;
-        while ((1 << a.lgC) < a.C) ++a.lgC;
-        a.S = adjoint ? p->SB : p->S1;
+        cols_fields<T>(p, a, adjoint);
         const size_t smem = adjoint ? p->smemB : p->smem1;
         const dim3 block(a.C * TT);
         static int done_b[64] = {}, done_1[64] = {};
@@ -731,22 +866,21 @@ int launch_cols(nufft_plan p, const PassArgs<T> &a0, bool adjoint, cudaStream_t 
 }
 
 template <typename T, int KM>
-int launch_rows(nufft_plan p, const PassArgs<T> &a0, bool adjoint, cudaStream_t s) {
+Beta<T, KM> beta_of(nufft_plan p) {
     Beta<T, KM> beta;
     for (int r = 0; r < KM; ++r)
         for (int q = 0; q < KM; ++q) beta.b[r][q] = (T)p->beta[r][q];
+    return beta;
+}
+
+template <typename T, int KM>
+int launch_rows(nufft_plan p, const PassArgs<T> &a0, bool adjoint, cudaStream_t s) {
+    const Beta<T, KM> beta = beta_of<T, KM>(p);
     return dispatch_P(p->L1, [&](auto PC) -> int {
         constexpr int P = decltype(PC)::value;
         constexpr int TT = P / e_of<T, P>();
         PassArgs<T> a = a0;
-        a.S = p->S2;
-        a.chunk = p->chunkA;
-        a.mbar_off = (int)p->mbar_off2;
-        a.G = adjoint ? p->GA : p->G;
-        a.CQ = p->CB;
-        a.lgCQ = 0;
-        while ((1 << a.lgCQ) < a.CQ) ++a.lgCQ;
-        if (a.chunk <= 0) return NUFFT_EINVAL;
+        if (int rc = rows_fields<T>(p, a, adjoint)) return rc;
         const int nt = adjoint ? p->ntA : (a.nranks > p->K ? p->nt2d : p->nt2);
         const dim3 block(nt * TT);
         static int done_a[64] = {}, done_2[64] = {};
@@ -763,10 +897,72 @@ int launch_rows(nufft_plan p, const PassArgs<T> &a0, bool adjoint, cudaStream_t 
     });
 }
 
+// Batched launches of one class of problems (same L and rank bound KM).  rep is the
+// member whose geometry covers every member: the largest rank count, and with it the
+// largest shared-memory layout; grid.y is the largest rank count (pass 1) or rank
+// split (pass B) of the class.  args / betas: device arrays, one entry per member.
+template <typename T>
+int launch_cols_many(nufft_plan rep, const PassArgs<T> *args, int nprob, int ny, bool adjoint,
+                     const void *in, void *out, cudaStream_t s) {
+    return dispatch_P_many(rep->L2, [&](auto PC) -> int {
+        constexpr int P = decltype(PC)::value;
+        constexpr int TT = P / e_of<T, P>();
+        const int C = adjoint ? rep->CB : rep->C1;
+        const size_t smem = adjoint ? rep->smemB : rep->smem1;
+        const dim3 grid(rep->L1 / C, ny, nprob), block(C * TT);
+        static int done_b[64] = {}, done_1[64] = {};
+        if (adjoint) {
+            auto kern = k_passB_many<T, P>;
+            if (int rc = set_smem(kern, smem, rep->device, done_b)) return rc;
+            kern<<<grid, block, smem, s>>>(args, (const cx<T> *)in, (cx<T> *)out);
+        } else {
+            auto kern = k_pass1_many<T, P>;
+            if (int rc = set_smem(kern, smem, rep->device, done_1)) return rc;
+            kern<<<grid, block, smem, s>>>(args, (const cx<T> *)in, (cx<T> *)out);
+        }
+        return launch_status();
+    });
+}
+
+template <typename T, int KM>
+int launch_rows_many(nufft_plan rep, const PassArgs<T> *args, const Beta<T, KM> *betas, int nprob,
+                     bool adjoint, const void *in, void *out, cudaStream_t s) {
+    return dispatch_P_many(rep->L1, [&](auto PC) -> int {
+        constexpr int P = decltype(PC)::value;
+        constexpr int TT = P / e_of<T, P>();
+        const int nt = adjoint ? rep->ntA : rep->nt2;
+        const size_t smem = adjoint ? rep->smemA : rep->smem2;
+        const dim3 grid(rep->NB, 1, nprob), block(nt * TT);
+        static int done_a[64] = {}, done_2[64] = {};
+        if (adjoint) {
+            auto kern = k_passA_many<T, P, KM>;
+            if (int rc = set_smem(kern, smem, rep->device, done_a)) return rc;
+            kern<<<grid, block, smem, s>>>(args, betas, (const cx<T> *)in, (cx<T> *)out);
+        } else {
+            auto kern = k_pass2_many<T, P, KM>;
+            if (int rc = set_smem(kern, smem, rep->device, done_2)) return rc;
+            kern<<<grid, block, smem, s>>>(args, betas, (const cx<T> *)in, (cx<T> *)out);
+        }
+        return launch_status();
+    });
+}
+
+// Common arguments of every pass of plan p (defined in exec.cu).
+template <typename T>
+PassArgs<T> base_args(nufft_plan p);
+
 // explicit instantiation declarations (defined in the inst_*.cu files)
 #define NUFFT_DECLARE_ROWS(T, KM) \
     extern template int launch_rows<T, KM>(nufft_plan, const PassArgs<T> &, bool, cudaStream_t);
 #define NUFFT_DECLARE_COLS(T) \
     extern template int launch_cols<T>(nufft_plan, const PassArgs<T> &, bool, cudaStream_t);
+// batched launchers: FP32 only
+#define NUFFT_DECLARE_MANY(KM)                                                                         \
+    extern template int launch_rows_many<float, KM>(nufft_plan, const PassArgs<float> *,              \
+                                                    const Beta<float, KM> *, int, bool, const void *, \
+                                                    void *, cudaStream_t);
+#define NUFFT_DECLARE_COLS_MANY()                                                                  \
+    extern template int launch_cols_many<float>(nufft_plan, const PassArgs<float> *, int, int, bool, \
+                                                const void *, void *, cudaStream_t);
 
 }  // namespace nufft

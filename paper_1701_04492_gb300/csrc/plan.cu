@@ -11,7 +11,10 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "fft_team.cuh"
@@ -388,6 +391,137 @@ void free_plan(nufft_plan p) {
 }  // namespace
 }  // namespace nufft
 
+namespace nufft {
+namespace {
+
+// One plan on grid L (a power of two, validated by the caller); long_cols: for odd
+// log2 L, the column FFT (length L2) is the longer one.
+int plan_create(nufft_plan *out, int64_t N, int64_t M, const double *x_dev, double eps, int prec,
+                int64_t L, unsigned flags, bool long_cols, cudaStream_t s) {
+    *out = nullptr;
+    nufft_plan p = new (std::nothrow) nufft_plan_s();
+    if (!p) return NUFFT_ENOMEM;
+    p->N = N; p->M = M; p->L = L; p->eps = eps; p->prec = prec; p->flags = flags;
+    int lg = 0;
+    while (((int64_t)1 << lg) < L) ++lg;
+    p->lg1 = long_cols ? lg / 2 : (lg + 1) / 2;
+    p->lg2 = lg - p->lg1;
+    p->L1 = 1 << p->lg1;
+    p->L2 = 1 << p->lg2;
+    if (cudaGetDevice(&p->device) != cudaSuccess) { free_plan(p); return NUFFT_ECUDA; }
+    if (flags & NUFFT_PLAN_TIMING)
+        for (cudaEvent_t &e : p->ev)
+            if (cudaEventCreate(&e) != cudaSuccess) { (void)cudaGetLastError(); free_plan(p); return NUFFT_ECUDA; }
+    const int rc = prec == NUFFT_F32 ? plan_device<float>(p, x_dev, s) : plan_device<double>(p, x_dev, s);
+    if (rc != NUFFT_OK) { free_plan(p); return rc; }
+    *out = p;
+    return NUFFT_OK;
+}
+
+// Device time (ms) of one forward and one adjoint exec of plan p on its own staging
+// buffers (zeroed): the best of three after one warm-up.
+int time_exec(nufft_plan p, cudaStream_t s, float *ms) {
+    const size_t cxs = p->prec == NUFFT_F32 ? 8 : 16;
+    NUFFT_CUDA_TRY(cudaMemsetAsync(p->cstage, 0, (size_t)p->N * cxs, s));
+    if (p->M > 0) NUFFT_CUDA_TRY(cudaMemsetAsync(p->fstage, 0, (size_t)p->M * cxs, s));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        (void)cudaGetLastError();
+        if (e0) cudaEventDestroy(e0);
+        return NUFFT_ECUDA;
+    }
+    int rc = NUFFT_OK;
+    float best = 1e30f;
+    for (int it = 0; it < 4 && !rc; ++it) {
+        if (cudaEventRecord(e0, s) != cudaSuccess) { rc = NUFFT_ECUDA; break; }
+        rc = nufft2_exec(p, p->cstage, p->fstage, s);
+        if (!rc) rc = nufft1_exec(p, p->fstage, p->cstage, s);
+        if (rc) break;
+        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = NUFFT_ECUDA;
+            break;
+        }
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (it > 0) best = std::min(best, t);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!rc) rc = nufft2_check(p, s);
+    *ms = best;
+    return rc;
+}
+
+// The tuner's choices, per process: (device, N, M rounded up to a power of two, eps,
+// precision, K on the default grid) -> (grid size, long columns).
+struct TuneKey {
+    int device;
+    int64_t N, Mb;
+    double eps;
+    int prec, K;
+    bool operator<(const TuneKey &o) const {
+        return std::tie(device, N, Mb, eps, prec, K) < std::tie(o.device, o.N, o.Mb, o.eps, o.prec, o.K);
+    }
+};
+std::mutex tune_mu;
+std::map<TuneKey, std::pair<int64_t, bool>> tune_cache;
+
+// Autotuned planning: the candidates are the default grid L0 and the oversampled
+// 2 L0 (section 2.3: a longer grid lowers gamma, and so K), each with either four-step
+// split when log2 L is odd; the one with the fastest forward + adjoint is kept.
+int plan_autotune(nufft_plan *out, int64_t N, int64_t M, const double *x_dev, double eps, int prec,
+                  int64_t L0, unsigned flags, cudaStream_t s) {
+    nufft_plan best = nullptr;
+    if (int rc = plan_create(&best, N, M, x_dev, eps, prec, L0, flags, false, s)) return rc;
+    int64_t Mb = 1;
+    while (Mb < M) Mb <<= 1;
+    const TuneKey key{best->device, N, Mb, eps, prec, best->K};
+    std::pair<int64_t, bool> choice(L0, false);
+    bool cached = false;
+    {
+        std::lock_guard<std::mutex> lk(tune_mu);
+        auto it = tune_cache.find(key);
+        if (it != tune_cache.end()) { choice = it->second; cached = true; }
+    }
+    if (cached) {
+        if (choice.first == L0 && !choice.second) { *out = best; return NUFFT_OK; }
+        free_plan(best);
+        return plan_create(out, N, M, x_dev, eps, prec, choice.first, flags, choice.second, s);
+    }
+    float tbest = 0.f;
+    if (int rc = time_exec(best, s, &tbest)) { free_plan(best); return rc; }
+    for (int64_t L = L0; L <= std::min<int64_t>(2 * L0, (int64_t)1 << LOG2_L_MAX); L *= 2) {
+        int lg = 0;
+        while (((int64_t)1 << lg) < L) ++lg;
+        for (int lc = 0; lc < 2; ++lc) {
+            if ((L == L0 && lc == 0) || (lc == 1 && lg % 2 == 0)) continue;
+            nufft_plan cand = nullptr;
+            int rc = plan_create(&cand, N, M, x_dev, eps, prec, L, flags, lc == 1, s);
+            if (rc == NUFFT_EUNSUPPORTED) continue;   // e.g. the shared-memory budget
+            if (rc) { free_plan(best); return rc; }
+            float t = 0.f;
+            if ((rc = time_exec(cand, s, &t))) { free_plan(cand); free_plan(best); return rc; }
+            if (t < tbest) {
+                free_plan(best);
+                best = cand;
+                tbest = t;
+                choice = {L, lc == 1};
+            } else {
+                free_plan(cand);
+            }
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(tune_mu);
+        tune_cache[key] = choice;
+    }
+    *out = best;
+    return NUFFT_OK;
+}
+
+}  // namespace
+}  // namespace nufft
+
 extern "C" int nufft2_plan(nufft_plan *out, int64_t N, int64_t M, const double *x_dev, double eps,
                            int prec, int64_t L, unsigned flags, void *stream) {
     using namespace nufft;
@@ -396,33 +530,22 @@ extern "C" int nufft2_plan(nufft_plan *out, int64_t N, int64_t M, const double *
     if (N < 1 || M < 0 || M >= ((int64_t)1 << 31) || !(eps > 0.0 && eps < 1.0)) return NUFFT_EINVAL;
     if (prec != NUFFT_F32 && prec != NUFFT_F64) return NUFFT_EINVAL;
     if (M > 0 && !x_dev) return NUFFT_EINVAL;
-    if (flags & ~(NUFFT_PLAN_UNFUSED | NUFFT_PLAN_TIMING)) return NUFFT_EINVAL;
+    if (flags & ~(NUFFT_PLAN_UNFUSED | NUFFT_PLAN_TIMING | NUFFT_PLAN_AUTOTUNE | NUFFT_PLAN_LONG_COLUMNS))
+        return NUFFT_EINVAL;
     if (N > ((int64_t)1 << LOG2_L_MAX)) return NUFFT_EUNSUPPORTED;
-    if (L == 0) {
+    const bool fixed_L = L != 0;
+    if (!fixed_L) {
         L = (int64_t)1 << LOG2_L_MIN;
         while (L < N) L <<= 1;
     } else {
         if (L < N || (L & (L - 1)) != 0) return NUFFT_EINVAL;
         if (L < ((int64_t)1 << LOG2_L_MIN) || L > ((int64_t)1 << LOG2_L_MAX)) return NUFFT_EUNSUPPORTED;
     }
-    nufft_plan p = new (std::nothrow) nufft_plan_s();
-    if (!p) return NUFFT_ENOMEM;
-    p->N = N; p->M = M; p->L = L; p->eps = eps; p->prec = prec; p->flags = flags;
-    int lg = 0;
-    while (((int64_t)1 << lg) < L) ++lg;
-    p->lg1 = (lg + 1) / 2;
-    p->lg2 = lg / 2;
-    p->L1 = 1 << p->lg1;
-    p->L2 = 1 << p->lg2;
-    if (cudaGetDevice(&p->device) != cudaSuccess) { free_plan(p); return NUFFT_ECUDA; }
     cudaStream_t s = (cudaStream_t)stream;
-    if (flags & NUFFT_PLAN_TIMING)
-        for (cudaEvent_t &e : p->ev)
-            if (cudaEventCreate(&e) != cudaSuccess) { (void)cudaGetLastError(); free_plan(p); return NUFFT_ECUDA; }
-    const int rc = prec == NUFFT_F32 ? plan_device<float>(p, x_dev, s) : plan_device<double>(p, x_dev, s);
-    if (rc != NUFFT_OK) { free_plan(p); return rc; }
-    *out = p;
-    return NUFFT_OK;
+    const unsigned pf = flags & (NUFFT_PLAN_UNFUSED | NUFFT_PLAN_TIMING);
+    if ((flags & NUFFT_PLAN_AUTOTUNE) && !fixed_L && !(flags & NUFFT_PLAN_LONG_COLUMNS))
+        return plan_autotune(out, N, M, x_dev, eps, prec, L, pf, s);
+    return plan_create(out, N, M, x_dev, eps, prec, L, pf, (flags & NUFFT_PLAN_LONG_COLUMNS) != 0, s);
 }
 
 extern "C" int nufft2_plan_info(nufft_plan p, int *K, double *gamma, int64_t *L, int64_t *work_bytes) {

@@ -1,0 +1,215 @@
+"""GPU: batches of uneven problems (batched launches, CUDA graph), the tuner's layouts.
+
+A batch runs each problem's own plan arithmetic, so its results must equal those of
+single plans exactly; each problem is also checked against the oracle (the low-rank
+oracle on the grid the plan chose, at the tolerances of test_gpu_nufft.py, and the
+direct sum of eq. (1.2) at eps for a few rows).
+"""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import direct, lowrank  # noqa: E402
+from paper_1701_04492_gb300 import workloads as wl  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_1701_04492_gb300 import api as a
+    return a
+
+
+def _rel2(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+TOL_REL = {"f32": 1e-5, "f64": 1e-13}
+CDT = {"f32": torch.complex64, "f64": torch.complex128}
+NPC = {"f32": np.complex64, "f64": np.complex128}
+
+
+def _problems(count, seed, lo=10, hi=15):
+    """Uneven sizes (non-powers of two), mixed eps, uniform samples; one empty problem."""
+    N, eps = wl.uneven_batch(count, seed, lo, hi)
+    r = np.random.default_rng(seed)
+    M = [int(n * f) for n, f in zip(N, r.uniform(0.5, 1.5, count))]
+    M[count // 2] = 0
+    xs = [wl.samples_uniform(m, seed + 100 + i) for i, m in enumerate(M)]
+    return [int(n) for n in N], xs, eps
+
+
+def _packed(prec, N, seed):
+    c = wl.coeffs_cn(int(sum(N)), seed).astype(NPC[prec])
+    return torch.tensor(c, device="cuda"), c.astype(np.complex128)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_batch_forward_matches_single_plans_and_oracle(api, prec):
+    N, xs, eps = _problems(20, 11)
+    b = api.Batch(N, xs, eps, prec)
+    c_dev, c = _packed(prec, N, 5)
+    f = b.forward(c_dev).cpu().numpy()
+    for i in range(b.count):
+        n0, n1 = b.offN[i], b.offN[i + 1]
+        m0, m1 = b.offM[i], b.offM[i + 1]
+        p = api.Plan(N[i], xs[i], eps[i], prec)
+        assert p.L == b.L[i] and p.K == b.K[i]
+        if m1 == m0:
+            continue
+        fi = p.forward(c_dev[n0:n1].contiguous()).cpu().numpy()
+        assert np.array_equal(f[m0:m1], fi), i        # the same arithmetic, bit for bit
+        P = lowrank.plan(N[i], xs[i], eps[i], int(b.L[i]))
+        fo = lowrank.nufft2(P, c[n0:n1])
+        assert _rel2(f[m0:m1], fo) <= TOL_REL[prec], i
+        rows = np.arange(0, m1 - m0, max(1, (m1 - m0) // 16))
+        fd = direct.nudft2(xs[i][rows], c[n0:n1])
+        bound = max(eps[i], 5e-6 if prec == "f32" else 1e-13) * np.sum(np.abs(c[n0:n1]))
+        assert np.max(np.abs(f[m0:m1][rows] - fd)) <= bound, i
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_batch_adjoint_matches_single_plans_and_oracle(api, prec):
+    N, xs, eps = _problems(16, 12)
+    b = api.Batch(N, xs, eps, prec)
+    g = wl.cotangent_cn(int(b.total_M), 6).astype(NPC[prec])
+    g_dev = torch.tensor(g, device="cuda")
+    cc = b.adjoint(g_dev).cpu().numpy()
+    for i in range(b.count):
+        n0, n1 = b.offN[i], b.offN[i + 1]
+        m0, m1 = b.offM[i], b.offM[i + 1]
+        if m1 == m0:
+            assert np.all(cc[n0:n1] == 0)
+            continue
+        p = api.Plan(N[i], xs[i], eps[i], prec)
+        ci = p.adjoint(g_dev[m0:m1].contiguous()).cpu().numpy()
+        assert np.array_equal(cc[n0:n1], ci), i
+        P = lowrank.plan(N[i], xs[i], eps[i], int(b.L[i]))
+        co = lowrank.nufft2_adjoint(P, g[m0:m1].astype(np.complex128))
+        assert _rel2(cc[n0:n1], co) <= TOL_REL[prec], i
+
+
+def test_batch_each_and_per_problem_match_batched(api):
+    N, xs, eps = _problems(24, 13)
+    b = api.Batch(N, xs, eps, "f32")
+    bp = api.Batch(N, xs, eps, "f32", per_problem=True)
+    assert bp.classes == b.count and b.classes < b.count
+    c_dev, _ = _packed("f32", N, 7)
+    f = b.forward(c_dev)
+    assert torch.equal(b.forward_each(c_dev), f)
+    assert torch.equal(bp.forward(c_dev), f)
+    g_dev = torch.tensor(wl.cotangent_cn(int(b.total_M), 8).astype(np.complex64), device="cuda")
+    ca = b.adjoint(g_dev)
+    assert torch.equal(b.adjoint_each(g_dev), ca)
+    assert torch.equal(bp.adjoint(g_dev), ca)
+    b.check()
+
+
+@pytest.mark.parametrize("per_problem", [False, True])
+def test_batch_graph_replay_matches_eager(api, per_problem):
+    N, xs, eps = _problems(24, 14)
+    eager = api.Batch(N, xs, eps, "f32", per_problem=per_problem)
+    gb = api.Batch(N, xs, eps, "f32", graph=True, per_problem=per_problem)
+    c_dev, _ = _packed("f32", N, 9)
+    g_dev = torch.tensor(wl.cotangent_cn(int(gb.total_M), 10).astype(np.complex64), device="cuda")
+    ref_f, ref_c = eager.forward(c_dev), eager.adjoint(g_dev)
+    f = torch.empty_like(ref_f)
+    cc = torch.empty_like(ref_c)
+    for it in range(4):        # eager, capture + replay, replay, replay
+        f.fill_(0)
+        cc.fill_(0)
+        gb.forward(c_dev, f)
+        gb.adjoint(g_dev, cc)
+        torch.cuda.synchronize()
+        assert torch.equal(f, ref_f), it
+        assert torch.equal(cc, ref_c), it
+    # other pointers: direct launches again, then a new graph
+    f2 = torch.empty_like(ref_f)
+    for it in range(3):
+        gb.forward(c_dev, f2)
+        assert torch.equal(f2, ref_f), it
+    gb.check()
+
+
+def test_batch_large_problem_runs_its_own_launches(api):
+    """A grid beyond 2^18 points (N = 300000 -> L = 2^19) joins an FP32 batch."""
+    N = [1500, 300000, 5000]
+    xs = [wl.samples_uniform(m, 20 + i) for i, m in enumerate([1700, 250000, 4000])]
+    eps = [1e-7, 1e-9, 1e-4]
+    b = api.Batch(N, xs, eps, "f32")
+    assert b.L[1] == 1 << 19 and b.classes == 3
+    c_dev, c = _packed("f32", N, 21)
+    f = b.forward(c_dev).cpu().numpy()
+    for i in range(3):
+        p = api.Plan(N[i], xs[i], eps[i], "f32")
+        fi = p.forward(c_dev[b.offN[i]:b.offN[i + 1]].contiguous()).cpu().numpy()
+        assert np.array_equal(f[b.offM[i]:b.offM[i + 1]], fi), i
+
+
+def test_batch_c5_shape_against_oracle_sample(api):
+    """The serving workload's shape: 512 problems, N log-uniform in [2^10, 2^18],
+    eps in {1e-4, 1e-7, 1e-12}, uniform x, M = N.  Every problem's first rows are
+    checked against the direct sum at its eps (FP32 floor 5e-6)."""
+    N, eps = wl.uneven_batch(512, 2024)
+    xs = [wl.samples_uniform(int(n), 3000 + i) for i, n in enumerate(N)]
+    b = api.Batch([int(n) for n in N], xs, eps, "f32", graph=True)
+    c_dev, c = _packed("f32", N, 31)
+    f = torch.empty(b.total_M, dtype=torch.complex64, device="cuda")
+    for _ in range(3):
+        b.forward(c_dev, f)
+    f = f.cpu().numpy()
+    ref = api.Batch([int(n) for n in N], xs, eps, "f32", per_problem=True).forward(c_dev).cpu().numpy()
+    assert np.array_equal(f, ref)
+    for i in range(0, 512, 37):
+        n0, n1, m0 = b.offN[i], b.offN[i + 1], b.offM[i]
+        rows = np.arange(8)
+        fd = direct.nudft2(xs[i][rows], c[n0:n1])
+        bound = max(eps[i], 5e-6) * np.sum(np.abs(c[n0:n1]))
+        assert np.max(np.abs(f[m0 + rows] - fd)) <= bound, i
+
+
+# ---- layouts the tuner explores ------------------------------------------------------
+
+@pytest.mark.parametrize("N", [2048, 3000, 1 << 15])
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_long_columns_split_matches_oracle(api, N, prec):
+    """The other four-step split of an odd log2 L (L2 = 2 L1) computes the same transform."""
+    x = wl.samples_uniform(N, 40)
+    L = 1024
+    while L < N:
+        L *= 2
+    if (L.bit_length() - 1) % 2 == 0:
+        L *= 2          # an odd log2 L, so that the split differs
+    p = api.Plan(N, x, 1e-9, prec, L=L, long_columns=True)
+    q = api.Plan(N, x, 1e-9, prec, L=L)
+    c = wl.coeffs_cn(N, 41).astype(NPC[prec])
+    c_dev = torch.tensor(c, device="cuda")
+    f = p.forward(c_dev).cpu().numpy()
+    P = lowrank.plan(N, x, 1e-9, L)
+    fo = lowrank.nufft2(P, c.astype(np.complex128))
+    assert _rel2(f, fo) <= TOL_REL[prec]
+    assert _rel2(f, q.forward(c_dev).cpu().numpy()) <= TOL_REL[prec]
+    g = wl.cotangent_cn(N, 42).astype(NPC[prec])
+    ca = p.adjoint(torch.tensor(g, device="cuda")).cpu().numpy()
+    assert _rel2(ca, lowrank.nufft2_adjoint(P, g.astype(np.complex128))) <= TOL_REL[prec]
+
+
+@pytest.mark.parametrize("N,eps", [(1500, 1e-12), (5000, 1e-7), (40000, 1e-4), (1 << 16, 1e-9)])
+def test_autotuned_plan_matches_oracle(api, N, eps):
+    x = wl.samples_uniform(N, 50)
+    p = api.Plan(N, x, eps, "f32", autotune=True)
+    L0 = 1024
+    while L0 < N:
+        L0 *= 2
+    assert p.L in (L0, 2 * L0)
+    c = wl.coeffs_cn(N, 51).astype(np.complex64)
+    f = p.forward(torch.tensor(c, device="cuda")).cpu().numpy()
+    P = lowrank.plan(N, x, eps, p.L)
+    assert P.K == p.K
+    assert _rel2(f, lowrank.nufft2(P, c.astype(np.complex128))) <= TOL_REL["f32"]
+    # the cached choice: a second plan of the same shape takes the same layout
+    p2 = api.Plan(N, wl.samples_uniform(N, 52), eps, "f32", autotune=True)
+    assert p2.L == p.L
