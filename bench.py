@@ -179,17 +179,6 @@ def run_ours(args):
         plan.adjoint(g, gc)            # dL/dc = A^H g
         plan.grad_x(g, fp, gx)         # dL/dx = Re(conj(g) f')
 
-    if args.only:
-        # profiling mode: only the named operation, no extra measurements
-        op = {"step": step, "fwd": lambda: plan.forward(c, f), "adj": lambda: plan.adjoint(f, gc),
-              "dx": lambda: plan.dx(c, g, gx)}[args.only]
-        for _ in range(args.warmup + args.steps):
-            op()
-        torch.cuda.synchronize(dev)
-        if rank == 0:
-            print(json.dumps({"only": args.only, "steps": args.steps, "warmup": args.warmup, "K": plan.K}))
-        return
-
     def timed(fn, steps, warmup):
         for _ in range(warmup):
             fn()
@@ -202,6 +191,21 @@ def run_ours(args):
             b.record(stream)
         torch.cuda.synchronize(dev)
         return [a.elapsed_time(b) for a, b in evs]
+
+    if args.only == "batch":
+        if rank == 0:
+            print(json.dumps({"batch_c5": batch_c5(api, dev, timed, args.steps)}), flush=True)
+        return
+    if args.only:
+        # profiling mode: only the named operation, no extra measurements
+        op = {"step": step, "fwd": lambda: plan.forward(c, f), "adj": lambda: plan.adjoint(f, gc),
+              "dx": lambda: plan.dx(c, g, gx)}[args.only]
+        for _ in range(args.warmup + args.steps):
+            op()
+        torch.cuda.synchronize(dev)
+        if rank == 0:
+            print(json.dumps({"only": args.only, "steps": args.steps, "warmup": args.warmup, "K": plan.K}))
+        return
 
     uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
     if ws > 1:
@@ -319,12 +323,58 @@ def run_ours(args):
             "clocks": clk.summary(),
         }
         line.update(extra)
+        if not args.no_batch:
+            line["batch_c5"] = batch_c5(api, dev, timed, args.steps)
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(plan, c_np, g_np, x, f)
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def batch_c5(api, dev, timed, steps):
+    """The serving workload: 512 independent problems, N log-uniform in [2^10, 2^18]
+    (integers, M = N), eps drawn from {1e-4, 1e-7, 1e-12}, uniform x, complex64 c.
+    Packed c, f (sum N values each); the same work run five ways."""
+    import torch
+    from paper_1701_04492_gb300 import workloads as wl
+    Ns, epss = wl.uneven_batch(512, SEED)
+    Ns = [int(n) for n in Ns]
+    xs = [wl.samples_uniform(n, SEED + 1 + i) for i, n in enumerate(Ns)]
+    tot = int(sum(Ns))
+    c = torch.tensor(wl.coeffs_cn(tot, SEED).astype(np.complex64), device=dev)
+    g = torch.tensor(wl.cotangent_cn(tot, SEED).astype(np.complex64), device=dev)
+    f = torch.empty(tot, dtype=torch.complex64, device=dev)
+    cc = torch.empty(tot, dtype=torch.complex64, device=dev)
+    out = {"workload": "512 problems, N=M=round(2^U[10,18]), eps in {1e-4,1e-7,1e-12}, uniform x, complex64",
+           "sum_N": tot, "unit": "Gpts/s (sum M / time)"}
+    variants = [("per_problem_launches", {"per_problem": True}, True),
+                ("per_problem_graph", {"per_problem": True, "graph": True}, False),
+                ("batched", {}, False),
+                ("batched_graph", {"graph": True}, False),
+                ("batched_autotuned", {"autotune": True}, False),
+                ("batched_graph_autotuned", {"graph": True, "autotune": True}, False)]
+    for name, kw, each in variants:
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        b = api.Batch(Ns, xs, epss, "f32", device=dev, **kw)
+        torch.cuda.synchronize(dev)
+        plan_s = time.perf_counter() - t0
+        if each:
+            fw, bw = (lambda: b.forward_each(c, f)), (lambda: b.adjoint_each(f, cc))
+        else:
+            fw, bw = (lambda: b.forward(c, f)), (lambda: b.adjoint(f, cc))
+        ms_f = timed(fw, steps, 3)
+        ms_fb = timed(lambda: (fw(), bw()), steps, 3)
+        b.check()
+        out[name] = {"fwd": tot * len(ms_f) / (sum(ms_f) * 1e-3) / 1e9,
+                     "fwd_bwd": tot * len(ms_fb) / (sum(ms_fb) * 1e-3) / 1e9,
+                     "fwd_ms": float(np.mean(ms_f)), "plan_s": plan_s,
+                     "launches_per_fwd": 2 * (b.count if each else b.classes),
+                     "grid_doubled": int(sum(int(L) > max(1024, 1 << (n - 1).bit_length()) for L, n in zip(b.L, Ns)))}
+        b.close()
+    return out
 
 
 def cpu_baseline(plan, c_np, g_np, x, f_gpu):
@@ -401,8 +451,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", choices=["step", "fwd", "adj", "dx"], default=None,
-                    help="profiling mode: run only this operation warmup+steps times, untimed")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 512-problem batch measurement")
+    ap.add_argument("--only", choices=["step", "fwd", "adj", "dx", "batch"], default=None,
+                    help="profiling mode: run only this operation warmup+steps times, untimed "
+                         "(batch: only the 512-problem batch measurement, timed)")
     args = ap.parse_args()
     if args.warmup < 3 and not args.only:
         args.warmup = 3

@@ -206,12 +206,14 @@ int nufft2_exec_noalloc(int64_t N, int64_t M, const double *x_dev, double eps, c
  * No counterpart in the paper, which plans and runs one transform at a time.  A
  * batch is `count` independent NUFFT-II problems (its own N_i, M_i, x_i, eps_i
  * each), each planned exactly as by nufft2_plan and run together: problems whose
- * grids have the same length L and whose ranks share a rank bound (4, 8, 12, 16)
- * form a class, and one kernel launch per pass covers a whole class, so a batch
+ * grids have the same length L and four-step split and whose ranks share a rank
+ * bound (4, 8, 12, 16) form a class, and one kernel launch per pass covers a whole class, so a batch
  * of 512 problems runs in a few dozen launches instead of 1024.  Batched launches
  * cover NUFFT_F32 problems on grids of up to 2^18 points; other problems run their
- * own plan's launches inside the batch calls.  Results are those of each problem's
- * own plan (the same arithmetic in the same order).
+ * own plan's launches inside the batch calls.  Forward results are bit-identical to
+ * each problem's own plan (the same arithmetic in the same order); the batched
+ * adjoint splits a class's rank sum over its own number of CTAs, so it agrees with
+ * the single plans to rounding.
  *
  * Packed layout: problem i's coefficients are c[offN_i .. offN_i + N_i) with
  * offN_i = sum_{j<i} N_j; its samples (x, f, g) are [offM_i .. offM_i + M_i) with

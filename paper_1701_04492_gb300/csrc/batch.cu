@@ -2,7 +2,7 @@
 //
 // Each problem has its own plan (rounding, rank, sort, tables: section 2.3's
 // planning stage, one per problem).  Problems whose grids have the same length L and
-// whose ranks share a rank bound KM form a class; one launch per pass then covers a
+// four-step split and whose ranks share a rank bound KM form a class; one launch per pass then covers a
 // whole class (blockIdx.z = the problem), reading each problem's arguments from a
 // device array built here once.  Batched launches exist for FP32 problems on grids
 // of up to 2^18 points; a larger problem fills the GPU alone, and an FP64 problem
@@ -20,6 +20,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "fill.cuh"
 #include "passes.cuh"
 
 namespace nufft {
@@ -34,6 +35,7 @@ struct nufft_batch_s {
     struct Class {
         int64_t L = 0;
         int KM = 0;
+        int lg1 = 0;            // the four-step split (log2 of the row length)
         bool single = false;    // one large problem: its own plan's launches
         std::vector<int> idx;   // members (problem indices)
         int rep = -1;           // member whose launch geometry covers the class
@@ -89,6 +91,14 @@ template <typename T, int KM>
 int build_class(nufft_batch b, nufft_batch_s::Class &c) {
     std::vector<PassArgs<T>> v1, v2, vA, vB;
     std::vector<Beta<T, KM>> be;
+    // pass B's rank split for the class: about four CTAs per SM over all its problems,
+    // at most any member's own split (whose partial-sum buffer it uses)
+    nufft_plan r = b->plans[c.rep];
+    const int blocks = (int)(r->L1 / r->CB) * (int)c.idx.size();
+    int sb = (4 * 152 + blocks - 1) / blocks;
+    for (int i : c.idx) sb = std::min(sb, b->plans[i]->SBsplit);
+    sb = std::max(1, sb);
+    c.nyB = sb;
     for (int i : c.idx) {
         nufft_plan p = b->plans[i];
         const PassArgs<T> a = base_args<T>(p);
@@ -97,6 +107,7 @@ int build_class(nufft_batch b, nufft_batch_s::Class &c) {
         if (int rc = rows_fields<T>(p, x2, false)) return rc;
         if (int rc = rows_fields<T>(p, xA, true)) return rc;
         cols_fields<T>(p, xB, true);
+        xB.SB = sb;
         // forward: in = c, out = f; adjoint: in = g, out = c
         x1.in_off = x2.in_off = b->offN[i];
         x1.out_off = x2.out_off = b->offM[i];
@@ -108,7 +119,6 @@ int build_class(nufft_batch b, nufft_batch_s::Class &c) {
         vB.push_back(xB);
         be.push_back(beta_of<T, KM>(p));
         c.ny1 = std::max(c.ny1, p->K);
-        c.nyB = std::max(c.nyB, p->SBsplit);
     }
     if (int rc = upload(&c.a1, v1)) return rc;
     if (int rc = upload(&c.a2, v2)) return rc;
@@ -230,21 +240,16 @@ int exec_many(nufft_batch b, bool adjoint, const void *in, void *out, cudaStream
 
 using nufft::free_batch;
 
-extern "C" int nufft2_plan_many(nufft_batch *out, int64_t count, const int64_t *N_host,
-                                const int64_t *M_host, const int64_t *L_host, const double *x_dev,
-                                const double *eps_host, int prec, unsigned flags, void *stream) {
-    using namespace nufft;
-    if (!out) return NUFFT_EINVAL;
+namespace nufft {
+namespace {
+
+// A batch from per-problem inputs: sample pointers xs[i], grid sizes L_host (or
+// NULL), four-step splits lc (or NULL).  flags may hold NUFFT_PLAN_AUTOTUNE for the
+// problems' own plans.  Inputs are validated by the caller.
+int plan_many_core(nufft_batch *out, int64_t count, const int64_t *N_host, const int64_t *M_host,
+                   const int64_t *L_host, const unsigned char *lc, const double *const *xs,
+                   const double *eps_host, int prec, unsigned flags, void *stream) {
     *out = nullptr;
-    if (count < 1 || count > 65535 || !N_host || !M_host || !eps_host) return NUFFT_EINVAL;
-    if (prec != NUFFT_F32 && prec != NUFFT_F64) return NUFFT_EINVAL;
-    if (flags & ~(NUFFT_BATCH_GRAPH | NUFFT_BATCH_PER_PROBLEM | NUFFT_PLAN_AUTOTUNE)) return NUFFT_EINVAL;
-    int64_t totM = 0;
-    for (int64_t i = 0; i < count; ++i) {
-        if (M_host[i] < 0 || M_host[i] >= ((int64_t)1 << 31)) return NUFFT_EINVAL;
-        totM += M_host[i];
-    }
-    if (totM > 0 && !x_dev) return NUFFT_EINVAL;
     nufft_batch b = new (std::nothrow) nufft_batch_s();
     if (!b) return NUFFT_ENOMEM;
     b->prec = prec;
@@ -256,10 +261,10 @@ extern "C" int nufft2_plan_many(nufft_batch *out, int64_t count, const int64_t *
         b->offN[i + 1] = b->offN[i] + N_host[i];
         b->offM[i + 1] = b->offM[i] + M_host[i];
     }
-    const unsigned pflags = flags & NUFFT_PLAN_AUTOTUNE;
     for (int64_t i = 0; i < count; ++i) {
-        const int rc = nufft2_plan(&b->plans[i], N_host[i], M_host[i], x_dev ? x_dev + b->offM[i] : nullptr,
-                                   eps_host[i], prec, L_host ? L_host[i] : 0, pflags, stream);
+        const unsigned pf = (flags & NUFFT_PLAN_AUTOTUNE) | (lc && lc[i] ? NUFFT_PLAN_LONG_COLUMNS : 0u);
+        const int rc = nufft2_plan(&b->plans[i], N_host[i], M_host[i], xs[i], eps_host[i], prec,
+                                   L_host ? L_host[i] : 0, pf, stream);
         if (rc) { free_batch(b); return rc; }
     }
     // classes: same L and rank bound; the representative has the largest K
@@ -268,13 +273,14 @@ extern "C" int nufft2_plan_many(nufft_batch *out, int64_t count, const int64_t *
         const bool single = prec == NUFFT_F64 || (flags & NUFFT_BATCH_PER_PROBLEM) ||
                             std::max(p->L1, p->L2) > MANY_P_MAX;
         auto it = std::find_if(b->cls.begin(), b->cls.end(), [&](const nufft_batch_s::Class &c) {
-            return !single && !c.single && c.L == p->L && c.KM == p->kmax;
+            return !single && !c.single && c.L == p->L && c.KM == p->kmax && c.lg1 == p->lg1;
         });
         if (it == b->cls.end()) {
             b->cls.emplace_back();
             it = b->cls.end() - 1;
             it->L = p->L;
             it->KM = p->kmax;
+            it->lg1 = p->lg1;
             it->single = single;
         }
         it->idx.push_back((int)i);
@@ -328,6 +334,157 @@ extern "C" int nufft2_plan_many(nufft_batch *out, int64_t count, const int64_t *
     }
     *out = b;
     return NUFFT_OK;
+}
+
+// Device time (ms) of one forward and one adjoint of the whole batch on scratch
+// buffers c (sum N) and f (sum M) holding hash values, L2 flushed before each run:
+// the best of three after a warm-up.
+int time_batch(nufft_batch b, void *c, void *f, void *flush, cudaStream_t s, float *ms) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        (void)cudaGetLastError();
+        if (e0) cudaEventDestroy(e0);
+        return NUFFT_ECUDA;
+    }
+    int rc = NUFFT_OK;
+    float best = 1e30f;
+    for (int it = 0; it < 4 && !rc; ++it) {
+        if (cudaMemsetAsync(flush, it, L2_FLUSH_BYTES, s) != cudaSuccess ||
+            cudaEventRecord(e0, s) != cudaSuccess) { rc = NUFFT_ECUDA; break; }
+        rc = exec_many<float>(b, false, c, f, s);
+        if (!rc) rc = exec_many<float>(b, true, f, c, s);
+        if (rc) break;
+        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = NUFFT_ECUDA;
+            break;
+        }
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (it > 0) best = std::min(best, t);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!rc) rc = nufft_batch_check(b, s);
+    *ms = best;
+    return rc;
+}
+
+// The batch autotuner (FP32 batched launches).  What a layout costs in a batch is its
+// share of a full GPU, not its latency alone, so layouts are compared class by class
+// on the batched launches themselves: for each class of the default layout (grid L0,
+// rows the longer FFT), its members are planned again on the oversampled grid 2 L0
+// (section 2.3: a longer grid lowers gamma and so K) and with the other four-step
+// split where log2 L is odd, each candidate batch is timed (forward + adjoint), and
+// the fastest layout is kept for those members.  Timed alone, a class measures what
+// it costs when classes run one after another; in a graph they overlap, so the batch
+// with the chosen layouts is then timed as a whole (graph or direct launches, as the
+// batch will run) against the default batch, and the faster batch is kept.
+int tune_many(nufft_batch *out, int64_t count, const int64_t *N, const int64_t *M, const double *const *xs,
+              const double *eps, unsigned flags, cudaStream_t s) {
+    nufft_batch b0 = nullptr;
+    if (int rc = plan_many_core(&b0, count, N, M, nullptr, nullptr, xs, eps, NUFFT_F32, flags, s)) return rc;
+    std::vector<int64_t> L(count);
+    std::vector<unsigned char> lc(count, 0);
+    for (int64_t i = 0; i < count; ++i) L[i] = b0->plans[i]->L;
+    void *c = nullptr, *f = nullptr, *flush = nullptr;
+    const size_t cn = (size_t)std::max<int64_t>(b0->offN.back(), 1), fm = (size_t)std::max<int64_t>(b0->offM.back(), 1);
+    int rc = NUFFT_OK;
+    if (cudaMalloc(&c, cn * 8) != cudaSuccess || cudaMalloc(&f, fm * 8) != cudaSuccess ||
+        cudaMalloc(&flush, L2_FLUSH_BYTES) != cudaSuccess ||
+        fill_hash<float>(c, 2 * (int64_t)cn, s) != cudaSuccess || fill_hash<float>(f, 2 * (int64_t)fm, s) != cudaSuccess)
+        rc = NUFFT_ECUDA;
+    bool changed = false;
+    const int64_t L_max_batched = (int64_t)MANY_P_MAX * MANY_P_MAX;
+    for (size_t k = 0; k < b0->cls.size() && !rc; ++k) {
+        const auto &cl = b0->cls[k];
+        if (cl.single) continue;
+        const size_t n = cl.idx.size();
+        std::vector<int64_t> sN(n), sM(n), sL(n);
+        std::vector<const double *> sx(n);
+        std::vector<double> se(n);
+        for (size_t q = 0; q < n; ++q) {
+            const int i = cl.idx[q];
+            sN[q] = N[i]; sM[q] = M[i]; sx[q] = xs[i]; se[q] = eps[i];
+        }
+        float tbest = 1e30f;
+        int64_t Lbest = cl.L;
+        bool lcbest = false;
+        for (int64_t Lc = cl.L; Lc <= std::min<int64_t>(2 * cl.L, L_max_batched) && !rc; Lc *= 2) {
+            int lg = 0;
+            while (((int64_t)1 << lg) < Lc) ++lg;
+            for (int lcc = 0; lcc < 2 && !rc; ++lcc) {
+                if (lcc == 1 && lg % 2 == 0) continue;
+                std::fill(sL.begin(), sL.end(), Lc);
+                std::vector<unsigned char> slc(n, (unsigned char)lcc);
+                nufft_batch t = nullptr;
+                int r2 = plan_many_core(&t, (int64_t)n, sN.data(), sM.data(), sL.data(), slc.data(), sx.data(),
+                                        se.data(), NUFFT_F32, flags & ~NUFFT_BATCH_GRAPH, s);
+                if (r2 == NUFFT_EUNSUPPORTED) continue;
+                if (r2) { rc = r2; break; }
+                float ms = 0.f;
+                r2 = time_batch(t, c, f, flush, s, &ms);
+                free_batch(t);
+                if (r2) { rc = r2; break; }
+                // the default layout wins ties: a new layout must save 3 %
+                if (Lc == cl.L && lcc == 0) tbest = ms;
+                else if (ms < 0.97f * tbest) { tbest = ms; Lbest = Lc; lcbest = lcc == 1; }
+            }
+        }
+        if (Lbest != cl.L || lcbest) {
+            changed = true;
+            for (int i : cl.idx) { L[i] = Lbest; lc[i] = lcbest ? 1 : 0; }
+        }
+    }
+    nufft_batch b1 = nullptr;
+    float t0 = 0.f, t1 = 0.f;
+    if (!rc && changed) rc = plan_many_core(&b1, count, N, M, L.data(), lc.data(), xs, eps, NUFFT_F32, flags, s);
+    if (!rc && changed) rc = time_batch(b0, c, f, flush, s, &t0);
+    if (!rc && changed) rc = time_batch(b1, c, f, flush, s, &t1);
+    cudaFree(c);
+    cudaFree(f);
+    cudaFree(flush);
+    if (rc) { free_batch(b0); free_batch(b1); return rc; }
+    if (changed && t1 < t0) {
+        free_batch(b0);
+        *out = b1;
+    } else {
+        free_batch(b1);
+        *out = b0;
+    }
+    return NUFFT_OK;
+}
+
+}  // namespace
+}  // namespace nufft
+
+extern "C" int nufft2_plan_many(nufft_batch *out, int64_t count, const int64_t *N_host,
+                                const int64_t *M_host, const int64_t *L_host, const double *x_dev,
+                                const double *eps_host, int prec, unsigned flags, void *stream) {
+    using namespace nufft;
+    if (!out) return NUFFT_EINVAL;
+    *out = nullptr;
+    if (count < 1 || count > 65535 || !N_host || !M_host || !eps_host) return NUFFT_EINVAL;
+    if (prec != NUFFT_F32 && prec != NUFFT_F64) return NUFFT_EINVAL;
+    if (flags & ~(NUFFT_BATCH_GRAPH | NUFFT_BATCH_PER_PROBLEM | NUFFT_PLAN_AUTOTUNE)) return NUFFT_EINVAL;
+    int64_t totM = 0;
+    for (int64_t i = 0; i < count; ++i) {
+        if (M_host[i] < 0 || M_host[i] >= ((int64_t)1 << 31)) return NUFFT_EINVAL;
+        totM += M_host[i];
+    }
+    if (totM > 0 && !x_dev) return NUFFT_EINVAL;
+    std::vector<const double *> xs((size_t)count, nullptr);
+    int64_t off = 0;
+    for (int64_t i = 0; i < count; ++i) {
+        xs[i] = M_host[i] > 0 ? x_dev + off : nullptr;
+        off += M_host[i];
+    }
+    const bool batched = prec == NUFFT_F32 && !(flags & NUFFT_BATCH_PER_PROBLEM);
+    bool L_free = true;   // no grid size fixed by the caller
+    for (int64_t i = 0; L_host && i < count; ++i) L_free = L_free && L_host[i] == 0;
+    if ((flags & NUFFT_PLAN_AUTOTUNE) && batched && L_free)
+        return tune_many(out, count, N_host, M_host, xs.data(), eps_host, flags & ~NUFFT_PLAN_AUTOTUNE,
+                         (cudaStream_t)stream);
+    return plan_many_core(out, count, N_host, M_host, L_host, nullptr, xs.data(), eps_host, prec, flags, stream);
 }
 
 extern "C" int nufft_batch_info(nufft_batch b, int64_t *classes, int64_t *total_N, int64_t *total_M,

@@ -180,7 +180,7 @@ __device__ __forceinline__ void pass1_body(const PassArgs<T> &a, const int bx, c
         // v_r(k) = T_r(z_k), z_k = (2k - N)/N, by the three-term recurrence run
         // across the elements (element-innermost for independent FMAs)
         const int Ni = (int)a.N;   // N < 2^23: 32-bit conversions (64-bit ones run on the FP64 pipe)
-        const T invN = T(1) / T(Ni);
+    const T invN = T(1) / T(Ni);
         constexpr int H = E < 8 ? E : 8;
 #pragma unroll
         for (int h0 = 0; h0 < E; h0 += H) {
@@ -571,7 +571,7 @@ __device__ __forceinline__ void passB_body(const PassArgs<T> &a, const int bx, c
     const int k1 = bx * a.C + cc;
     const int s = by, SB = a.SB;
     const int Ni = (int)a.N;   // N < 2^23: 32-bit conversions (64-bit ones run on the FP64 pipe)
-        const T invN = T(1) / T(Ni);
+    const T invN = T(1) / T(Ni);
     const int bufsz = a.C * a.S;                        // elements per buffer
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + 2 * bufsz);
     __shared__ int cta_failed;

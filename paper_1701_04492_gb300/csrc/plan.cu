@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "fft_team.cuh"
+#include "fill.cuh"
 #include "nufft_internal.h"
 
 namespace nufft {
@@ -419,11 +420,12 @@ int plan_create(nufft_plan *out, int64_t N, int64_t M, const double *x_dev, doub
 }
 
 // Device time (ms) of one forward and one adjoint exec of plan p on its own staging
-// buffers (zeroed): the best of three after one warm-up.
-int time_exec(nufft_plan p, cudaStream_t s, float *ms) {
-    const size_t cxs = p->prec == NUFFT_F32 ? 8 : 16;
-    NUFFT_CUDA_TRY(cudaMemsetAsync(p->cstage, 0, (size_t)p->N * cxs, s));
-    if (p->M > 0) NUFFT_CUDA_TRY(cudaMemsetAsync(p->fstage, 0, (size_t)p->M * cxs, s));
+// buffers (filled with hash values), L2 flushed before each run: the best of three
+// after one warm-up.
+int time_exec(nufft_plan p, void *flush, cudaStream_t s, float *ms) {
+    const bool f32 = p->prec == NUFFT_F32;
+    NUFFT_CUDA_TRY(f32 ? fill_hash<float>(p->cstage, 2 * p->N, s) : fill_hash<double>(p->cstage, 2 * p->N, s));
+    NUFFT_CUDA_TRY(f32 ? fill_hash<float>(p->fstage, 2 * p->M, s) : fill_hash<double>(p->fstage, 2 * p->M, s));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         (void)cudaGetLastError();
@@ -433,7 +435,8 @@ int time_exec(nufft_plan p, cudaStream_t s, float *ms) {
     int rc = NUFFT_OK;
     float best = 1e30f;
     for (int it = 0; it < 4 && !rc; ++it) {
-        if (cudaEventRecord(e0, s) != cudaSuccess) { rc = NUFFT_ECUDA; break; }
+        if (cudaMemsetAsync(flush, it, L2_FLUSH_BYTES, s) != cudaSuccess ||
+            cudaEventRecord(e0, s) != cudaSuccess) { rc = NUFFT_ECUDA; break; }
         rc = nufft2_exec(p, p->cstage, p->fstage, s);
         if (!rc) rc = nufft1_exec(p, p->fstage, p->cstage, s);
         if (rc) break;
@@ -488,8 +491,17 @@ int plan_autotune(nufft_plan *out, int64_t N, int64_t M, const double *x_dev, do
         free_plan(best);
         return plan_create(out, N, M, x_dev, eps, prec, choice.first, flags, choice.second, s);
     }
+    struct Flush {
+        void *p = nullptr;
+        ~Flush() { cudaFree(p); }
+    } flush;
+    if (cudaMalloc(&flush.p, L2_FLUSH_BYTES) != cudaSuccess) {
+        (void)cudaGetLastError();
+        free_plan(best);
+        return NUFFT_ENOMEM;
+    }
     float tbest = 0.f;
-    if (int rc = time_exec(best, s, &tbest)) { free_plan(best); return rc; }
+    if (int rc = time_exec(best, flush.p, s, &tbest)) { free_plan(best); return rc; }
     for (int64_t L = L0; L <= std::min<int64_t>(2 * L0, (int64_t)1 << LOG2_L_MAX); L *= 2) {
         int lg = 0;
         while (((int64_t)1 << lg) < L) ++lg;
@@ -500,7 +512,7 @@ int plan_autotune(nufft_plan *out, int64_t N, int64_t M, const double *x_dev, do
             if (rc == NUFFT_EUNSUPPORTED) continue;   // e.g. the shared-memory budget
             if (rc) { free_plan(best); return rc; }
             float t = 0.f;
-            if ((rc = time_exec(cand, s, &t))) { free_plan(cand); free_plan(best); return rc; }
+            if ((rc = time_exec(cand, flush.p, s, &t))) { free_plan(cand); free_plan(best); return rc; }
             if (t < tbest) {
                 free_plan(best);
                 best = cand;

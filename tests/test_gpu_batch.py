@@ -1,7 +1,9 @@
 """GPU: batches of uneven problems (batched launches, CUDA graph), the tuner's layouts.
 
-A batch runs each problem's own plan arithmetic, so its results must equal those of
-single plans exactly; each problem is also checked against the oracle (the low-rank
+A batch runs each problem's own plan arithmetic: its forward results must equal those of
+single plans exactly.  The batched adjoint splits each class's rank sum over its own
+number of CTAs, so it agrees with single plans to FP32 rounding (2-norm 1e-6).  Each
+problem is also checked against the oracle (the low-rank
 oracle on the grid the plan chose, at the tolerances of test_gpu_nufft.py, and the
 direct sum of eq. (1.2) at eps for a few rows).
 """
@@ -86,7 +88,10 @@ def test_batch_adjoint_matches_single_plans_and_oracle(api, prec):
             continue
         p = api.Plan(N[i], xs[i], eps[i], prec)
         ci = p.adjoint(g_dev[m0:m1].contiguous()).cpu().numpy()
-        assert np.array_equal(cc[n0:n1], ci), i
+        if prec == "f64":
+            assert np.array_equal(cc[n0:n1], ci), i      # FP64 batches run each plan's launches
+        else:
+            assert _rel2(cc[n0:n1], ci) <= 1e-6, i
         P = lowrank.plan(N[i], xs[i], eps[i], int(b.L[i]))
         co = lowrank.nufft2_adjoint(P, g[m0:m1].astype(np.complex128))
         assert _rel2(cc[n0:n1], co) <= TOL_REL[prec], i
@@ -102,9 +107,10 @@ def test_batch_each_and_per_problem_match_batched(api):
     assert torch.equal(b.forward_each(c_dev), f)
     assert torch.equal(bp.forward(c_dev), f)
     g_dev = torch.tensor(wl.cotangent_cn(int(b.total_M), 8).astype(np.complex64), device="cuda")
-    ca = b.adjoint(g_dev)
-    assert torch.equal(b.adjoint_each(g_dev), ca)
-    assert torch.equal(bp.adjoint(g_dev), ca)
+    ca = b.adjoint(g_dev).cpu().numpy()
+    ce = b.adjoint_each(g_dev)
+    assert torch.equal(bp.adjoint(g_dev), ce)          # both run each plan's own launches
+    assert _rel2(ce.cpu().numpy(), ca) <= 1e-6
     b.check()
 
 
@@ -213,3 +219,25 @@ def test_autotuned_plan_matches_oracle(api, N, eps):
     # the cached choice: a second plan of the same shape takes the same layout
     p2 = api.Plan(N, wl.samples_uniform(N, 52), eps, "f32", autotune=True)
     assert p2.L == p.L
+
+
+def test_batch_autotuned_matches_oracle(api):
+    """The batch tuner may move a class to the grid 2 L0 or the other split; every
+    problem still computes its transform (low-rank oracle on the grid it got)."""
+    N, xs, eps = _problems(40, 15, lo=10, hi=14)
+    b = api.Batch(N, xs, eps, "f32", autotune=True)
+    c_dev, c = _packed("f32", N, 16)
+    f = b.forward(c_dev).cpu().numpy()
+    g = wl.cotangent_cn(int(b.total_M), 17).astype(np.complex64)
+    cc = b.adjoint(torch.tensor(g, device="cuda")).cpu().numpy()
+    for i in range(b.count):
+        n0, n1 = b.offN[i], b.offN[i + 1]
+        m0, m1 = b.offM[i], b.offM[i + 1]
+        L0 = max(1024, 1 << (N[i] - 1).bit_length())
+        assert b.L[i] in (L0, 2 * L0)
+        if m1 == m0:
+            continue
+        P = lowrank.plan(N[i], xs[i], eps[i], int(b.L[i]))
+        assert P.K == b.K[i]
+        assert _rel2(f[m0:m1], lowrank.nufft2(P, c[n0:n1])) <= TOL_REL["f32"], i
+        assert _rel2(cc[n0:n1], lowrank.nufft2_adjoint(P, g[m0:m1].astype(np.complex128))) <= TOL_REL["f32"], i
