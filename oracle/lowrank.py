@@ -247,3 +247,45 @@ def dense_A(P):
 def dense_AK(P):
     """The rank-K approximation A_K = U V^T of eq. (2.6)."""
     return P.U @ P.V.T
+
+
+# ---------------------------------------------------------------------------
+# Two dimensions (section 4, eq. (4.4))
+# ---------------------------------------------------------------------------
+#
+# Reading of section 4's indices (garbled between m and n in the text): C is m x n,
+# k1 < m pairs with x and k2 < n with y; x is rounded on an m-point grid and y on an
+# n-point grid.  Each direction is the 1D method of section 2 with accuracy eps / 2:
+# with |A^x - A^x_K| <= e_x and |A^y - A^y_K| <= e_y entrywise, the product of the two
+# approximations is off by at most e_x + e_y + e_x e_y = eps (1 + eps / 4).
+
+
+@dataclass
+class Plan2D:
+    m: int
+    n: int
+    px: Plan        # the x direction: N = m frequencies, samples x
+    py: Plan        # the y direction: N = n frequencies, samples y
+
+
+def plan2d(m, n, x, y, eps, Lx=None, Ly=None):
+    """Planning stage of the 2D NUFFT-II: one 1D plan per direction at eps / 2."""
+    return Plan2D(m=int(m), n=int(n), px=plan(m, x, eps / 2.0, Lx), py=plan(n, y, eps / 2.0, Ly))
+
+
+def nufft2_2d(P, C):
+    """f_j = sum_{r1, r2} u^x_r1(j) u^y_r2(j) [F2(D_{v^x_r1} C D_{v^y_r2})][t^x_j, t^y_j]  (eq. (4.4)).
+
+    Each term is a full 2D FFT of the scaled (zero-padded) coefficient matrix, read at
+    the rounded grid point of every sample.
+    """
+    C = np.asarray(C, dtype=np.complex128)
+    px, py = P.px, P.py
+    f = np.zeros(px.M, dtype=np.complex128)
+    for r1 in range(px.K):
+        for r2 in range(py.K):
+            W = np.zeros((px.L, py.L), dtype=np.complex128)
+            W[:P.m, :P.n] = px.V[:, r1][:, None] * C * py.V[:, r2][None, :]
+            X = np.fft.fft2(W)
+            f += px.U[:, r1] * py.U[:, r2] * X[px.t, py.t]
+    return f

@@ -280,3 +280,54 @@ def test_x_derivative_against_torch_autograd():
     # d loss / d c in torch's convention (conjugate Wirtinger, x2) is A^H g.
     gc = ct.grad.numpy()
     assert np.max(np.abs(lowrank.nufft2_adjoint(P, g) - gc)) <= 1e-11 * np.sum(np.abs(g))
+
+
+# ---- two dimensions (section 4, eq. (4.4)) ----------------------------------------
+
+@pytest.mark.parametrize("m,n", [(16, 24), (32, 8), (40, 40)])
+@pytest.mark.parametrize("eps", [1e-4, 1e-9, 1e-12])
+def test_2d_within_bound_of_direct_sum(m, n, eps):
+    """|f_K - f|_inf <= (eps (1 + eps/4) + rounding) ||C||_1 (the product bound of the
+    two directions at eps / 2 each), against the direct 2D sum of eq. (4.1)."""
+    M = 300
+    x, y = wl.samples_2d_uniform(M, 70 + m)
+    r = np.random.default_rng(m * n)
+    C = (r.standard_normal((m, n)) + 1j * r.standard_normal((m, n))) / np.sqrt(2)
+    P = lowrank.plan2d(m, n, x, y, eps)
+    f = lowrank.nufft2_2d(P, C)
+    fd = direct.nudft2_2d(x, y, C)
+    assert np.max(np.abs(f - fd)) <= (eps * (1 + eps / 4) + 1e-13) * np.sum(np.abs(C))
+
+
+def test_2d_separable_is_product_of_1d_sums():
+    """C = a b^T: f_j = (sum_k1 a_k1 e^{-2 pi i k1 x_j}) (sum_k2 b_k2 e^{-2 pi i k2 y_j}),
+    which pins the pairing of k1 with x and k2 with y (m != n)."""
+    m, n, M = 24, 40, 200
+    x, y = wl.samples_2d_uniform(M, 81)
+    a = wl.coeffs_cn(m, 82)
+    b = wl.coeffs_cn(n, 83)
+    P = lowrank.plan2d(m, n, x, y, 1e-12)
+    f = lowrank.nufft2_2d(P, np.outer(a, b))
+    ref = direct.nudft2(x, a) * direct.nudft2(y, b)
+    assert np.max(np.abs(f - ref)) <= 2e-12 * np.sum(np.abs(a)) * np.sum(np.abs(b))
+
+
+def test_2d_single_column_is_the_1d_method():
+    """n = 1: only k2 = 0, so the 2D transform is the 1D transform of C[:, 0] in x."""
+    m, M = 64, 150
+    x, y = wl.samples_2d_uniform(M, 84)
+    c = wl.coeffs_cn(m, 85)
+    P = lowrank.plan2d(m, 1, x, y, 1e-10)
+    f = lowrank.nufft2_2d(P, c[:, None])
+    assert np.max(np.abs(f - direct.nudft2(x, c))) <= 1.1e-10 * np.sum(np.abs(c))
+
+
+def test_2d_planted_phase_sign_breaks_the_bound(monkeypatch):
+    """The e^{+i pi d} misprint of the Lemma's proof, planted in the oracle, fails the pin."""
+    m, n, M = 16, 16, 100
+    x, y = wl.samples_2d_uniform(M, 86)
+    C = np.outer(wl.coeffs_cn(m, 87), wl.coeffs_cn(n, 88))
+    monkeypatch.setattr(lowrank, "phase", lambda d: np.exp(1j * np.pi * np.asarray(d)))
+    P = lowrank.plan2d(m, n, x, y, 1e-9)
+    f = lowrank.nufft2_2d(P, C)
+    assert np.max(np.abs(f - direct.nudft2_2d(x, y, C))) > 1e-3 * np.sum(np.abs(C))
