@@ -201,6 +201,39 @@ int nufft_kernel_times(nufft_plan p, float *ms_out, int cap, int *count);
 int nufft2_exec_noalloc(int64_t N, int64_t M, const double *x_dev, double eps, const void *c_dev,
                         void *f_dev, void *stream);
 
+/* ---- The two-dimensional NUFFT-II (section 4) ---------------------------------
+ *
+ *     f_j = sum_{k1<m} sum_{k2<n} C[k1][k2] exp(-2 pi i (k1 x_j + k2 y_j))   (eq. (4.1))
+ *
+ * computed as eq. (4.4): each direction is the 1D method at accuracy eps / 2 (x
+ * rounded on an m-point grid, y on an n-point grid; the tensor product of the two
+ * rank-K approximations is then within eps (1 + eps / 4) of the 2D matrix entrywise),
+ * and f is a sum over K_x K_y diagonally scaled 2D FFTs, read at each sample's grid
+ * point.  The transforms along k1 (one per x rank) are shared by every y rank.
+ * Grids are powers of two of at least 32 points per direction (oversampled when m or n
+ * is not one).
+ *
+ * Reading of section 4's indices, which the text mixes up between m and n: C is m x n,
+ * k1 < m pairs with x and k2 < n with y.
+ *
+ *   m, n    1 <= m, n <= 2048.
+ *   M       number of samples, 0 <= M < 2^31.
+ *   x_dev, y_dev   M doubles each on the device; read during the call only.
+ *   prec    NUFFT_F32 (the 2D kernels are FP32; NUFFT_F64 returns NUFFT_EUNSUPPORTED).
+ *   flags   0 or NUFFT_PLAN_TIMING.
+ *
+ * The plan is a nufft_plan: nufft2_exec(p, C_dev, f_dev, stream) computes f from the
+ * row-major m x n matrix C (complex64); nufft2_exec_batch and nufft_destroy apply;
+ * the other exec calls return NUFFT_EUNSUPPORTED on a 2D plan.  nufft2_plan_info
+ * reports K_x, gamma_x and L = L_x L_y.  Synchronises `stream`. */
+int nufft2d_plan(nufft_plan *out, int64_t m, int64_t n, int64_t M, const double *x_dev, const double *y_dev,
+                 double eps, int prec, unsigned flags, void *stream);
+
+/* Ranks, gammas and grid sizes of a 2D plan, per direction.  Any output may be NULL.
+ * NUFFT_EINVAL for a 1D plan. */
+int nufft2d_plan_info(nufft_plan p, int *Kx, int *Ky, double *gamma_x, double *gamma_y, int64_t *Lx,
+                      int64_t *Ly);
+
 /* ---- Batches: many independent problems of uneven sizes ----------------------
  *
  * No counterpart in the paper, which plans and runs one transform at a time.  A

@@ -278,6 +278,70 @@ def nufft2(c, x, eps=1e-9, plan=None, L=0):
 __all__ = ["Plan", "nufft2", "NufftError", "NUFFT_F32", "NUFFT_F64"]
 
 
+class Plan2D:
+    """A planned 2D NUFFT-II (section 4, eq. (4.4)) on samples (x_j, y_j).
+
+    f_j = sum_{k1<m, k2<n} C[k1, k2] exp(-2 pi i (k1 x_j + k2 y_j)), C an m x n complex64
+    tensor (row-major).  Each direction runs the 1D method at eps / 2.
+    """
+
+    def __init__(self, m, n, x, y, eps, precision="f32", timing=False, device=None):
+        lib = _lib.load()
+        device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        x = torch.as_tensor(x).detach().to(device=device, dtype=torch.float64).contiguous().reshape(-1)
+        y = torch.as_tensor(y).detach().to(device=device, dtype=torch.float64).contiguous().reshape(-1)
+        if x.numel() != y.numel():
+            raise ValueError("x and y must have the same length")
+        self.device = device
+        self.m, self.n, self.M = int(m), int(n), int(x.numel())
+        self.prec = _prec(precision)
+        self.cdtype = _CDTYPE[self.prec]
+        h = ctypes.c_void_p()
+        with torch.cuda.device(device):
+            rc = lib.nufft2d_plan(ctypes.byref(h), self.m, self.n, self.M, _ptr(x) if self.M else None,
+                                  _ptr(y) if self.M else None, float(eps), self.prec,
+                                  NUFFT_PLAN_TIMING if timing else 0, _stream(device))
+        check(rc, "nufft2d_plan")
+        self._h = h
+        Kx, Ky, gx, gy = ctypes.c_int(), ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+        Lx, Ly = ctypes.c_int64(), ctypes.c_int64()
+        check(lib.nufft2d_plan_info(h, ctypes.byref(Kx), ctypes.byref(Ky), ctypes.byref(gx), ctypes.byref(gy),
+                                    ctypes.byref(Lx), ctypes.byref(Ly)), "nufft2d_plan_info")
+        self.Kx, self.Ky, self.gamma_x, self.gamma_y = Kx.value, Ky.value, gx.value, gy.value
+        self.Lx, self.Ly = Lx.value, Ly.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            torch.cuda.synchronize(self.device)
+            _lib.load().nufft_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def forward(self, C, out=None):
+        """f = the 2D NUFFT-II of the m x n matrix C."""
+        if C.device != self.device or C.dtype != self.cdtype or not C.is_contiguous() or C.numel() != self.m * self.n:
+            raise ValueError("C must be a contiguous %s tensor of %d x %d elements on %s"
+                             % (self.cdtype, self.m, self.n, self.device))
+        f = out if out is not None else torch.empty(self.M, dtype=self.cdtype, device=self.device)
+        if f.device != self.device or f.dtype != self.cdtype or not f.is_contiguous() or f.numel() != self.M:
+            raise ValueError("f must be a contiguous %s tensor of %d elements" % (self.cdtype, self.M))
+        with torch.cuda.device(self.device):
+            check(_lib.load().nufft2_exec(self._h, _ptr(C), _ptr(f), _stream(self.device)), "nufft2_exec")
+        return f
+
+    def kernel_times(self):
+        """Device milliseconds of the column and row pass of the last forward (timing=True)."""
+        buf = (ctypes.c_float * 8)()
+        k = ctypes.c_int()
+        check(_lib.load().nufft_kernel_times(self._h, buf, 8, ctypes.byref(k)), "nufft_kernel_times")
+        return list(buf[: k.value])
+
+
 class Batch:
     """Many independent NUFFT-II problems of uneven sizes, run together.
 

@@ -2,6 +2,8 @@
 // and the unfused comparator (the section 2.3 one-liner run step by step).
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include <algorithm>
 #include <cstdint>
 
@@ -19,6 +21,11 @@ NUFFT_DECLARE_ROWS(double, 12)
 NUFFT_DECLARE_ROWS(double, 16)
 NUFFT_DECLARE_COLS(float)
 NUFFT_DECLARE_COLS(double)
+NUFFT_DECLARE_COLS_2D()
+NUFFT_DECLARE_2D(4)
+NUFFT_DECLARE_2D(8)
+NUFFT_DECLARE_2D(12)
+NUFFT_DECLARE_2D(16)
 
 namespace {
 
@@ -344,8 +351,37 @@ int plan_unfused_factors(nufft_plan p, cudaStream_t s) {
     return NUFFT_OK;
 }
 
+// The 2D transform (section 4, eq. (4.4)): FP32 plans only.
+int exec_forward_2d(nufft_plan p, const void *C, void *f, cudaStream_t s) {
+    using T = float;
+    if (p->M == 0) return NUFFT_OK;
+    PassArgs<T> a = base_args<T>(p);
+    a.in = (const cx<T> *)C;
+    a.out = (cx<T> *)f;
+    a.ncol = (int)p->N2;
+    a.ldc = (int)p->N2;
+    a.K2 = p->K2;
+    a.dsorted2 = (const T *)p->dsorted2;
+    a.vy = (const T *)p->vy;
+    a.inv_gamma2 = p->gamma2 > 0.0 ? (T)(1.0 / p->gamma2) : T(0);
+    if (int rc = mark(p, s, true)) return rc;
+    if (int rc = launch_cols_2d<T>(p, a, s)) return rc;
+    if (int rc = mark(p, s, false)) return rc;
+    int rc = NUFFT_EUNSUPPORTED;
+    switch (p->kmax) {
+        case 4: rc = launch_rows_2d<T, 4>(p, a, s); break;
+        case 8: rc = launch_rows_2d<T, 8>(p, a, s); break;
+        case 12: rc = launch_rows_2d<T, 12>(p, a, s); break;
+        case 16: rc = launch_rows_2d<T, 16>(p, a, s); break;
+        default: break;
+    }
+    if (rc) return rc;
+    return mark(p, s, false);
+}
+
 template <typename T>
 int exec_forward(nufft_plan p, const void *c, void *f, cudaStream_t s) {
+    if (p->dims == 2) return std::is_same<T, float>::value ? exec_forward_2d(p, c, f, s) : NUFFT_EUNSUPPORTED;
     if (p->M == 0) return NUFFT_OK;
     PassArgs<T> a = base_args<T>(p);
     a.in = (const cx<T> *)c;
@@ -486,6 +522,7 @@ extern "C" int nufft2_exec(nufft_plan p, const void *c_dev, void *f_dev, void *s
 }
 
 extern "C" int nufft1_exec(nufft_plan p, const void *g_dev, void *c_dev, void *stream) {
+    if (p && p->dims == 2) return NUFFT_EUNSUPPORTED;   // the 2D transform has its forward only
     if (!p || !c_dev || (p->M > 0 && !g_dev)) return NUFFT_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     return p->prec == NUFFT_F32 ? exec_adjoint<float>(p, g_dev, c_dev, s)
@@ -494,6 +531,7 @@ extern "C" int nufft1_exec(nufft_plan p, const void *g_dev, void *c_dev, void *s
 
 extern "C" int nufft2_exec_dx(nufft_plan p, const void *c_dev, const void *g_dev, void *gx_dev,
                               int accumulate, void *stream) {
+    if (p && p->dims == 2) return NUFFT_EUNSUPPORTED;   // the 2D transform has its forward only
     if (!p || !c_dev || (p->M > 0 && (!g_dev || !gx_dev))) return NUFFT_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     return p->prec == NUFFT_F32 ? exec_dx<float>(p, c_dev, g_dev, gx_dev, accumulate, s)
@@ -502,6 +540,7 @@ extern "C" int nufft2_exec_dx(nufft_plan p, const void *c_dev, const void *g_dev
 
 extern "C" int nufft2_exec_deriv(nufft_plan p, const void *c_dev, void *f_dev, void *fprime_dev,
                                  void *stream) {
+    if (p && p->dims == 2) return NUFFT_EUNSUPPORTED;   // the 2D transform has its forward only
     if (!p || !c_dev || (p->M > 0 && (!f_dev || !fprime_dev))) return NUFFT_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     return p->prec == NUFFT_F32 ? nufft::exec_deriv<float>(p, c_dev, f_dev, fprime_dev, s)
@@ -510,6 +549,7 @@ extern "C" int nufft2_exec_deriv(nufft_plan p, const void *c_dev, void *f_dev, v
 
 extern "C" int nufft2_grad_x(nufft_plan p, const void *g_dev, const void *fprime_dev, void *gx_dev,
                              int accumulate, void *stream) {
+    if (p && p->dims == 2) return NUFFT_EUNSUPPORTED;   // the 2D transform has its forward only
     if (!p || (p->M > 0 && (!g_dev || !fprime_dev || !gx_dev))) return NUFFT_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     return p->prec == NUFFT_F32 ? nufft::exec_grad_x<float>(p, g_dev, fprime_dev, gx_dev, accumulate, s)
@@ -530,6 +570,7 @@ extern "C" int nufft2_exec_batch(nufft_plan p, int64_t B, const void *c_dev, int
 }
 
 extern "C" int nufft2_exec_host(nufft_plan p, const void *c_host, void *f_host, void *stream) {
+    if (p && p->dims == 2) return NUFFT_EUNSUPPORTED;   // the 2D transform has its forward only
     if (!p || !c_host || (p->M > 0 && !f_host)) return NUFFT_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t cxs = p->prec == NUFFT_F32 ? 8 : 16;
@@ -542,6 +583,7 @@ extern "C" int nufft2_exec_host(nufft_plan p, const void *c_host, void *f_host, 
 }
 
 extern "C" int nufft2_exec_unfused(nufft_plan p, const void *c_dev, void *f_dev, void *stream) {
+    if (p && p->dims == 2) return NUFFT_EUNSUPPORTED;   // the 2D transform has its forward only
     if (!p || !c_dev || (p->M > 0 && !f_dev)) return NUFFT_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     return p->prec == NUFFT_F32 ? exec_unfused<float>(p, c_dev, f_dev, s)

@@ -27,6 +27,7 @@ struct Beta { T b[KM][KM]; };
 struct nufft_plan_s {
     int64_t N = 0, M = 0, L = 0;
     int L1 = 0, L2 = 0, lg1 = 0, lg2 = 0;
+    int dims = 1;          // 2: the transform of section 4 (N = m, N2 = n; L2 = Lx rows, L1 = Ly)
     int prec = 0;
     int K = 1;
     int kmax = 4;          // rank rounded up to 4, 8, 12 or 16 (kernel template)
@@ -72,6 +73,17 @@ struct nufft_plan_s {
     void *Ufac = nullptr;      // FP64 plans: u_r in sorted order, M x K complex
     void *Vfac = nullptr;      // FP64 plans: v_r, K x N real
     int64_t work_bytes = 0;
+
+    // the 2D transform: the y direction (x uses N, K, gamma, beta, t_j, d_j, dsorted)
+    int64_t N2 = 0;            // n
+    int K2 = 1;
+    double gamma2 = 0.0;
+    double beta2[nufft::KMAX_ALL][nufft::KMAX_ALL] = {};
+    double alpha2[nufft::KMAX_ALL][nufft::KMAX_ALL] = {};
+    int32_t *t2_j = nullptr;   // t^y in sample order
+    double *d2_j = nullptr;    // d^y in sample order
+    void *dsorted2 = nullptr;  // d^y in sorted order
+    void *vy = nullptr;        // T_r2(2 k2 / n - 1), K2 x L1
 
     // NUFFT_PLAN_TIMING: events around each launch of the last exec call
     cudaEvent_t ev[8] = {};

@@ -80,6 +80,12 @@ struct PassArgs {
     T inv_gamma;
     int SB;               // pass B: rank splits (CTAs per column block)
     int64_t in_off, out_off;   // batched launches: this problem's offsets into the packed in / out
+    // two dimensions (section 4): N = m is the x extent, the y direction has K2 ranks
+    int ncol, ldc;        // pass 1: valid columns (n) and the row stride of C (n)
+    int K2;               // rank in y
+    const T *dsorted2;    // d^y in sorted order
+    const T *vy;          // T_r2(2 k2 / n - 1) for k2 < n (0 beyond), K2 x L1
+    T inv_gamma2;         // 1 / gamma_y
 };
 
 // T_r(z) by the three-term recurrence (NIST 18.9.1).
@@ -140,7 +146,10 @@ __device__ __forceinline__ cx<T> *smem_base() {
 
 // ---- pass 1: V-scale + column FFTs (length L2) + four-step twiddle ----------------
 // Shared memory: C exchange slots of S elements, then the four-step table [q][cc].
-template <typename T, int P2>
+// TWO_D: the column pass of section 4's transform.  C is row-major m x n (row stride
+// ldc), the column element e is the x-frequency k1 < m (z = (2 e - m) / m), a column is
+// the y-frequency k2 < n, and there is no four-step twiddle (the 2D DFT separates).
+template <typename T, int P2, bool TWO_D = false>
 __device__ __forceinline__ void pass1_body(const PassArgs<T> &a, const int bx, const int by) {
     constexpr int E = e_of<T, P2>();
     using TF = TeamFft<T, P2, E, false>;
@@ -151,18 +160,28 @@ __device__ __forceinline__ void pass1_body(const PassArgs<T> &a, const int bx, c
     const int k1 = bx * a.C + cc;
     const int r = by;
     cx<T> *ftab = smem + a.C * a.S;
-    fill_fourstep<T, E, TT>(a, k1, tt, ftab + cc, a.C);
+    if constexpr (!TWO_D) fill_fourstep<T, E, TT>(a, k1, tt, ftab + cc, a.C);
     cx<T> v[E];
-    if (a.mode & MODE_PLAIN_IN) {
+    const int k0 = k1 + a.L1 * tt, kstride = a.L1 * TT;   // 1D: element m is c[k0 + m kstride]
+    if constexpr (TWO_D) {
+        // element e = tt + TT m of column k1: C[e][k1]
+        const bool col_ok = k1 < a.ncol;
+        const cx<T> *cb = a.in + (int64_t)tt * a.ldc + k1;
+        const int64_t estride = (int64_t)TT * a.ldc;
+#pragma unroll
+        for (int m = 0; m < E; ++m)
+            v[m] = (col_ok && tt + TT * m < a.N) ? cb[m * estride] : mk<T>(0, 0);
+    } else if (a.mode & MODE_PLAIN_IN) {
         const cx<T> *W = a.in + (int64_t)r * a.L + k1 + a.L1 * tt;
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = W[m * (a.L1 * TT)];
     } else {
-        const int k0 = k1 + a.L1 * tt, kstride = a.L1 * TT;
         const cx<T> *cb = a.in + k0;
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = k0 + m * kstride < a.N ? cb[m * kstride] : mk<T>(0, 0);
-        if constexpr (kFactors<T>) {
+    }
+    if (!(a.mode & MODE_PLAIN_IN)) {
+        if constexpr (kFactors<T> && !TWO_D) {
             // x_k = v_r(k) c_k with the plan's V
             const T *vr = a.vfac + (int64_t)r * a.N;
 #pragma unroll
@@ -180,14 +199,14 @@ __device__ __forceinline__ void pass1_body(const PassArgs<T> &a, const int bx, c
         // v_r(k) = T_r(z_k), z_k = (2k - N)/N, by the three-term recurrence run
         // across the elements (element-innermost for independent FMAs)
         const int Ni = (int)a.N;   // N < 2^23: 32-bit conversions (64-bit ones run on the FP64 pipe)
-    const T invN = T(1) / T(Ni);
+        const T invN = T(1) / T(Ni);
         constexpr int H = E < 8 ? E : 8;
 #pragma unroll
         for (int h0 = 0; h0 < E; h0 += H) {
             T z2[H], ta[H], tb[H];
 #pragma unroll
             for (int m = 0; m < H; ++m) {
-                const int k = k1 + a.L1 * (tt + TT * (h0 + m));
+                const int k = TWO_D ? tt + TT * (h0 + m) : k1 + a.L1 * (tt + TT * (h0 + m));
                 const T z = T(2 * k - Ni) * invN;
                 z2[m] = T(2) * z;
                 ta[m] = T(1);
@@ -218,17 +237,22 @@ __device__ __forceinline__ void pass1_body(const PassArgs<T> &a, const int bx, c
         }
     }
     TF::run(v, tt, smem + cc * a.S, a.twc);
-    __syncthreads();   // the four-step table is complete
-    const cx<T> base = twiddle_L<T>(a, tt * k1);
     // output n2 = tt + TT q(e) goes to Y_r[n2][k1]
     cx<T> *yb = a.Y + (int64_t)r * a.L + tt * a.L1 + k1;
     const int ystride = TT * a.L1;
-    const cx<T> *fb = ftab + cc;
+    if constexpr (TWO_D) {
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int q = TF::out_q(e);
-        const cx<T> w = cmul<T>(base, fb[q * a.C]);
-        yb[q * ystride] = cmul<T>(v[e], w);
+        for (int e = 0; e < E; ++e) yb[TF::out_q(e) * ystride] = v[e];
+    } else {
+        __syncthreads();   // the four-step table is complete
+        const cx<T> base = twiddle_L<T>(a, tt * k1);
+        const cx<T> *fb = ftab + cc;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int q = TF::out_q(e);
+            const cx<T> w = cmul<T>(base, fb[q * a.C]);
+            yb[q * ystride] = cmul<T>(v[e], w);
+        }
     }
 }
 
@@ -684,6 +708,127 @@ __device__ __forceinline__ void passB_body(const PassArgs<T> &a, const int bx, c
     if (threadIdx.x == 0) a.counters[bx] = 0;   // ready for the next call
 }
 
+
+// ---- 2D row pass (section 4, eq. (4.4)) ---------------------------------------------
+// One CTA per x-grid row s1 = b.  For each r1 the row W_r1[s1][:] of pass 1's output
+// arrives by bulk copy (two buffers: the row of r1 + 2 is fetched while r1 + 1 is
+// used), and the teams transform it once per r2 under the y-scale,
+// X_r1r2[s1][:] = F_L1(i^r2 T_r2(z^y) o W_r1[s1][:]), one slot each.  The samples on
+// row s1 then add u^x_r1 sum_r2 u^y_r2 X_r1r2[s1][t^y] to their partial sums (fscr,
+// sorted order, the same thread for a sample at every r1); at the last r1 the phase
+// exp(-i pi (d^x + d^y)) is applied and f written.  The pass-1 transforms over k1 are
+// shared by every r2, which is the saving the paper notes after eq. (4.4).
+// Shared memory: two row buffers (L1 each), K2 slots of S, two mbarriers.
+template <typename T, int P1, int KM, typename BT>
+__device__ __forceinline__ void pass2d_body(const PassArgs<T> &a, const BT &betax, const BT &betay,
+                                            const int b) {
+    constexpr int E = e_of<T, P1>();
+    using TF = TeamFft<T, P1, E, false>;
+    constexpr int TT = TF::TT;
+    cx<T> *smem = smem_base<T>();
+    const int team = threadIdx.x / TT, tt = threadIdx.x % TT;
+    const int nt = blockDim.x / TT;
+    const int K1 = a.K, K2 = a.K2;
+    cx<T> *stg = smem;                 // two rows as copied
+    cx<T> *slots = smem + 2 * P1;      // K2 transformed rows
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(slots + K2 * a.S);
+    __shared__ int cta_failed;
+    constexpr uint32_t ROW_BYTES = P1 * sizeof(cx<T>);
+    const cx<T> *rows = a.Y + (int64_t)b * a.L1;   // W_r1[s1][:] at rows + r1 L
+    if (threadIdx.x == 0) {
+        cta_failed = 0;
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        fence_mbar_init();
+        for (int i = 0; i < 2 && i < K1; ++i) {
+            mbar_arrive_expect_tx(&mbar[i], ROW_BYTES);
+            bulk_copy_g2s(stg + i * P1, rows + (int64_t)i * a.L, ROW_BYTES, &mbar[i]);
+        }
+    }
+    __syncthreads();
+    const int i0 = a.bstart[b], i1 = a.bstart[b + 1];
+    const T invg = a.inv_gamma, invg2 = a.inv_gamma2;
+    for (int r1 = 0; r1 < K1; ++r1) {
+        const int buf = r1 & 1;
+        mbar_wait_bounded(&mbar[buf], (r1 >> 1) & 1, a.err, &cta_failed);
+        const cx<T> *row = stg + buf * P1;
+        auto round = [&](const int j0, auto pred) {   // one r2 per team; PRED: idle teams
+            constexpr bool PRED = decltype(pred)::value;
+            const int r2 = j0 + team;
+            const bool act = !PRED || r2 < K2;
+            cx<T> *sm = slots + (act ? r2 : 0) * a.S;
+            const T *vy = a.vy + (int64_t)(act ? r2 : 0) * P1;
+            cx<T> v[E];
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const int k = tt + TT * m;
+                const cx<T> w = row[k];
+                const T sc = act ? vy[k] : T(0);
+                v[m] = mul_ipow<T>(mk<T>(sc * w.x, sc * w.y), r2);
+            }
+            TF::template run<PRED>(v, tt, sm, a.twr, act);
+            if (act) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) sm[TF::out_padded(tt, e)] = v[e];
+            }
+        };
+        for (int j0 = 0; j0 < K2; j0 += nt) {
+            if (j0 + nt <= K2) round(j0, std::false_type{});
+            else round(j0, std::true_type{});
+        }
+        __syncthreads();   // the K2 rows are complete and stg[buf] is no longer read
+        if (threadIdx.x == 0 && r1 + 2 < K1) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&mbar[buf], ROW_BYTES);
+            bulk_copy_g2s(stg + buf * P1, rows + (int64_t)(r1 + 2) * a.L, ROW_BYTES, &mbar[buf]);
+        }
+#pragma unroll 1
+        for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+            const int n1 = a.tsorted[i] >> a.lg2;   // t^y
+            const T dx = a.dsorted[i], dy = a.dsorted2[i];
+            // mu^x_r1 = sum_p beta^x_r1p T_p(d^x / gamma_x), mu^y_r2 likewise in y
+            T Tp[KM];
+            const T xi = dx * invg;
+            Tp[0] = T(1);
+            if (KM > 1) Tp[1] = xi;
+#pragma unroll
+            for (int q = 2; q < KM; ++q) Tp[q] = fma(T(2) * xi, Tp[q - 1], -Tp[q - 2]);
+            T mux = T(0);
+#pragma unroll
+            for (int q = 0; q < KM; ++q)
+                if (((q ^ r1) & 1) == 0) mux = fma(beta_at(betax, r1, q), Tp[q], mux);
+            const T eta = dy * invg2;
+            Tp[0] = T(1);
+            if (KM > 1) Tp[1] = eta;
+#pragma unroll
+            for (int q = 2; q < KM; ++q) Tp[q] = fma(T(2) * eta, Tp[q - 1], -Tp[q - 2]);
+            cx<T> S = mk<T>(0, 0);
+#pragma unroll
+            for (int r2 = 0; r2 < KM; ++r2) {
+                if (r2 < K2) {
+                    T mu = T(0);
+#pragma unroll
+                    for (int q = (r2 & 1); q < KM; q += 2) mu = fma(beta_at(betay, r2, q), Tp[q], mu);
+                    const cx<T> x = slots[r2 * a.S + padi<E>(n1)];
+                    S.x = fma(mu, x.x, S.x);
+                    S.y = fma(mu, x.y, S.y);
+                }
+            }
+            cx<T> acc = r1 == 0 ? mk<T>(0, 0) : a.fscr[i];
+            acc.x = fma(mux, S.x, acc.x);
+            acc.y = fma(mux, S.y, acc.y);
+            if (r1 + 1 < K1) {
+                a.fscr[i] = acc;
+            } else {
+                T sn, cs;
+                sincospi_t<T>(dx + dy, &sn, &cs);
+                a.out[a.perm[i]] = mk<T>(fma(acc.x, cs, acc.y * sn), fma(acc.y, cs, -acc.x * sn));
+            }
+        }
+        __syncthreads();   // the slots are rewritten at the next r1
+    }
+}
+
 // ---- kernels ----------------------------------------------------------------------
 // One plan per launch: the arguments are kernel parameters.
 template <typename T, int P2>
@@ -703,6 +848,17 @@ __global__ void __launch_bounds__(256) k_passA(const __grid_constant__ PassArgs<
 template <typename T, int P2>
 __global__ void __launch_bounds__(128, 3) k_passB(const __grid_constant__ PassArgs<T> a) {
     passB_body<T, P2>(a, blockIdx.x, blockIdx.y);
+}
+// the 2D transform (section 4): column pass and row pass
+template <typename T, int P2>
+__global__ void __launch_bounds__(256, 2) k_pass1_2d(const __grid_constant__ PassArgs<T> a) {
+    pass1_body<T, P2, true>(a, blockIdx.x, blockIdx.y);
+}
+template <typename T, int P1, int KM>
+__global__ void __launch_bounds__(256) k_pass2d(const __grid_constant__ PassArgs<T> a,
+                                                const __grid_constant__ Beta<T, KM> betax,
+                                                const __grid_constant__ Beta<T, KM> betay) {
+    pass2d_body<T, P1, KM>(a, betax, betay, blockIdx.x);
 }
 
 // Many independent plans per launch (a batch of uneven problems): blockIdx.z is the
@@ -947,6 +1103,46 @@ int launch_rows_many(nufft_plan rep, const PassArgs<T> *args, const Beta<T, KM> 
     });
 }
 
+// The 2D transform of plan p (section 4).  Column pass: pass 1 in its 2D mode over the
+// L1 = Ly columns of length L2 = Lx, grid.y = K (the x rank).
+template <typename T>
+int launch_cols_2d(nufft_plan p, const PassArgs<T> &a0, cudaStream_t s) {
+    PassArgs<T> a = a0;
+    cols_fields<T>(p, a, false);
+    return dispatch_P(p->L2, [&](auto PC) -> int {
+        constexpr int P = decltype(PC)::value;
+        constexpr int TT = P / e_of<T, P>();
+        static int done[64] = {};
+        auto kern = k_pass1_2d<T, P>;
+        if (int r = set_smem(kern, p->smem1, p->device, done)) return r;
+        kern<<<dim3(p->L1 / a.C, p->K), dim3(a.C * TT), p->smem1, s>>>(a);
+        return launch_status();
+    });
+}
+
+// Row pass of the 2D transform: one CTA per x-grid row.  beta: [r][p] of the x
+// direction (K ranks) in p->beta, of y (K2) in p->beta2.
+template <typename T, int KM>
+int launch_rows_2d(nufft_plan p, const PassArgs<T> &a0, cudaStream_t s) {
+    PassArgs<T> a = a0;
+    a.S = p->S2;
+    Beta<T, KM> bx, by;
+    for (int r = 0; r < KM; ++r)
+        for (int q = 0; q < KM; ++q) {
+            bx.b[r][q] = (T)p->beta[r][q];
+            by.b[r][q] = (T)p->beta2[r][q];
+        }
+    return dispatch_P(p->L1, [&](auto PC) -> int {
+        constexpr int P = decltype(PC)::value;
+        constexpr int TT = P / e_of<T, P>();
+        static int done[64] = {};
+        auto kern = k_pass2d<T, P, KM>;
+        if (int r = set_smem(kern, p->smem2, p->device, done)) return r;
+        kern<<<dim3(p->L2), dim3(p->nt2 * TT), p->smem2, s>>>(a, bx, by);
+        return launch_status();
+    });
+}
+
 // Common arguments of every pass of plan p (defined in exec.cu).
 template <typename T>
 PassArgs<T> base_args(nufft_plan p);
@@ -961,6 +1157,10 @@ PassArgs<T> base_args(nufft_plan p);
     extern template int launch_rows_many<float, KM>(nufft_plan, const PassArgs<float> *,              \
                                                     const Beta<float, KM> *, int, bool, const void *, \
                                                     void *, cudaStream_t);
+#define NUFFT_DECLARE_2D(KM) \
+    extern template int launch_rows_2d<float, KM>(nufft_plan, const PassArgs<float> &, cudaStream_t);
+#define NUFFT_DECLARE_COLS_2D() \
+    extern template int launch_cols_2d<float>(nufft_plan, const PassArgs<float> &, cudaStream_t);
 #define NUFFT_DECLARE_COLS_MANY()                                                                  \
     extern template int launch_cols_many<float>(nufft_plan, const PassArgs<float> *, int, int, bool, \
                                                 const void *, void *, cudaStream_t);

@@ -252,17 +252,70 @@ int build_tables(nufft_plan p, cudaStream_t s) {
     return upload_table<T>(&p->twhi, re, im, s, &p->work_bytes);
 }
 
+// Bucket the samples: a stable LSD radix sort by (bucket, n1, row) of the grid index
+// t_j, then t and d (and d2, for the 2D transform) in sorted order and the bucket
+// boundaries.
+template <typename T>
+int sort_samples(nufft_plan p, cudaStream_t s) {
+    const int64_t M = p->M;
+    struct Scratch {
+        int32_t *ka = nullptr, *va = nullptr, *kb = nullptr, *vb = nullptr, *cnt = nullptr;
+        ~Scratch() { cudaFree(ka); cudaFree(va); cudaFree(kb); cudaFree(vb); cudaFree(cnt); }
+    } sc;
+    const size_t Mi = (size_t)std::max<int64_t>(M, 1);
+    NUFFT_CUDA_TRY(cudaMalloc(&p->tsorted, Mi * sizeof(int32_t)));
+    NUFFT_CUDA_TRY(cudaMalloc(&p->perm, Mi * sizeof(int32_t)));
+    NUFFT_CUDA_TRY(cudaMalloc(&p->dsorted, Mi * sizeof(T)));
+    if (p->dims == 2) NUFFT_CUDA_TRY(cudaMalloc(&p->dsorted2, Mi * sizeof(T)));
+    NUFFT_CUDA_TRY(cudaMalloc(&p->bstart, (size_t)(p->NB + 1) * sizeof(int32_t)));
+    p->work_bytes += (int64_t)(Mi * (2 * sizeof(int32_t) + sizeof(T)) + (p->NB + 1) * sizeof(int32_t));
+    NUFFT_CUDA_TRY(cudaMalloc(&sc.ka, Mi * sizeof(int32_t)));
+    NUFFT_CUDA_TRY(cudaMalloc(&sc.va, Mi * sizeof(int32_t)));
+    NUFFT_CUDA_TRY(cudaMalloc(&sc.kb, Mi * sizeof(int32_t)));
+    const int nchunks = (int)std::max<int64_t>(1, (M + SORT_CHUNK - 1) / SORT_CHUNK);
+    NUFFT_CUDA_TRY(cudaMalloc(&sc.cnt, (size_t)SORT_BINS * nchunks * sizeof(int32_t)));
+    int32_t *kin = sc.ka, *vin = sc.va, *kout = sc.kb, *vout = p->perm;
+    if (M > 0) {
+        k_keys<<<grid_for(M, 256), 256, 0, s>>>(p->t_j, M, p->lg1, p->lg2, p->B2, kin, vin);
+        NUFFT_CUDA_TRY(cudaGetLastError());
+        const int lgL = p->lg1 + p->lg2;
+        const int passes = (lgL + SORT_BITS - 1) / SORT_BITS;
+        NUFFT_CUDA_TRY(cudaMalloc(&sc.vb, Mi * sizeof(int32_t)));
+        for (int ps = 0; ps < passes; ++ps) {
+            // the last pass lands in perm
+            vout = (ps == passes - 1) ? p->perm : (vin == sc.va ? sc.vb : sc.va);
+            kout = (kin == sc.ka) ? sc.kb : sc.ka;
+            const int shift = ps * SORT_BITS;
+            k_hist<<<nchunks, SORT_THREADS, 0, s>>>(kin, M, shift, nchunks, sc.cnt);
+            k_scan<<<1, 1024, 0, s>>>(sc.cnt, (int64_t)SORT_BINS * nchunks);
+            k_scatter<<<nchunks, SORT_THREADS, 0, s>>>(kin, vin, M, shift, nchunks, sc.cnt, kout, vout);
+            NUFFT_CUDA_TRY(cudaGetLastError());
+            kin = kout;
+            vin = vout;
+        }
+        k_build<T><<<grid_for(M, 256), 256, 0, s>>>(p->perm, p->t_j, p->d_j, M, p->tsorted,
+                                                    (T *)p->dsorted);
+        if (p->dims == 2)   // d^y in the same order (t is written again, unchanged)
+            k_build<T><<<grid_for(M, 256), 256, 0, s>>>(p->perm, p->t_j, p->d2_j, M, p->tsorted,
+                                                        (T *)p->dsorted2);
+        NUFFT_CUDA_TRY(cudaGetLastError());
+    }
+    // bucket = key >> (lg1 + log2 B2)
+    int lgB2 = 0;
+    while ((1 << lgB2) < p->B2) ++lgB2;
+    k_bstart<<<grid_for(M + 1, 256), 256, 0, s>>>(kin, M, p->lg1 + lgB2, p->NB, p->bstart);
+    NUFFT_CUDA_TRY(cudaGetLastError());
+    NUFFT_CUDA_TRY(cudaStreamSynchronize(s));   // before the scratch is freed
+    return NUFFT_OK;
+}
+
 template <typename T>
 int plan_device(nufft_plan p, const double *x, cudaStream_t s) {
     const int64_t M = p->M;
     struct Scratch {
         unsigned long long *gbits = nullptr;
         int *bad = nullptr;
-        int32_t *ka = nullptr, *va = nullptr, *kb = nullptr, *vb = nullptr, *cnt = nullptr;
-        ~Scratch() {
-            cudaFree(gbits); cudaFree(bad); cudaFree(ka); cudaFree(va);
-            cudaFree(kb); cudaFree(vb); cudaFree(cnt);
-        }
+        ~Scratch() { cudaFree(gbits); cudaFree(bad); }
     } sc;
     const size_t Mi = (size_t)std::max<int64_t>(M, 1);
     NUFFT_CUDA_TRY(cudaMalloc(&sc.gbits, sizeof(unsigned long long)));
@@ -310,45 +363,7 @@ int plan_device(nufft_plan p, const double *x, cudaStream_t s) {
     int rc = plan_geometry<T>(p);
     if (rc) return rc;
 
-    // bucket the samples: stable sort by (bucket, n1, row)
-    NUFFT_CUDA_TRY(cudaMalloc(&p->tsorted, Mi * sizeof(int32_t)));
-    NUFFT_CUDA_TRY(cudaMalloc(&p->perm, Mi * sizeof(int32_t)));
-    NUFFT_CUDA_TRY(cudaMalloc(&p->dsorted, Mi * sizeof(T)));
-    NUFFT_CUDA_TRY(cudaMalloc(&p->bstart, (size_t)(p->NB + 1) * sizeof(int32_t)));
-    p->work_bytes += (int64_t)(Mi * (2 * sizeof(int32_t) + sizeof(T)) + (p->NB + 1) * sizeof(int32_t));
-    NUFFT_CUDA_TRY(cudaMalloc(&sc.ka, Mi * sizeof(int32_t)));
-    NUFFT_CUDA_TRY(cudaMalloc(&sc.va, Mi * sizeof(int32_t)));
-    NUFFT_CUDA_TRY(cudaMalloc(&sc.kb, Mi * sizeof(int32_t)));
-    const int nchunks = (int)std::max<int64_t>(1, (M + SORT_CHUNK - 1) / SORT_CHUNK);
-    NUFFT_CUDA_TRY(cudaMalloc(&sc.cnt, (size_t)SORT_BINS * nchunks * sizeof(int32_t)));
-    int32_t *kin = sc.ka, *vin = sc.va, *kout = sc.kb, *vout = p->perm;
-    if (M > 0) {
-        k_keys<<<grid_for(M, 256), 256, 0, s>>>(p->t_j, M, p->lg1, p->lg2, p->B2, kin, vin);
-        NUFFT_CUDA_TRY(cudaGetLastError());
-        const int lgL = p->lg1 + p->lg2;
-        const int passes = (lgL + SORT_BITS - 1) / SORT_BITS;
-        NUFFT_CUDA_TRY(cudaMalloc(&sc.vb, Mi * sizeof(int32_t)));
-        for (int ps = 0; ps < passes; ++ps) {
-            // the last pass lands in perm
-            vout = (ps == passes - 1) ? p->perm : (vin == sc.va ? sc.vb : sc.va);
-            kout = (kin == sc.ka) ? sc.kb : sc.ka;
-            const int shift = ps * SORT_BITS;
-            k_hist<<<nchunks, SORT_THREADS, 0, s>>>(kin, M, shift, nchunks, sc.cnt);
-            k_scan<<<1, 1024, 0, s>>>(sc.cnt, (int64_t)SORT_BINS * nchunks);
-            k_scatter<<<nchunks, SORT_THREADS, 0, s>>>(kin, vin, M, shift, nchunks, sc.cnt, kout, vout);
-            NUFFT_CUDA_TRY(cudaGetLastError());
-            kin = kout;
-            vin = vout;
-        }
-        k_build<T><<<grid_for(M, 256), 256, 0, s>>>(p->perm, p->t_j, p->d_j, M, p->tsorted,
-                                                    (T *)p->dsorted);
-        NUFFT_CUDA_TRY(cudaGetLastError());
-    }
-    // bucket = key >> (lg1 + log2 B2)
-    int lgB2 = 0;
-    while ((1 << lgB2) < p->B2) ++lgB2;
-    k_bstart<<<grid_for(M + 1, 256), 256, 0, s>>>(kin, M, p->lg1 + lgB2, p->NB, p->bstart);
-    NUFFT_CUDA_TRY(cudaGetLastError());
+    if ((rc = sort_samples<T>(p, s))) return rc;
 
     if ((rc = build_tables<T>(p, s))) return rc;
 
@@ -383,7 +398,7 @@ void free_plan(nufft_plan p) {
     if (!p) return;
     void *bufs[] = {p->tsorted, p->perm, p->bstart, p->t_j, p->dsorted, p->d_j, p->twst1,
                     p->twst2, p->twhi, p->twlo, p->Y, p->fscr, p->cstage, p->fstage, p->U, p->V, p->Xg,
-                    p->part, p->counters, p->err, p->Ufac, p->Vfac};
+                    p->part, p->counters, p->err, p->Ufac, p->Vfac, p->t2_j, p->d2_j, p->dsorted2, p->vy};
     for (void *b : bufs) if (b) cudaFree(b);
     for (cudaEvent_t e : p->ev) if (e) cudaEventDestroy(e);
     delete p;
@@ -391,6 +406,168 @@ void free_plan(nufft_plan p) {
 
 }  // namespace
 }  // namespace nufft
+
+namespace nufft {
+namespace {
+
+// ---- the 2D transform (section 4) ---------------------------------------------------
+
+__global__ void k_combine_t(int32_t *__restrict__ t, const int32_t *__restrict__ ty, int64_t M, int lgx) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < M; j += (int64_t)gridDim.x * blockDim.x)
+        t[j] = (ty[j] << lgx) | t[j];   // t = Lx t^y + t^x: row t^x, position t^y
+}
+
+// Rounding in each direction (eqs. (2.8)-(2.9) on the m- and n-point grids, read of
+// section 4), a rank per direction at eps / 2, the combined grid index, sort, tables.
+template <typename T>
+int plan_device_2d(nufft_plan p, const double *x, const double *y, cudaStream_t s) {
+    const int64_t M = p->M;
+    const size_t Mi = (size_t)std::max<int64_t>(M, 1);
+    struct Scratch {
+        unsigned long long *gbits = nullptr;
+        int *bad = nullptr;
+        ~Scratch() { cudaFree(gbits); cudaFree(bad); }
+    } sc;
+    NUFFT_CUDA_TRY(cudaMalloc(&sc.gbits, 2 * sizeof(unsigned long long)));
+    NUFFT_CUDA_TRY(cudaMalloc(&sc.bad, sizeof(int)));
+    NUFFT_CUDA_TRY(cudaMalloc(&p->t_j, Mi * sizeof(int32_t)));
+    NUFFT_CUDA_TRY(cudaMalloc(&p->d_j, Mi * sizeof(double)));
+    NUFFT_CUDA_TRY(cudaMalloc(&p->t2_j, Mi * sizeof(int32_t)));
+    NUFFT_CUDA_TRY(cudaMalloc(&p->d2_j, Mi * sizeof(double)));
+    NUFFT_CUDA_TRY(cudaMemsetAsync(sc.gbits, 0, 2 * sizeof(unsigned long long), s));
+    NUFFT_CUDA_TRY(cudaMemsetAsync(sc.bad, 0, sizeof(int), s));
+    const int64_t Lx = p->L2, Ly = p->L1;
+    if (M > 0) {
+        k_round<<<grid_for(M, 256), 256, 0, s>>>(x, M, (double)Lx, Lx, (double)p->N / (double)Lx, p->t_j,
+                                                 p->d_j, sc.gbits, sc.bad);
+        k_round<<<grid_for(M, 256), 256, 0, s>>>(y, M, (double)Ly, Ly, (double)p->N2 / (double)Ly, p->t2_j,
+                                                 p->d2_j, sc.gbits + 1, sc.bad);
+        k_combine_t<<<grid_for(M, 256), 256, 0, s>>>(p->t_j, p->t2_j, M, p->lg2);
+        NUFFT_CUDA_TRY(cudaGetLastError());
+    }
+    unsigned long long gb[2] = {0, 0};
+    int bad = 0;
+    NUFFT_CUDA_TRY(cudaMemcpyAsync(gb, sc.gbits, sizeof(gb), cudaMemcpyDeviceToHost, s));
+    NUFFT_CUDA_TRY(cudaMemcpyAsync(&bad, sc.bad, sizeof(bad), cudaMemcpyDeviceToHost, s));
+    NUFFT_CUDA_TRY(cudaStreamSynchronize(s));
+    if (bad) return NUFFT_EINVAL;
+    std::memcpy(&p->gamma, &gb[0], sizeof(double));
+    std::memcpy(&p->gamma2, &gb[1], sizeof(double));
+    // ranks and coefficients per direction (eq. (2.6)); beta folds both primes
+    auto coeffs = [](double eps, double gamma, int *K, double (*beta)[KMAX_ALL], double (*alpha)[KMAX_ALL]) {
+        *K = choose_rank(eps, gamma);
+        for (int r = 0; r < KMAX_ALL; ++r)
+            for (int q = 0; q < KMAX_ALL; ++q) beta[r][q] = alpha[r][q] = 0.0;
+        if (gamma == 0.0) {
+            beta[0][0] = alpha[0][0] = 1.0;
+            return;
+        }
+        std::vector<double> al((size_t)*K * *K);
+        chebyshev_alpha(*K, gamma, al.data());
+        for (int r = 0; r < *K; ++r)
+            for (int q = 0; q < *K; ++q) {
+                alpha[q][r] = al[q * *K + r];
+                beta[r][q] = (r == 0 ? 0.5 : 1.0) * (q == 0 ? 0.5 : 1.0) * al[q * *K + r];
+            }
+    };
+    coeffs(p->eps / 2.0, p->gamma, &p->K, p->beta, p->alpha);
+    coeffs(p->eps / 2.0, p->gamma2, &p->K2, p->beta2, p->alpha2);
+    const int km = std::max(p->K, p->K2);
+    p->kmax = std::min(KMAX_ALL, ((km + 3) / 4) * 4);
+
+    // geometry: pass 1 from the 1D rules; the row pass holds two row buffers, K2 slots
+    // and two mbarriers, with teams for K2 row FFTs per r1
+    if (int rc = plan_geometry<T>(p)) return rc;
+    p->B2 = 1;
+    p->NB = p->L2;
+    {
+        constexpr int EM = sizeof(T) == 4 ? 32 : 16;
+        const int E1 = std::min(EM, p->L1), TT1 = p->L1 / E1;
+        const int maxt = std::max(1, 256 / TT1);
+        const int rounds = (p->K2 + maxt - 1) / maxt;
+        int nt = (p->K2 + rounds - 1) / rounds;
+        if (nt * TT1 < 64) nt = std::min(maxt, std::max(nt, (64 + TT1 - 1) / TT1));
+        p->nt2 = std::max(1, nt);
+        p->smem2 = ((size_t)2 * p->L1 + (size_t)p->K2 * p->S2) * 2 * sizeof(T) + 2 * sizeof(uint64_t);
+        if (p->smem2 > SMEM_BUDGET) return NUFFT_EUNSUPPORTED;
+    }
+
+    int rc = sort_samples<T>(p, s);
+    if (rc) return rc;
+    if ((rc = build_tables<T>(p, s))) return rc;
+    // the y-scale T_r2(2 k2 / n - 1) for k2 < n, 0 beyond (the 1/2 of r2 = 0 is in beta)
+    {
+        std::vector<T> h((size_t)p->K2 * p->L1, T(0));
+        for (int r = 0; r < p->K2; ++r)
+            for (int64_t k = 0; k < p->N2; ++k) {
+                const double z = (2.0 * (double)k - (double)p->N2) / (double)p->N2;
+                double a0 = 1.0, a1 = z, tr = r == 0 ? 1.0 : z;
+                for (int q = 2; q <= r; ++q) {
+                    tr = 2.0 * z * a1 - a0;
+                    a0 = a1;
+                    a1 = tr;
+                }
+                h[(size_t)r * p->L1 + k] = (T)tr;
+            }
+        NUFFT_CUDA_TRY(cudaMalloc(&p->vy, h.size() * sizeof(T)));
+        NUFFT_CUDA_TRY(cudaMemcpyAsync(p->vy, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+        NUFFT_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    const size_t cxs = 2 * sizeof(T);
+    NUFFT_CUDA_TRY(cudaMalloc(&p->Y, (size_t)p->K * p->L * cxs));
+    NUFFT_CUDA_TRY(cudaMalloc(&p->fscr, Mi * cxs));
+    NUFFT_CUDA_TRY(cudaMalloc(&p->err, sizeof(int)));
+    NUFFT_CUDA_TRY(cudaMemsetAsync(p->err, 0, sizeof(int), s));
+    p->work_bytes += (int64_t)(((size_t)p->K * p->L + Mi) * cxs + Mi * (2 * sizeof(int32_t) + 2 * sizeof(double)));
+    NUFFT_CUDA_TRY(cudaStreamSynchronize(s));
+    return NUFFT_OK;
+}
+
+}  // namespace
+}  // namespace nufft
+
+extern "C" int nufft2d_plan(nufft_plan *out, int64_t m, int64_t n, int64_t M, const double *x_dev,
+                            const double *y_dev, double eps, int prec, unsigned flags, void *stream) {
+    using namespace nufft;
+    if (!out) return NUFFT_EINVAL;
+    *out = nullptr;
+    if (m < 1 || n < 1 || M < 0 || M >= ((int64_t)1 << 31) || !(eps > 0.0 && eps < 1.0)) return NUFFT_EINVAL;
+    if (prec != NUFFT_F32 && prec != NUFFT_F64) return NUFFT_EINVAL;
+    if (M > 0 && (!x_dev || !y_dev)) return NUFFT_EINVAL;
+    if (flags & ~NUFFT_PLAN_TIMING) return NUFFT_EINVAL;
+    if (prec != NUFFT_F32) return NUFFT_EUNSUPPORTED;   // the 2D kernels are FP32
+    if (m > 2048 || n > 2048) return NUFFT_EUNSUPPORTED;
+    int64_t Lx = 32, Ly = 32;
+    while (Lx < m) Lx <<= 1;
+    while (Ly < n) Ly <<= 1;
+    nufft_plan p = new (std::nothrow) nufft_plan_s();
+    if (!p) return NUFFT_ENOMEM;
+    p->dims = 2;
+    p->N = m; p->N2 = n; p->M = M; p->L = Lx * Ly; p->eps = eps; p->prec = prec; p->flags = flags;
+    p->L1 = (int)Ly; p->L2 = (int)Lx;
+    while ((1 << p->lg1) < p->L1) ++p->lg1;
+    while ((1 << p->lg2) < p->L2) ++p->lg2;
+    if (cudaGetDevice(&p->device) != cudaSuccess) { free_plan(p); return NUFFT_ECUDA; }
+    if (flags & NUFFT_PLAN_TIMING)
+        for (cudaEvent_t &e : p->ev)
+            if (cudaEventCreate(&e) != cudaSuccess) { (void)cudaGetLastError(); free_plan(p); return NUFFT_ECUDA; }
+    const int rc = plan_device_2d<float>(p, x_dev, y_dev, (cudaStream_t)stream);
+    if (rc != NUFFT_OK) { free_plan(p); return rc; }
+    *out = p;
+    return NUFFT_OK;
+}
+
+extern "C" int nufft2d_plan_info(nufft_plan p, int *Kx, int *Ky, double *gamma_x, double *gamma_y, int64_t *Lx,
+                                 int64_t *Ly) {
+    if (!p || p->dims != 2) return NUFFT_EINVAL;
+    if (Kx) *Kx = p->K;
+    if (Ky) *Ky = p->K2;
+    if (gamma_x) *gamma_x = p->gamma;
+    if (gamma_y) *gamma_y = p->gamma2;
+    if (Lx) *Lx = p->L2;
+    if (Ly) *Ly = p->L1;
+    return NUFFT_OK;
+}
 
 namespace nufft {
 namespace {
@@ -571,6 +748,7 @@ extern "C" int nufft2_plan_info(nufft_plan p, int *K, double *gamma, int64_t *L,
 
 extern "C" int nufft2_plan_export(nufft_plan p, int32_t *t_dev, double *d_dev, double *alpha_host,
                                   void *stream) {
+    if (p && p->dims == 2) return NUFFT_EUNSUPPORTED;
     if (!p) return NUFFT_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     if (p->M > 0 && t_dev)

@@ -1,0 +1,122 @@
+"""GPU parity of the 2D NUFFT-II (section 4, eq. (4.4)) against the oracle.
+
+FP32 exec vs the 2D low-rank oracle on the same grids: ||df||_2 / ||f||_2 <= 1e-5 (FFT
+rounding, as in 1D).  vs the direct 2D sum of eq. (4.1): |df|_inf <= max(eps (1 + eps/4),
+5e-6) ||C||_1 (the product bound of the two directions at eps / 2 each, floored at the
+FP32 target).
+"""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import direct, lowrank  # noqa: E402
+from paper_1701_04492_gb300 import workloads as wl  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_1701_04492_gb300 import api as a
+    return a
+
+
+def _rel2(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _coeffs(m, n, seed):
+    r = np.random.default_rng(seed)
+    C = (r.standard_normal((m, n)) + 1j * r.standard_normal((m, n))) / np.sqrt(2)
+    return C.astype(np.complex64)
+
+
+@pytest.mark.parametrize("m,n,M", [(64, 64, 5000), (100, 40, 3000), (32, 256, 2000), (256, 32, 4000),
+                                   (1024, 48, 6000)])
+@pytest.mark.parametrize("eps", [1e-4, 1e-6, 1e-9])
+def test_2d_matches_oracle(api, m, n, M, eps):
+    x, y = wl.samples_2d_uniform(M, m + 7 * n)
+    C = _coeffs(m, n, m * n)
+    p = api.Plan2D(m, n, x, y, eps)
+    P = lowrank.plan2d(m, n, x, y, eps, p.Lx, p.Ly)
+    assert (p.Kx, p.Ky) == (P.px.K, P.py.K)
+    assert p.gamma_x == P.px.gamma and p.gamma_y == P.py.gamma
+    f = p.forward(torch.tensor(C, device="cuda")).cpu().numpy()
+    fo = lowrank.nufft2_2d(P, C.astype(np.complex128))
+    assert _rel2(f, fo) <= 1e-5
+    rows = np.arange(0, M, max(1, M // 50))
+    fd = direct.nudft2_2d(x[rows], y[rows], C.astype(np.complex128))
+    bound = max(eps * (1 + eps / 4), 5e-6) * np.sum(np.abs(C))
+    assert np.max(np.abs(f[rows] - fd)) <= bound
+
+
+def test_2d_separable_is_product_of_1d_sums(api):
+    m, n, M = 128, 64, 4000
+    x, y = wl.samples_2d_uniform(M, 90)
+    a = wl.coeffs_cn(m, 91).astype(np.complex64)
+    b = wl.coeffs_cn(n, 92).astype(np.complex64)
+    C = np.outer(a, b).astype(np.complex64)
+    p = api.Plan2D(m, n, x, y, 1e-6)
+    f = p.forward(torch.tensor(C, device="cuda")).cpu().numpy()
+    ref = direct.nudft2_2d(x, y, C.astype(np.complex128))
+    assert np.max(np.abs(f - ref)) <= 5e-6 * np.sum(np.abs(C))
+
+
+def test_2d_on_grid_is_the_2d_fft(api):
+    """Samples on the grid (x = s/m, y = t/n): gamma = 0 in both directions, K = 1, and
+    the transform is the plain 2D FFT read at the samples."""
+    m, n = 64, 128
+    r = np.random.default_rng(93)
+    s = r.integers(0, m, 3000)
+    t = r.integers(0, n, 3000)
+    x, y = s / m, t / n
+    C = _coeffs(m, n, 94)
+    p = api.Plan2D(m, n, x, y, 1e-9)
+    assert (p.Kx, p.Ky) == (1, 1)
+    f = p.forward(torch.tensor(C, device="cuda")).cpu().numpy()
+    ref = np.fft.fft2(C.astype(np.complex128))[s, t]
+    assert _rel2(f, ref) <= 1e-6
+
+
+def test_2d_deterministic_and_empty(api):
+    m, n, M = 256, 256, 20000
+    x, y = wl.samples_2d_uniform(M, 95)
+    C = torch.tensor(_coeffs(m, n, 96), device="cuda")
+    p = api.Plan2D(m, n, x, y, 1e-6)
+    f1 = p.forward(C).clone()
+    f2 = p.forward(C)
+    assert torch.equal(f1, f2)
+    e = api.Plan2D(m, n, np.zeros(0), np.zeros(0), 1e-6)
+    assert e.forward(C).numel() == 0
+
+
+def test_2d_full_size_sampled_rows(api):
+    """m = n = 1024, M = 2^20, eps = 1e-6, uniform samples, c ~ CN(0,1)/(1 + k1^2 + k2^2)^(1/2):
+    every 8192nd sample against the direct 2D sum."""
+    m = n = 1024
+    M = 1 << 20
+    x, y = wl.samples_2d_uniform(M, 2024)
+    C = wl.coeffs_2d_decay(m, n, 2024).astype(np.complex64)
+    p = api.Plan2D(m, n, x, y, 1e-6)
+    assert (p.Kx, p.Ky) == (lowrank.choose_K(5e-7, p.gamma_x), lowrank.choose_K(5e-7, p.gamma_y))
+    f = p.forward(torch.tensor(C, device="cuda")).cpu().numpy()
+    rows = np.arange(0, M, 8192)
+    fd = direct.nudft2_2d(x[rows], y[rows], C.astype(np.complex128))
+    assert np.max(np.abs(f[rows] - fd)) <= 5e-6 * np.sum(np.abs(C))
+    assert _rel2(f[rows], fd) <= 1e-5
+
+
+def test_2d_rejects_fp64_and_unsupported_calls(api):
+    from paper_1701_04492_gb300._lib import NufftError
+    x, y = wl.samples_2d_uniform(100, 97)
+    with pytest.raises(NufftError):
+        api.Plan2D(64, 64, x, y, 1e-6, precision="f64")
+    p = api.Plan2D(64, 64, x, y, 1e-6)
+    lib = __import__("paper_1701_04492_gb300._lib", fromlist=["load"]).load()
+    g = torch.zeros(100, dtype=torch.complex64, device="cuda")
+    c = torch.zeros(64 * 64, dtype=torch.complex64, device="cuda")
+    import ctypes
+    rc = lib.nufft1_exec(p._h, ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(c.data_ptr()), None)
+    assert rc == -4
