@@ -194,7 +194,8 @@ def run_ours(args):
 
     if args.only == "batch":
         if rank == 0:
-            print(json.dumps({"batch_c5": batch_c5(api, dev, timed, args.steps)}), flush=True)
+            print(json.dumps({"batch_c5": batch_c5(api, dev, timed, args.steps),
+                              "nufft2d_c3": bench_2d(api, dev, timed, args.steps)}), flush=True)
         return
     if args.only:
         # profiling mode: only the named operation, no extra measurements
@@ -325,6 +326,7 @@ def run_ours(args):
         line.update(extra)
         if not args.no_batch:
             line["batch_c5"] = batch_c5(api, dev, timed, args.steps)
+            line["nufft2d_c3"] = bench_2d(api, dev, timed, args.steps)
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(plan, c_np, g_np, x, f)
         print(json.dumps(line), flush=True)
@@ -375,6 +377,40 @@ def batch_c5(api, dev, timed, steps):
                      "grid_doubled": int(sum(int(L) > max(1024, 1 << (n - 1).bit_length()) for L, n in zip(b.L, Ns)))}
         b.close()
     return out
+
+
+def bench_2d(api, dev, timed, steps):
+    """The 2D workload of section 4: m = n = 1024, M = 2^20 uniform samples in [0,1)^2,
+    eps = 1e-6 (K_x = K_y = 10 at eps/2), C[k1][k2] ~ CN(0,1)/(1 + k1^2 + k2^2)^(1/2)
+    complex64; forward Gpts/s with per-pass device times and algorithmic flops."""
+    import torch
+    from paper_1701_04492_gb300 import workloads as wl
+    m = n = 1024
+    M = 1 << 20
+    x, y = wl.samples_2d_uniform(M, SEED)
+    C = torch.tensor(wl.coeffs_2d_decay(m, n, SEED).astype(np.complex64), device=dev)
+    f = torch.empty(M, dtype=torch.complex64, device=dev)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    p = api.Plan2D(m, n, x, y, 1e-6, device=dev, timing=True)
+    torch.cuda.synchronize(dev)
+    plan_s = time.perf_counter() - t0
+    ms = timed(lambda: p.forward(C, f), steps, 3)
+    kt = []
+    for _ in range(steps):
+        p.forward(C, f)
+        kt.append(p.kernel_times())
+    k1, k2 = float(np.median([k[0] for k in kt])), float(np.median([k[1] for k in kt]))
+    Kx, Ky, Lx, Ly = p.Kx, p.Ky, p.Lx, p.Ly
+    L = Lx * Ly
+    fl_cols = 5.0 * Kx * L * np.log2(Lx) + 2.0 * Kx * m * n
+    fl_rows = 5.0 * Kx * Ky * L * np.log2(Ly) + 8.0 * Kx * Ky * M
+    peak_tf = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    return {"workload": "2D NUFFT-II m=n=1024, M=2^20 uniform (x,y), eps=1e-6, C~CN(0,1)/sqrt(1+k1^2+k2^2) complex64",
+            "Kx": Kx, "Ky": Ky, "fwd_gpts": M * len(ms) / (sum(ms) * 1e-3) / 1e9, "fwd_ms": float(np.mean(ms)),
+            "plan_s": plan_s, "kernel_ms": {"cols": k1, "rows": k2},
+            "alu_frac": {"cols": fl_cols / (k1 * 1e-3) / 1e12 / peak_tf, "rows": fl_rows / (k2 * 1e-3) / 1e12 / peak_tf},
+            "launches_per_fwd": 2}
 
 
 def cpu_baseline(plan, c_np, g_np, x, f_gpu):
@@ -454,7 +490,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-problem batch measurement")
     ap.add_argument("--only", choices=["step", "fwd", "adj", "dx", "batch"], default=None,
                     help="profiling mode: run only this operation warmup+steps times, untimed "
-                         "(batch: only the 512-problem batch measurement, timed)")
+                         "(batch: only the 512-problem batch and the 2D measurements, timed)")
     args = ap.parse_args()
     if args.warmup < 3 and not args.only:
         args.warmup = 3
