@@ -289,3 +289,60 @@ def nufft2_2d(P, C):
             X = np.fft.fft2(W)
             f += px.U[:, r1] * py.U[:, r2] * X[px.t, py.t]
     return f
+
+
+# ---------------------------------------------------------------------------
+# Inverse NUFFT-II (section 3.3): CG on the normal equations
+# ---------------------------------------------------------------------------
+#
+# A c = f with A the N x N NUDFT-II matrix of perturbed equispaced samples
+# (0 <= gamma < 1/2).  A^H A is Toeplitz, (A^H A)_jk = sum_p exp(2 pi i x_p (j - k)),
+# Hermitian positive definite; its first column is A^H applied to the all-ones vector
+# (A e_0 = 1), and a product with it is one FFT and one inverse FFT of size 2N through
+# the circulant matrix whose first column is [t_0, ..., t_{N-1}, 0, conj(t_{N-1}), ...,
+# conj(t_1)].
+
+
+def toeplitz_column(P):
+    """t_d = sum_p exp(2 pi i x_p d), d = 0..N-1: the first column of A^H A, as A^H 1."""
+    return nufft2_adjoint(P, np.ones(P.M, dtype=np.complex128))
+
+
+def circulant_eigenvalues(t):
+    """FFT of the 2N-circulant that embeds the Hermitian Toeplitz matrix with column t."""
+    N = t.size
+    col = np.zeros(2 * N, dtype=np.complex128)
+    col[:N] = t
+    col[N + 1:] = np.conj(t[1:][::-1])
+    return np.fft.fft(col)
+
+
+def toeplitz_apply(lam, x):
+    """(A^H A) x: the first N entries of the circulant product of the zero-padded x."""
+    N = x.size
+    y = np.fft.ifft(lam * np.fft.fft(np.concatenate([x, np.zeros(N, dtype=np.complex128)])))
+    return y[:N]
+
+
+def inverse_cg(P, f, tol, maxit):
+    """Solve A c = f by CG on A^H A c = A^H f (section 3.3).  Stops when the residual of
+    the normal equations has fallen by tol relative to A^H f, or after maxit iterations.
+    Returns (c, iterations, final relative residual)."""
+    lam = circulant_eigenvalues(toeplitz_column(P))
+    b = nufft2_adjoint(P, np.asarray(f, dtype=np.complex128))
+    c = np.zeros(P.N, dtype=np.complex128)
+    r = b.copy()
+    p = r.copy()
+    rs = float(np.vdot(r, r).real)
+    bnorm = math.sqrt(rs)
+    it = 0
+    while it < maxit and math.sqrt(rs) > tol * bnorm:
+        Ap = toeplitz_apply(lam, p)
+        alpha = rs / float(np.vdot(p, Ap).real)
+        c += alpha * p
+        r -= alpha * Ap
+        rs_new = float(np.vdot(r, r).real)
+        p = r + (rs_new / rs) * p
+        rs = rs_new
+        it += 1
+    return c, it, (math.sqrt(rs) / bnorm if bnorm > 0 else 0.0)

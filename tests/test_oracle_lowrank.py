@@ -331,3 +331,54 @@ def test_2d_planted_phase_sign_breaks_the_bound(monkeypatch):
     P = lowrank.plan2d(m, n, x, y, 1e-9)
     f = lowrank.nufft2_2d(P, C)
     assert np.max(np.abs(f - direct.nudft2_2d(x, y, C))) > 1e-3 * np.sum(np.abs(C))
+
+
+# ---- inverse NUFFT-II (section 3.3) -------------------------------------------------
+
+def test_toeplitz_product_is_the_dense_normal_matrix():
+    """The circulant product equals the dense A^H A applied to a vector (A exact)."""
+    N = 96
+    x = wl.samples_perturbed(N, 100, 0.25)
+    P = lowrank.plan(N, x, 1e-14)
+    lam = lowrank.circulant_eigenvalues(lowrank.toeplitz_column(P))
+    v = wl.coeffs_cn(N, 101)
+    A = np.exp(-2j * np.pi * np.outer(x, np.arange(N)))
+    ref = A.conj().T @ (A @ v)
+    assert np.max(np.abs(lowrank.toeplitz_apply(lam, v) - ref)) <= 1e-11 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("gamma", [1 / 32, 1 / 8, 1 / 4])
+def test_inverse_recovers_coefficients(gamma):
+    """f = A c exactly (the direct sum); CG on the normal equations returns c."""
+    N = 256
+    x = wl.samples_perturbed(N, 102, gamma)
+    c = wl.coeffs_cn(N, 103)
+    f = direct.nudft2(x, c)
+    P = lowrank.plan(N, x, 1e-14)
+    cs, it, rr = lowrank.inverse_cg(P, f, 1e-13, 500)
+    assert rr <= 1e-13
+    assert np.linalg.norm(cs - c) / np.linalg.norm(c) <= 1e-10
+    assert it < 100
+
+
+def test_inverse_on_the_grid_is_the_inverse_fft_in_one_step():
+    """gamma = 0: A = F, A^H A = N I, and one CG step gives ifft(f)."""
+    N = 128
+    x = wl.samples_equispaced(N)
+    f = wl.coeffs_cn(N, 104)
+    P = lowrank.plan(N, x, 1e-14)
+    cs, it, rr = lowrank.inverse_cg(P, f, 1e-13, 10)
+    assert it == 1
+    assert np.max(np.abs(cs - np.fft.ifft(f))) <= 1e-14 * np.max(np.abs(f))
+
+
+def test_inverse_iterations_grow_with_gamma():
+    """Fig. 3.1: more perturbed samples need more CG iterations (fixed N, seed, tol)."""
+    N = 512
+    its = []
+    for gamma in (0.0, 1 / 32, 1 / 8, 7 / 16):
+        x = wl.samples_perturbed(N, 105, gamma) if gamma > 0 else wl.samples_equispaced(N)
+        c = wl.coeffs_cn(N, 106)
+        P = lowrank.plan(N, x, 1e-14)
+        its.append(lowrank.inverse_cg(P, direct.nudft2(x, c), 1e-12, 2000)[1])
+    assert its[0] == 1 and its[0] < its[1] <= its[2] < its[3]
