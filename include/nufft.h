@@ -201,6 +201,29 @@ int nufft_kernel_times(nufft_plan p, float *ms_out, int cap, int *count);
 int nufft2_exec_noalloc(int64_t N, int64_t M, const double *x_dev, double eps, const void *c_dev,
                         void *f_dev, void *stream);
 
+/* Inverse NUFFT-II (section 3.3): solve A c = f for c (N values) from f (M values),
+ * A the NUDFT-II matrix of the plan's samples, by conjugate gradients on the normal
+ * equations A^H A c = A^H f.  A^H A is Toeplitz (entries sum_p exp(2 pi i x_p (j - k)));
+ * its first column is A^H applied to the all-ones vector, and each iteration applies it
+ * with one FFT and one inverse FFT of P >= 2N points through its circulant embedding.
+ * The paper takes perturbed equispaced samples with gamma < 1/2 (M = N) so that A is
+ * invertible; with M > N this is the least-squares solution when A has full column rank.
+ *
+ *   f_dev, c_dev   M and N complex values of the plan's precision (device).
+ *   tol            stop when ||A^H f - A^H A c||_2 <= tol ||A^H f||_2 (reachable tol: ~1e-13
+ *                  in FP64 plans, ~1e-6 in FP32 plans); the accuracy of c is further limited
+ *                  by the plan's eps and by the conditioning of A.
+ *   maxit          at most this many iterations (0: c = 0).
+ *   iterations, relres   if not NULL: iterations taken and the final relative residual.
+ *
+ * The first call on a plan builds the solver state (an FFT plan of P points, the
+ * circulant's eigenvalues, four work vectors: allocates device memory); later calls
+ * reuse it.  Synchronises `stream` once per iteration (the convergence test reads the
+ * residual).  Errors: NUFFT_EINVAL, NUFFT_EUNSUPPORTED (2D plans; 2N beyond 2^22),
+ * NUFFT_ENOMEM, NUFFT_ECUDA, NUFFT_ETIMEOUT (see nufft2_check). */
+int nufft2_inverse(nufft_plan p, const void *f_dev, void *c_dev, double tol, int maxit, int *iterations,
+                   double *relres, void *stream);
+
 /* ---- The two-dimensional NUFFT-II (section 4) ---------------------------------
  *
  *     f_j = sum_{k1<m} sum_{k2<n} C[k1][k2] exp(-2 pi i (k1 x_j + k2 y_j))   (eq. (4.1))

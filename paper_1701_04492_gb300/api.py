@@ -138,6 +138,19 @@ class Plan:
             check(_lib.load().nufft2_exec(self._h, _ptr(c), _ptr(f), _stream(self.device)), "nufft2_exec")
         return f
 
+    def inverse(self, f, tol=1e-12, maxit=1000, out=None):
+        """Solve A c = f by CG on the normal equations (section 3.3).
+
+        Returns (c, iterations, relative residual of the normal equations)."""
+        self._cx(f, self.M, "f")
+        c = out if out is not None else torch.empty(self.N, dtype=self.cdtype, device=self.device)
+        self._cx(c, self.N, "c")
+        it, rr = ctypes.c_int(), ctypes.c_double()
+        with torch.cuda.device(self.device):
+            check(_lib.load().nufft2_inverse(self._h, _ptr(f), _ptr(c), float(tol), int(maxit), ctypes.byref(it),
+                                             ctypes.byref(rr), _stream(self.device)), "nufft2_inverse")
+        return c, it.value, rr.value
+
     def adjoint(self, g, out=None):
         """c = A^H g (the conjugate transpose of forward)."""
         self._cx(g, self.M, "g")

@@ -85,6 +85,14 @@ struct nufft_plan_s {
     void *dsorted2 = nullptr;  // d^y in sorted order
     void *vy = nullptr;        // T_r2(2 k2 / n - 1), K2 x L1
 
+    // the inverse transform (section 3.3), built by the first nufft2_inverse call
+    nufft_plan_s *inv_fft = nullptr;   // FFT of P >= 2N points (a gamma = 0 plan)
+    int64_t inv_P = 0;
+    void *inv_lam = nullptr, *inv_x = nullptr, *inv_z = nullptr;   // P complex each
+    void *inv_r = nullptr, *inv_p = nullptr, *inv_ap = nullptr;    // N complex each
+    double *inv_part = nullptr, *inv_scal = nullptr;               // reductions, scalars
+    double *inv_host = nullptr;                                    // pinned readback
+
     // NUFFT_PLAN_TIMING: events around each launch of the last exec call
     cudaEvent_t ev[8] = {};
     int nev = 0;       // events recorded by the last exec call

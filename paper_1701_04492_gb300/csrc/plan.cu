@@ -398,8 +398,11 @@ void free_plan(nufft_plan p) {
     if (!p) return;
     void *bufs[] = {p->tsorted, p->perm, p->bstart, p->t_j, p->dsorted, p->d_j, p->twst1,
                     p->twst2, p->twhi, p->twlo, p->Y, p->fscr, p->cstage, p->fstage, p->U, p->V, p->Xg,
-                    p->part, p->counters, p->err, p->Ufac, p->Vfac, p->t2_j, p->d2_j, p->dsorted2, p->vy};
+                    p->part, p->counters, p->err, p->Ufac, p->Vfac, p->t2_j, p->d2_j, p->dsorted2, p->vy,
+                    p->inv_lam, p->inv_x, p->inv_z, p->inv_r, p->inv_p, p->inv_ap, p->inv_part, p->inv_scal};
     for (void *b : bufs) if (b) cudaFree(b);
+    if (p->inv_host) cudaFreeHost(p->inv_host);
+    if (p->inv_fft) free_plan(p->inv_fft);
     for (cudaEvent_t e : p->ev) if (e) cudaEventDestroy(e);
     delete p;
 }
