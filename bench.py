@@ -195,7 +195,9 @@ def run_ours(args):
     if args.only == "batch":
         if rank == 0:
             print(json.dumps({"batch_c5": batch_c5(api, dev, timed, args.steps),
-                              "nufft2d_c3": bench_2d(api, dev, timed, args.steps)}), flush=True)
+                              "nufft2d_c3": bench_2d(api, dev, timed, args.steps),
+                              "inverse": bench_inverse(api, dev),
+                              "autograd_c4": bench_autograd_c4(api, dev, timed, args.steps)}), flush=True)
         return
     if args.only:
         # profiling mode: only the named operation, no extra measurements
@@ -327,6 +329,8 @@ def run_ours(args):
         if not args.no_batch:
             line["batch_c5"] = batch_c5(api, dev, timed, args.steps)
             line["nufft2d_c3"] = bench_2d(api, dev, timed, args.steps)
+            line["inverse"] = bench_inverse(api, dev)
+            line["autograd_c4"] = bench_autograd_c4(api, dev, timed, args.steps)
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(plan, c_np, g_np, x, f)
         print(json.dumps(line), flush=True)
@@ -413,6 +417,58 @@ def bench_2d(api, dev, timed, steps):
             "launches_per_fwd": 2}
 
 
+def bench_inverse(api, dev):
+    """The inverse NUFFT-II of section 3.3 at N = 2^20 on the perturbed grid with
+    gamma = 1/8 (Fig. 3.1's middle case): f = A c for a known c, then CG to tol, timed end
+    to end on the device (the solver's per-iteration host check included), FP64 and FP32."""
+    import torch
+    from paper_1701_04492_gb300 import workloads as wl
+    N = 1 << 20
+    x = wl.samples_perturbed(N, SEED, 1 / 8)
+    out = {"workload": "inverse NUFFT-II, N=M=2^20, perturbed grid gamma=1/8, CG on A^H A (Toeplitz, 2N circulant)"}
+    for prec, eps, tol, cdt in (("f64", 1e-14, 1e-12, torch.complex128), ("f32", 1e-7, 1e-5, torch.complex64)):
+        c = torch.tensor(wl.coeffs_cn(N, SEED), dtype=cdt, device=dev)
+        p = api.Plan(N, x, eps, prec, device=dev)
+        f = p.forward(c)
+        p.inverse(f, tol=tol, maxit=1)          # builds the solver state
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        cs, it, rr = p.inverse(f, tol=tol, maxit=1000)
+        torch.cuda.synchronize(dev)
+        sec = time.perf_counter() - t0
+        err = float(torch.linalg.vector_norm(cs - c) / torch.linalg.vector_norm(c))
+        out[prec] = {"tol": tol, "iterations": it, "relres": rr, "ms": sec * 1e3, "ms_per_iteration": sec * 1e3 / max(it, 1),
+                     "rel_err_vs_c": err}
+        del p
+    return out
+
+
+def bench_autograd_c4(api, dev, timed, steps):
+    """The differentiable workload: N = M = 2^18, 64 complex64 coefficient vectors sharing
+    uniform x, loss = sum |f - f*|^2; one step = forward (with f' for dL/dx) + backward
+    (A^H g per member, dL/dx summed), through torch.autograd."""
+    import torch
+    from paper_1701_04492_gb300 import workloads as wl
+    N = M = 1 << 18
+    B = 64
+    x = wl.samples_uniform(M, SEED)
+    plan = api.Plan(N, x, 1e-9, "f32", device=dev)
+    c0 = torch.tensor(np.stack([wl.coeffs_cn(N, SEED + b) for b in range(B)]).astype(np.complex64), device=dev)
+    ft = plan.forward(torch.tensor(wl.coeffs_cn(N, SEED + B).astype(np.complex64), device=dev))
+    xt = torch.tensor(x, dtype=torch.float64, device=dev, requires_grad=True)
+    c = c0.clone().requires_grad_(True)
+
+    def train_step():
+        c.grad = None
+        xt.grad = None
+        f = api.nufft2(c, xt, plan=plan)
+        ((f - ft[None, :]).abs() ** 2).sum().backward()
+    ms = timed(train_step, steps, 3)
+    return {"workload": "autograd NUFFT-II, N=M=2^18, batch 64 complex64, x shared, loss sum|f-f*|^2, grads to c and x",
+            "ms_per_step": float(np.mean(ms)), "gpts_per_s": B * M * len(ms) / (sum(ms) * 1e-3) / 1e9,
+            "gpu_launches_per_step": B * 5}
+
+
 def cpu_baseline(plan, c_np, g_np, x, f_gpu):
     """The oracle as it stands, one FP64 fwd+bwd step at a time on this host, for
     about 10-20 s; also the GPU result's error against it."""
@@ -490,7 +546,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-problem batch measurement")
     ap.add_argument("--only", choices=["step", "fwd", "adj", "dx", "batch"], default=None,
                     help="profiling mode: run only this operation warmup+steps times, untimed "
-                         "(batch: only the 512-problem batch and the 2D measurements, timed)")
+                         "(batch: only the 512-problem batch, 2D and inverse measurements, timed)")
     args = ap.parse_args()
     if args.warmup < 3 and not args.only:
         args.warmup = 3

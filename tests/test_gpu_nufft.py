@@ -343,3 +343,41 @@ def test_autograd_finite_differences_fp64(api):
         fd_re = (loss_of(x, c0 + h * e) - loss_of(x, c0 - h * e)) / (2 * h)
         # torch's complex gradient: d loss / d Re c_k = Re(grad_k)
         assert abs(c.grad[k].real.item() - fd_re) <= 1e-6 * max(1.0, abs(fd_re))
+
+
+def test_autograd_training_batch_n2e18(api):
+    """The differentiable workload at its full size: N = M = 2^18, a batch of 64 complex64
+    coefficient vectors sharing uniform x, loss = sum |f - f*|^2 with f* = A c* for a
+    seeded c*.  dL/dc of four batch members against the FP64 oracle gradient
+    2 A^H (A c - A c*); dL/dx on 32 sampled rows against the direct derivative sum of
+    eq. (1.2) summed over the whole batch, sum_b Re(conj(g_b) f'_b)."""
+    N = M = 1 << 18
+    B = 64
+    x = wl.samples_uniform(M, 2024)
+    cs = np.stack([wl.coeffs_cn(N, 500 + b).astype(np.complex64) for b in range(B)])
+    ct = wl.coeffs_cn(N, 599).astype(np.complex64)
+    plan = api.Plan(N, x, 1e-9, "f32")
+    ftarget = plan.forward(_dev(ct, torch.complex64))
+    xt = torch.tensor(x, dtype=torch.float64, device="cuda", requires_grad=True)
+    c = _dev(cs, torch.complex64).requires_grad_(True)
+    f = api.nufft2(c, xt, plan=plan)
+    loss = ((f - ftarget[None, :]).abs() ** 2).sum()
+    loss.backward()
+    gc = c.grad.cpu().numpy()
+    gxg = xt.grad.cpu().numpy()
+    fg = f.detach().cpu().numpy()
+    ftg = ftarget.cpu().numpy()
+    # dL/dc against the FP64 oracle for a few members
+    P = lowrank.plan(N, x, 1e-9, plan.L)
+    ft64 = lowrank.nufft2(P, ct.astype(np.complex128))
+    for b in (0, 17, 42, 63):
+        gb = 2.0 * (lowrank.nufft2(P, cs[b].astype(np.complex128)) - ft64)
+        assert _rel2(gc[b], lowrank.nufft2_adjoint(P, gb)) <= 1e-4, b
+    # dL/dx on sampled rows: sum_b Re(conj(g_bj) f'_bj), f' by the direct derivative sum
+    rows = np.arange(0, M, M // 32)
+    ref = np.zeros(rows.size)
+    for b in range(B):
+        gb = 2.0 * (fg[b, rows].astype(np.complex128) - ftg[rows])
+        fpb = direct.nudft2_deriv(x[rows], cs[b].astype(np.complex128))
+        ref += np.real(np.conj(gb) * fpb)
+    assert _rel2(gxg[rows], ref) <= 1e-4
