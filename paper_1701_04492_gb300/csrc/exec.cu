@@ -90,21 +90,40 @@ int plan_geometry(nufft_plan p) {
         if (nt * TT1 < 64) nt = std::min(maxt, std::max(nt, (64 + TT1 - 1) / TT1));
         return std::max(1, nt);
     };
-    auto choose = [&](int Gmax, auto bytes, int *Gout, int *ntout) -> bool {
+    auto choose = [&](int Gmax, auto bytes, int *Gout, int *ntout, size_t cap) -> bool {
         int G = Gmax;
-        while (G > 1 && bytes(G, teams(G * p->B2)) > SMEM_BUDGET) --G;
+        while (G > 1 && bytes(G, teams(G * p->B2)) > cap) --G;
         *Gout = G;
         *ntout = teams(G * p->B2);
         return bytes(G, *ntout) <= SMEM_BUDGET;
     };
-    // pass 2 stages up to K + 1 ranks (the derivative mode adds rank K)
+    // pass 2 stages up to K + 1 ranks (the derivative mode adds rank K, and its gather
+    // needs them all in one group)
     int nt_dummy = 1;
-    if (!choose(p->K + 1, bytes2, &p->G, &nt_dummy)) return NUFFT_EUNSUPPORTED;
+    if (!choose(p->K + 1, bytes2, &p->G, &nt_dummy, SMEM_BUDGET)) return NUFFT_EUNSUPPORTED;
     p->nt2 = teams(std::min(p->G, p->K) * p->B2);   // forward: K ranks
     p->nt2d = teams(p->G * p->B2);                  // derivative: K + 1 ranks
     p->mbar_off2 = body2(p->G);
     p->smem2 = bytes2(p->G, 1);
-    if (!choose(p->K, bytesA, &p->GA, &p->ntA)) return NUFFT_EUNSUPPORTED;
+    // The plain forward stages fewer ranks at a time, so that four CTAs fit per SM (228 KB
+    // of shared memory each): measured faster at 2^20 (78 -> 74 us) while a group holds
+    // at least a third of the ranks.  Pass A, whose samples are staged again for every
+    // group, was slower so (102 -> 130 us) and keeps the largest group.
+    const size_t cap4 = (size_t)228 * 1024 / 4 - 2 * 1024;
+    p->Gf = std::min(p->G, p->K);
+    p->nt2f = p->nt2;
+    p->mbar_off2f = p->mbar_off2;
+    p->smem2f = p->smem2;
+    {
+        int Gc = 1, ntc = 1;
+        if (choose(p->K, bytes2, &Gc, &ntc, cap4) && Gc < p->Gf && Gc >= (p->K + 2) / 3 && bytes2(Gc, 1) <= cap4) {
+            p->Gf = Gc;
+            p->nt2f = ntc;
+            p->mbar_off2f = body2(Gc);
+            p->smem2f = bytes2(Gc, 1);
+        }
+    }
+    if (!choose(p->K, bytesA, &p->GA, &p->ntA, SMEM_BUDGET)) return NUFFT_EUNSUPPORTED;
     p->smemA = bytesA(p->GA, p->ntA);
     if (p->smem1 > SMEM_BUDGET || p->smemB > SMEM_BUDGET) return NUFFT_EUNSUPPORTED;
     return NUFFT_OK;

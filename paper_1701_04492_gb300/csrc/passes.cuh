@@ -1037,7 +1037,15 @@ int launch_rows(nufft_plan p, const PassArgs<T> &a0, bool adjoint, cudaStream_t 
         constexpr int TT = P / e_of<T, P>();
         PassArgs<T> a = a0;
         if (int rc = rows_fields<T>(p, a, adjoint)) return rc;
-        const int nt = adjoint ? p->ntA : (a.nranks > p->K ? p->nt2d : p->nt2);
+        int nt = adjoint ? p->ntA : (a.nranks > p->K ? p->nt2d : p->nt2);
+        size_t smem2 = p->smem2;
+        if (!adjoint && a.nranks <= p->K && !(a.mode & MODE_DERIV)) {
+            // the plain forward's own geometry (fewer ranks per group, more CTAs per SM)
+            a.G = p->Gf;
+            a.mbar_off = (int)p->mbar_off2f;
+            nt = p->nt2f;
+            smem2 = p->smem2f;
+        }
         const dim3 block(nt * TT);
         static int done_a[64] = {}, done_2[64] = {};
         if (adjoint) {
@@ -1046,8 +1054,8 @@ int launch_rows(nufft_plan p, const PassArgs<T> &a0, bool adjoint, cudaStream_t 
             kern<<<dim3(p->NB), block, p->smemA, s>>>(a, beta);
         } else {
             auto kern = k_pass2<T, P, KM>;
-            if (int rc = set_smem(kern, p->smem2, p->device, done_2)) return rc;
-            kern<<<dim3(p->NB), block, p->smem2, s>>>(a, beta);
+            if (int rc = set_smem(kern, smem2, p->device, done_2)) return rc;
+            kern<<<dim3(p->NB), block, smem2, s>>>(a, beta);
         }
         return launch_status();
     });
