@@ -77,7 +77,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", self.uuid, "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "20"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
         except Exception:
@@ -87,6 +87,13 @@ class ClockSampler:
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
+
+    def wait_first(self, busy, limit_s=3.0):
+        """Run busy() (untimed GPU work) until the sampler has reported once, so that its
+        samples cover the timed region that follows."""
+        t0 = time.perf_counter()
+        while self.proc is not None and not self.lines and time.perf_counter() - t0 < limit_s:
+            busy()
 
     def __exit__(self, *exc):
         if self.proc is not None:
@@ -215,6 +222,7 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize(dev)
     with ClockSampler(uuid) as clk:
+        clk.wait_first(lambda: (step(), torch.cuda.synchronize(dev)))   # extra untimed steps
         step_ms = timed(step, args.steps, args.warmup)
     if ws > 1:
         dist.barrier()
