@@ -293,7 +293,7 @@ int plan_many_core(nufft_batch *out, int64_t count, const int64_t *N_host, const
     for (auto &c : b->cls) {
         if (c.single) continue;
         nufft_plan r = b->plans[c.rep];
-        const size_t E1 = (size_t)std::min<int>(EmaxT<float>::v, r->L1);
+        const size_t E1 = (size_t)std::min<int>(EmaxT<float, PK_ROW_ADJ>::v, r->L1);   // pass A's tables
         for (size_t q = 0; q < c.idx.size();) {
             nufft_plan m = b->plans[c.idx[q]];
             const size_t needA = m->smemA + (size_t)std::max(0, r->ntA - m->ntA) * E1 * 8;

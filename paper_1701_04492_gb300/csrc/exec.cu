@@ -54,15 +54,21 @@ int clamp_pow2(int v, int lo, int hi) { return std::max(lo, std::min(hi, v)); }
 
 template <typename T>
 int plan_geometry(nufft_plan p) {
-    constexpr int EM = EmaxT<T>::v;
-    const int E1 = std::min(EM, p->L1), TT1 = p->L1 / E1;
-    const int E2 = std::min(EM, p->L2), TT2 = p->L2 / E2;
+    // values per thread of each pass's team FFT (see EmaxT) and the team sizes
+    const int E1 = std::min(EmaxT<T, PK_ROW_FWD>::v, p->L1), TT1 = p->L1 / E1;      // pass 2
+    const int E1a = std::min(EmaxT<T, PK_ROW_ADJ>::v, p->L1), TT1a = p->L1 / E1a;   // pass A
+    const int E2 = std::min(EmaxT<T, PK_COL_FWD>::v, p->L2), TT2 = p->L2 / E2;      // pass 1
+    const int E2b = std::min(EmaxT<T, PK_COL_ADJ>::v, p->L2), TT2b = p->L2 / E2b;   // pass B
     const size_t cxs = 2 * sizeof(T);
     // column passes: C columns per CTA, columns fastest across the lanes
     p->C1 = clamp_pow2(256 / TT2, 1, p->L1);
-    p->CB = clamp_pow2(128 / TT2, 1, p->L1);   // one 32 KiB tile of the adjoint intermediate
+    // one 32 KiB tile of the adjoint intermediate: pass A writes it (each of its rows a
+    // run of CB columns, a whole 32-byte sector or more), pass B fetches it by one bulk
+    // copy; pass B's CTA then has CB TT2b threads (256 in FP32, 128 in FP64)
+    p->CB = clamp_pow2((int)(32768 / ((size_t)p->L2 * cxs)), 1, p->L1);
+    (void)TT2b;
     p->S1 = slot_stride<T>(p->L2, E2, p->C1);
-    p->SB = slot_stride<T>(p->L2, E2, p->CB);
+    p->SB = slot_stride<T>(p->L2, E2b, p->CB);
     p->smem1 = ((size_t)p->C1 * p->S1 + (size_t)p->C1 * E2) * cxs;   // slots + four-step table
     // two tile buffers (copy landing zone and exchange slots), then two mbarriers
     p->smemB = ((2 * (size_t)p->CB * p->SB * cxs + 15) / 16) * 16 + 2 * sizeof(uint64_t);
@@ -72,7 +78,7 @@ int plan_geometry(nufft_plan p) {
     p->B2 = clamp_pow2(1024 / p->L1, 1, p->L2);
     p->NB = p->L2 / p->B2;
     p->S2 = slot_stride<T>(p->L1, E1, std::max(1, nbank<T>() / TT1));
-    const int maxt = std::max(1, 256 / TT1);
+    p->SA = slot_stride<T>(p->L1, E1a, std::max(1, nbank<T>() / TT1a));
     p->chunkA = 512;
     const size_t staging = (size_t)p->chunkA * (sizeof(int32_t) + sizeof(T)) + (size_t)p->chunkA * cxs;
     // one slot per staged row (idle teams need none)
@@ -81,16 +87,20 @@ int plan_geometry(nufft_plan p) {
     auto body2 = [&](int G) { return (nslots(G) * p->S2 * cxs + 15) / 16 * 16; };
     auto bytes2 = [&](int G, int nt) { return body2(G) + nslots(G) * sizeof(uint64_t) + 0 * nt; };
     // pass A: slots, four-step tables, staged samples
-    auto bytesA = [&](int G, int nt) { return (nslots(G) * p->S2 + (size_t)nt * E1) * cxs + staging; };
-    // teams for J row FFTs: the fewest rounds with at most 256 threads, then the
-    // fewest teams that still take that many rounds
-    auto teams = [&](int J) {
-        const int rounds = (J + maxt - 1) / maxt;
-        int nt = (J + rounds - 1) / rounds;
-        if (nt * TT1 < 64) nt = std::min(maxt, std::max(nt, (64 + TT1 - 1) / TT1));
-        return std::max(1, nt);
+    auto bytesA = [&](int G, int nt) { return (nslots(G) * p->SA + (size_t)nt * E1a) * cxs + staging; };
+    // teams (of TTr threads) for J row FFTs: the fewest rounds with at most 256
+    // threads, then the fewest teams that still take that many rounds
+    auto teams_of = [](int TTr) {
+        const int maxt = std::max(1, 256 / TTr);
+        return [=](int J) {
+            const int rounds = (J + maxt - 1) / maxt;
+            int nt = (J + rounds - 1) / rounds;
+            if (nt * TTr < 64) nt = std::min(maxt, std::max(nt, (64 + TTr - 1) / TTr));
+            return std::max(1, nt);
+        };
     };
-    auto choose = [&](int Gmax, auto bytes, int *Gout, int *ntout, size_t cap) -> bool {
+    const auto teams = teams_of(TT1), teamsA = teams_of(TT1a);
+    auto choose = [&](int Gmax, auto bytes, auto teams, int *Gout, int *ntout, size_t cap) -> bool {
         int G = Gmax;
         while (G > 1 && bytes(G, teams(G * p->B2)) > cap) --G;
         *Gout = G;
@@ -100,7 +110,7 @@ int plan_geometry(nufft_plan p) {
     // pass 2 stages up to K + 1 ranks (the derivative mode adds rank K, and its gather
     // needs them all in one group)
     int nt_dummy = 1;
-    if (!choose(p->K + 1, bytes2, &p->G, &nt_dummy, SMEM_BUDGET)) return NUFFT_EUNSUPPORTED;
+    if (!choose(p->K + 1, bytes2, teams, &p->G, &nt_dummy, SMEM_BUDGET)) return NUFFT_EUNSUPPORTED;
     p->nt2 = teams(std::min(p->G, p->K) * p->B2);   // forward: K ranks
     p->nt2d = teams(p->G * p->B2);                  // derivative: K + 1 ranks
     p->mbar_off2 = body2(p->G);
@@ -116,14 +126,15 @@ int plan_geometry(nufft_plan p) {
     p->smem2f = p->smem2;
     {
         int Gc = 1, ntc = 1;
-        if (choose(p->K, bytes2, &Gc, &ntc, cap4) && Gc < p->Gf && Gc >= (p->K + 2) / 3 && bytes2(Gc, 1) <= cap4) {
+        if (choose(p->K, bytes2, teams, &Gc, &ntc, cap4) && Gc < p->Gf && Gc >= (p->K + 2) / 3 &&
+            bytes2(Gc, 1) <= cap4) {
             p->Gf = Gc;
             p->nt2f = ntc;
             p->mbar_off2f = body2(Gc);
             p->smem2f = bytes2(Gc, 1);
         }
     }
-    if (!choose(p->K, bytesA, &p->GA, &p->ntA, SMEM_BUDGET)) return NUFFT_EUNSUPPORTED;
+    if (!choose(p->K, bytesA, teamsA, &p->GA, &p->ntA, SMEM_BUDGET)) return NUFFT_EUNSUPPORTED;
     p->smemA = bytesA(p->GA, p->ntA);
     if (p->smem1 > SMEM_BUDGET || p->smemB > SMEM_BUDGET) return NUFFT_EUNSUPPORTED;
     return NUFFT_OK;

@@ -152,6 +152,25 @@ __device__ __forceinline__ int padi_run(int pbase, int i) {
     }
 }
 
+// The passes, for the choice of their team FFT's values per thread E.
+enum PassKind : int { PK_COL_FWD = 0, PK_ROW_FWD = 1, PK_ROW_ADJ = 2, PK_COL_ADJ = 3 };
+
+// E per pass (the FFT length is P <= E^3; a team has P / E threads).  FP32: the forward
+// row pass and the adjoint column pass take E = 16 (twice the threads, one more
+// exchange), which measured faster at 2^20 (pass 2 74 -> 68 us, pass B 72 -> 59 us); pass 1
+// and pass A were faster with E = 32 (50 vs 58 us, 101 vs 115 us).  FP64: E = 16.
+template <typename T> struct EmaxBase;
+template <> struct EmaxBase<float> {
+    __host__ __device__ static constexpr int of(int kind) { return (kind == PK_ROW_FWD || kind == PK_COL_ADJ) ? 16 : 32; }
+};
+template <> struct EmaxBase<double> {
+    __host__ __device__ static constexpr int of(int) { return 16; }
+};
+template <typename T, int KIND> struct EmaxT { static constexpr int v = EmaxBase<T>::of(KIND); };
+template <typename T, int P, int KIND> __host__ __device__ constexpr int e_of() {
+    return P < EmaxT<T, KIND>::v ? P : EmaxT<T, KIND>::v;
+}
+
 template <typename T, int P, int E, bool INV>
 struct TeamFft {
     static_assert(P % E == 0, "P must be a multiple of E");

@@ -113,13 +113,14 @@ __device__ float2 w_exact(long long n, long long m) {
     return make_float2((float)c, (float)(-s));
 }
 
-__global__ void na_tables(int P1, int P2, int64_t L, float2 *tw1, float2 *tw2, float2 *hi, float2 *lo,
-                          int32_t *bstart, int nb1) {
+__global__ void na_tables(int P1, int EM1, int P2, int EM2, int64_t L, float2 *tw1, float2 *tw2, float2 *hi,
+                          float2 *lo, int32_t *bstart, int nb1) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
     for (int pass = 0; pass < 2; ++pass) {
         const int P = pass ? P2 : P1;
         float2 *tw = pass ? tw2 : tw1;
-        const int E = P < 32 ? P : 32, TT = P / E;
+        const int EM = pass ? EM2 : EM1;
+        const int E = P < EM ? P : EM, TT = P / E;
         const int R0 = E, R1 = TT > 1 ? (TT < E ? TT : E) : 1, R2 = TT / R1;
         const int n1 = (R1 - 1) * R0, n2 = R2 > 1 ? (R2 - 1) * R0 * R1 : 0;
         for (int q = tid; q < n1; q += nth) tw[q] = w_exact((long long)R0 * R1, (long long)(q / R0 + 1) * (q % R0));
@@ -245,7 +246,11 @@ extern "C" int nufft2_exec_noalloc(int64_t N, int64_t M, const double *x_dev, do
     float2 *tw1 = (float2 *)(base + OFF_TW1), *tw2 = (float2 *)(base + OFF_TW2);
     float2 *hi = (float2 *)(base + OFF_TWHI), *lo = (float2 *)(base + OFF_TWLO);
     int32_t *bstart = (int32_t *)(base + OFF_BSTART);
-    na_tables<<<16, 256, 0, s>>>(pl.L1, pl.L2, pl.L, tw1, tw2, hi, lo, bstart, pl.NB);
+    // pass 2 (rows) and pass 1 (columns), each with its own values per thread
+    na_tables<<<16, 256, 0, s>>>(pl.L1, EmaxT<float, PK_ROW_FWD>::v, pl.L2, EmaxT<float, PK_COL_FWD>::v, pl.L, tw1,
+                                 tw2, hi, lo, bstart, pl.NB);
+    pl.twst1 = tw1;   // the launchers take each pass's table from the plan
+    pl.twst2 = tw2;
     NUFFT_CUDA_TRY(cudaGetLastError());
 
     PassArgs<float> a{};

@@ -54,7 +54,7 @@ struct nufft_plan_s {
     size_t smemA = 0;      // of pass A
     size_t smem1 = 0;      // of pass 1
     size_t smemB = 0;      // of pass B
-    int S1 = 0, SB = 0, S2 = 0;   // slot strides (elements)
+    int S1 = 0, SB = 0, S2 = 0, SA = 0;   // slot strides (elements): pass 1, B, 2, A
 
     double beta[nufft::KMAX_ALL][nufft::KMAX_ALL] = {};   // [r][p] = w_r w_p alpha_pr
     double alpha[nufft::KMAX_ALL][nufft::KMAX_ALL] = {};  // a_pr = i^r alpha_pr
@@ -63,7 +63,8 @@ struct nufft_plan_s {
     int32_t *tsorted = nullptr, *perm = nullptr, *bstart = nullptr, *t_j = nullptr;
     void *dsorted = nullptr;   // d in sorted order, plan precision
     double *d_j = nullptr;     // d in sample order, FP64 (unfused factors)
-    void *twst1 = nullptr, *twst2 = nullptr;   // stage twiddle tables for lengths L1, L2
+    void *twst1 = nullptr, *twst2 = nullptr;   // stage twiddle tables: pass 2 (L1), pass 1 (L2)
+    void *twst1a = nullptr, *twst2b = nullptr; // and pass A (L1), pass B (L2): each pass's own E
     void *twhi = nullptr, *twlo = nullptr;     // four-step twiddle, two levels
     void *Y = nullptr;         // (K + 1) * L complex: intermediate between the passes
     void *fscr = nullptr;      // M complex: partial sums when G < K

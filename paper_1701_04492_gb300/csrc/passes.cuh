@@ -45,10 +45,6 @@ enum PassMode : int {
 // carry no code for it.
 template <typename T> constexpr bool kFactors = std::is_same<T, double>::value;
 
-template <typename T> struct EmaxT;
-template <> struct EmaxT<float> { static constexpr int v = 32; };
-template <> struct EmaxT<double> { static constexpr int v = 16; };
-template <typename T, int P> __host__ __device__ constexpr int e_of() { return P < EmaxT<T>::v ? P : EmaxT<T>::v; }
 
 template <typename T>
 struct PassArgs {
@@ -151,7 +147,7 @@ __device__ __forceinline__ cx<T> *smem_base() {
 // the y-frequency k2 < n, and there is no four-step twiddle (the 2D DFT separates).
 template <typename T, int P2, bool TWO_D = false>
 __device__ __forceinline__ void pass1_body(const PassArgs<T> &a, const int bx, const int by) {
-    constexpr int E = e_of<T, P2>();
+    constexpr int E = e_of<T, P2, PK_COL_FWD>();
     using TF = TeamFft<T, P2, E, false>;
     constexpr int TT = TF::TT;
     cx<T> *smem = smem_base<T>();
@@ -259,7 +255,7 @@ __device__ __forceinline__ void pass1_body(const PassArgs<T> &a, const int bx, c
 // ---- pass 2: row FFTs (length L1) into shared memory, then gather/U-scale/rank-sum --
 template <typename T, int P1, int KM, typename BT>
 __device__ __forceinline__ void pass2_body(const PassArgs<T> &a, const BT &beta, const int bx) {
-    constexpr int E = e_of<T, P1>();
+    constexpr int E = e_of<T, P1, PK_ROW_FWD>();
     using TF = TeamFft<T, P1, E, false>;
     constexpr int TT = TF::TT;
     cx<T> *smem = smem_base<T>();
@@ -444,7 +440,7 @@ __device__ __forceinline__ void pass2_body(const PassArgs<T> &a, const BT &beta,
 // ---- pass A (adjoint): segmented scatter into shared memory, inverse row FFTs -----
 template <typename T, int P1, int KM, typename BT>
 __device__ __forceinline__ void passA_body(const PassArgs<T> &a, const BT &beta, const int bx) {
-    constexpr int E = e_of<T, P1>();
+    constexpr int E = e_of<T, P1, PK_ROW_ADJ>();
     using TF = TeamFft<T, P1, E, true>;
     constexpr int TT = TF::TT;
     cx<T> *smem = smem_base<T>();
@@ -584,9 +580,15 @@ __device__ __forceinline__ void passA_body(const PassArgs<T> &a, const BT &beta,
 // each CTA stores its partial sum to part[s], and the last CTA of the column block
 // (an atomic ticket, no waiting) adds the SB partials in the fixed order
 // s = 0..SB-1, so the result does not depend on which CTA finishes last.
+// Pass B's CTA: a 32 KiB tile of CB columns, TT threads each (E = 16): 256 threads in
+// FP32 (CB = 4096 / L2 columns of L2 / 16 threads), 128 in FP64.
+template <typename T> struct PassBBounds;
+template <> struct PassBBounds<float> { static constexpr int threads = 256, blocks = 2; };
+template <> struct PassBBounds<double> { static constexpr int threads = 128, blocks = 3; };
+
 template <typename T, int P2>
 __device__ __forceinline__ void passB_body(const PassArgs<T> &a, const int bx, const int by) {
-    constexpr int E = e_of<T, P2>();
+    constexpr int E = e_of<T, P2, PK_COL_ADJ>();
     using TF = TeamFft<T, P2, E, true>;
     constexpr int TT = TF::TT;
     cx<T> *smem = smem_base<T>();
@@ -722,7 +724,7 @@ __device__ __forceinline__ void passB_body(const PassArgs<T> &a, const int bx, c
 template <typename T, int P1, int KM, typename BT>
 __device__ __forceinline__ void pass2d_body(const PassArgs<T> &a, const BT &betax, const BT &betay,
                                             const int b) {
-    constexpr int E = e_of<T, P1>();
+    constexpr int E = e_of<T, P1, PK_ROW_FWD>();
     using TF = TeamFft<T, P1, E, false>;
     constexpr int TT = TF::TT;
     cx<T> *smem = smem_base<T>();
@@ -846,7 +848,7 @@ __global__ void __launch_bounds__(256) k_passA(const __grid_constant__ PassArgs<
     passA_body<T, P1, KM>(a, beta, blockIdx.x);
 }
 template <typename T, int P2>
-__global__ void __launch_bounds__(128, 3) k_passB(const __grid_constant__ PassArgs<T> a) {
+__global__ void __launch_bounds__(PassBBounds<T>::threads, PassBBounds<T>::blocks) k_passB(const __grid_constant__ PassArgs<T> a) {
     passB_body<T, P2>(a, blockIdx.x, blockIdx.y);
 }
 // the 2D transform (section 4): column pass and row pass
@@ -916,7 +918,7 @@ __global__ void __launch_bounds__(256) k_passA_many(const PassArgs<T> *__restric
     passA_body<T, P1, KM>(a, BetaShared<T, KM>{&sb.b[0][0]}, blockIdx.x);
 }
 template <typename T, int P2>
-__global__ void __launch_bounds__(128, 3) k_passB_many(const PassArgs<T> *__restrict__ args,
+__global__ void __launch_bounds__(PassBBounds<T>::threads, PassBBounds<T>::blocks) k_passB_many(const PassArgs<T> *__restrict__ args,
                                                        const cx<T> *in, cx<T> *out) {
     __shared__ PassArgs<T> a;
     many_args<T>(a, args, in, out);
@@ -983,12 +985,14 @@ void cols_fields(nufft_plan p, PassArgs<T> &a, bool adjoint) {
     while ((1 << a.lgC) < a.C) ++a.lgC;
     a.S = adjoint ? p->SB : p->S1;
     a.SB = p->SBsplit;
+    a.twc = (const cx<T> *)(adjoint ? p->twst2b : p->twst2);   // each pass's own stage layout
 }
 
 // The fields a row-pass launch adds to base_args (single and batched launches).
 template <typename T>
 int rows_fields(nufft_plan p, PassArgs<T> &a, bool adjoint) {
-    a.S = p->S2;
+    a.S = adjoint ? p->SA : p->S2;
+    a.twr = (const cx<T> *)(adjoint ? p->twst1a : p->twst1);   // each pass's own stage layout
     a.chunk = p->chunkA;
     a.mbar_off = (int)p->mbar_off2;
     a.G = adjoint ? p->GA : p->G;
@@ -1002,7 +1006,7 @@ template <typename T>
 int launch_cols(nufft_plan p, const PassArgs<T> &a0, bool adjoint, cudaStream_t s) {
     return dispatch_P(p->L2, [&](auto PC) -> int {
         constexpr int P = decltype(PC)::value;
-        constexpr int TT = P / e_of<T, P>();
+        const int TT = adjoint ? P / e_of<T, P, PK_COL_ADJ>() : P / e_of<T, P, PK_COL_FWD>();
         PassArgs<T> a = a0;
         cols_fields<T>(p, a, adjoint);
         const size_t smem = adjoint ? p->smemB : p->smem1;
@@ -1034,7 +1038,7 @@ int launch_rows(nufft_plan p, const PassArgs<T> &a0, bool adjoint, cudaStream_t 
     const Beta<T, KM> beta = beta_of<T, KM>(p);
     return dispatch_P(p->L1, [&](auto PC) -> int {
         constexpr int P = decltype(PC)::value;
-        constexpr int TT = P / e_of<T, P>();
+        const int TT = adjoint ? P / e_of<T, P, PK_ROW_ADJ>() : P / e_of<T, P, PK_ROW_FWD>();
         PassArgs<T> a = a0;
         if (int rc = rows_fields<T>(p, a, adjoint)) return rc;
         int nt = adjoint ? p->ntA : (a.nranks > p->K ? p->nt2d : p->nt2);
@@ -1070,7 +1074,7 @@ int launch_cols_many(nufft_plan rep, const PassArgs<T> *args, int nprob, int ny,
                      const void *in, void *out, cudaStream_t s) {
     return dispatch_P_many(rep->L2, [&](auto PC) -> int {
         constexpr int P = decltype(PC)::value;
-        constexpr int TT = P / e_of<T, P>();
+        const int TT = adjoint ? P / e_of<T, P, PK_COL_ADJ>() : P / e_of<T, P, PK_COL_FWD>();
         const int C = adjoint ? rep->CB : rep->C1;
         const size_t smem = adjoint ? rep->smemB : rep->smem1;
         const dim3 grid(rep->L1 / C, ny, nprob), block(C * TT);
@@ -1093,7 +1097,7 @@ int launch_rows_many(nufft_plan rep, const PassArgs<T> *args, const Beta<T, KM> 
                      bool adjoint, const void *in, void *out, cudaStream_t s) {
     return dispatch_P_many(rep->L1, [&](auto PC) -> int {
         constexpr int P = decltype(PC)::value;
-        constexpr int TT = P / e_of<T, P>();
+        const int TT = adjoint ? P / e_of<T, P, PK_ROW_ADJ>() : P / e_of<T, P, PK_ROW_FWD>();
         const int nt = adjoint ? rep->ntA : rep->nt2;
         const size_t smem = adjoint ? rep->smemA : rep->smem2;
         const dim3 grid(rep->NB, 1, nprob), block(nt * TT);
@@ -1119,7 +1123,7 @@ int launch_cols_2d(nufft_plan p, const PassArgs<T> &a0, cudaStream_t s) {
     cols_fields<T>(p, a, false);
     return dispatch_P(p->L2, [&](auto PC) -> int {
         constexpr int P = decltype(PC)::value;
-        constexpr int TT = P / e_of<T, P>();
+        constexpr int TT = P / e_of<T, P, PK_COL_FWD>();
         static int done[64] = {};
         auto kern = k_pass1_2d<T, P>;
         if (int r = set_smem(kern, p->smem1, p->device, done)) return r;
@@ -1142,7 +1146,7 @@ int launch_rows_2d(nufft_plan p, const PassArgs<T> &a0, cudaStream_t s) {
         }
     return dispatch_P(p->L1, [&](auto PC) -> int {
         constexpr int P = decltype(PC)::value;
-        constexpr int TT = P / e_of<T, P>();
+        constexpr int TT = P / e_of<T, P, PK_ROW_FWD>();
         static int done[64] = {};
         auto kern = k_pass2d<T, P, KM>;
         if (int r = set_smem(kern, p->smem2, p->device, done)) return r;

@@ -215,8 +215,7 @@ int upload_table(void **dst, const std::vector<double> &re, const std::vector<do
 // radices E, then min(E, P/E), then the rest): stage s >= 1 with radix R after NS
 // points holds w_{NS R}^{i j} at offset + (i - 1) NS + j.
 template <typename T>
-int stage_table(int P, void **dst, cudaStream_t s, int64_t *bytes) {
-    const int EM = sizeof(T) == 4 ? 32 : 16;
+int stage_table(int P, int EM, void **dst, cudaStream_t s, int64_t *bytes) {
     const int E = std::min(EM, P), TT = P / E;
     const int R0 = E, R1 = TT > 1 ? std::min(E, TT) : 1, R2 = TT / R1;
     std::vector<double> re, im;
@@ -237,9 +236,12 @@ int stage_table(int P, void **dst, cudaStream_t s, int64_t *bytes) {
 
 template <typename T>
 int build_tables(nufft_plan p, cudaStream_t s) {
-    int rc = stage_table<T>(p->L1, &p->twst1, s, &p->work_bytes);
+    // each pass's stage table for its own values per thread
+    int rc = stage_table<T>(p->L1, EmaxT<T, PK_ROW_FWD>::v, &p->twst1, s, &p->work_bytes);
     if (rc) return rc;
-    if ((rc = stage_table<T>(p->L2, &p->twst2, s, &p->work_bytes))) return rc;
+    if ((rc = stage_table<T>(p->L1, EmaxT<T, PK_ROW_ADJ>::v, &p->twst1a, s, &p->work_bytes))) return rc;
+    if ((rc = stage_table<T>(p->L2, EmaxT<T, PK_COL_FWD>::v, &p->twst2, s, &p->work_bytes))) return rc;
+    if ((rc = stage_table<T>(p->L2, EmaxT<T, PK_COL_ADJ>::v, &p->twst2b, s, &p->work_bytes))) return rc;
     std::vector<double> re, im;
     // four-step twiddle w_L^m = w_L^(4096 m_hi) * w_L^(m_lo), m = 4096 m_hi + m_lo
     const int64_t nlo = std::min<int64_t>(p->L, TW_BASE);
@@ -397,7 +399,7 @@ int plan_device(nufft_plan p, const double *x, cudaStream_t s) {
 void free_plan(nufft_plan p) {
     if (!p) return;
     void *bufs[] = {p->tsorted, p->perm, p->bstart, p->t_j, p->dsorted, p->d_j, p->twst1,
-                    p->twst2, p->twhi, p->twlo, p->Y, p->fscr, p->cstage, p->fstage, p->U, p->V, p->Xg,
+                    p->twst2, p->twst1a, p->twst2b, p->twhi, p->twlo, p->Y, p->fscr, p->cstage, p->fstage, p->U, p->V, p->Xg,
                     p->part, p->counters, p->err, p->Ufac, p->Vfac, p->t2_j, p->d2_j, p->dsorted2, p->vy,
                     p->inv_lam, p->inv_x, p->inv_z, p->inv_r, p->inv_p, p->inv_ap, p->inv_part, p->inv_scal};
     for (void *b : bufs) if (b) cudaFree(b);
@@ -484,8 +486,7 @@ int plan_device_2d(nufft_plan p, const double *x, const double *y, cudaStream_t 
     p->B2 = 1;
     p->NB = p->L2;
     {
-        constexpr int EM = sizeof(T) == 4 ? 32 : 16;
-        const int E1 = std::min(EM, p->L1), TT1 = p->L1 / E1;
+        const int E1 = std::min(EmaxT<T, PK_ROW_FWD>::v, p->L1), TT1 = p->L1 / E1;
         const int maxt = std::max(1, 256 / TT1);
         const int rounds = (p->K2 + maxt - 1) / maxt;
         int nt = (p->K2 + rounds - 1) / rounds;
