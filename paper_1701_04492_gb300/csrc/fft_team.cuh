@@ -155,13 +155,13 @@ __device__ __forceinline__ int padi_run(int pbase, int i) {
 // The passes, for the choice of their team FFT's values per thread E.
 enum PassKind : int { PK_COL_FWD = 0, PK_ROW_FWD = 1, PK_ROW_ADJ = 2, PK_COL_ADJ = 3 };
 
-// E per pass (the FFT length is P <= E^3; a team has P / E threads).  FP32: the forward
-// row pass and the adjoint column pass take E = 16 (twice the threads, one more
-// exchange), which measured faster at 2^20 (pass 2 74 -> 68 us, pass B 72 -> 59 us); pass 1
-// and pass A were faster with E = 32 (50 vs 58 us, 101 vs 115 us).  FP64: E = 16.
+// E per pass (the FFT length is P <= E^3; a team has P / E threads).  FP32: the row
+// passes and the adjoint column pass take E = 16 (twice the threads, one more exchange),
+// measured faster at 2^20 (pass 2 74 -> 68 us, pass A 101 -> 93 us, pass B 72 -> 64 us);
+// pass 1 was faster with E = 32 (50 against 58 us).  FP64: E = 16.
 template <typename T> struct EmaxBase;
 template <> struct EmaxBase<float> {
-    __host__ __device__ static constexpr int of(int kind) { return (kind == PK_ROW_FWD || kind == PK_COL_ADJ) ? 16 : 32; }
+    __host__ __device__ static constexpr int of(int kind) { return kind == PK_COL_FWD ? 32 : 16; }
 };
 template <> struct EmaxBase<double> {
     __host__ __device__ static constexpr int of(int) { return 16; }
