@@ -226,11 +226,7 @@ def run_ours(args):
         step_ms = timed(step, args.steps, args.warmup)
     if ws > 1:
         dist.barrier()
-    tot = torch.tensor([sum(step_ms)], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
-    total_ms = float(tot.item())
-    value = ws * M * args.steps / (total_ms * 1e-3) / 1e9
+    total_ms, value = job_throughput(sum(step_ms), ws, M * args.steps, dev)
 
     extra = {}
     if rank == 0:
@@ -345,6 +341,19 @@ def run_ours(args):
     if ws > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def job_throughput(local_ms, ws, units_per_rank, device):
+    """Whole-job throughput of N replicas: the timed region is the slowest rank's
+    (max over ranks), and the job processed ws x units_per_rank points in it.
+    Returns (max ms, Gpts/s)."""
+    import torch
+    import torch.distributed as dist
+    tot = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    if ws > 1:
+        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+    total_ms = float(tot.item())
+    return total_ms, ws * units_per_rank / (total_ms * 1e-3) / 1e9
 
 
 def batch_c5(api, dev, timed, steps):

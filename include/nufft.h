@@ -331,6 +331,23 @@ int nufft_batch_check(nufft_batch b, void *stream);
  * flight on the batch. */
 int nufft_batch_destroy(nufft_batch b);
 
+/* ---- Test hooks: failure detection without a GPU fault ------------------------
+ * No counterpart in the paper.  Failures are made on the host, or by a bounded
+ * device-side wait; nothing here faults, traps or hangs a GPU. */
+
+/* Make a device allocation of the library fail as if out of memory: the one after the
+ * next `after` allocations (after >= 0; after < 0 turns the injection off).  The call
+ * that meets it returns NUFFT_ENOMEM and releases what it had allocated (plans,
+ * batches, the inverse's solver state).  Process-wide; for tests. */
+int nufft_test_fail_alloc(int after);
+
+/* Launch one CTA that waits on an mbarrier which nothing completes.  Its bounded wait
+ * gives up after the library's time limit (2 s), records the timeout in an error word
+ * and returns, so the context stays usable.  Returns NUFFT_ETIMEOUT (the expected
+ * outcome), NUFFT_OK (the wait completed: a bug) or NUFFT_ECUDA.  Synchronises
+ * `stream`. */
+int nufft_test_wait_timeout(void *stream);
+
 /* Synchronise `stream` and report whether any exec call on this plan since the
  * last check had a device-side wait give up (a bulk copy that did not complete
  * within its time limit): NUFFT_ETIMEOUT, and the results of those calls are

@@ -42,6 +42,8 @@ SIGNATURES = {
     "nufft2_check": (_i32, [_vp, _vp]),
     "nufft2_exec_noalloc": (_i32, [_i64, _i64, _vp, _dbl, _vp, _vp, _vp]),
     "nufft_strerror": (ctypes.c_char_p, [_i32]),
+    "nufft_test_fail_alloc": (_i32, [_i32]),
+    "nufft_test_wait_timeout": (_i32, [_vp]),
     "nufft2_inverse": (_i32, [_vp, _vp, _vp, _dbl, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_dbl), _vp]),
     "nufft2d_plan": (_i32, [ctypes.POINTER(_vp), _i64, _i64, _i64, _vp, _vp, _dbl, _i32, _u32, _vp]),
     "nufft2d_plan_info": (_i32, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_dbl),

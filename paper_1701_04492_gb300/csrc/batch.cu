@@ -22,6 +22,7 @@
 
 #include "fill.cuh"
 #include "passes.cuh"
+#include "nvtx_range.h"
 
 namespace nufft {
 NUFFT_DECLARE_COLS_MANY()
@@ -81,7 +82,7 @@ void free_batch(nufft_batch b) {
 
 template <typename V>
 int upload(void **dst, const std::vector<V> &h) {
-    NUFFT_CUDA_TRY(cudaMalloc(dst, h.size() * sizeof(V)));
+    NUFFT_CUDA_TRY(dev_malloc((void **)dst, h.size() * sizeof(V)));
     NUFFT_CUDA_TRY(cudaMemcpy(*dst, h.data(), h.size() * sizeof(V), cudaMemcpyHostToDevice));
     return NUFFT_OK;
 }
@@ -389,8 +390,8 @@ int tune_many(nufft_batch *out, int64_t count, const int64_t *N, const int64_t *
     void *c = nullptr, *f = nullptr, *flush = nullptr;
     const size_t cn = (size_t)std::max<int64_t>(b0->offN.back(), 1), fm = (size_t)std::max<int64_t>(b0->offM.back(), 1);
     int rc = NUFFT_OK;
-    if (cudaMalloc(&c, cn * 8) != cudaSuccess || cudaMalloc(&f, fm * 8) != cudaSuccess ||
-        cudaMalloc(&flush, L2_FLUSH_BYTES) != cudaSuccess ||
+    if (dev_malloc((void **)&c, cn * 8) != cudaSuccess || dev_malloc((void **)&f, fm * 8) != cudaSuccess ||
+        dev_malloc((void **)&flush, L2_FLUSH_BYTES) != cudaSuccess ||
         fill_hash<float>(c, 2 * (int64_t)cn, s) != cudaSuccess || fill_hash<float>(f, 2 * (int64_t)fm, s) != cudaSuccess)
         rc = NUFFT_ECUDA;
     bool changed = false;
@@ -460,6 +461,7 @@ int tune_many(nufft_batch *out, int64_t count, const int64_t *N, const int64_t *
 extern "C" int nufft2_plan_many(nufft_batch *out, int64_t count, const int64_t *N_host,
                                 const int64_t *M_host, const int64_t *L_host, const double *x_dev,
                                 const double *eps_host, int prec, unsigned flags, void *stream) {
+    nufft::NvtxRange nvtx_range_("nufft2_plan_many");
     using namespace nufft;
     if (!out) return NUFFT_EINVAL;
     *out = nullptr;
@@ -501,6 +503,7 @@ extern "C" int nufft_batch_info(nufft_batch b, int64_t *classes, int64_t *total_
 }
 
 extern "C" int nufft2_exec_many(nufft_batch b, const void *c_dev, void *f_dev, void *stream) {
+    nufft::NvtxRange nvtx_range_("nufft2_exec_many");
     if (!b || !c_dev || (b->offM.back() > 0 && !f_dev)) return NUFFT_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     return b->prec == NUFFT_F32 ? nufft::exec_many<float>(b, false, c_dev, f_dev, s)
@@ -508,6 +511,7 @@ extern "C" int nufft2_exec_many(nufft_batch b, const void *c_dev, void *f_dev, v
 }
 
 extern "C" int nufft1_exec_many(nufft_batch b, const void *g_dev, void *c_dev, void *stream) {
+    nufft::NvtxRange nvtx_range_("nufft1_exec_many");
     if (!b || !c_dev || (b->offM.back() > 0 && !g_dev)) return NUFFT_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     return b->prec == NUFFT_F32 ? nufft::exec_many<float>(b, true, g_dev, c_dev, s)
@@ -515,6 +519,7 @@ extern "C" int nufft1_exec_many(nufft_batch b, const void *g_dev, void *c_dev, v
 }
 
 extern "C" int nufft2_exec_each(nufft_batch b, const void *c_dev, void *f_dev, int adjoint, void *stream) {
+    nufft::NvtxRange nvtx_range_("nufft2_exec_each");
     if (!b || !c_dev || (b->offM.back() > 0 && !f_dev)) return NUFFT_EINVAL;
     const size_t cxs = b->prec == NUFFT_F32 ? 8 : 16;
     for (size_t i = 0; i < b->plans.size(); ++i) {

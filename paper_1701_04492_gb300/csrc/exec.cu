@@ -8,6 +8,7 @@
 #include <cstdint>
 
 #include "passes.cuh"
+#include "nvtx_range.h"
 
 namespace nufft {
 
@@ -333,8 +334,8 @@ template <typename T>
 int plan_factor_tables(nufft_plan p, cudaStream_t s) {
     const size_t cxs = 2 * sizeof(T);
     const int64_t M = std::max<int64_t>(p->M, 1);
-    NUFFT_CUDA_TRY(cudaMalloc(&p->Ufac, (size_t)M * p->K * cxs));
-    NUFFT_CUDA_TRY(cudaMalloc(&p->Vfac, (size_t)p->N * p->K * sizeof(T)));
+    NUFFT_CUDA_TRY(dev_malloc((void **)&p->Ufac, (size_t)M * p->K * cxs));
+    NUFFT_CUDA_TRY(dev_malloc((void **)&p->Vfac, (size_t)p->N * p->K * sizeof(T)));
     p->work_bytes += (int64_t)((size_t)M * p->K * cxs + (size_t)p->N * p->K * sizeof(T));
     Beta<double, KMAX_ALL> aw{};
     for (int r = 0; r < p->K; ++r)
@@ -358,15 +359,15 @@ template <typename T>
 int plan_unfused_factors(nufft_plan p, cudaStream_t s) {
     const size_t cxs = 2 * sizeof(T);
     const int64_t M = std::max<int64_t>(p->M, 1);
-    NUFFT_CUDA_TRY(cudaMalloc(&p->U, (size_t)M * p->K * cxs));
-    NUFFT_CUDA_TRY(cudaMalloc(&p->V, (size_t)p->N * p->K * sizeof(T)));
-    NUFFT_CUDA_TRY(cudaMalloc(&p->Xg, (size_t)p->K * p->L * cxs));
+    NUFFT_CUDA_TRY(dev_malloc((void **)&p->U, (size_t)M * p->K * cxs));
+    NUFFT_CUDA_TRY(dev_malloc((void **)&p->V, (size_t)p->N * p->K * sizeof(T)));
+    NUFFT_CUDA_TRY(dev_malloc((void **)&p->Xg, (size_t)p->K * p->L * cxs));
     p->work_bytes += (int64_t)((size_t)M * p->K * cxs + (size_t)p->N * p->K * sizeof(T) +
                                (size_t)p->K * p->L * cxs);
     if ((size_t)p->K * p->M > (size_t)(p->K + 1) * p->L) {   // the gathered K x M block reuses Y
         cudaFree(p->Y);
         p->Y = nullptr;
-        NUFFT_CUDA_TRY(cudaMalloc(&p->Y, (size_t)p->K * p->M * cxs));
+        NUFFT_CUDA_TRY(dev_malloc((void **)&p->Y, (size_t)p->K * p->M * cxs));
         p->work_bytes += (int64_t)(((size_t)p->K * p->M - (size_t)(p->K + 1) * p->L) * cxs);
     }
     Beta<double, KMAX_ALL> aw{};
@@ -545,6 +546,7 @@ using nufft::exec_forward;
 using nufft::exec_unfused;
 
 extern "C" int nufft2_exec(nufft_plan p, const void *c_dev, void *f_dev, void *stream) {
+    nufft::NvtxRange nvtx_range_("nufft2_exec");
     if (!p || !c_dev || (p->M > 0 && !f_dev)) return NUFFT_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     return p->prec == NUFFT_F32 ? exec_forward<float>(p, c_dev, f_dev, s)
@@ -552,6 +554,7 @@ extern "C" int nufft2_exec(nufft_plan p, const void *c_dev, void *f_dev, void *s
 }
 
 extern "C" int nufft1_exec(nufft_plan p, const void *g_dev, void *c_dev, void *stream) {
+    nufft::NvtxRange nvtx_range_("nufft1_exec");
     if (p && p->dims == 2) return NUFFT_EUNSUPPORTED;   // the 2D transform has its forward only
     if (!p || !c_dev || (p->M > 0 && !g_dev)) return NUFFT_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
@@ -561,6 +564,7 @@ extern "C" int nufft1_exec(nufft_plan p, const void *g_dev, void *c_dev, void *s
 
 extern "C" int nufft2_exec_dx(nufft_plan p, const void *c_dev, const void *g_dev, void *gx_dev,
                               int accumulate, void *stream) {
+    nufft::NvtxRange nvtx_range_("nufft2_exec_dx");
     if (p && p->dims == 2) return NUFFT_EUNSUPPORTED;   // the 2D transform has its forward only
     if (!p || !c_dev || (p->M > 0 && (!g_dev || !gx_dev))) return NUFFT_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
@@ -570,6 +574,7 @@ extern "C" int nufft2_exec_dx(nufft_plan p, const void *c_dev, const void *g_dev
 
 extern "C" int nufft2_exec_deriv(nufft_plan p, const void *c_dev, void *f_dev, void *fprime_dev,
                                  void *stream) {
+    nufft::NvtxRange nvtx_range_("nufft2_exec_deriv");
     if (p && p->dims == 2) return NUFFT_EUNSUPPORTED;   // the 2D transform has its forward only
     if (!p || !c_dev || (p->M > 0 && (!f_dev || !fprime_dev))) return NUFFT_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
@@ -579,6 +584,7 @@ extern "C" int nufft2_exec_deriv(nufft_plan p, const void *c_dev, void *f_dev, v
 
 extern "C" int nufft2_grad_x(nufft_plan p, const void *g_dev, const void *fprime_dev, void *gx_dev,
                              int accumulate, void *stream) {
+    nufft::NvtxRange nvtx_range_("nufft2_grad_x");
     if (p && p->dims == 2) return NUFFT_EUNSUPPORTED;   // the 2D transform has its forward only
     if (!p || (p->M > 0 && (!g_dev || !fprime_dev || !gx_dev))) return NUFFT_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
@@ -613,6 +619,7 @@ extern "C" int nufft2_exec_host(nufft_plan p, const void *c_host, void *f_host, 
 }
 
 extern "C" int nufft2_exec_unfused(nufft_plan p, const void *c_dev, void *f_dev, void *stream) {
+    nufft::NvtxRange nvtx_range_("nufft2_exec_unfused");
     if (p && p->dims == 2) return NUFFT_EUNSUPPORTED;   // the 2D transform has its forward only
     if (!p || !c_dev || (p->M > 0 && !f_dev)) return NUFFT_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;

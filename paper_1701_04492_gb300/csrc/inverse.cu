@@ -19,6 +19,7 @@
 #include <new>
 
 #include "passes.cuh"
+#include "nvtx_range.h"
 
 namespace nufft {
 NUFFT_DECLARE_COLS(float)
@@ -175,8 +176,21 @@ int fft_natural(nufft_plan fp, const void *in, int64_t n_valid, void *out, cudaS
     return launch_rows<T, 4>(fp, a, false, s);
 }
 
+// Free the solver state (after a failed build, so that the next call starts afresh).
+void drop_state(nufft_plan p) {
+    for (void *q : {p->inv_lam, p->inv_x, p->inv_z, p->inv_r, p->inv_p, p->inv_ap, (void *)p->inv_part,
+                    (void *)p->inv_scal})
+        if (q) cudaFree(q);
+    if (p->inv_host) cudaFreeHost(p->inv_host);
+    if (p->inv_fft) nufft_destroy(p->inv_fft);
+    p->inv_lam = p->inv_x = p->inv_z = p->inv_r = p->inv_p = p->inv_ap = nullptr;
+    p->inv_part = p->inv_scal = p->inv_host = nullptr;
+    p->inv_fft = nullptr;
+    p->inv_P = 0;
+}
+
 template <typename T>
-int build_state(nufft_plan p, cudaStream_t s) {
+int build_state_impl(nufft_plan p, cudaStream_t s) {
     const size_t cxs = 2 * sizeof(T);
     int64_t P = 1024;
     while (P < 2 * p->N) P <<= 1;
@@ -184,19 +198,19 @@ int build_state(nufft_plan p, cudaStream_t s) {
     if (int rc = nufft2_plan(&p->inv_fft, P, 0, nullptr, 0.5, p->prec, P, 0, s)) return rc;
     if (p->inv_fft->K != 1 || p->inv_fft->kmax != 4) return NUFFT_ESTATE;
     p->inv_P = P;
-    NUFFT_CUDA_TRY(cudaMalloc(&p->inv_lam, (size_t)P * cxs));
-    NUFFT_CUDA_TRY(cudaMalloc(&p->inv_x, (size_t)P * cxs));
-    NUFFT_CUDA_TRY(cudaMalloc(&p->inv_z, (size_t)P * cxs));
-    NUFFT_CUDA_TRY(cudaMalloc(&p->inv_r, (size_t)p->N * cxs));
-    NUFFT_CUDA_TRY(cudaMalloc(&p->inv_p, (size_t)p->N * cxs));
-    NUFFT_CUDA_TRY(cudaMalloc(&p->inv_ap, (size_t)p->N * cxs));
-    NUFFT_CUDA_TRY(cudaMalloc(&p->inv_part, RED_BLOCKS * sizeof(double)));
-    NUFFT_CUDA_TRY(cudaMalloc(&p->inv_scal, S_COUNT * sizeof(double)));
+    NUFFT_CUDA_TRY(dev_malloc((void **)&p->inv_lam, (size_t)P * cxs));
+    NUFFT_CUDA_TRY(dev_malloc((void **)&p->inv_x, (size_t)P * cxs));
+    NUFFT_CUDA_TRY(dev_malloc((void **)&p->inv_z, (size_t)P * cxs));
+    NUFFT_CUDA_TRY(dev_malloc((void **)&p->inv_r, (size_t)p->N * cxs));
+    NUFFT_CUDA_TRY(dev_malloc((void **)&p->inv_p, (size_t)p->N * cxs));
+    NUFFT_CUDA_TRY(dev_malloc((void **)&p->inv_ap, (size_t)p->N * cxs));
+    NUFFT_CUDA_TRY(dev_malloc((void **)&p->inv_part, RED_BLOCKS * sizeof(double)));
+    NUFFT_CUDA_TRY(dev_malloc((void **)&p->inv_scal, S_COUNT * sizeof(double)));
     NUFFT_CUDA_TRY(cudaMallocHost(&p->inv_host, 2 * sizeof(double)));
     p->work_bytes += (int64_t)((3 * (size_t)P + 3 * (size_t)p->N) * cxs);
     // t = A^H 1 (its first N entries are the Toeplitz column), then lambda
     void *ones = nullptr;
-    NUFFT_CUDA_TRY(cudaMalloc(&ones, (size_t)std::max<int64_t>(p->M, 1) * cxs));
+    NUFFT_CUDA_TRY(dev_malloc((void **)&ones, (size_t)std::max<int64_t>(p->M, 1) * cxs));
     k_ones<T><<<grid1(p->M), RED_THREADS, 0, s>>>((cx<T> *)ones, p->M);
     int rc = nufft1_exec(p, ones, p->inv_r, s);
     if (!rc) {
@@ -206,6 +220,13 @@ int build_state(nufft_plan p, cudaStream_t s) {
     if (!rc) rc = fft_natural<T>(p->inv_fft, p->inv_z, P, p->inv_lam, s);
     if (!rc && cudaStreamSynchronize(s) != cudaSuccess) rc = NUFFT_ECUDA;
     cudaFree(ones);
+    return rc;
+}
+
+template <typename T>
+int build_state(nufft_plan p, cudaStream_t s) {
+    const int rc = build_state_impl<T>(p, s);
+    if (rc) drop_state(p);
     return rc;
 }
 
@@ -254,6 +275,7 @@ int solve(nufft_plan p, const void *f, void *c, double tol, int maxit, int *iter
 
 extern "C" int nufft2_inverse(nufft_plan p, const void *f_dev, void *c_dev, double tol, int maxit, int *iterations,
                               double *relres, void *stream) {
+    nufft::NvtxRange nvtx_range_("nufft2_inverse");
     if (!p || !c_dev || (p->M > 0 && !f_dev) || !(tol >= 0.0) || maxit < 0) return NUFFT_EINVAL;
     if (p->dims == 2) return NUFFT_EUNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;

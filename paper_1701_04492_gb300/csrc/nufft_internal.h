@@ -115,6 +115,9 @@ inline int mark(nufft_plan p, cudaStream_t s, bool first) {
 
 namespace nufft {
 
+// hooks.cu: cudaMalloc, unless a test has injected a failure (nufft_test_fail_alloc)
+cudaError_t dev_malloc(void **p, size_t bytes);
+
 // host_math.cpp
 double bessel_j_int(int n, double z);
 void chebyshev_alpha(int K, double gamma, double *alpha /* K*K, [p*K + r] */);

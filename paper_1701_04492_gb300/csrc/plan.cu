@@ -20,6 +20,7 @@
 #include "fft_team.cuh"
 #include "fill.cuh"
 #include "nufft_internal.h"
+#include "nvtx_range.h"
 
 namespace nufft {
 namespace {
@@ -204,7 +205,7 @@ int upload_table(void **dst, const std::vector<double> &re, const std::vector<do
     const size_t n = re.size();
     std::vector<T> h(2 * n);
     for (size_t i = 0; i < n; ++i) { h[2 * i] = (T)re[i]; h[2 * i + 1] = (T)im[i]; }
-    NUFFT_CUDA_TRY(cudaMalloc(dst, h.size() * sizeof(T)));
+    NUFFT_CUDA_TRY(dev_malloc((void **)dst, h.size() * sizeof(T)));
     *bytes += (int64_t)(h.size() * sizeof(T));
     NUFFT_CUDA_TRY(cudaMemcpyAsync(*dst, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
     NUFFT_CUDA_TRY(cudaStreamSynchronize(s));   // h goes out of scope
@@ -265,24 +266,24 @@ int sort_samples(nufft_plan p, cudaStream_t s) {
         ~Scratch() { cudaFree(ka); cudaFree(va); cudaFree(kb); cudaFree(vb); cudaFree(cnt); }
     } sc;
     const size_t Mi = (size_t)std::max<int64_t>(M, 1);
-    NUFFT_CUDA_TRY(cudaMalloc(&p->tsorted, Mi * sizeof(int32_t)));
-    NUFFT_CUDA_TRY(cudaMalloc(&p->perm, Mi * sizeof(int32_t)));
-    NUFFT_CUDA_TRY(cudaMalloc(&p->dsorted, Mi * sizeof(T)));
-    if (p->dims == 2) NUFFT_CUDA_TRY(cudaMalloc(&p->dsorted2, Mi * sizeof(T)));
-    NUFFT_CUDA_TRY(cudaMalloc(&p->bstart, (size_t)(p->NB + 1) * sizeof(int32_t)));
+    NUFFT_CUDA_TRY(dev_malloc((void **)&p->tsorted, Mi * sizeof(int32_t)));
+    NUFFT_CUDA_TRY(dev_malloc((void **)&p->perm, Mi * sizeof(int32_t)));
+    NUFFT_CUDA_TRY(dev_malloc((void **)&p->dsorted, Mi * sizeof(T)));
+    if (p->dims == 2) NUFFT_CUDA_TRY(dev_malloc((void **)&p->dsorted2, Mi * sizeof(T)));
+    NUFFT_CUDA_TRY(dev_malloc((void **)&p->bstart, (size_t)(p->NB + 1) * sizeof(int32_t)));
     p->work_bytes += (int64_t)(Mi * (2 * sizeof(int32_t) + sizeof(T)) + (p->NB + 1) * sizeof(int32_t));
-    NUFFT_CUDA_TRY(cudaMalloc(&sc.ka, Mi * sizeof(int32_t)));
-    NUFFT_CUDA_TRY(cudaMalloc(&sc.va, Mi * sizeof(int32_t)));
-    NUFFT_CUDA_TRY(cudaMalloc(&sc.kb, Mi * sizeof(int32_t)));
+    NUFFT_CUDA_TRY(dev_malloc((void **)&sc.ka, Mi * sizeof(int32_t)));
+    NUFFT_CUDA_TRY(dev_malloc((void **)&sc.va, Mi * sizeof(int32_t)));
+    NUFFT_CUDA_TRY(dev_malloc((void **)&sc.kb, Mi * sizeof(int32_t)));
     const int nchunks = (int)std::max<int64_t>(1, (M + SORT_CHUNK - 1) / SORT_CHUNK);
-    NUFFT_CUDA_TRY(cudaMalloc(&sc.cnt, (size_t)SORT_BINS * nchunks * sizeof(int32_t)));
+    NUFFT_CUDA_TRY(dev_malloc((void **)&sc.cnt, (size_t)SORT_BINS * nchunks * sizeof(int32_t)));
     int32_t *kin = sc.ka, *vin = sc.va, *kout = sc.kb, *vout = p->perm;
     if (M > 0) {
         k_keys<<<grid_for(M, 256), 256, 0, s>>>(p->t_j, M, p->lg1, p->lg2, p->B2, kin, vin);
         NUFFT_CUDA_TRY(cudaGetLastError());
         const int lgL = p->lg1 + p->lg2;
         const int passes = (lgL + SORT_BITS - 1) / SORT_BITS;
-        NUFFT_CUDA_TRY(cudaMalloc(&sc.vb, Mi * sizeof(int32_t)));
+        NUFFT_CUDA_TRY(dev_malloc((void **)&sc.vb, Mi * sizeof(int32_t)));
         for (int ps = 0; ps < passes; ++ps) {
             // the last pass lands in perm
             vout = (ps == passes - 1) ? p->perm : (vin == sc.va ? sc.vb : sc.va);
@@ -320,10 +321,10 @@ int plan_device(nufft_plan p, const double *x, cudaStream_t s) {
         ~Scratch() { cudaFree(gbits); cudaFree(bad); }
     } sc;
     const size_t Mi = (size_t)std::max<int64_t>(M, 1);
-    NUFFT_CUDA_TRY(cudaMalloc(&sc.gbits, sizeof(unsigned long long)));
-    NUFFT_CUDA_TRY(cudaMalloc(&sc.bad, sizeof(int)));
-    NUFFT_CUDA_TRY(cudaMalloc(&p->t_j, Mi * sizeof(int32_t)));
-    NUFFT_CUDA_TRY(cudaMalloc(&p->d_j, Mi * sizeof(double)));
+    NUFFT_CUDA_TRY(dev_malloc((void **)&sc.gbits, sizeof(unsigned long long)));
+    NUFFT_CUDA_TRY(dev_malloc((void **)&sc.bad, sizeof(int)));
+    NUFFT_CUDA_TRY(dev_malloc((void **)&p->t_j, Mi * sizeof(int32_t)));
+    NUFFT_CUDA_TRY(dev_malloc((void **)&p->d_j, Mi * sizeof(double)));
     p->work_bytes += (int64_t)(Mi * (sizeof(int32_t) + sizeof(double)));
     NUFFT_CUDA_TRY(cudaMemsetAsync(sc.gbits, 0, sizeof(unsigned long long), s));
     NUFFT_CUDA_TRY(cudaMemsetAsync(sc.bad, 0, sizeof(int), s));
@@ -371,15 +372,15 @@ int plan_device(nufft_plan p, const double *x, cudaStream_t s) {
 
     // work buffers
     const size_t cxs = 2 * sizeof(T);
-    NUFFT_CUDA_TRY(cudaMalloc(&p->Y, (size_t)(p->K + 1) * p->L * cxs));   // rank K: the derivative
-    NUFFT_CUDA_TRY(cudaMalloc(&p->fscr, Mi * cxs));
-    NUFFT_CUDA_TRY(cudaMalloc(&p->cstage, (size_t)p->N * cxs));
-    NUFFT_CUDA_TRY(cudaMalloc(&p->fstage, Mi * cxs));
-    NUFFT_CUDA_TRY(cudaMalloc(&p->err, sizeof(int)));
+    NUFFT_CUDA_TRY(dev_malloc((void **)&p->Y, (size_t)(p->K + 1) * p->L * cxs));   // rank K: the derivative
+    NUFFT_CUDA_TRY(dev_malloc((void **)&p->fscr, Mi * cxs));
+    NUFFT_CUDA_TRY(dev_malloc((void **)&p->cstage, (size_t)p->N * cxs));
+    NUFFT_CUDA_TRY(dev_malloc((void **)&p->fstage, Mi * cxs));
+    NUFFT_CUDA_TRY(dev_malloc((void **)&p->err, sizeof(int)));
     NUFFT_CUDA_TRY(cudaMemsetAsync(p->err, 0, sizeof(int), s));
     if (p->SBsplit > 1) {
-        NUFFT_CUDA_TRY(cudaMalloc(&p->part, (size_t)p->SBsplit * p->L * cxs));
-        NUFFT_CUDA_TRY(cudaMalloc(&p->counters, (size_t)(p->L1 / p->CB) * sizeof(int)));
+        NUFFT_CUDA_TRY(dev_malloc((void **)&p->part, (size_t)p->SBsplit * p->L * cxs));
+        NUFFT_CUDA_TRY(dev_malloc((void **)&p->counters, (size_t)(p->L1 / p->CB) * sizeof(int)));
         NUFFT_CUDA_TRY(cudaMemsetAsync(p->counters, 0, (size_t)(p->L1 / p->CB) * sizeof(int), s));
         p->work_bytes += (int64_t)((size_t)p->SBsplit * p->L * cxs + (p->L1 / p->CB) * sizeof(int));
     }
@@ -433,12 +434,12 @@ int plan_device_2d(nufft_plan p, const double *x, const double *y, cudaStream_t 
         int *bad = nullptr;
         ~Scratch() { cudaFree(gbits); cudaFree(bad); }
     } sc;
-    NUFFT_CUDA_TRY(cudaMalloc(&sc.gbits, 2 * sizeof(unsigned long long)));
-    NUFFT_CUDA_TRY(cudaMalloc(&sc.bad, sizeof(int)));
-    NUFFT_CUDA_TRY(cudaMalloc(&p->t_j, Mi * sizeof(int32_t)));
-    NUFFT_CUDA_TRY(cudaMalloc(&p->d_j, Mi * sizeof(double)));
-    NUFFT_CUDA_TRY(cudaMalloc(&p->t2_j, Mi * sizeof(int32_t)));
-    NUFFT_CUDA_TRY(cudaMalloc(&p->d2_j, Mi * sizeof(double)));
+    NUFFT_CUDA_TRY(dev_malloc((void **)&sc.gbits, 2 * sizeof(unsigned long long)));
+    NUFFT_CUDA_TRY(dev_malloc((void **)&sc.bad, sizeof(int)));
+    NUFFT_CUDA_TRY(dev_malloc((void **)&p->t_j, Mi * sizeof(int32_t)));
+    NUFFT_CUDA_TRY(dev_malloc((void **)&p->d_j, Mi * sizeof(double)));
+    NUFFT_CUDA_TRY(dev_malloc((void **)&p->t2_j, Mi * sizeof(int32_t)));
+    NUFFT_CUDA_TRY(dev_malloc((void **)&p->d2_j, Mi * sizeof(double)));
     NUFFT_CUDA_TRY(cudaMemsetAsync(sc.gbits, 0, 2 * sizeof(unsigned long long), s));
     NUFFT_CUDA_TRY(cudaMemsetAsync(sc.bad, 0, sizeof(int), s));
     const int64_t Lx = p->L2, Ly = p->L1;
@@ -513,14 +514,14 @@ int plan_device_2d(nufft_plan p, const double *x, const double *y, cudaStream_t 
                 }
                 h[(size_t)r * p->L1 + k] = (T)tr;
             }
-        NUFFT_CUDA_TRY(cudaMalloc(&p->vy, h.size() * sizeof(T)));
+        NUFFT_CUDA_TRY(dev_malloc((void **)&p->vy, h.size() * sizeof(T)));
         NUFFT_CUDA_TRY(cudaMemcpyAsync(p->vy, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
         NUFFT_CUDA_TRY(cudaStreamSynchronize(s));
     }
     const size_t cxs = 2 * sizeof(T);
-    NUFFT_CUDA_TRY(cudaMalloc(&p->Y, (size_t)p->K * p->L * cxs));
-    NUFFT_CUDA_TRY(cudaMalloc(&p->fscr, Mi * cxs));
-    NUFFT_CUDA_TRY(cudaMalloc(&p->err, sizeof(int)));
+    NUFFT_CUDA_TRY(dev_malloc((void **)&p->Y, (size_t)p->K * p->L * cxs));
+    NUFFT_CUDA_TRY(dev_malloc((void **)&p->fscr, Mi * cxs));
+    NUFFT_CUDA_TRY(dev_malloc((void **)&p->err, sizeof(int)));
     NUFFT_CUDA_TRY(cudaMemsetAsync(p->err, 0, sizeof(int), s));
     p->work_bytes += (int64_t)(((size_t)p->K * p->L + Mi) * cxs + Mi * (2 * sizeof(int32_t) + 2 * sizeof(double)));
     NUFFT_CUDA_TRY(cudaStreamSynchronize(s));
@@ -532,6 +533,7 @@ int plan_device_2d(nufft_plan p, const double *x, const double *y, cudaStream_t 
 
 extern "C" int nufft2d_plan(nufft_plan *out, int64_t m, int64_t n, int64_t M, const double *x_dev,
                             const double *y_dev, double eps, int prec, unsigned flags, void *stream) {
+    nufft::NvtxRange nvtx_range_("nufft2d_plan");
     using namespace nufft;
     if (!out) return NUFFT_EINVAL;
     *out = nullptr;
@@ -676,7 +678,7 @@ int plan_autotune(nufft_plan *out, int64_t N, int64_t M, const double *x_dev, do
         void *p = nullptr;
         ~Flush() { cudaFree(p); }
     } flush;
-    if (cudaMalloc(&flush.p, L2_FLUSH_BYTES) != cudaSuccess) {
+    if (dev_malloc((void **)&flush.p, L2_FLUSH_BYTES) != cudaSuccess) {
         (void)cudaGetLastError();
         free_plan(best);
         return NUFFT_ENOMEM;
@@ -717,6 +719,7 @@ int plan_autotune(nufft_plan *out, int64_t N, int64_t M, const double *x_dev, do
 
 extern "C" int nufft2_plan(nufft_plan *out, int64_t N, int64_t M, const double *x_dev, double eps,
                            int prec, int64_t L, unsigned flags, void *stream) {
+    nufft::NvtxRange nvtx_range_("nufft2_plan");
     using namespace nufft;
     if (!out) return NUFFT_EINVAL;
     *out = nullptr;
