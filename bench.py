@@ -50,6 +50,15 @@ def _dist():
     return ws, rank, local
 
 
+def workload_config(N, M, K, gamma, L, ws):
+    """The bench line's config, the same for both arms."""
+    return {"workload": "1D NUFFT-II fwd+bwd (fwd with df/dx, adjoint A^H, dL/dx), N=M=2^20, "
+                        "eps=1e-9, perturbed grid x_j=j/N+0.5u_j/N, c,g~CN(0,1) complex64",
+            "N": N, "M": M, "eps": EPS, "K": K, "gamma": gamma, "L": L,
+            "parallelism": "replicas" if ws > 1 else "single-gpu",
+            "l2": "flushed before every timed step (512 MiB write)"}
+
+
 def _workload():
     from paper_1701_04492_gb300 import workloads as wl
     N = 1 << N_LOG2
@@ -318,11 +327,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "Gpts/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "1D NUFFT-II fwd+bwd (fwd with df/dx, adjoint A^H, dL/dx), N=M=2^20, "
-                                   "eps=1e-9, perturbed grid x_j=j/N+0.5u_j/N, c,g~CN(0,1) complex64",
-                       "N": N, "M": M, "eps": EPS, "K": K, "gamma": plan.gamma, "L": L,
-                       "parallelism": "replicas" if ws > 1 else "single-gpu",
-                       "l2": "flushed before every timed step (512 MiB write)"},
+            "config": workload_config(N, M, K, plan.gamma, L, ws),
             "plan_ms": plan_ms,
             "roofline": roof,
             "e2e": e2e,
@@ -544,9 +549,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "1D NUFFT-II fwd+bwd (fwd, adjoint A^H, d/dx), N=M=2^20, eps=1e-9, "
-                                   "perturbed grid x_j=j/N+0.5u_j/N, c,g~CN(0,1)", "N": N, "M": x.size,
-                       "eps": EPS, "K": P.K},
+            "config": workload_config(N, x.size, P.K, P.gamma, P.L, ws),
             "cpu_baseline": {"value": v, "unit": "Gpts/s", "cores": 1, "kind": "oracle",
                              "sample": "full fwd+bwd steps of the workload in numpy FP64, plan excluded"},
             "e2e": {"value": v, "unit": "Gpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
