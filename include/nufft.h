@@ -157,11 +157,30 @@ int nufft2_exec_deriv(nufft_plan p, const void *c_dev, void *f_dev, void *fprime
 int nufft2_grad_x(nufft_plan p, const void *g_dev, const void *fprime_dev, void *gx_dev, int accumulate,
                   void *stream);
 
-/* B independent transforms sharing the plan: f_b = A c_b, b = 0..B-1, with
- * c_b at c_dev + b*ldc elements and f_b at f_dev + b*ldf elements
- * (ldc >= N, ldf >= M). */
+/* B coefficient vectors on one plan (the same samples): f_b = A c_b, b = 0..B-1, with
+ * c_b at c_dev + b*ldc elements and f_b at f_dev + b*ldf elements (ldc >= N,
+ * ldf >= M).  FP32 plans on grids of up to 2^18 points run all members in one launch
+ * per pass (each member has its own slice of a per-plan workspace, allocated by the
+ * first call with a given or larger B); other plans run the members in turn.  Results
+ * are bit-identical to B nufft2_exec calls. */
 int nufft2_exec_batch(nufft_plan p, int64_t B, const void *c_dev, int64_t ldc,
                       void *f_dev, int64_t ldf, void *stream);
+
+/* The adjoint of B members: c_b = A^H g_b (g_b at g_dev + b*ldg, ldg >= M; c_b at
+ * c_dev + b*ldc, ldc >= N).  Batched launches as nufft2_exec_batch; bit-identical to B
+ * nufft1_exec calls. */
+int nufft1_exec_batch(nufft_plan p, int64_t B, const void *g_dev, int64_t ldg, void *c_dev, int64_t ldc,
+                      void *stream);
+
+/* nufft2_exec_deriv for B members: f_b and fprime_b = df_b/dx at f_dev, fprime_dev +
+ * b*ldf (ldf >= M); c_b at c_dev + b*ldc.  Batched launches as nufft2_exec_batch. */
+int nufft2_exec_deriv_batch(nufft_plan p, int64_t B, const void *c_dev, int64_t ldc, void *f_dev,
+                            void *fprime_dev, int64_t ldf, void *stream);
+
+/* gx_j (+)= sum_b Re(conj(g_bj) fprime_bj) over B members (g_b, fprime_b at + b*ld,
+ * ld >= M): the x-gradient of a loss summed over a batch sharing x, in one launch. */
+int nufft2_grad_x_batch(nufft_plan p, int64_t B, const void *g_dev, const void *fprime_dev, int64_t ld,
+                        void *gx_dev, int accumulate, void *stream);
 
 /* The same as nufft2_exec with HOST buffers: copies c host->device into a
  * plan-owned staging buffer, runs the transform, copies f device->host and

@@ -209,6 +209,49 @@ class Plan:
                                                 _stream(self.device)), "nufft2_exec_batch")
         return f
 
+    def _batch2(self, t, n, name):
+        if t.dim() != 2 or t.shape[1] != n or t.dtype != self.cdtype or t.stride(1) != 1 or t.device != self.device:
+            raise ValueError("%s must be (B, %d) %s with unit inner stride on %s" % (name, n, self.cdtype, self.device))
+        return t
+
+    def adjoint_batch(self, g, out=None):
+        """c[b] = A^H g[b] for a (B, M) batch."""
+        self._batch2(g, self.M, "g")
+        B = g.shape[0]
+        c = out if out is not None else torch.empty(B, self.N, dtype=self.cdtype, device=self.device)
+        self._batch2(c, self.N, "c")
+        with torch.cuda.device(self.device):
+            check(_lib.load().nufft1_exec_batch(self._h, B, _ptr(g), g.stride(0), _ptr(c), c.stride(0),
+                                                _stream(self.device)), "nufft1_exec_batch")
+        return c
+
+    def forward_deriv_batch(self, c, out=None, out_deriv=None):
+        """(f[b], f'[b]) for a (B, N) batch: the forward and df/dx of every member."""
+        self._batch2(c, self.N, "c")
+        B = c.shape[0]
+        f = out if out is not None else torch.empty(B, self.M, dtype=self.cdtype, device=self.device)
+        fp = out_deriv if out_deriv is not None else torch.empty(B, self.M, dtype=self.cdtype, device=self.device)
+        self._batch2(f, self.M, "f")
+        self._batch2(fp, self.M, "fprime")
+        if f.stride(0) != fp.stride(0):
+            raise ValueError("f and fprime must have the same row stride")
+        with torch.cuda.device(self.device):
+            check(_lib.load().nufft2_exec_deriv_batch(self._h, B, _ptr(c), c.stride(0), _ptr(f), _ptr(fp),
+                                                      f.stride(0), _stream(self.device)), "nufft2_exec_deriv_batch")
+        return f, fp
+
+    def grad_x_batch(self, g, fprime, out=None, accumulate=False):
+        """gx (+)= sum_b Re(conj(g[b]) fprime[b]) for (B, M) batches."""
+        self._batch2(g, self.M, "g")
+        self._batch2(fprime, self.M, "fprime")
+        if g.stride(0) != fprime.stride(0) or g.shape[0] != fprime.shape[0]:
+            raise ValueError("g and fprime must have the same shape and row stride")
+        gx = out if out is not None else torch.empty(self.M, dtype=self.rdtype, device=self.device)
+        with torch.cuda.device(self.device):
+            check(_lib.load().nufft2_grad_x_batch(self._h, g.shape[0], _ptr(g), _ptr(fprime), g.stride(0), _ptr(gx),
+                                                  1 if accumulate else 0, _stream(self.device)), "nufft2_grad_x_batch")
+        return gx
+
     def forward_host(self, c_host, f_host):
         """f_host = A c_host with host (ideally pinned) tensors; synchronises."""
         if c_host.device.type != "cpu" or f_host.device.type != "cpu":
@@ -246,10 +289,7 @@ class _Nufft2(torch.autograd.Function):
         if not want_dx:
             f = plan.forward_batch(cc) if batched else plan.forward(cc)
         elif batched:
-            f = torch.empty(cc.shape[0], plan.M, dtype=plan.cdtype, device=plan.device)
-            fp = torch.empty_like(f)
-            for b in range(cc.shape[0]):
-                plan.forward_deriv(cc[b], f[b], fp[b])
+            f, fp = plan.forward_deriv_batch(cc)
         else:
             f, fp = plan.forward_deriv(cc)
         ctx.save_for_backward(fp if fp is not None else torch.empty(0, device=plan.device))
@@ -264,14 +304,13 @@ class _Nufft2(torch.autograd.Function):
         gc = gx = None
         if ctx.needs_input_grad[0]:
             if ctx.batched:
-                gc = torch.stack([plan.adjoint(g[b].contiguous()) for b in range(g.shape[0])])
+                gc = plan.adjoint_batch(g)
             else:
                 gc = plan.adjoint(g)
         if ctx.needs_input_grad[1]:
             gx = torch.empty(plan.M, dtype=plan.rdtype, device=plan.device)
             if ctx.batched:
-                for b in range(g.shape[0]):
-                    plan.grad_x(g[b].contiguous(), fp[b], gx, accumulate=b > 0)
+                plan.grad_x_batch(g, fp, gx)
             else:
                 plan.grad_x(g, fp, gx)
             gx = gx.to(torch.float64)

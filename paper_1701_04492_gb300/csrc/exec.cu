@@ -592,19 +592,6 @@ extern "C" int nufft2_grad_x(nufft_plan p, const void *g_dev, const void *fprime
                                 : nufft::exec_grad_x<double>(p, g_dev, fprime_dev, gx_dev, accumulate, s);
 }
 
-extern "C" int nufft2_exec_batch(nufft_plan p, int64_t B, const void *c_dev, int64_t ldc,
-                                 void *f_dev, int64_t ldf, void *stream) {
-    if (!p || B < 0 || ldc < p->N || ldf < p->M) return NUFFT_EINVAL;
-    if (B > 0 && (!c_dev || (p->M > 0 && !f_dev))) return NUFFT_EINVAL;
-    const size_t cxs = p->prec == NUFFT_F32 ? 8 : 16;
-    for (int64_t b = 0; b < B; ++b) {
-        const void *cb = (const char *)c_dev + (size_t)(b * ldc) * cxs;
-        void *fb = (char *)f_dev + (size_t)(b * ldf) * cxs;
-        if (int rc = nufft2_exec(p, cb, fb, stream)) return rc;
-    }
-    return NUFFT_OK;
-}
-
 extern "C" int nufft2_exec_host(nufft_plan p, const void *c_host, void *f_host, void *stream) {
     if (p && p->dims == 2) return NUFFT_EUNSUPPORTED;   // the 2D transform has its forward only
     if (!p || !c_host || (p->M > 0 && !f_host)) return NUFFT_EINVAL;

@@ -96,6 +96,16 @@ struct nufft_plan_s {
     double *inv_part = nullptr, *inv_scal = nullptr;               // reductions, scalars
     double *inv_host = nullptr;                                    // pinned readback
 
+    // batches of coefficient vectors on this plan (shared samples), for up to sb_cap
+    // members: per-member slices of the intermediate, partial sums, pass B's partials
+    // and tickets; the members' kernel arguments (device, and pinned staging guarded
+    // by sb_ev) and coefficient tables
+    int64_t sb_cap = 0;
+    void *sb_Y = nullptr, *sb_fscr = nullptr, *sb_part = nullptr;
+    int *sb_cnt = nullptr;
+    void *sb_args = nullptr, *sb_beta = nullptr, *sb_host = nullptr;
+    cudaEvent_t sb_ev = nullptr;
+
     // NUFFT_PLAN_TIMING: events around each launch of the last exec call
     cudaEvent_t ev[8] = {};
     int nev = 0;       // events recorded by the last exec call

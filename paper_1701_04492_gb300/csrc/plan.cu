@@ -405,6 +405,10 @@ void free_plan(nufft_plan p) {
                     p->inv_lam, p->inv_x, p->inv_z, p->inv_r, p->inv_p, p->inv_ap, p->inv_part, p->inv_scal};
     for (void *b : bufs) if (b) cudaFree(b);
     if (p->inv_host) cudaFreeHost(p->inv_host);
+    for (void *b : {p->sb_Y, p->sb_fscr, p->sb_part, (void *)p->sb_cnt, p->sb_args, p->sb_beta})
+        if (b) cudaFree(b);
+    if (p->sb_host) cudaFreeHost(p->sb_host);
+    if (p->sb_ev) cudaEventDestroy(p->sb_ev);
     if (p->inv_fft) free_plan(p->inv_fft);
     for (cudaEvent_t e : p->ev) if (e) cudaEventDestroy(e);
     delete p;

@@ -381,3 +381,32 @@ def test_autograd_training_batch_n2e18(api):
         fpb = direct.nudft2_deriv(x[rows], cs[b].astype(np.complex128))
         ref += np.real(np.conj(gb) * fpb)
     assert _rel2(gxg[rows], ref) <= 1e-4
+
+
+@pytest.mark.parametrize("prec,N", [("f32", 4096), ("f32", 3000), ("f64", 4096), ("f32", 1 << 19)])
+def test_batch_calls_match_single_calls(api, prec, N):
+    """nufft2_exec_batch / nufft1_exec_batch / nufft2_exec_deriv_batch: one launch per
+    pass for a batch sharing x (FP32 grids up to 2^18), else member by member; both
+    must equal the single-vector calls bit for bit; grad_x_batch sums the members."""
+    B, M = 6, N + 123
+    x = wl.samples_uniform(M, 70)
+    cdt = _cdt(prec)
+    plan = api.Plan(N, x, 1e-9, prec)
+    c = _dev(np.stack([_cast(wl.coeffs_cn(N, 700 + b), prec) for b in range(B)]), cdt)
+    g = _dev(np.stack([wl.cotangent_cn(M, 800 + b) for b in range(B)]).astype(np.complex64 if prec == "f32"
+                                                                                else np.complex128), cdt)
+    f = plan.forward_batch(c)
+    gc = plan.adjoint_batch(g)
+    fd, fpd = plan.forward_deriv_batch(c)
+    for b in (0, B - 1):
+        assert torch.equal(f[b], plan.forward(c[b].contiguous())), b
+        assert torch.equal(gc[b], plan.adjoint(g[b].contiguous())), b
+        f1, fp1 = plan.forward_deriv(c[b].contiguous())
+        assert torch.equal(fd[b], f1) and torch.equal(fpd[b], fp1), b
+    gx = plan.grad_x_batch(g, fpd)
+    ref = sum(plan.grad_x(g[b].contiguous(), fpd[b].contiguous()).double() for b in range(B))
+    tol = 1e-5 if prec == "f32" else 1e-12
+    assert float((gx.double() - ref).abs().max() / ref.abs().max()) <= tol
+    # a larger batch reallocates the workspace; results stay the same
+    c2 = torch.cat([c, c])
+    assert torch.equal(plan.forward_batch(c2)[B:], f)
