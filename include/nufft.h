@@ -182,6 +182,17 @@ int nufft2_exec_deriv_batch(nufft_plan p, int64_t B, const void *c_dev, int64_t 
 int nufft2_grad_x_batch(nufft_plan p, int64_t B, const void *g_dev, const void *fprime_dev, int64_t ld,
                         void *gx_dev, int accumulate, void *stream);
 
+/* One training step with HOST buffers: f = A c and f' = df/dx (nufft2_exec_deriv),
+ * A^H g (nufft1_exec) and gx_j = Re(conj(g_j) f'_j) (nufft2_grad_x), with c and g
+ * copied in and f, A^H g and gx copied out.  The copies run on a stream of the plan's
+ * own, each as soon as its data is ready, overlapping the transforms; `stream` waits for
+ * the last one, and the host buffers hold the results once `stream` has completed (the
+ * call does not synchronise).  Pinned host memory makes the copies asynchronous.
+ * c_host, gc_host N complex; g_host, f_host M complex; gx_host M reals of the plan's
+ * precision.  The first call allocates the plan's device copies of g, f', A^H g, gx. */
+int nufft2_step_host(nufft_plan p, const void *c_host, const void *g_host, void *f_host, void *gc_host,
+                     void *gx_host, void *stream);
+
 /* The same as nufft2_exec with HOST buffers: copies c host->device into a
  * plan-owned staging buffer, runs the transform, copies f device->host and
  * synchronises `stream`. */

@@ -40,6 +40,7 @@ SIGNATURES = {
     "nufft2_exec_deriv_batch": (_i32, [_vp, _i64, _vp, _i64, _vp, _vp, _i64, _vp]),
     "nufft2_grad_x_batch": (_i32, [_vp, _i64, _vp, _vp, _i64, _vp, _i32, _vp]),
     "nufft2_exec_host": (_i32, [_vp, _vp, _vp, _vp]),
+    "nufft2_step_host": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "nufft2_exec_unfused": (_i32, [_vp, _vp, _vp, _vp]),
     "nufft_kernel_times": (_i32, [_vp, ctypes.POINTER(ctypes.c_float), _i32, ctypes.POINTER(_i32)]),
     "nufft2_check": (_i32, [_vp, _vp]),

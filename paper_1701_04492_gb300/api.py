@@ -252,6 +252,19 @@ class Plan:
                                                   1 if accumulate else 0, _stream(self.device)), "nufft2_grad_x_batch")
         return gx
 
+    def step_host(self, c_host, g_host, f_host, gc_host, gx_host):
+        """One training step with host (ideally pinned) tensors: f = A c, A^H g into gc_host
+        and dL/dx = Re(conj(g) f') into gx_host, copies overlapped with the transforms.
+        Asynchronous: the host tensors hold the results once the current stream has
+        completed."""
+        for t, n, dt in ((c_host, self.N, self.cdtype), (g_host, self.M, self.cdtype), (f_host, self.M, self.cdtype),
+                         (gc_host, self.N, self.cdtype), (gx_host, self.M, self.rdtype)):
+            if t.device.type != "cpu" or t.dtype != dt or not t.is_contiguous() or t.numel() != n:
+                raise ValueError("host tensors must be contiguous CPU tensors of the plan's sizes and types")
+        with torch.cuda.device(self.device):
+            check(_lib.load().nufft2_step_host(self._h, _ptr(c_host), _ptr(g_host), _ptr(f_host), _ptr(gc_host),
+                                               _ptr(gx_host), _stream(self.device)), "nufft2_step_host")
+
     def forward_host(self, c_host, f_host):
         """f_host = A c_host with host (ideally pinned) tensors; synchronises."""
         if c_host.device.type != "cpu" or f_host.device.type != "cpu":

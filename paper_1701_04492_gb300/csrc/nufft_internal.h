@@ -100,6 +100,11 @@ struct nufft_plan_s {
     // members: per-member slices of the intermediate, partial sums, pass B's partials
     // and tickets; the members' kernel arguments (device, and pinned staging guarded
     // by sb_ev) and coefficient tables
+    // nufft2_step_host: device copies of g, f', A^H g and gx; a copy stream and events
+    void *st_g = nullptr, *st_fp = nullptr, *st_gc = nullptr, *st_gx = nullptr;
+    cudaStream_t st_copy = nullptr;
+    cudaEvent_t st_ev[6] = {};
+
     int64_t sb_cap = 0;
     void *sb_Y = nullptr, *sb_fscr = nullptr, *sb_part = nullptr;
     int *sb_cnt = nullptr;

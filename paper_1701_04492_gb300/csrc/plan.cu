@@ -408,6 +408,11 @@ void free_plan(nufft_plan p) {
     for (void *b : {p->sb_Y, p->sb_fscr, p->sb_part, (void *)p->sb_cnt, p->sb_args, p->sb_beta})
         if (b) cudaFree(b);
     if (p->sb_host) cudaFreeHost(p->sb_host);
+    for (void *b : {p->st_g, p->st_fp, p->st_gc, p->st_gx})
+        if (b) cudaFree(b);
+    if (p->st_copy) cudaStreamDestroy(p->st_copy);
+    for (cudaEvent_t e : p->st_ev)
+        if (e) cudaEventDestroy(e);
     if (p->sb_ev) cudaEventDestroy(p->sb_ev);
     if (p->inv_fft) free_plan(p->inv_fft);
     for (cudaEvent_t e : p->ev) if (e) cudaEventDestroy(e);

@@ -410,3 +410,28 @@ def test_batch_calls_match_single_calls(api, prec, N):
     # a larger batch reallocates the workspace; results stay the same
     c2 = torch.cat([c, c])
     assert torch.equal(plan.forward_batch(c2)[B:], f)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_step_host_matches_device_calls(api, prec):
+    """nufft2_step_host (host buffers, overlapped copies) returns what the device calls do."""
+    N, M = 5000, 6000
+    x = wl.samples_perturbed(M, 71, 0.5) * (N / M)
+    plan = api.Plan(N, x, 1e-9, prec)
+    cdt, rdt = _cdt(prec), (torch.float32 if prec == "f32" else torch.float64)
+    c = torch.tensor(_cast(wl.coeffs_cn(N, 72), prec).astype(np.complex64 if prec == "f32" else np.complex128))
+    g = torch.tensor(wl.cotangent_cn(M, 73).astype(np.complex64 if prec == "f32" else np.complex128))
+    ch, gh = c.pin_memory(), g.pin_memory()
+    fh = torch.empty(M, dtype=cdt).pin_memory()
+    gch = torch.empty(N, dtype=cdt).pin_memory()
+    gxh = torch.empty(M, dtype=rdt).pin_memory()
+    cd, gd = c.cuda(), g.cuda()
+    f_ref, fp_ref = plan.forward_deriv(cd)
+    gc_ref = plan.adjoint(gd)
+    gx_ref = plan.grad_x(gd, fp_ref)
+    for _ in range(2):
+        plan.step_host(ch, gh, fh, gch, gxh)
+        torch.cuda.synchronize()
+        assert torch.equal(fh, f_ref.cpu())
+        assert torch.equal(gch, gc_ref.cpu())
+        assert torch.equal(gxh, gx_ref.cpu())
