@@ -297,6 +297,11 @@ def run_ours(args):
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
                 "flops_per_launch": flops[dom]}
         hbm = json.load(open(PEAKS_PATH))["hbm_gbs"] if os.path.exists(PEAKS_PATH) else 6800.0
+        if traffic is not None:
+            # the DRAM bytes ncu counted for one launch (cold L2) over its measured time
+            roof["dram_GBps"] = traffic / (kavg[dom] * 1e-3) / 1e9
+            roof["dram_frac_of_measured_hbm"] = roof["dram_GBps"] / hbm
+            roof["dram_bytes_per_point"] = traffic / M
         fwd_s = extra["fwd_ms"] * 1e-3
         extra["hbm_algorithmic"] = {
             "bytes_per_point": 24, "fwd_GBps": 24.0 * M / fwd_s / 1e9,
