@@ -116,25 +116,14 @@ int plan_geometry(nufft_plan p) {
     p->nt2d = teams(p->G * p->B2);                  // derivative: K + 1 ranks
     p->mbar_off2 = body2(p->G);
     p->smem2 = bytes2(p->G, 1);
-    // The plain forward stages fewer ranks at a time, so that four CTAs fit per SM (228 KB
-    // of shared memory each): measured faster at 2^20 (78 -> 74 us) while a group holds
-    // at least a third of the ranks.  Pass A, whose samples are staged again for every
-    // group, was slower so (102 -> 130 us) and keeps the largest group.
-    const size_t cap4 = (size_t)228 * 1024 / 4 - 2 * 1024;
+    // The plain forward's own geometry (launch_rows takes it for K ranks without the
+    // derivative).  A smaller group, so that four CTAs fit per SM, was faster (78 -> 74
+    // us) until the row passes kept their stage twiddles in registers: at about 120
+    // registers per thread four CTAs no longer fit, so the forward stages all K ranks.
     p->Gf = std::min(p->G, p->K);
     p->nt2f = p->nt2;
     p->mbar_off2f = p->mbar_off2;
     p->smem2f = p->smem2;
-    {
-        int Gc = 1, ntc = 1;
-        if (choose(p->K, bytes2, teams, &Gc, &ntc, cap4) && Gc < p->Gf && Gc >= (p->K + 2) / 3 &&
-            bytes2(Gc, 1) <= cap4) {
-            p->Gf = Gc;
-            p->nt2f = ntc;
-            p->mbar_off2f = body2(Gc);
-            p->smem2f = bytes2(Gc, 1);
-        }
-    }
     if (!choose(p->K, bytesA, teamsA, &p->GA, &p->ntA, SMEM_BUDGET)) return NUFFT_EUNSUPPORTED;
     p->smemA = bytesA(p->GA, p->ntA);
     if (p->smem1 > SMEM_BUDGET || p->smemB > SMEM_BUDGET) return NUFFT_EUNSUPPORTED;

@@ -219,6 +219,51 @@ struct TeamFft {
         }
     }
 
+    // A thread's stage twiddles depend only on its lane tt, not on the transform, so a
+    // thread that runs several transforms can load them once into registers (Tw) and
+    // reuse them: stage 1 (radix R1 after R0 points), then stage 2 (radix R2 after R0 R1).
+    static constexpr int NW1 = R1 > 1 ? (E / R1) * (R1 - 1) : 0;
+    static constexpr int NW2 = R2 > 1 ? (E / R2) * (R2 - 1) : 0;
+    struct Tw {
+        cx<T> w[NW1 + NW2 > 0 ? NW1 + NW2 : 1];
+    };
+    __device__ __forceinline__ static void load_tw(Tw& t, int tt, const cx<T>* __restrict__ tw) {
+        if constexpr (R1 > 1) {
+#pragma unroll
+            for (int b = 0; b < E / R1; ++b) {
+                const int j = (tt + TT * b) & (R0 - 1);
+#pragma unroll
+                for (int i = 1; i < R1; ++i) t.w[b * (R1 - 1) + i - 1] = __ldg(&tw[TW_OFF1 + (i - 1) * R0 + j]);
+            }
+        }
+        if constexpr (R2 > 1) {
+            constexpr int NS = R0 * R1;
+#pragma unroll
+            for (int b = 0; b < E / R2; ++b) {
+                const int j = (tt + TT * b) & (NS - 1);
+#pragma unroll
+                for (int i = 1; i < R2; ++i) t.w[NW1 + b * (R2 - 1) + i - 1] = __ldg(&tw[TW_OFF2 + (i - 1) * NS + j]);
+            }
+        }
+    }
+    template <int R, int NS, int WOFF>
+    __device__ __forceinline__ static void stage_reg(cx<T> (&a)[E], const Tw& t) {
+#pragma unroll
+        for (int b = 0; b < E / R; ++b) {
+            cx<T> s[R];
+#pragma unroll
+            for (int i = 0; i < R; ++i) s[i] = a[b * R + i];
+#pragma unroll
+            for (int i = 1; i < R; ++i) {
+                const cx<T> w = t.w[WOFF + b * (R - 1) + i - 1];
+                s[i] = INV ? cmulc<T>(s[i], w) : cmul<T>(s[i], w);
+            }
+            Dft<R, INV, T>::run(s);
+#pragma unroll
+            for (int i = 0; i < R; ++i) a[b * R + i] = s[i];
+        }
+    }
+
     // Write the outputs of a stage (radix R after NS) to sm; read the inputs of the
     // next stage (radix Rn).
     // PRED: a round in which some teams are idle.  A thread with act = false (an idle
@@ -284,6 +329,20 @@ struct TeamFft {
             if constexpr (R2 > 1) {
                 exchange<R1, R0, R2, PRED>(a, tt, sm, act);
                 stage<R2, R0 * R1, TW_OFF2>(a, tt, tw);
+            }
+        }
+    }
+
+    // run() with the stage twiddles already in registers (load_tw).
+    template <bool PRED = false>
+    __device__ __forceinline__ static void run_reg(cx<T> (&a)[E], int tt, cx<T>* sm, const Tw& t, bool act = true) {
+        stage<R0, 1, 0>(a, tt, nullptr);
+        if constexpr (R1 > 1) {
+            exchange<R0, 1, R1, PRED>(a, tt, sm, act);
+            stage_reg<R1, R0, 0>(a, t);
+            if constexpr (R2 > 1) {
+                exchange<R1, R0, R2, PRED>(a, tt, sm, act);
+                stage_reg<R2, R0 * R1, NW1>(a, t);
             }
         }
     }

@@ -45,6 +45,10 @@ enum PassMode : int {
 // carry no code for it.
 template <typename T> constexpr bool kFactors = std::is_same<T, double>::value;
 
+// The row passes keep each lane's stage twiddles in registers across its row FFTs
+// (FP32; in FP64 they would take twice the registers).
+template <typename T> constexpr bool kTwReg = std::is_same<T, float>::value;
+
 
 template <typename T>
 struct PassArgs {
@@ -287,6 +291,9 @@ __device__ __forceinline__ void pass2_body(const PassArgs<T> &a, const BT &beta,
                 bulk_copy_g2s(smem + q * a.S, src, ROW_BYTES, &mbar[q]);
             }
         }
+        // this lane's stage twiddles, loaded once for all its row FFTs of this group
+        typename TF::Tw twreg;
+        if constexpr (kTwReg<T>) TF::load_tw(twreg, tt, a.twr);
         // one round of row FFTs, one job per team; PRED: a round with idle teams
         auto round = [&](const int j0, auto pred) {
             constexpr bool PRED = decltype(pred)::value;
@@ -298,7 +305,8 @@ __device__ __forceinline__ void pass2_body(const PassArgs<T> &a, const BT &beta,
 #pragma unroll
             for (int m = 0; m < E; ++m) v[m] = act ? sm[tt + TT * m] : mk<T>(0, 0);   // row as copied
             __syncthreads();   // the row is read before the transform reuses its slot
-            TF::template run<PRED>(v, tt, sm, a.twr, act);
+            if constexpr (kTwReg<T>) TF::template run_reg<PRED>(v, tt, sm, twreg, act);
+            else TF::template run<PRED>(v, tt, sm, a.twr, act);
             if (act) {
 #pragma unroll
                 for (int e = 0; e < E; ++e) sm[TF::out_padded(tt, e)] = v[e];
@@ -531,6 +539,9 @@ __device__ __forceinline__ void passA_body(const PassArgs<T> &a, const BT &beta,
             }
         }
         __syncthreads();
+        // this lane's stage twiddles, loaded once for all its row FFTs of this group
+        typename TF::Tw twreg;
+        if constexpr (kTwReg<T>) TF::load_tw(twreg, tt, a.twr);
         cx<T> *ftab = smem + nslots * a.S + team * E;   // this team's four-step table
         auto round = [&](const int j0, auto pred) {   // PRED: a round with idle teams
             constexpr bool PRED = decltype(pred)::value;
@@ -548,7 +559,8 @@ __device__ __forceinline__ void passA_body(const PassArgs<T> &a, const BT &beta,
             }
             fill_fourstep<T, E, TT>(a, n2, tt, ftab, 1);
             __syncthreads();
-            TF::template run<PRED>(v, tt, sm, a.twr, act);
+            if constexpr (kTwReg<T>) TF::template run_reg<PRED>(v, tt, sm, twreg, act);
+            else TF::template run<PRED>(v, tt, sm, a.twr, act);
             if (act) {
                 // column-tiled layout for pass B: Y'_r[k1 / CQ][n2][k1 % CQ], so each
                 // CQ-column tile of a rank is one contiguous block
@@ -754,6 +766,9 @@ __device__ __forceinline__ void pass2d_body(const PassArgs<T> &a, const BT &beta
         const int buf = r1 & 1;
         mbar_wait_bounded(&mbar[buf], (r1 >> 1) & 1, a.err, &cta_failed);
         const cx<T> *row = stg + buf * P1;
+        // this lane's stage twiddles, loaded once for all its row FFTs of this r1
+        typename TF::Tw twreg;
+        if constexpr (kTwReg<T>) TF::load_tw(twreg, tt, a.twr);
         auto round = [&](const int j0, auto pred) {   // one r2 per team; PRED: idle teams
             constexpr bool PRED = decltype(pred)::value;
             const int r2 = j0 + team;
@@ -768,7 +783,8 @@ __device__ __forceinline__ void pass2d_body(const PassArgs<T> &a, const BT &beta
                 const T sc = act ? vy[k] : T(0);
                 v[m] = mul_ipow<T>(mk<T>(sc * w.x, sc * w.y), r2);
             }
-            TF::template run<PRED>(v, tt, sm, a.twr, act);
+            if constexpr (kTwReg<T>) TF::template run_reg<PRED>(v, tt, sm, twreg, act);
+            else TF::template run<PRED>(v, tt, sm, a.twr, act);
             if (act) {
 #pragma unroll
                 for (int e = 0; e < E; ++e) sm[TF::out_padded(tt, e)] = v[e];
