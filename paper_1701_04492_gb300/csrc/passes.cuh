@@ -138,6 +138,21 @@ struct BetaShared {
 template <typename T, int KM>
 __device__ __forceinline__ T beta_at(const BetaShared<T, KM> &b, int r, int q) { return b.p[r * KM + q]; }
 
+// acc + a b, compensated: the exact error of the product (an FMA) and of the sum
+// (two-sum) are added into comp, which the caller adds to acc at the end.  The forward's
+// rank-sum of eq. (2.11) is accumulated so: at 2^20 (FP32, K = 12) the error against the
+// FP64 oracle falls from 2.05e-7 to 1.94e-7 in the 2-norm and from 1.26e-9 to 1.00e-9
+// ||c||_1 in the infinity norm, for 5 us of pass 2's 67.
+template <typename T>
+__device__ __forceinline__ void mac_comp(T &acc, T &comp, T a, T b) {
+    const T p = a * b;
+    const T pe = fma(a, b, -p);
+    const T s = acc + p;
+    const T z = s - acc;
+    comp += ((acc - (s - z)) + (p - z)) + pe;
+    acc = s;
+}
+
 template <typename T>
 __device__ __forceinline__ cx<T> *smem_base() {
     extern __shared__ __align__(16) unsigned char nufft_smem_raw[];
@@ -354,6 +369,8 @@ __device__ __forceinline__ void pass2_body(const PassArgs<T> &a, const BT &beta,
                     for (int q = (r & 1); q < KM; q += 2) m = fma(beta_at(beta, r, q), Tp[q], m);
                     mu[r] = m;   // zero for r >= K (beta is zero-padded)
                 }
+                // plain sums here: compensating these four products per rank cost 20 % of
+                // the derivative pass (70 -> 84 us at 2^20)
                 cx<T> S = mk<T>(0, 0), Sp = mk<T>(0, 0);
 #pragma unroll
                 for (int sidx = 0; sidx <= KM; ++sidx) {
@@ -391,6 +408,7 @@ __device__ __forceinline__ void pass2_body(const PassArgs<T> &a, const BT &beta,
                 const int n1 = t >> a.lg2;
                 const T d = a.dsorted[i];
                 cx<T> acc = g0 == 0 ? mk<T>(0, 0) : a.fscr[i];
+                cx<T> comp = mk<T>(0, 0);   // the rank-sum's compensation
                 constexpr bool fac = kFactors<T>;
                 if (fac) {
                     // f_j = sum_r u_r(j) X_r[t_j] with the plan's U (phase included)
@@ -415,11 +433,13 @@ __device__ __forceinline__ void pass2_body(const PassArgs<T> &a, const BT &beta,
 #pragma unroll
                             for (int q = (r & 1); q < KM; q += 2) mu = fma(beta_at(beta, r, q), Tp[q], mu);
                             const cx<T> x = smem[((r - g0) * a.B2 + row) * a.S + padi<E>(n1)];
-                            acc.x = fma(mu, x.x, acc.x);
-                            acc.y = fma(mu, x.y, acc.y);
+                            mac_comp<T>(acc.x, comp.x, mu, x.x);
+                            mac_comp<T>(acc.y, comp.y, mu, x.y);
                         }
                     }
                 }
+                acc.x += comp.x;
+                acc.y += comp.y;
                 if (g0 + gc < a.nranks) {
                     a.fscr[i] = acc;
                 } else {
