@@ -341,6 +341,7 @@ def run_ours(args):
             line["inverse"] = bench_inverse(api, dev)
             line["autograd_c4"] = bench_autograd_c4(api, dev, timed, args.steps)
         if ws == 1 and not args.no_cpu_baseline:
+            plan.forward(c, f)   # the plain forward's f for the accuracy record
             line["cpu_baseline"] = cpu_baseline(plan, c_np, g_np, x, f)
         print(json.dumps(line), flush=True)
     if ws > 1:

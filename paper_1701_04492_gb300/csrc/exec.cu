@@ -606,10 +606,11 @@ extern "C" int nufft2_exec_unfused(nufft_plan p, const void *c_dev, void *f_dev,
 namespace nufft {
 namespace {
 
-// One training step with host buffers: upload c and g, the forward with f', the adjoint
-// and dL/dx, download f, A^H g and gx.  The copies run on the plan's own stream, each as
-// soon as its data is ready (g during the forward, f during the adjoint, A^H g during
-// dL/dx); the caller's stream waits for the last one.
+// One training step with host buffers: upload g and c, the adjoint, the forward with f'
+// and dL/dx, download A^H g, f and gx.  The adjoint needs only g, so it runs while c is
+// still arriving; the copies run on the plan's own stream, each as soon as its data is
+// ready (A^H g leaves during the forward, f during dL/dx), and the caller's stream waits
+// for the last one.
 template <typename T>
 int step_host(nufft_plan p, const void *c_h, const void *g_h, void *f_h, void *gc_h, void *gx_h, cudaStream_t s) {
     const size_t cxs = 2 * sizeof(T), Mi = (size_t)std::max<int64_t>(p->M, 1);
@@ -623,25 +624,25 @@ int step_host(nufft_plan p, const void *c_h, const void *g_h, void *f_h, void *g
         p->work_bytes += (int64_t)(Mi * (2 * cxs + sizeof(T)) + (size_t)p->N * cxs);
     }
     cudaStream_t cs = p->st_copy;
-    cudaEvent_t *ev = p->st_ev;   // 0 start, 1 c in, 2 g in, 3 f ready, 4 A^H g ready, 5 all out
+    cudaEvent_t *ev = p->st_ev;   // 0 start / gx ready, 1 g in, 2 c in, 3 A^H g ready, 4 f ready, 5 all out
     NUFFT_CUDA_TRY(cudaEventRecord(ev[0], s));
     NUFFT_CUDA_TRY(cudaStreamWaitEvent(cs, ev[0], 0));
-    NUFFT_CUDA_TRY(cudaMemcpyAsync(p->cstage, c_h, (size_t)p->N * cxs, cudaMemcpyHostToDevice, cs));
-    NUFFT_CUDA_TRY(cudaEventRecord(ev[1], cs));
     if (p->M > 0) NUFFT_CUDA_TRY(cudaMemcpyAsync(p->st_g, g_h, (size_t)p->M * cxs, cudaMemcpyHostToDevice, cs));
+    NUFFT_CUDA_TRY(cudaEventRecord(ev[1], cs));
+    NUFFT_CUDA_TRY(cudaMemcpyAsync(p->cstage, c_h, (size_t)p->N * cxs, cudaMemcpyHostToDevice, cs));
     NUFFT_CUDA_TRY(cudaEventRecord(ev[2], cs));
     NUFFT_CUDA_TRY(cudaStreamWaitEvent(s, ev[1], 0));
-    if (int rc = exec_deriv<T>(p, p->cstage, p->fstage, p->st_fp, s)) return rc;
+    if (int rc = exec_adjoint<T>(p, p->st_g, p->st_gc, s)) return rc;
     NUFFT_CUDA_TRY(cudaEventRecord(ev[3], s));
     NUFFT_CUDA_TRY(cudaStreamWaitEvent(s, ev[2], 0));
-    if (int rc = exec_adjoint<T>(p, p->st_g, p->st_gc, s)) return rc;
+    if (int rc = exec_deriv<T>(p, p->cstage, p->fstage, p->st_fp, s)) return rc;
     NUFFT_CUDA_TRY(cudaEventRecord(ev[4], s));
     if (int rc = exec_grad_x<T>(p, p->st_g, p->st_fp, p->st_gx, 0, s)) return rc;
+    NUFFT_CUDA_TRY(cudaEventRecord(ev[0], s));   // gx ready
     NUFFT_CUDA_TRY(cudaStreamWaitEvent(cs, ev[3], 0));
-    if (p->M > 0) NUFFT_CUDA_TRY(cudaMemcpyAsync(f_h, p->fstage, (size_t)p->M * cxs, cudaMemcpyDeviceToHost, cs));
-    NUFFT_CUDA_TRY(cudaStreamWaitEvent(cs, ev[4], 0));
     NUFFT_CUDA_TRY(cudaMemcpyAsync(gc_h, p->st_gc, (size_t)p->N * cxs, cudaMemcpyDeviceToHost, cs));
-    NUFFT_CUDA_TRY(cudaEventRecord(ev[0], s));   // gx ready (reusing the start event)
+    NUFFT_CUDA_TRY(cudaStreamWaitEvent(cs, ev[4], 0));
+    if (p->M > 0) NUFFT_CUDA_TRY(cudaMemcpyAsync(f_h, p->fstage, (size_t)p->M * cxs, cudaMemcpyDeviceToHost, cs));
     NUFFT_CUDA_TRY(cudaStreamWaitEvent(cs, ev[0], 0));
     if (p->M > 0) NUFFT_CUDA_TRY(cudaMemcpyAsync(gx_h, p->st_gx, (size_t)p->M * sizeof(T), cudaMemcpyDeviceToHost, cs));
     NUFFT_CUDA_TRY(cudaEventRecord(ev[5], cs));
