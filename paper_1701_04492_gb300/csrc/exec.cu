@@ -101,9 +101,9 @@ int plan_geometry(nufft_plan p) {
         };
     };
     const auto teams = teams_of(TT1), teamsA = teams_of(TT1a);
-    auto choose = [&](int Gmax, auto bytes, auto teams, int *Gout, int *ntout, size_t cap) -> bool {
+    auto choose = [&](int Gmax, auto bytes, auto teams, int *Gout, int *ntout) -> bool {
         int G = Gmax;
-        while (G > 1 && bytes(G, teams(G * p->B2)) > cap) --G;
+        while (G > 1 && bytes(G, teams(G * p->B2)) > SMEM_BUDGET) --G;
         *Gout = G;
         *ntout = teams(G * p->B2);
         return bytes(G, *ntout) <= SMEM_BUDGET;
@@ -111,20 +111,15 @@ int plan_geometry(nufft_plan p) {
     // pass 2 stages up to K + 1 ranks (the derivative mode adds rank K, and its gather
     // needs them all in one group)
     int nt_dummy = 1;
-    if (!choose(p->K + 1, bytes2, teams, &p->G, &nt_dummy, SMEM_BUDGET)) return NUFFT_EUNSUPPORTED;
+    if (!choose(p->K + 1, bytes2, teams, &p->G, &nt_dummy)) return NUFFT_EUNSUPPORTED;
     p->nt2 = teams(std::min(p->G, p->K) * p->B2);   // forward: K ranks
     p->nt2d = teams(p->G * p->B2);                  // derivative: K + 1 ranks
     p->mbar_off2 = body2(p->G);
     p->smem2 = bytes2(p->G, 1);
-    // The plain forward's own geometry (launch_rows takes it for K ranks without the
-    // derivative).  A smaller group, so that four CTAs fit per SM, was faster (78 -> 74
-    // us) until the row passes kept their stage twiddles in registers: at about 120
-    // registers per thread four CTAs no longer fit, so the forward stages all K ranks.
-    p->Gf = std::min(p->G, p->K);
-    p->nt2f = p->nt2;
-    p->mbar_off2f = p->mbar_off2;
-    p->smem2f = p->smem2;
-    if (!choose(p->K, bytesA, teamsA, &p->GA, &p->ntA, SMEM_BUDGET)) return NUFFT_EUNSUPPORTED;
+    // (A smaller group for the plain forward, so that four CTAs fit per SM, was faster,
+    // 78 -> 74 us at 2^20, until the row passes kept their stage twiddles in registers: at
+    // about 120 registers per thread four CTAs no longer fit.)
+    if (!choose(p->K, bytesA, teamsA, &p->GA, &p->ntA)) return NUFFT_EUNSUPPORTED;
     p->smemA = bytesA(p->GA, p->ntA);
     if (p->smem1 > SMEM_BUDGET || p->smemB > SMEM_BUDGET) return NUFFT_EUNSUPPORTED;
     return NUFFT_OK;

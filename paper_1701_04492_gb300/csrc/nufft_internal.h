@@ -41,8 +41,6 @@ struct nufft_plan_s {
     int G = 1;             // ranks staged together in pass 2 (up to K + 1)
     int nt2 = 1;           // teams per pass-2 CTA (forward: K ranks)
     int nt2d = 1;          // teams per pass-2 CTA in the derivative mode (K + 1 ranks)
-    int Gf = 1, nt2f = 1;  // pass 2 of the plain forward (K ranks): group and teams
-    size_t smem2f = 0, mbar_off2f = 0;   // and its shared memory
     int GA = 1;            // ranks staged together in pass A
     int ntA = 1;           // teams per pass-A CTA
     int C1 = 1;            // columns per pass-1 CTA

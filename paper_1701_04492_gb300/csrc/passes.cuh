@@ -1077,15 +1077,8 @@ int launch_rows(nufft_plan p, const PassArgs<T> &a0, bool adjoint, cudaStream_t 
         const int TT = adjoint ? P / e_of<T, P, PK_ROW_ADJ>() : P / e_of<T, P, PK_ROW_FWD>();
         PassArgs<T> a = a0;
         if (int rc = rows_fields<T>(p, a, adjoint)) return rc;
-        int nt = adjoint ? p->ntA : (a.nranks > p->K ? p->nt2d : p->nt2);
-        size_t smem2 = p->smem2;
-        if (!adjoint && a.nranks <= p->K && !(a.mode & MODE_DERIV)) {
-            // the plain forward's own geometry (fewer ranks per group, more CTAs per SM)
-            a.G = p->Gf;
-            a.mbar_off = (int)p->mbar_off2f;
-            nt = p->nt2f;
-            smem2 = p->smem2f;
-        }
+        const int nt = adjoint ? p->ntA : (a.nranks > p->K ? p->nt2d : p->nt2);
+        const size_t smem2 = p->smem2;
         const dim3 block(nt * TT);
         static int done_a[64] = {}, done_2[64] = {};
         if (adjoint) {
