@@ -63,12 +63,16 @@ enum nufft_status {
 #define NUFFT_PLAN_AUTOTUNE 4u /* with L = 0 (and no NUFFT_PLAN_LONG_COLUMNS): time the
                                   candidate layouts -- the default grid L0 and the
                                   oversampled 2 L0 (section 2.3), each with either
-                                  four-step split when log2 L is odd -- by one forward
+                                  four-step split when log2 L is odd and either pass-1
+                                  tile (NUFFT_PLAN_HALF_TILE) -- by one forward
                                   and one adjoint exec each (CUDA events, best of 3
                                   after a warm-up), and keep the fastest.  Choices are
                                   cached per process by (device, N, M rounded up to a
                                   power of two, eps, prec, K), so a repeated shape
                                   plans once.  Synchronises `stream` per candidate. */
+#define NUFFT_PLAN_HALF_TILE 64u /* pass 1 (the column pass) takes half as many
+                                  columns per CTA: twice the CTAs of half the threads (the
+                                  autotuners' tile axis).  Results agree to rounding. */
 #define NUFFT_PLAN_LONG_COLUMNS 16u /* for odd log2 L: the four-step split
                                   L = L1 L2 takes the longer FFT on the columns
                                   (L2 = 2 L1) instead of the rows (L1 = 2 L2).

@@ -19,6 +19,7 @@ NUFFT_PLAN_AUTOTUNE = 4
 NUFFT_BATCH_GRAPH = 8
 NUFFT_PLAN_LONG_COLUMNS = 16
 NUFFT_BATCH_PER_PROBLEM = 32
+NUFFT_PLAN_HALF_TILE = 64
 STATUS = {0: "NUFFT_OK", -1: "NUFFT_EINVAL", -2: "NUFFT_ENOMEM", -3: "NUFFT_ECUDA",
           -4: "NUFFT_EUNSUPPORTED", -5: "NUFFT_ESTATE", -6: "NUFFT_ETIMEOUT"}
 

@@ -12,7 +12,8 @@ import ctypes
 import torch
 
 from . import _lib
-from ._lib import (NUFFT_BATCH_GRAPH, NUFFT_BATCH_PER_PROBLEM, NUFFT_F32, NUFFT_F64, NUFFT_PLAN_AUTOTUNE, NUFFT_PLAN_LONG_COLUMNS,
+from ._lib import (NUFFT_BATCH_GRAPH, NUFFT_BATCH_PER_PROBLEM, NUFFT_F32, NUFFT_F64, NUFFT_PLAN_AUTOTUNE,
+                   NUFFT_PLAN_HALF_TILE, NUFFT_PLAN_LONG_COLUMNS,
                    NUFFT_PLAN_TIMING, NUFFT_PLAN_UNFUSED, NufftError, check)
 
 _CDTYPE = {NUFFT_F32: torch.complex64, NUFFT_F64: torch.complex128}
@@ -49,10 +50,11 @@ class Plan:
     timing : record per-kernel device times (:meth:`kernel_times`)
     autotune : with L = 0, time the grid L0 against 2 L0 and both four-step splits, keep the fastest
     long_columns : for odd log2 L, put the longer FFT of the four-step split on the columns
+    half_tile : the column pass takes half as many columns per CTA
     """
 
     def __init__(self, N, x, eps, precision="f32", L=0, unfused=False, timing=False, device=None,
-                 autotune=False, long_columns=False):
+                 autotune=False, long_columns=False, half_tile=False):
         lib = _lib.load()
         device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         if not isinstance(x, torch.Tensor):
@@ -68,7 +70,8 @@ class Plan:
                                  float(eps), self.prec, int(L),
                                  (NUFFT_PLAN_UNFUSED if unfused else 0) | (NUFFT_PLAN_TIMING if timing else 0)
                                  | (NUFFT_PLAN_AUTOTUNE if autotune else 0)
-                                 | (NUFFT_PLAN_LONG_COLUMNS if long_columns else 0),
+                                 | (NUFFT_PLAN_LONG_COLUMNS if long_columns else 0)
+                                 | (NUFFT_PLAN_HALF_TILE if half_tile else 0),
                                  _stream(device))
         check(rc, "nufft2_plan")
         self._h = h

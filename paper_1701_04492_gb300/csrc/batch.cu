@@ -37,6 +37,7 @@ struct nufft_batch_s {
         int64_t L = 0;
         int KM = 0;
         int lg1 = 0;            // the four-step split (log2 of the row length)
+        int C1 = 0;             // pass 1's columns per CTA
         bool single = false;    // one large problem: its own plan's launches
         std::vector<int> idx;   // members (problem indices)
         int rep = -1;           // member whose launch geometry covers the class
@@ -244,12 +245,12 @@ using nufft::free_batch;
 namespace nufft {
 namespace {
 
-// A batch from per-problem inputs: sample pointers xs[i], grid sizes L_host (or
-// NULL), four-step splits lc (or NULL).  flags may hold NUFFT_PLAN_AUTOTUNE for the
-// problems' own plans.  Inputs are validated by the caller.
+// A batch from per-problem inputs: sample pointers xs[i], layouts lays (or NULL: each
+// problem's default).  flags may hold NUFFT_PLAN_AUTOTUNE for the problems' own plans.
+// Inputs are validated by the caller.
 int plan_many_core(nufft_batch *out, int64_t count, const int64_t *N_host, const int64_t *M_host,
-                   const int64_t *L_host, const unsigned char *lc, const double *const *xs,
-                   const double *eps_host, int prec, unsigned flags, void *stream) {
+                   const Layout *lays, const double *const *xs, const double *eps_host, int prec, unsigned flags,
+                   void *stream) {
     *out = nullptr;
     nufft_batch b = new (std::nothrow) nufft_batch_s();
     if (!b) return NUFFT_ENOMEM;
@@ -263,9 +264,8 @@ int plan_many_core(nufft_batch *out, int64_t count, const int64_t *N_host, const
         b->offM[i + 1] = b->offM[i] + M_host[i];
     }
     for (int64_t i = 0; i < count; ++i) {
-        const unsigned pf = (flags & NUFFT_PLAN_AUTOTUNE) | (lc && lc[i] ? NUFFT_PLAN_LONG_COLUMNS : 0u);
-        const int rc = nufft2_plan(&b->plans[i], N_host[i], M_host[i], xs[i], eps_host[i], prec,
-                                   L_host ? L_host[i] : 0, pf, stream);
+        const int rc = plan_layout(&b->plans[i], N_host[i], M_host[i], xs[i], eps_host[i], prec,
+                                   lays ? lays[i] : Layout{}, flags & NUFFT_PLAN_AUTOTUNE, (cudaStream_t)stream);
         if (rc) { free_batch(b); return rc; }
     }
     // classes: same L and rank bound; the representative has the largest K
@@ -274,7 +274,7 @@ int plan_many_core(nufft_batch *out, int64_t count, const int64_t *N_host, const
         const bool single = prec == NUFFT_F64 || (flags & NUFFT_BATCH_PER_PROBLEM) ||
                             std::max(p->L1, p->L2) > MANY_P_MAX;
         auto it = std::find_if(b->cls.begin(), b->cls.end(), [&](const nufft_batch_s::Class &c) {
-            return !single && !c.single && c.L == p->L && c.KM == p->kmax && c.lg1 == p->lg1;
+            return !single && !c.single && c.L == p->L && c.KM == p->kmax && c.lg1 == p->lg1 && c.C1 == p->C1;
         });
         if (it == b->cls.end()) {
             b->cls.emplace_back();
@@ -282,6 +282,7 @@ int plan_many_core(nufft_batch *out, int64_t count, const int64_t *N_host, const
             it->L = p->L;
             it->KM = p->kmax;
             it->lg1 = p->lg1;
+            it->C1 = p->C1;
             it->single = single;
         }
         it->idx.push_back((int)i);
@@ -383,10 +384,9 @@ int time_batch(nufft_batch b, void *c, void *f, void *flush, cudaStream_t s, flo
 int tune_many(nufft_batch *out, int64_t count, const int64_t *N, const int64_t *M, const double *const *xs,
               const double *eps, unsigned flags, cudaStream_t s) {
     nufft_batch b0 = nullptr;
-    if (int rc = plan_many_core(&b0, count, N, M, nullptr, nullptr, xs, eps, NUFFT_F32, flags, s)) return rc;
-    std::vector<int64_t> L(count);
-    std::vector<unsigned char> lc(count, 0);
-    for (int64_t i = 0; i < count; ++i) L[i] = b0->plans[i]->L;
+    if (int rc = plan_many_core(&b0, count, N, M, nullptr, xs, eps, NUFFT_F32, flags, s)) return rc;
+    std::vector<Layout> lay((size_t)count);
+    for (int64_t i = 0; i < count; ++i) lay[i].L = b0->plans[i]->L;
     void *c = nullptr, *f = nullptr, *flush = nullptr;
     const size_t cn = (size_t)std::max<int64_t>(b0->offN.back(), 1), fm = (size_t)std::max<int64_t>(b0->offM.back(), 1);
     int rc = NUFFT_OK;
@@ -400,7 +400,7 @@ int tune_many(nufft_batch *out, int64_t count, const int64_t *N, const int64_t *
         const auto &cl = b0->cls[k];
         if (cl.single) continue;
         const size_t n = cl.idx.size();
-        std::vector<int64_t> sN(n), sM(n), sL(n);
+        std::vector<int64_t> sN(n), sM(n);
         std::vector<const double *> sx(n);
         std::vector<double> se(n);
         for (size_t q = 0; q < n; ++q) {
@@ -408,37 +408,41 @@ int tune_many(nufft_batch *out, int64_t count, const int64_t *N, const int64_t *
             sN[q] = N[i]; sM[q] = M[i]; sx[q] = xs[i]; se[q] = eps[i];
         }
         float tbest = 1e30f;
-        int64_t Lbest = cl.L;
-        bool lcbest = false;
+        Layout best;
+        best.L = cl.L;
         for (int64_t Lc = cl.L; Lc <= std::min<int64_t>(2 * cl.L, L_max_batched) && !rc; Lc *= 2) {
             int lg = 0;
             while (((int64_t)1 << lg) < Lc) ++lg;
-            for (int lcc = 0; lcc < 2 && !rc; ++lcc) {
-                if (lcc == 1 && lg % 2 == 0) continue;
-                std::fill(sL.begin(), sL.end(), Lc);
-                std::vector<unsigned char> slc(n, (unsigned char)lcc);
-                nufft_batch t = nullptr;
-                int r2 = plan_many_core(&t, (int64_t)n, sN.data(), sM.data(), sL.data(), slc.data(), sx.data(),
-                                        se.data(), NUFFT_F32, flags & ~NUFFT_BATCH_GRAPH, s);
-                if (r2 == NUFFT_EUNSUPPORTED) continue;
-                if (r2) { rc = r2; break; }
-                float ms = 0.f;
-                r2 = time_batch(t, c, f, flush, s, &ms);
-                free_batch(t);
-                if (r2) { rc = r2; break; }
-                // the default layout wins ties: a new layout must save 3 %
-                if (Lc == cl.L && lcc == 0) tbest = ms;
-                else if (ms < 0.97f * tbest) { tbest = ms; Lbest = Lc; lcbest = lcc == 1; }
-            }
+            for (int lcc = 0; lcc < 2 && !rc; ++lcc)
+                for (int c1s = 0; c1s < 2 && !rc; ++c1s) {
+                    if (lcc == 1 && lg % 2 == 0) continue;
+                    Layout cand;
+                    cand.L = Lc;
+                    cand.long_cols = lcc == 1;
+                    cand.c1_shift = c1s;
+                    std::vector<Layout> sl(n, cand);
+                    nufft_batch t = nullptr;
+                    int r2 = plan_many_core(&t, (int64_t)n, sN.data(), sM.data(), sl.data(), sx.data(), se.data(),
+                                            NUFFT_F32, flags & ~NUFFT_BATCH_GRAPH, s);
+                    if (r2 == NUFFT_EUNSUPPORTED || r2 == NUFFT_EINVAL) continue;
+                    if (r2) { rc = r2; break; }
+                    float ms = 0.f;
+                    r2 = time_batch(t, c, f, flush, s, &ms);
+                    free_batch(t);
+                    if (r2) { rc = r2; break; }
+                    // the default layout wins ties: a new layout must save 3 %
+                    if (Lc == cl.L && lcc == 0 && c1s == 0) tbest = ms;
+                    else if (ms < 0.97f * tbest) { tbest = ms; best = cand; }
+                }
         }
-        if (Lbest != cl.L || lcbest) {
+        if (best.L != cl.L || best.long_cols || best.c1_shift) {
             changed = true;
-            for (int i : cl.idx) { L[i] = Lbest; lc[i] = lcbest ? 1 : 0; }
+            for (int i : cl.idx) lay[i] = best;
         }
     }
     nufft_batch b1 = nullptr;
     float t0 = 0.f, t1 = 0.f;
-    if (!rc && changed) rc = plan_many_core(&b1, count, N, M, L.data(), lc.data(), xs, eps, NUFFT_F32, flags, s);
+    if (!rc && changed) rc = plan_many_core(&b1, count, N, M, lay.data(), xs, eps, NUFFT_F32, flags, s);
     if (!rc && changed) rc = time_batch(b0, c, f, flush, s, &t0);
     if (!rc && changed) rc = time_batch(b1, c, f, flush, s, &t1);
     cudaFree(c);
@@ -486,7 +490,13 @@ extern "C" int nufft2_plan_many(nufft_batch *out, int64_t count, const int64_t *
     if ((flags & NUFFT_PLAN_AUTOTUNE) && batched && L_free)
         return tune_many(out, count, N_host, M_host, xs.data(), eps_host, flags & ~NUFFT_PLAN_AUTOTUNE,
                          (cudaStream_t)stream);
-    return plan_many_core(out, count, N_host, M_host, L_host, nullptr, xs.data(), eps_host, prec, flags, stream);
+    std::vector<Layout> lays;
+    if (L_host) {
+        lays.resize((size_t)count);
+        for (int64_t i = 0; i < count; ++i) lays[i].L = L_host[i];
+    }
+    return plan_many_core(out, count, N_host, M_host, L_host ? lays.data() : nullptr, xs.data(), eps_host, prec, flags,
+                          stream);
 }
 
 extern "C" int nufft_batch_info(nufft_batch b, int64_t *classes, int64_t *total_N, int64_t *total_M,

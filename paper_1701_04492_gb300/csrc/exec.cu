@@ -62,7 +62,7 @@ int plan_geometry(nufft_plan p) {
     const int E2b = std::min(EmaxT<T, PK_COL_ADJ>::v, p->L2), TT2b = p->L2 / E2b;   // pass B
     const size_t cxs = 2 * sizeof(T);
     // column passes: C columns per CTA, columns fastest across the lanes
-    p->C1 = clamp_pow2(256 / TT2, 1, p->L1);
+    p->C1 = clamp_pow2((256 / TT2) >> p->c1_shift, 1, p->L1);
     // one 32 KiB tile of the adjoint intermediate: pass A writes it (each of its rows a
     // run of CB columns, a whole 32-byte sector or more), pass B fetches it by one bulk
     // copy; pass B's CTA then has CB TT2b threads (256 in FP32, 128 in FP64)

@@ -44,6 +44,7 @@ struct nufft_plan_s {
     int GA = 1;            // ranks staged together in pass A
     int ntA = 1;           // teams per pass-A CTA
     int C1 = 1;            // columns per pass-1 CTA
+    int c1_shift = 0;      // the tuners' tile axis: C1 halved c1_shift times
     int CB = 1;            // columns per pass-B CTA
     int SBsplit = 1;       // rank splits of pass B (CTAs per column block)
     int chunkA = 512;      // samples staged per chunk in pass A
@@ -127,6 +128,16 @@ inline int mark(nufft_plan p, cudaStream_t s, bool first) {
 }  // namespace nufft
 
 namespace nufft {
+
+// plan.cu: a plan with a given layout (the autotuners' axes): grid size L (0: the
+// default), the four-step split, pass 1's columns per CTA halved c1_shift times
+struct Layout {
+    int64_t L = 0;
+    bool long_cols = false;
+    int c1_shift = 0;
+};
+int plan_layout(nufft_plan *out, int64_t N, int64_t M, const double *x_dev, double eps, int prec,
+                const Layout &lay, unsigned flags, cudaStream_t s);
 
 // hooks.cu: cudaMalloc, unless a test has injected a failure (nufft_test_fail_alloc)
 cudaError_t dev_malloc(void **p, size_t bytes);

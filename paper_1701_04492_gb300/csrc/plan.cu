@@ -587,17 +587,20 @@ extern "C" int nufft2d_plan_info(nufft_plan p, int *Kx, int *Ky, double *gamma_x
 namespace nufft {
 namespace {
 
-// One plan on grid L (a power of two, validated by the caller); long_cols: for odd
-// log2 L, the column FFT (length L2) is the longer one.
+// One plan with layout lay (lay.L a power of two, validated by the caller): lay.long_cols
+// for odd log2 L puts the longer FFT on the columns (L2 = 2 L1); lay.c1_shift halves
+// pass 1's columns per CTA.
 int plan_create(nufft_plan *out, int64_t N, int64_t M, const double *x_dev, double eps, int prec,
-                int64_t L, unsigned flags, bool long_cols, cudaStream_t s) {
+                const Layout &lay, unsigned flags, cudaStream_t s) {
     *out = nullptr;
     nufft_plan p = new (std::nothrow) nufft_plan_s();
     if (!p) return NUFFT_ENOMEM;
+    const int64_t L = lay.L;
     p->N = N; p->M = M; p->L = L; p->eps = eps; p->prec = prec; p->flags = flags;
+    p->c1_shift = lay.c1_shift;
     int lg = 0;
     while (((int64_t)1 << lg) < L) ++lg;
-    p->lg1 = long_cols ? lg / 2 : (lg + 1) / 2;
+    p->lg1 = lay.long_cols ? lg / 2 : (lg + 1) / 2;
     p->lg2 = lg - p->lg1;
     p->L1 = 1 << p->lg1;
     p->L2 = 1 << p->lg2;
@@ -648,7 +651,7 @@ int time_exec(nufft_plan p, void *flush, cudaStream_t s, float *ms) {
 }
 
 // The tuner's choices, per process: (device, N, M rounded up to a power of two, eps,
-// precision, K on the default grid) -> (grid size, long columns).
+// precision, K on the default grid) -> layout.
 struct TuneKey {
     int device;
     int64_t N, Mb;
@@ -659,19 +662,22 @@ struct TuneKey {
     }
 };
 std::mutex tune_mu;
-std::map<TuneKey, std::pair<int64_t, bool>> tune_cache;
+std::map<TuneKey, Layout> tune_cache;
 
 // Autotuned planning: the candidates are the default grid L0 and the oversampled
 // 2 L0 (section 2.3: a longer grid lowers gamma, and so K), each with either four-step
-// split when log2 L is odd; the one with the fastest forward + adjoint is kept.
+// split when log2 L is odd (the radices of the two passes) and with pass 1's default or
+// half number of columns per CTA (the tile); the one with the fastest forward + adjoint
+// is kept.
 int plan_autotune(nufft_plan *out, int64_t N, int64_t M, const double *x_dev, double eps, int prec,
                   int64_t L0, unsigned flags, cudaStream_t s) {
     nufft_plan best = nullptr;
-    if (int rc = plan_create(&best, N, M, x_dev, eps, prec, L0, flags, false, s)) return rc;
+    Layout choice;
+    choice.L = L0;
+    if (int rc = plan_create(&best, N, M, x_dev, eps, prec, choice, flags, s)) return rc;
     int64_t Mb = 1;
     while (Mb < M) Mb <<= 1;
     const TuneKey key{best->device, N, Mb, eps, prec, best->K};
-    std::pair<int64_t, bool> choice(L0, false);
     bool cached = false;
     {
         std::lock_guard<std::mutex> lk(tune_mu);
@@ -679,9 +685,9 @@ int plan_autotune(nufft_plan *out, int64_t N, int64_t M, const double *x_dev, do
         if (it != tune_cache.end()) { choice = it->second; cached = true; }
     }
     if (cached) {
-        if (choice.first == L0 && !choice.second) { *out = best; return NUFFT_OK; }
+        if (choice.L == L0 && !choice.long_cols && choice.c1_shift == 0) { *out = best; return NUFFT_OK; }
         free_plan(best);
-        return plan_create(out, N, M, x_dev, eps, prec, choice.first, flags, choice.second, s);
+        return plan_create(out, N, M, x_dev, eps, prec, choice, flags, s);
     }
     struct Flush {
         void *p = nullptr;
@@ -697,23 +703,28 @@ int plan_autotune(nufft_plan *out, int64_t N, int64_t M, const double *x_dev, do
     for (int64_t L = L0; L <= std::min<int64_t>(2 * L0, (int64_t)1 << LOG2_L_MAX); L *= 2) {
         int lg = 0;
         while (((int64_t)1 << lg) < L) ++lg;
-        for (int lc = 0; lc < 2; ++lc) {
-            if ((L == L0 && lc == 0) || (lc == 1 && lg % 2 == 0)) continue;
-            nufft_plan cand = nullptr;
-            int rc = plan_create(&cand, N, M, x_dev, eps, prec, L, flags, lc == 1, s);
-            if (rc == NUFFT_EUNSUPPORTED) continue;   // e.g. the shared-memory budget
-            if (rc) { free_plan(best); return rc; }
-            float t = 0.f;
-            if ((rc = time_exec(cand, flush.p, s, &t))) { free_plan(cand); free_plan(best); return rc; }
-            if (t < tbest) {
-                free_plan(best);
-                best = cand;
-                tbest = t;
-                choice = {L, lc == 1};
-            } else {
-                free_plan(cand);
+        for (int lc = 0; lc < 2; ++lc)
+            for (int c1s = 0; c1s < 2; ++c1s) {
+                if ((L == L0 && lc == 0 && c1s == 0) || (lc == 1 && lg % 2 == 0)) continue;
+                Layout cl;
+                cl.L = L;
+                cl.long_cols = lc == 1;
+                cl.c1_shift = c1s;
+                nufft_plan cand = nullptr;
+                int rc = plan_create(&cand, N, M, x_dev, eps, prec, cl, flags, s);
+                if (rc == NUFFT_EUNSUPPORTED) continue;   // e.g. the shared-memory budget
+                if (rc) { free_plan(best); return rc; }
+                float t = 0.f;
+                if ((rc = time_exec(cand, flush.p, s, &t))) { free_plan(cand); free_plan(best); return rc; }
+                if (t < tbest) {
+                    free_plan(best);
+                    best = cand;
+                    tbest = t;
+                    choice = cl;
+                } else {
+                    free_plan(cand);
+                }
             }
-        }
     }
     {
         std::lock_guard<std::mutex> lk(tune_mu);
@@ -735,7 +746,8 @@ extern "C" int nufft2_plan(nufft_plan *out, int64_t N, int64_t M, const double *
     if (N < 1 || M < 0 || M >= ((int64_t)1 << 31) || !(eps > 0.0 && eps < 1.0)) return NUFFT_EINVAL;
     if (prec != NUFFT_F32 && prec != NUFFT_F64) return NUFFT_EINVAL;
     if (M > 0 && !x_dev) return NUFFT_EINVAL;
-    if (flags & ~(NUFFT_PLAN_UNFUSED | NUFFT_PLAN_TIMING | NUFFT_PLAN_AUTOTUNE | NUFFT_PLAN_LONG_COLUMNS))
+    if (flags & ~(NUFFT_PLAN_UNFUSED | NUFFT_PLAN_TIMING | NUFFT_PLAN_AUTOTUNE | NUFFT_PLAN_LONG_COLUMNS |
+                  NUFFT_PLAN_HALF_TILE))
         return NUFFT_EINVAL;
     if (N > ((int64_t)1 << LOG2_L_MAX)) return NUFFT_EUNSUPPORTED;
     const bool fixed_L = L != 0;
@@ -748,10 +760,37 @@ extern "C" int nufft2_plan(nufft_plan *out, int64_t N, int64_t M, const double *
     }
     cudaStream_t s = (cudaStream_t)stream;
     const unsigned pf = flags & (NUFFT_PLAN_UNFUSED | NUFFT_PLAN_TIMING);
-    if ((flags & NUFFT_PLAN_AUTOTUNE) && !fixed_L && !(flags & NUFFT_PLAN_LONG_COLUMNS))
+    if ((flags & NUFFT_PLAN_AUTOTUNE) && !fixed_L && !(flags & (NUFFT_PLAN_LONG_COLUMNS | NUFFT_PLAN_HALF_TILE)))
         return plan_autotune(out, N, M, x_dev, eps, prec, L, pf, s);
-    return plan_create(out, N, M, x_dev, eps, prec, L, pf, (flags & NUFFT_PLAN_LONG_COLUMNS) != 0, s);
+    Layout lay;
+    lay.L = L;
+    lay.long_cols = (flags & NUFFT_PLAN_LONG_COLUMNS) != 0;
+    lay.c1_shift = (flags & NUFFT_PLAN_HALF_TILE) ? 1 : 0;
+    return plan_create(out, N, M, x_dev, eps, prec, lay, pf, s);
 }
+
+namespace nufft {
+// A plan with a given layout, for the batch tuner (the same checks as nufft2_plan).
+int plan_layout(nufft_plan *out, int64_t N, int64_t M, const double *x_dev, double eps, int prec,
+                const Layout &lay, unsigned flags, cudaStream_t s) {
+    if (!out) return NUFFT_EINVAL;
+    *out = nullptr;
+    if (lay.L == 0 && !lay.long_cols && lay.c1_shift == 0)
+        return nufft2_plan(out, N, M, x_dev, eps, prec, 0, flags, s);
+    if (N < 1 || M < 0 || M >= ((int64_t)1 << 31) || !(eps > 0.0 && eps < 1.0)) return NUFFT_EINVAL;
+    if (prec != NUFFT_F32 && prec != NUFFT_F64) return NUFFT_EINVAL;
+    if (M > 0 && !x_dev) return NUFFT_EINVAL;
+    Layout l = lay;
+    if (l.L == 0) {
+        l.L = (int64_t)1 << LOG2_L_MIN;
+        while (l.L < N) l.L <<= 1;
+    }
+    if (l.L < N || (l.L & (l.L - 1)) != 0) return NUFFT_EINVAL;
+    if (l.L < ((int64_t)1 << LOG2_L_MIN) || l.L > ((int64_t)1 << LOG2_L_MAX)) return NUFFT_EUNSUPPORTED;
+    if (l.c1_shift < 0 || l.c1_shift > 4) return NUFFT_EINVAL;
+    return plan_create(out, N, M, x_dev, eps, prec, l, flags & (NUFFT_PLAN_UNFUSED | NUFFT_PLAN_TIMING), s);
+}
+}  // namespace nufft
 
 extern "C" int nufft2_plan_info(nufft_plan p, int *K, double *gamma, int64_t *L, int64_t *work_bytes) {
     if (!p) return NUFFT_EINVAL;

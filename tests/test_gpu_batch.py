@@ -241,3 +241,23 @@ def test_batch_autotuned_matches_oracle(api):
         assert P.K == b.K[i]
         assert _rel2(f[m0:m1], lowrank.nufft2(P, c[n0:n1])) <= TOL_REL["f32"], i
         assert _rel2(cc[n0:n1], lowrank.nufft2_adjoint(P, g[m0:m1].astype(np.complex128))) <= TOL_REL["f32"], i
+
+
+@pytest.mark.parametrize("N,long_cols", [(2048, False), (3000, True), (1 << 15, False), (1 << 17, True)])
+def test_half_tile_matches_oracle(api, N, long_cols):
+    """The tuners' tile axis: the column pass with half the columns per CTA computes the
+    same transform (forward and adjoint), alone and with the other four-step split."""
+    x = wl.samples_uniform(N, 43)
+    L = 1024
+    while L < N:
+        L *= 2
+    if long_cols and (L.bit_length() - 1) % 2 == 0:
+        L *= 2
+    p = api.Plan(N, x, 1e-9, "f32", L=L, half_tile=True, long_columns=long_cols)
+    c = wl.coeffs_cn(N, 44).astype(np.complex64)
+    f = p.forward(torch.tensor(c, device="cuda")).cpu().numpy()
+    P = lowrank.plan(N, x, 1e-9, L)
+    assert _rel2(f, lowrank.nufft2(P, c.astype(np.complex128))) <= TOL_REL["f32"]
+    g = wl.cotangent_cn(N, 45).astype(np.complex64)
+    ca = p.adjoint(torch.tensor(g, device="cuda")).cpu().numpy()
+    assert _rel2(ca, lowrank.nufft2_adjoint(P, g.astype(np.complex128))) <= TOL_REL["f32"]
