@@ -52,7 +52,8 @@ enum nufft_status {
     NUFFT_ECUDA = -3,         /* a CUDA call failed (no device, launch error, ...) */
     NUFFT_EUNSUPPORTED = -4,  /* size beyond what this build handles */
     NUFFT_ESTATE = -5,        /* call needs a plan option that was not set */
-    NUFFT_ETIMEOUT = -6       /* a bounded device-side wait gave up (see nufft2_check) */
+    NUFFT_ETIMEOUT = -6,      /* a bounded device-side wait gave up (see nufft2_check) */
+    NUFFT_ECHECK = -7         /* an index check failed (builds with NUFFT_CHECK; see nufft2_check) */
 };
 
 /* Plan flags. */
@@ -386,7 +387,10 @@ int nufft_test_wait_timeout(void *stream);
 /* Synchronise `stream` and report whether any exec call on this plan since the
  * last check had a device-side wait give up (a bulk copy that did not complete
  * within its time limit): NUFFT_ETIMEOUT, and the results of those calls are
- * invalid; else NUFFT_OK.  Clears the condition. */
+ * invalid; or, in a library built with NUFFT_CHECK (libnufft_check.so: every
+ * data-dependent shared and global index is checked, and an out-of-range access is
+ * recorded and skipped instead of made), whether an index check failed:
+ * NUFFT_ECHECK; else NUFFT_OK.  Clears the condition. */
 int nufft2_check(nufft_plan p, void *stream);
 
 /* Human-readable name of a status code. */

@@ -10,7 +10,8 @@ import ctypes
 import os
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libnufft.so")
+# NUFFT_LIB selects another build of the same ABI, e.g. the checked libnufft_check.so
+LIB_PATH = os.environ.get("NUFFT_LIB") or os.path.join(_PKG, "libnufft.so")
 
 NUFFT_F32, NUFFT_F64 = 0, 1
 NUFFT_PLAN_UNFUSED = 1
@@ -21,7 +22,8 @@ NUFFT_PLAN_LONG_COLUMNS = 16
 NUFFT_BATCH_PER_PROBLEM = 32
 NUFFT_PLAN_HALF_TILE = 64
 STATUS = {0: "NUFFT_OK", -1: "NUFFT_EINVAL", -2: "NUFFT_ENOMEM", -3: "NUFFT_ECUDA",
-          -4: "NUFFT_EUNSUPPORTED", -5: "NUFFT_ESTATE", -6: "NUFFT_ETIMEOUT"}
+          -4: "NUFFT_EUNSUPPORTED", -5: "NUFFT_ESTATE", -6: "NUFFT_ETIMEOUT",
+          -7: "NUFFT_ECHECK"}
 
 # name -> (restype, argtypes), mirroring include/nufft.h
 _vp, _i64, _i32, _dbl, _u32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_uint
@@ -78,8 +80,8 @@ def load():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise RuntimeError("libnufft.so is not built (run paper_1701_04492_gb300.build.build()); "
-                               "there is no CPU fallback")
+            raise RuntimeError("%s is not built (run paper_1701_04492_gb300.build.build()); "
+                               "there is no CPU fallback" % LIB_PATH)
         lib = ctypes.CDLL(LIB_PATH)
         for name, (res, args) in SIGNATURES.items():
             fn = getattr(lib, name)

@@ -13,6 +13,24 @@ namespace nufft {
 
 constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;   // 2 s
 
+// Bits of the device error word (nufft2_check).
+constexpr int ERR_TIMEOUT = 1;   // a bounded wait gave up
+constexpr int ERR_INDEX = 2;     // an index check failed (NUFFT_CHECK builds)
+
+// The index check of NUFFT_CHECK builds: ok is the in-range condition of an access the
+// caller makes only when this returns true.  A failure is recorded in the error word.
+// Without NUFFT_CHECK it is true and the condition is discarded.
+__device__ __forceinline__ bool idx_ok(bool ok, int *err) {
+#ifdef NUFFT_CHECK
+    if (!ok && err) atomicOr(err, ERR_INDEX);
+    return ok;
+#else
+    (void)ok;
+    (void)err;
+    return true;
+#endif
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
@@ -76,7 +94,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
         if (mbar_try_wait(bar, parity)) return true;
         if (global_ns() - t0 > WAIT_LIMIT_NS) {
             *cta_failed = 1;
-            if (err) atomicOr(err, 1);
+            if (err) atomicOr(err, ERR_TIMEOUT);
             return false;
         }
     }

@@ -255,18 +255,23 @@ __device__ __forceinline__ void pass1_body(const PassArgs<T> &a, const int bx, c
     // output n2 = tt + TT q(e) goes to Y_r[n2][k1]
     cx<T> *yb = a.Y + (int64_t)r * a.L + tt * a.L1 + k1;
     const int ystride = TT * a.L1;
+    const bool y_ok = idx_ok(r < a.nranks && k1 < a.L1 && tt < TT, a.err);   // stores only: barriers follow
     if constexpr (TWO_D) {
+        if (y_ok) {
 #pragma unroll
-        for (int e = 0; e < E; ++e) yb[TF::out_q(e) * ystride] = v[e];
+            for (int e = 0; e < E; ++e) yb[TF::out_q(e) * ystride] = v[e];
+        }
     } else {
         __syncthreads();   // the four-step table is complete
         const cx<T> base = twiddle_L<T>(a, tt * k1);
         const cx<T> *fb = ftab + cc;
+        if (y_ok) {
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const int q = TF::out_q(e);
-            const cx<T> w = cmul<T>(base, fb[q * a.C]);
-            yb[q * ystride] = cmul<T>(v[e], w);
+            for (int e = 0; e < E; ++e) {
+                const int q = TF::out_q(e);
+                const cx<T> w = cmul<T>(base, fb[q * a.C]);
+                yb[q * ystride] = cmul<T>(v[e], w);
+            }
         }
     }
 }
@@ -281,7 +286,8 @@ __device__ __forceinline__ void pass2_body(const PassArgs<T> &a, const BT &beta,
     const int nt = blockDim.x / TT;
     const int team = threadIdx.x / TT, tt = threadIdx.x % TT;
     const int b = bx;
-    const int i0 = a.bstart[b], i1 = a.bstart[b + 1];
+    int i0 = a.bstart[b], i1 = a.bstart[b + 1];
+    if (!idx_ok(i0 >= 0 && i0 <= i1 && i1 <= a.M, a.err)) i1 = i0 = 0;   // no samples (barriers follow)
     const int L2m = a.L2 - 1;
     const int Gs = a.G > 0 ? a.G : 1;   // never a zero stride
     // one mbarrier per slot: the rows of a rank group arrive by bulk copy (TMA)
@@ -354,6 +360,7 @@ __device__ __forceinline__ void pass2_body(const PassArgs<T> &a, const BT &beta,
                 const int t = a.tsorted[i];
                 const int row = (t & L2m) - b * a.B2;
                 const int n1 = t >> a.lg2;
+                if (!idx_ok(row >= 0 && row < a.B2 && n1 >= 0 && n1 < a.L1, a.err)) continue;
                 const T d = a.dsorted[i];
                 const T xi = d * a.inv_gamma;
                 T Tp[KM];
@@ -392,6 +399,7 @@ __device__ __forceinline__ void pass2_body(const PassArgs<T> &a, const BT &beta,
                 const cx<T> ph = mk<T>(fma(Sp.x, cs, Sp.y * sn), fma(Sp.y, cs, -Sp.x * sn));
                 const cx<T> fp = mk<T>(a.piN * ph.y, -a.piN * ph.x);   // -i pi N (phase Sp)
                 const int j = a.perm[i];
+                if (!idx_ok(j >= 0 && j < a.M, a.err)) continue;
                 if (a.out) a.out[j] = f;
                 if (a.out2) a.out2[j] = fp;
                 if (a.mode & MODE_GX) {
@@ -406,6 +414,7 @@ __device__ __forceinline__ void pass2_body(const PassArgs<T> &a, const BT &beta,
                 const int t = a.tsorted[i];
                 const int row = (t & L2m) - b * a.B2;
                 const int n1 = t >> a.lg2;
+                if (!idx_ok(row >= 0 && row < a.B2 && n1 >= 0 && n1 < a.L1, a.err)) continue;
                 const T d = a.dsorted[i];
                 cx<T> acc = g0 == 0 ? mk<T>(0, 0) : a.fscr[i];
                 cx<T> comp = mk<T>(0, 0);   // the rank-sum's compensation
@@ -450,6 +459,7 @@ __device__ __forceinline__ void pass2_body(const PassArgs<T> &a, const BT &beta,
                         val = mk<T>(fma(acc.x, cs, acc.y * sn), fma(acc.y, cs, -acc.x * sn));
                     }
                     const int j = a.perm[i];
+                    if (!idx_ok(j >= 0 && j < a.M, a.err)) continue;
                     if (a.mode & MODE_GX) {
                         const cx<T> gg = a.g[j];
                         const T re = fma(gg.x, val.x, gg.y * val.y);
@@ -475,7 +485,8 @@ __device__ __forceinline__ void passA_body(const PassArgs<T> &a, const BT &beta,
     const int nt = blockDim.x / TT;
     const int team = threadIdx.x / TT, tt = threadIdx.x % TT;
     const int b = bx;
-    const int i0 = a.bstart[b], i1 = a.bstart[b + 1];
+    int i0 = a.bstart[b], i1 = a.bstart[b + 1];
+    if (!idx_ok(i0 >= 0 && i0 <= i1 && i1 <= a.M, a.err)) i1 = i0 = 0;   // no samples (barriers follow)
     const int L2m = a.L2 - 1;
     const int Gs = a.G > 0 ? a.G : 1;   // never a zero stride
     for (int g0 = 0; g0 < a.K; g0 += Gs) {
@@ -496,7 +507,8 @@ __device__ __forceinline__ void passA_body(const PassArgs<T> &a, const BT &beta,
             for (int i = threadIdx.x; i < n; i += blockDim.x) {
                 st_t[i] = a.tsorted[c0 + i];
                 st_d[i] = a.dsorted[c0 + i];
-                st_g[i] = a.in[a.perm[c0 + i]];
+                const int j = a.perm[c0 + i];
+                st_g[i] = idx_ok(j >= 0 && j < a.M, a.err) ? a.in[j] : mk<T>(0, 0);
             }
             __syncthreads();
             for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -516,7 +528,8 @@ __device__ __forceinline__ void passA_body(const PassArgs<T> &a, const BT &beta,
                     } else {
                         if (a.tsorted[c0 + i2] != t) break;
                         d = a.dsorted[c0 + i2];
-                        gg = a.in[a.perm[c0 + i2]];
+                        const int j = a.perm[c0 + i2];
+                        gg = idx_ok(j >= 0 && j < a.M, a.err) ? a.in[j] : mk<T>(0, 0);
                     }
                     if constexpr (kFactors<T>) {
                         // Z_r += conj(u_r(j)) g_j with the plan's U
@@ -553,6 +566,7 @@ __device__ __forceinline__ void passA_body(const PassArgs<T> &a, const BT &beta,
                 }
                 const int row = (t & L2m) - b * a.B2;
                 const int n1 = t >> a.lg2;
+                if (!idx_ok(row >= 0 && row < a.B2 && n1 >= 0 && n1 < a.L1, a.err)) continue;
 #pragma unroll
                 for (int r = 0; r < KM; ++r)
                     if (r >= g0 && r < g0 + gc) smem[((r - g0) * a.B2 + row) * a.S + padi<E>(n1)] = acc[r];
@@ -780,7 +794,8 @@ __device__ __forceinline__ void pass2d_body(const PassArgs<T> &a, const BT &beta
         }
     }
     __syncthreads();
-    const int i0 = a.bstart[b], i1 = a.bstart[b + 1];
+    int i0 = a.bstart[b], i1 = a.bstart[b + 1];
+    if (!idx_ok(i0 >= 0 && i0 <= i1 && i1 <= a.M, a.err)) i1 = i0 = 0;   // no samples (barriers follow)
     const T invg = a.inv_gamma, invg2 = a.inv_gamma2;
     for (int r1 = 0; r1 < K1; ++r1) {
         const int buf = r1 & 1;
@@ -823,6 +838,7 @@ __device__ __forceinline__ void pass2d_body(const PassArgs<T> &a, const BT &beta
 #pragma unroll 1
         for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
             const int n1 = a.tsorted[i] >> a.lg2;   // t^y
+            if (!idx_ok(n1 >= 0 && n1 < a.L1, a.err)) continue;
             const T dx = a.dsorted[i], dy = a.dsorted2[i];
             // mu^x_r1 = sum_p beta^x_r1p T_p(d^x / gamma_x), mu^y_r2 likewise in y
             T Tp[KM];
@@ -860,7 +876,9 @@ __device__ __forceinline__ void pass2d_body(const PassArgs<T> &a, const BT &beta
             } else {
                 T sn, cs;
                 sincospi_t<T>(dx + dy, &sn, &cs);
-                a.out[a.perm[i]] = mk<T>(fma(acc.x, cs, acc.y * sn), fma(acc.y, cs, -acc.x * sn));
+                const int j = a.perm[i];
+                if (idx_ok(j >= 0 && j < a.M, a.err))
+                    a.out[j] = mk<T>(fma(acc.x, cs, acc.y * sn), fma(acc.y, cs, -acc.x * sn));
             }
         }
         __syncthreads();   // the slots are rewritten at the next r1

@@ -17,6 +17,7 @@
 #include <tuple>
 #include <vector>
 
+#include "async_copy.cuh"
 #include "fft_team.cuh"
 #include "fill.cuh"
 #include "nufft_internal.h"
@@ -837,7 +838,7 @@ extern "C" int nufft2_check(nufft_plan p, void *stream) {
     if (h) {
         NUFFT_CUDA_TRY(cudaMemsetAsync(p->err, 0, sizeof(int), s));
         NUFFT_CUDA_TRY(cudaStreamSynchronize(s));
-        return NUFFT_ETIMEOUT;
+        return (h & nufft::ERR_TIMEOUT) ? NUFFT_ETIMEOUT : NUFFT_ECHECK;
     }
     return NUFFT_OK;
 }
@@ -856,6 +857,7 @@ extern "C" const char *nufft_strerror(int code) {
         case NUFFT_EUNSUPPORTED: return "unsupported size";
         case NUFFT_ESTATE: return "plan lacks the option this call needs";
         case NUFFT_ETIMEOUT: return "a device-side wait timed out; results of the affected calls are invalid";
+        case NUFFT_ECHECK: return "an index check failed (NUFFT_CHECK build); results of the affected calls are invalid";
         default: return "unknown status";
     }
 }

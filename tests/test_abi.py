@@ -55,5 +55,5 @@ def test_argument_errors_without_gpu(lib):
     assert lib.nufft2_exec_batch(None, 1, None, 1, None, 1, None) == -1
     assert lib.nufft2_plan_info(None, None, None, None, None) == -1
     assert lib.nufft_destroy(None) == 0
-    for code in (0, -1, -2, -3, -4, -5):
-        assert lib.nufft_strerror(code)
+    msgs = [lib.nufft_strerror(code) for code in (0, -1, -2, -3, -4, -5, -6, -7)]
+    assert all(msgs) and len(set(msgs)) == len(msgs)       # every status has its own message

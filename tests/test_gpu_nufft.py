@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path through the C ABI against the CPU oracle.
 
-Tolerances (derived in DESIGN.md, "Tolerances"):
+Tolerances (each follows from the rounding of the path it checks):
   FP64 exec  vs the low-rank oracle: ||df||_2 / ||f||_2 <= 1e-13 (same method,
              rounding only); vs the direct sum: |df|_inf <= (eps + 1e-13) ||c||_1.
   FP32 exec  vs the low-rank oracle: ||df||_2 / ||f||_2 <= 1e-5 (FP32 FFT rounding,
