@@ -213,6 +213,7 @@ def run_ours(args):
             print(json.dumps({"batch_c5": batch_c5(api, dev, timed, args.steps),
                               "nufft2d_c3": bench_2d(api, dev, timed, args.steps),
                               "inverse": bench_inverse(api, dev),
+                              "worst_grid_e3": worst_grid_sweep(api, dev, timed, args.steps),
                               "autograd_c4": bench_autograd_c4(api, dev, timed, args.steps)}), flush=True)
         return
     if args.only:
@@ -339,6 +340,7 @@ def run_ours(args):
             line["batch_c5"] = batch_c5(api, dev, timed, args.steps)
             line["nufft2d_c3"] = bench_2d(api, dev, timed, args.steps)
             line["inverse"] = bench_inverse(api, dev)
+            line["worst_grid_e3"] = worst_grid_sweep(api, dev, timed, args.steps)
             line["autograd_c4"] = bench_autograd_c4(api, dev, timed, args.steps)
         if ws == 1 and not args.no_cpu_baseline:
             plan.forward(c, f)   # the plain forward's f for the accuracy record
@@ -438,6 +440,27 @@ def bench_2d(api, dev, timed, steps):
             "plan_s": plan_s, "kernel_ms": {"cols": k1, "rows": k2},
             "alu_frac": {"cols": fl_cols / (k1 * 1e-3) / 1e12 / peak_tf, "rows": fl_rows / (k2 * 1e-3) / 1e12 / peak_tf},
             "launches_per_fwd": 2}
+
+
+def worst_grid_sweep(api, dev, timed, steps):
+    """Section 2.4's worst grid at N = M = 2^20, eps = 1e-9: two shifted halves,
+    x_j = (j + gamma)/N for j <= N/2 and (j - gamma)/N above, so every |delta_j| = gamma.
+    gamma in {1/2, 1/8, 1/32, 0} sets K (12, 9, 7, 1); forward and forward+adjoint Gpts/s."""
+    import torch
+    from paper_1701_04492_gb300 import workloads as wl
+    N = 1 << 20
+    c = torch.tensor(wl.coeffs_cn(N, SEED).astype(np.complex64), device=dev)
+    f = torch.empty(N, dtype=torch.complex64, device=dev)
+    gc = torch.empty(N, dtype=torch.complex64, device=dev)
+    out = {"workload": "1D NUFFT-II on the worst grid, N=M=2^20, eps=1e-9, c~CN(0,1) complex64"}
+    for gname, gamma in (("1/2", 0.5), ("1/8", 1 / 8), ("1/32", 1 / 32), ("0", 0.0)):
+        p = api.Plan(N, wl.samples_worst(N, gamma), EPS, "f32", device=dev)
+        fw = timed(lambda: p.forward(c, f), steps, 3)
+        fb = timed(lambda: (p.forward(c, f), p.adjoint(f, gc)), steps, 3)
+        out[gname] = {"K": p.K, "gamma": p.gamma, "fwd_gpts": N * len(fw) / (sum(fw) * 1e-3) / 1e9,
+                      "fwd_adj_gpts": N * len(fb) / (sum(fb) * 1e-3) / 1e9}
+        del p
+    return out
 
 
 def bench_inverse(api, dev):

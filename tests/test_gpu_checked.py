@@ -36,7 +36,9 @@ def _child():
     cdt = {"f32": np.complex64, "f64": np.complex128}
     # 1D: odd sizes (ragged tiles and buckets), clustered and uniform samples, both precisions
     for prec, N, M, eps, kind in [("f32", 3001, 4999, 1e-6, "uniform"), ("f32", 70000, 33333, 1e-4, "perturbed"),
-                                  ("f64", 5003, 2047, 1e-12, "uniform"), ("f64", 1 << 15, 40001, 1e-9, "perturbed")]:
+                                  ("f64", 5003, 2047, 1e-12, "uniform"), ("f64", 1 << 15, 40001, 1e-9, "perturbed"),
+                                  ("f32", 1 << 20, 1 << 20, 1e-9, "perturbed")] + \
+                                 [("f64", n, 7, 1e-9, "uniform") for n in (1, 2, 3, 5, 7, 8, 1000)]:
         x = wl.samples_uniform(M, N + M) if kind == "uniform" else wl.samples_perturbed(M, N + M, 1 / 8)
         nc = cdt[prec]
         p = api.Plan(N, x, eps, prec)

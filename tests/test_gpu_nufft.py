@@ -203,6 +203,32 @@ def test_full_size_against_oracle(api, prec, kind):
     assert _rel2(ah, lowrank.nufft2_adjoint(P, g)) <= TOL_REL[prec]
 
 
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("gamma", [0.5, 1 / 8, 1 / 32, 0.0])
+def test_full_size_worst_grid_closed_form(api, prec, gamma):
+    """Section 2.4's worst grid at N = 2^20: each half is a shifted uniform grid, so the
+    exact transform of the whole vector is one FFT per half (a closed form, no oracle
+    involved); the error bound ||A - A_K||_max <= eps gives |df|_inf <= eps ||c||_1
+    (section 2.4's bounds, plus the FP32 rounding of the FFT in single precision)."""
+    N = 1 << 20
+    x = wl.samples_worst(N, gamma)
+    c = _cast(wl.coeffs_cn(N, 12), prec)
+    plan = api.Plan(N, x, 1e-9, prec)
+    assert plan.gamma == pytest.approx(gamma, abs=1e-12)
+    assert plan.K == lowrank.choose_K(1e-9, plan.gamma)
+    f = plan.forward(_dev(c, _cdt(prec))).cpu().numpy()
+    k = np.arange(N)
+    cc = c.astype(np.complex128)
+    plus = np.fft.fft(cc * np.exp(-2j * math.pi * gamma * k / N))
+    minus = np.fft.fft(cc * np.exp(2j * math.pi * gamma * k / N))
+    ref = np.where(k <= N // 2, plus, minus)
+    tol = (1e-9 + 1e-13) if prec == "f64" else 5e-6
+    assert np.max(np.abs(f - ref)) <= tol * np.sum(np.abs(cc))
+    # the 2-norm form of the same bound: ||df||_2 <= N eps ||c||_2, plus FP32 FFT rounding
+    rnd = 1e-13 if prec == "f64" else TOL_REL[prec]
+    assert np.linalg.norm(f - ref) <= N * 1e-9 * np.linalg.norm(cc) + rnd * np.linalg.norm(ref)
+
+
 # ---- unfused comparator, host path, batch, determinism -------------------------------------
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
