@@ -355,13 +355,27 @@ __device__ __forceinline__ void pass2_body(const PassArgs<T> &a, const BT &beta,
             // A_K((-2 pi i k) o c) is -pi i N (X_r - i X_{r+1}/2 + i X_{r-1}/2) (r >= 1;
             // X_0 - i X_1 for r = 0), so f'_j = -pi i N e^{-i pi d} sum_{s<=K} rho_s X_s[t_j]
             // with rho_s = mu_s + i (mu_{s+1}/2 - mu_{s-1}/2 [s >= 2] - mu_0 [s = 1]).
+            // software-pipelined: the next sample's t, d and j are loaded while this
+            // one is formed
+            int tn = 0, jn = 0;
+            T dn = T(0);
+            if (i0 + (int)threadIdx.x < i1) {
+                tn = a.tsorted[i0 + threadIdx.x];
+                dn = a.dsorted[i0 + threadIdx.x];
+                jn = a.perm[i0 + threadIdx.x];
+            }
 #pragma unroll 1
             for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-                const int t = a.tsorted[i];
+                const int t = tn, j = jn;
+                const T d = dn;
+                if (i + (int)blockDim.x < i1) {
+                    tn = a.tsorted[i + blockDim.x];
+                    dn = a.dsorted[i + blockDim.x];
+                    jn = a.perm[i + blockDim.x];
+                }
                 const int row = (t & L2m) - b * a.B2;
                 const int n1 = t >> a.lg2;
                 if (!idx_ok(row >= 0 && row < a.B2 && n1 >= 0 && n1 < a.L1, a.err)) continue;
-                const T d = a.dsorted[i];
                 const T xi = d * a.inv_gamma;
                 T Tp[KM];
                 Tp[0] = T(1);
@@ -398,7 +412,6 @@ __device__ __forceinline__ void pass2_body(const PassArgs<T> &a, const BT &beta,
                 const cx<T> f = mk<T>(fma(S.x, cs, S.y * sn), fma(S.y, cs, -S.x * sn));
                 const cx<T> ph = mk<T>(fma(Sp.x, cs, Sp.y * sn), fma(Sp.y, cs, -Sp.x * sn));
                 const cx<T> fp = mk<T>(a.piN * ph.y, -a.piN * ph.x);   // -i pi N (phase Sp)
-                const int j = a.perm[i];
                 if (!idx_ok(j >= 0 && j < a.M, a.err)) continue;
                 if (a.out) a.out[j] = f;
                 if (a.out2) a.out2[j] = fp;
@@ -409,13 +422,26 @@ __device__ __forceinline__ void pass2_body(const PassArgs<T> &a, const BT &beta,
                 }
             }
         } else {
-#pragma unroll 2
+            // software-pipelined as the derivative mode's loop
+            int tn = 0, jn = 0;
+            T dn = T(0);
+            if (i0 + (int)threadIdx.x < i1) {
+                tn = a.tsorted[i0 + threadIdx.x];
+                dn = a.dsorted[i0 + threadIdx.x];
+                jn = a.perm[i0 + threadIdx.x];
+            }
+#pragma unroll 1
             for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-                const int t = a.tsorted[i];
+                const int t = tn, j = jn;
+                const T d = dn;
+                if (i + (int)blockDim.x < i1) {
+                    tn = a.tsorted[i + blockDim.x];
+                    dn = a.dsorted[i + blockDim.x];
+                    jn = a.perm[i + blockDim.x];
+                }
                 const int row = (t & L2m) - b * a.B2;
                 const int n1 = t >> a.lg2;
                 if (!idx_ok(row >= 0 && row < a.B2 && n1 >= 0 && n1 < a.L1, a.err)) continue;
-                const T d = a.dsorted[i];
                 cx<T> acc = g0 == 0 ? mk<T>(0, 0) : a.fscr[i];
                 cx<T> comp = mk<T>(0, 0);   // the rank-sum's compensation
                 constexpr bool fac = kFactors<T>;
@@ -458,7 +484,6 @@ __device__ __forceinline__ void pass2_body(const PassArgs<T> &a, const BT &beta,
                         sincospi_t<T>(d, &sn, &cs);
                         val = mk<T>(fma(acc.x, cs, acc.y * sn), fma(acc.y, cs, -acc.x * sn));
                     }
-                    const int j = a.perm[i];
                     if (!idx_ok(j >= 0 && j < a.M, a.err)) continue;
                     if (a.mode & MODE_GX) {
                         const cx<T> gg = a.g[j];
@@ -493,22 +518,56 @@ __device__ __forceinline__ void passA_body(const PassArgs<T> &a, const BT &beta,
         const int gc = min(Gs, a.K - g0);
         const int njobs = gc * a.B2;
         const int nslots = Gs * a.B2;   // fixed offsets for the tables and staging below
+        const int chunk = a.chunk > 0 ? a.chunk : 1;   // never a zero stride
+        // a chunk's t, d and j are fetched into registers one chunk ahead (up to PF per
+        // thread), so that their loads are in flight during the previous chunk's scatter
+        // (or, for the first, during the zero fill); the gather of g waits for j only
+        constexpr int PF = 2;
+        const bool pf = chunk <= PF * (int)blockDim.x;
+        int pt[PF], pj[PF];
+        T pd[PF];
+        auto fetch = [&](const int c0) {
+            const int n = min(chunk, i1 - c0);
+#pragma unroll
+            for (int u = 0; u < PF; ++u) {
+                const int i = threadIdx.x + u * blockDim.x;
+                if (i < n) {
+                    pt[u] = a.tsorted[c0 + i];
+                    pd[u] = a.dsorted[c0 + i];
+                    pj[u] = a.perm[c0 + i];
+                }
+            }
+        };
+        if (pf && i0 < i1) fetch(i0);
         for (int idx = threadIdx.x; idx < njobs * a.S; idx += blockDim.x) smem[idx] = mk<T>(0, 0);
         __syncthreads();
         // the bucket's samples, staged chunk by chunk: t, d and the gathered g
         int32_t *st_t = reinterpret_cast<int32_t *>(smem + nslots * a.S + nt * E);
         T *st_d = reinterpret_cast<T *>(st_t + a.chunk);
         cx<T> *st_g = reinterpret_cast<cx<T> *>(st_d + a.chunk);
-        const int chunk = a.chunk > 0 ? a.chunk : 1;   // never a zero stride
         for (int c0 = i0; c0 < i1; c0 += chunk) {
             const int n = min(chunk, i1 - c0);
             __syncthreads();   // the previous chunk is consumed
+            if (pf) {
+#pragma unroll
+                for (int u = 0; u < PF; ++u) {
+                    const int i = threadIdx.x + u * blockDim.x;
+                    if (i < n) {
+                        st_t[i] = pt[u];
+                        st_d[i] = pd[u];
+                        const int j = pj[u];
+                        st_g[i] = idx_ok(j >= 0 && j < a.M, a.err) ? a.in[j] : mk<T>(0, 0);
+                    }
+                }
+                if (c0 + chunk < i1) fetch(c0 + chunk);
+            } else {
 #pragma unroll 4
-            for (int i = threadIdx.x; i < n; i += blockDim.x) {
-                st_t[i] = a.tsorted[c0 + i];
-                st_d[i] = a.dsorted[c0 + i];
-                const int j = a.perm[c0 + i];
-                st_g[i] = idx_ok(j >= 0 && j < a.M, a.err) ? a.in[j] : mk<T>(0, 0);
+                for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                    st_t[i] = a.tsorted[c0 + i];
+                    st_d[i] = a.dsorted[c0 + i];
+                    const int j = a.perm[c0 + i];
+                    st_g[i] = idx_ok(j >= 0 && j < a.M, a.err) ? a.in[j] : mk<T>(0, 0);
+                }
             }
             __syncthreads();
             for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -835,11 +894,31 @@ __device__ __forceinline__ void pass2d_body(const PassArgs<T> &a, const BT &beta
             mbar_arrive_expect_tx(&mbar[buf], ROW_BYTES);
             bulk_copy_g2s(stg + buf * P1, rows + (int64_t)(r1 + 2) * a.L, ROW_BYTES, &mbar[buf]);
         }
+        // software-pipelined: the next sample's t, d^x, d^y and partial sum are loaded
+        // while this one is formed
+        int tn = 0;
+        T dxn = T(0), dyn = T(0);
+        cx<T> accn = mk<T>(0, 0);
+        if (i0 + (int)threadIdx.x < i1) {
+            const int i = i0 + threadIdx.x;
+            tn = a.tsorted[i];
+            dxn = a.dsorted[i];
+            dyn = a.dsorted2[i];
+            if (r1 > 0) accn = a.fscr[i];
+        }
 #pragma unroll 1
         for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-            const int n1 = a.tsorted[i] >> a.lg2;   // t^y
+            const int n1 = tn >> a.lg2;   // t^y
+            const T dx = dxn, dy = dyn;
+            cx<T> acc = accn;
+            if (i + (int)blockDim.x < i1) {
+                const int in = i + blockDim.x;
+                tn = a.tsorted[in];
+                dxn = a.dsorted[in];
+                dyn = a.dsorted2[in];
+                if (r1 > 0) accn = a.fscr[in];
+            }
             if (!idx_ok(n1 >= 0 && n1 < a.L1, a.err)) continue;
-            const T dx = a.dsorted[i], dy = a.dsorted2[i];
             // mu^x_r1 = sum_p beta^x_r1p T_p(d^x / gamma_x), mu^y_r2 likewise in y
             T Tp[KM];
             const T xi = dx * invg;
@@ -868,7 +947,6 @@ __device__ __forceinline__ void pass2d_body(const PassArgs<T> &a, const BT &beta
                     S.y = fma(mu, x.y, S.y);
                 }
             }
-            cx<T> acc = r1 == 0 ? mk<T>(0, 0) : a.fscr[i];
             acc.x = fma(mux, S.x, acc.x);
             acc.y = fma(mux, S.y, acc.y);
             if (r1 + 1 < K1) {
