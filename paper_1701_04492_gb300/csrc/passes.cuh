@@ -636,6 +636,14 @@ __device__ __forceinline__ void passA_body(const PassArgs<T> &a, const BT &beta,
         typename TF::Tw twreg;
         if constexpr (kTwReg<T>) TF::load_tw(twreg, tt, a.twr);
         cx<T> *ftab = smem + nslots * a.S + team * E;   // this team's four-step table
+        // with one row per bucket (B2 = 1) every job has the same row n2 = b: its
+        // four-step table and base twiddle are made once for all the rounds
+        const bool one_row = a.B2 == 1;
+        cx<T> base1 = mk<T>(1, 0);
+        if (one_row) {
+            fill_fourstep<T, E, TT>(a, b, tt, ftab, 1);
+            base1 = twiddle_L<T>(a, b * tt);
+        }
         auto round = [&](const int j0, auto pred) {   // PRED: a round with idle teams
             constexpr bool PRED = decltype(pred)::value;
             const int job = j0 + team;
@@ -650,14 +658,15 @@ __device__ __forceinline__ void passA_body(const PassArgs<T> &a, const BT &beta,
                 else if constexpr (TT % E == 0) v[m] = sm[padi_run<E, TT>(padi<E>(tt), m)];
                 else v[m] = sm[padi<E>(tt + TT * m)];
             }
-            fill_fourstep<T, E, TT>(a, n2, tt, ftab, 1);
+            if (!one_row) fill_fourstep<T, E, TT>(a, n2, tt, ftab, 1);
+            // the base twiddle w_L^{n2 tt}, loaded before the transform hides its latency
+            const cx<T> base = one_row ? base1 : twiddle_L<T>(a, n2 * tt);
             __syncthreads();
             if constexpr (kTwReg<T>) TF::template run_reg<PRED>(v, tt, sm, twreg, act);
             else TF::template run<PRED>(v, tt, sm, a.twr, act);
             if (act) {
                 // column-tiled layout for pass B: Y'_r[k1 / CQ][n2][k1 % CQ], so each
                 // CQ-column tile of a rank is one contiguous block
-                const cx<T> base = twiddle_L<T>(a, n2 * tt);
                 cx<T> *dst = a.Y + (int64_t)(g0 + rl) * a.L + n2 * a.CQ;
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
@@ -666,7 +675,7 @@ __device__ __forceinline__ void passA_body(const PassArgs<T> &a, const BT &beta,
                         cmulc<T>(v[e], cmul<T>(base, ftab[TF::out_q(e)]));
                 }
             }
-            __syncthreads();   // the next job refills ftab
+            __syncthreads();   // the next job may refill ftab
         };
         for (int j0 = 0; j0 < njobs; j0 += nt) {
             if (j0 + nt <= njobs) round(j0, std::false_type{});
@@ -801,16 +810,28 @@ __device__ __forceinline__ void passB_body(const PassArgs<T> &a, const int bx, c
     __syncthreads();
     if (ticket != SB - 1) return;
     __threadfence();
+    // the sum over s2 = 0..SB-1 in that order, H elements at a time so that their
+    // loads are in flight together; this CTA's own partial comes from its registers
+    constexpr int H = E < 8 ? E : 8;
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int k = k1 + a.L1 * TF::out_index(tt, e);
-        cx<T> t = mk<T>(0, 0);
+    for (int h0 = 0; h0 < E; h0 += H) {
+        cx<T> t[H];
+#pragma unroll
+        for (int m = 0; m < H; ++m) t[m] = mk<T>(0, 0);
         for (int s2 = 0; s2 < SB; ++s2) {
-            const cx<T> pv = __ldcg(&a.part[(int64_t)s2 * a.L + k]);
-            t.x += pv.x;
-            t.y += pv.y;
+#pragma unroll
+            for (int m = 0; m < H; ++m) {
+                const int k = k1 + a.L1 * TF::out_index(tt, h0 + m);
+                const cx<T> pv = s2 == s ? acc[h0 + m] : __ldcg(&a.part[(int64_t)s2 * a.L + k]);
+                t[m].x += pv.x;
+                t[m].y += pv.y;
+            }
         }
-        if (k < a.N) a.out[k] = t;
+#pragma unroll
+        for (int m = 0; m < H; ++m) {
+            const int k = k1 + a.L1 * TF::out_index(tt, h0 + m);
+            if (k < a.N) a.out[k] = t[m];
+        }
     }
     if (threadIdx.x == 0) a.counters[bx] = 0;   // ready for the next call
 }
