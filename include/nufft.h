@@ -278,11 +278,14 @@ int nufft2_inverse(nufft_plan p, const void *f_dev, void *c_dev, double tol, int
  *   m, n    1 <= m, n <= 2048.
  *   M       number of samples, 0 <= M < 2^31.
  *   x_dev, y_dev   M doubles each on the device; read during the call only.
- *   prec    NUFFT_F32 (the 2D kernels are FP32; NUFFT_F64 returns NUFFT_EUNSUPPORTED).
+ *   prec    NUFFT_F32 (C and f complex64) or NUFFT_F64 (complex128).  When the
+ *           transformed rows of all K_y ranks do not fit in shared memory (FP64 rows
+ *           of 1024 or more points, FP32 rows of 2048), the row pass transforms and
+ *           gathers the y ranks in groups.
  *   flags   0 or NUFFT_PLAN_TIMING.
  *
  * The plan is a nufft_plan: nufft2_exec(p, C_dev, f_dev, stream) computes f from the
- * row-major m x n matrix C (complex64); nufft2_exec_batch and nufft_destroy apply;
+ * row-major m x n matrix C (of the plan's precision); nufft2_exec_batch and nufft_destroy apply;
  * the other exec calls return NUFFT_EUNSUPPORTED on a 2D plan.  nufft2_plan_info
  * reports K_x, gamma_x and L = L_x L_y.  Synchronises `stream`. */
 int nufft2d_plan(nufft_plan *out, int64_t m, int64_t n, int64_t M, const double *x_dev, const double *y_dev,

@@ -350,7 +350,8 @@ class Plan2D:
     """A planned 2D NUFFT-II (section 4, eq. (4.4)) on samples (x_j, y_j).
 
     f_j = sum_{k1<m, k2<n} C[k1, k2] exp(-2 pi i (k1 x_j + k2 y_j)), C an m x n complex64
-    tensor (row-major).  Each direction runs the 1D method at eps / 2.
+    (precision "f32") or complex128 ("f64") tensor (row-major).  Each direction runs the 1D
+    method at eps / 2.
     """
 
     def __init__(self, m, n, x, y, eps, precision="f32", timing=False, device=None):

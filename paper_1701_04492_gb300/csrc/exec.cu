@@ -27,6 +27,11 @@ NUFFT_DECLARE_2D(4)
 NUFFT_DECLARE_2D(8)
 NUFFT_DECLARE_2D(12)
 NUFFT_DECLARE_2D(16)
+NUFFT_DECLARE_COLS_2D_T(double)
+NUFFT_DECLARE_2D_T(double, 4)
+NUFFT_DECLARE_2D_T(double, 8)
+NUFFT_DECLARE_2D_T(double, 12)
+NUFFT_DECLARE_2D_T(double, 16)
 
 namespace {
 
@@ -367,8 +372,8 @@ int plan_unfused_factors(nufft_plan p, cudaStream_t s) {
 }
 
 // The 2D transform (section 4, eq. (4.4)): FP32 plans only.
+template <typename T>
 int exec_forward_2d(nufft_plan p, const void *C, void *f, cudaStream_t s) {
-    using T = float;
     if (p->M == 0) return NUFFT_OK;
     PassArgs<T> a = base_args<T>(p);
     a.in = (const cx<T> *)C;
@@ -396,7 +401,7 @@ int exec_forward_2d(nufft_plan p, const void *C, void *f, cudaStream_t s) {
 
 template <typename T>
 int exec_forward(nufft_plan p, const void *c, void *f, cudaStream_t s) {
-    if (p->dims == 2) return std::is_same<T, float>::value ? exec_forward_2d(p, c, f, s) : NUFFT_EUNSUPPORTED;
+    if (p->dims == 2) return exec_forward_2d<T>(p, c, f, s);
     if (p->M == 0) return NUFFT_OK;
     PassArgs<T> a = base_args<T>(p);
     a.in = (const cx<T> *)c;

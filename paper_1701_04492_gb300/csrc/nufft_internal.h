@@ -39,6 +39,7 @@ struct nufft_plan_s {
     int B2 = 1;            // grid rows per pass-2 bucket
     int NB = 1;            // number of buckets = L2 / B2
     int G = 1;             // ranks staged together in pass 2 (up to K + 1)
+    int G2d = 1;           // 2D row pass: y-ranks transformed and gathered per group
     int nt2 = 1;           // teams per pass-2 CTA (forward: K ranks)
     int nt2d = 1;          // teams per pass-2 CTA in the derivative mode (K + 1 ranks)
     int GA = 1;            // ranks staged together in pass A

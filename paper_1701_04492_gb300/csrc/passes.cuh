@@ -857,9 +857,12 @@ __device__ __forceinline__ void pass2d_body(const PassArgs<T> &a, const BT &beta
     const int team = threadIdx.x / TT, tt = threadIdx.x % TT;
     const int nt = blockDim.x / TT;
     const int K1 = a.K, K2 = a.K2;
+    // the K2 y-ranks of a row are transformed and gathered G2 at a time (all at once
+    // when their slots fit; the FP64 rows of the longest grids take two groups or more)
+    const int G2 = a.G > 0 ? min(a.G, K2) : K2;
     cx<T> *stg = smem;                 // two rows as copied
-    cx<T> *slots = smem + 2 * P1;      // K2 transformed rows
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(slots + K2 * a.S);
+    cx<T> *slots = smem + 2 * P1;      // G2 transformed rows
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(slots + G2 * a.S);
     __shared__ int cta_failed;
     constexpr uint32_t ROW_BYTES = P1 * sizeof(cx<T>);
     const cx<T> *rows = a.Y + (int64_t)b * a.L1;   // W_r1[s1][:] at rows + r1 L
@@ -884,103 +887,117 @@ __device__ __forceinline__ void pass2d_body(const PassArgs<T> &a, const BT &beta
         // this lane's stage twiddles, loaded once for all its row FFTs of this r1
         typename TF::Tw twreg;
         if constexpr (kTwReg<T>) TF::load_tw(twreg, tt, a.twr);
-        auto round = [&](const int j0, auto pred) {   // one r2 per team; PRED: idle teams
-            constexpr bool PRED = decltype(pred)::value;
-            const int r2 = j0 + team;
-            const bool act = !PRED || r2 < K2;
-            cx<T> *sm = slots + (act ? r2 : 0) * a.S;
-            const T *vy = a.vy + (int64_t)(act ? r2 : 0) * P1;
-            cx<T> v[E];
+        for (int g2 = 0; g2 < K2; g2 += G2) {
+            const int gc2 = min(G2, K2 - g2);
+            auto round = [&](const int j0, auto pred) {   // one r2 per team; PRED: idle teams
+                constexpr bool PRED = decltype(pred)::value;
+                const int jj = j0 + team;
+                const bool act = !PRED || jj < gc2;
+                const int r2 = g2 + (act ? jj : 0);
+                cx<T> *sm = slots + (act ? jj : 0) * a.S;
+                const T *vy = a.vy + (int64_t)r2 * P1;
+                cx<T> v[E];
 #pragma unroll
-            for (int m = 0; m < E; ++m) {
-                const int k = tt + TT * m;
-                const cx<T> w = row[k];
-                const T sc = act ? vy[k] : T(0);
-                v[m] = mul_ipow<T>(mk<T>(sc * w.x, sc * w.y), r2);
-            }
-            if constexpr (kTwReg<T>) TF::template run_reg<PRED>(v, tt, sm, twreg, act);
-            else TF::template run<PRED>(v, tt, sm, a.twr, act);
-            if (act) {
-#pragma unroll
-                for (int e = 0; e < E; ++e) sm[TF::out_padded(tt, e)] = v[e];
-            }
-        };
-        for (int j0 = 0; j0 < K2; j0 += nt) {
-            if (j0 + nt <= K2) round(j0, std::false_type{});
-            else round(j0, std::true_type{});
-        }
-        __syncthreads();   // the K2 rows are complete and stg[buf] is no longer read
-        if (threadIdx.x == 0 && r1 + 2 < K1) {
-            fence_proxy_async_smem();
-            mbar_arrive_expect_tx(&mbar[buf], ROW_BYTES);
-            bulk_copy_g2s(stg + buf * P1, rows + (int64_t)(r1 + 2) * a.L, ROW_BYTES, &mbar[buf]);
-        }
-        // software-pipelined: the next sample's t, d^x, d^y and partial sum are loaded
-        // while this one is formed
-        int tn = 0;
-        T dxn = T(0), dyn = T(0);
-        cx<T> accn = mk<T>(0, 0);
-        if (i0 + (int)threadIdx.x < i1) {
-            const int i = i0 + threadIdx.x;
-            tn = a.tsorted[i];
-            dxn = a.dsorted[i];
-            dyn = a.dsorted2[i];
-            if (r1 > 0) accn = a.fscr[i];
-        }
-#pragma unroll 1
-        for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-            const int n1 = tn >> a.lg2;   // t^y
-            const T dx = dxn, dy = dyn;
-            cx<T> acc = accn;
-            if (i + (int)blockDim.x < i1) {
-                const int in = i + blockDim.x;
-                tn = a.tsorted[in];
-                dxn = a.dsorted[in];
-                dyn = a.dsorted2[in];
-                if (r1 > 0) accn = a.fscr[in];
-            }
-            if (!idx_ok(n1 >= 0 && n1 < a.L1, a.err)) continue;
-            // mu^x_r1 = sum_p beta^x_r1p T_p(d^x / gamma_x), mu^y_r2 likewise in y
-            T Tp[KM];
-            const T xi = dx * invg;
-            Tp[0] = T(1);
-            if (KM > 1) Tp[1] = xi;
-#pragma unroll
-            for (int q = 2; q < KM; ++q) Tp[q] = fma(T(2) * xi, Tp[q - 1], -Tp[q - 2]);
-            T mux = T(0);
-#pragma unroll
-            for (int q = 0; q < KM; ++q)
-                if (((q ^ r1) & 1) == 0) mux = fma(beta_at(betax, r1, q), Tp[q], mux);
-            const T eta = dy * invg2;
-            Tp[0] = T(1);
-            if (KM > 1) Tp[1] = eta;
-#pragma unroll
-            for (int q = 2; q < KM; ++q) Tp[q] = fma(T(2) * eta, Tp[q - 1], -Tp[q - 2]);
-            cx<T> S = mk<T>(0, 0);
-#pragma unroll
-            for (int r2 = 0; r2 < KM; ++r2) {
-                if (r2 < K2) {
-                    T mu = T(0);
-#pragma unroll
-                    for (int q = (r2 & 1); q < KM; q += 2) mu = fma(beta_at(betay, r2, q), Tp[q], mu);
-                    const cx<T> x = slots[r2 * a.S + padi<E>(n1)];
-                    S.x = fma(mu, x.x, S.x);
-                    S.y = fma(mu, x.y, S.y);
+                for (int m = 0; m < E; ++m) {
+                    const int k = tt + TT * m;
+                    const cx<T> w = row[k];
+                    const T sc = act ? vy[k] : T(0);
+                    v[m] = mul_ipow<T>(mk<T>(sc * w.x, sc * w.y), r2);
                 }
+                if constexpr (kTwReg<T>) TF::template run_reg<PRED>(v, tt, sm, twreg, act);
+                else TF::template run<PRED>(v, tt, sm, a.twr, act);
+                if (act) {
+#pragma unroll
+                    for (int e = 0; e < E; ++e) sm[TF::out_padded(tt, e)] = v[e];
+                }
+            };
+            for (int j0 = 0; j0 < gc2; j0 += nt) {
+                if (j0 + nt <= gc2) round(j0, std::false_type{});
+                else round(j0, std::true_type{});
             }
-            acc.x = fma(mux, S.x, acc.x);
-            acc.y = fma(mux, S.y, acc.y);
-            if (r1 + 1 < K1) {
-                a.fscr[i] = acc;
-            } else {
-                T sn, cs;
-                sincospi_t<T>(dx + dy, &sn, &cs);
-                const int j = a.perm[i];
-                if (idx_ok(j >= 0 && j < a.M, a.err))
-                    a.out[j] = mk<T>(fma(acc.x, cs, acc.y * sn), fma(acc.y, cs, -acc.x * sn));
+            __syncthreads();   // the group's rows are complete (and, after the last, stg[buf] is read)
+            if (threadIdx.x == 0 && g2 + gc2 == K2 && r1 + 2 < K1) {
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&mbar[buf], ROW_BYTES);
+                bulk_copy_g2s(stg + buf * P1, rows + (int64_t)(r1 + 2) * a.L, ROW_BYTES, &mbar[buf]);
             }
+            // the gather; ONE: all K2 y-ranks in one group (g2 = 0, gc2 = K2), so that its
+            // tests reduce to constants where the group is the whole
+            auto gather = [&](auto one) {
+                constexpr bool ONE = decltype(one)::value;
+                const int gb = ONE ? 0 : g2, ge = ONE ? K2 : g2 + gc2;   // ranks [gb, ge)
+                const bool first = r1 == 0 && (ONE || g2 == 0);   // no partial sum yet
+                const bool fin = r1 + 1 == K1 && (ONE || ge == K2);   // the sums are complete
+                // software-pipelined: the next sample's t, d^x, d^y and partial sum are loaded
+                // while this one is formed
+                int tn = 0;
+                T dxn = T(0), dyn = T(0);
+                cx<T> accn = mk<T>(0, 0);
+                if (i0 + (int)threadIdx.x < i1) {
+                    const int i = i0 + threadIdx.x;
+                    tn = a.tsorted[i];
+                    dxn = a.dsorted[i];
+                    dyn = a.dsorted2[i];
+                    if (!first) accn = a.fscr[i];
+                }
+#pragma unroll 1
+                for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+                    const int n1 = tn >> a.lg2;   // t^y
+                    const T dx = dxn, dy = dyn;
+                    cx<T> acc = accn;
+                    if (i + (int)blockDim.x < i1) {
+                        const int in = i + blockDim.x;
+                        tn = a.tsorted[in];
+                        dxn = a.dsorted[in];
+                        dyn = a.dsorted2[in];
+                        if (!first) accn = a.fscr[in];
+                    }
+                    if (!idx_ok(n1 >= 0 && n1 < a.L1, a.err)) continue;
+                    // mu^x_r1 = sum_p beta^x_r1p T_p(d^x / gamma_x), mu^y_r2 likewise in y
+                    T Tp[KM];
+                    const T xi = dx * invg;
+                    Tp[0] = T(1);
+                    if (KM > 1) Tp[1] = xi;
+#pragma unroll
+                    for (int q = 2; q < KM; ++q) Tp[q] = fma(T(2) * xi, Tp[q - 1], -Tp[q - 2]);
+                    T mux = T(0);
+#pragma unroll
+                    for (int q = 0; q < KM; ++q)
+                        if (((q ^ r1) & 1) == 0) mux = fma(beta_at(betax, r1, q), Tp[q], mux);
+                    const T eta = dy * invg2;
+                    Tp[0] = T(1);
+                    if (KM > 1) Tp[1] = eta;
+#pragma unroll
+                    for (int q = 2; q < KM; ++q) Tp[q] = fma(T(2) * eta, Tp[q - 1], -Tp[q - 2]);
+                    cx<T> S = mk<T>(0, 0);
+#pragma unroll
+                    for (int r2 = 0; r2 < KM; ++r2) {
+                        if (r2 >= gb && r2 < ge) {
+                            T mu = T(0);
+#pragma unroll
+                            for (int q = (r2 & 1); q < KM; q += 2) mu = fma(beta_at(betay, r2, q), Tp[q], mu);
+                            const cx<T> x = slots[(r2 - gb) * a.S + padi<E>(n1)];
+                            S.x = fma(mu, x.x, S.x);
+                            S.y = fma(mu, x.y, S.y);
+                        }
+                    }
+                    acc.x = fma(mux, S.x, acc.x);
+                    acc.y = fma(mux, S.y, acc.y);
+                    if (!fin) {
+                        a.fscr[i] = acc;
+                    } else {
+                        T sn, cs;
+                        sincospi_t<T>(dx + dy, &sn, &cs);
+                        const int j = a.perm[i];
+                        if (idx_ok(j >= 0 && j < a.M, a.err))
+                            a.out[j] = mk<T>(fma(acc.x, cs, acc.y * sn), fma(acc.y, cs, -acc.x * sn));
+                    }
+                }
+            };
+            if (G2 >= K2) gather(std::true_type{});
+            else gather(std::false_type{});
+            __syncthreads();   // the slots are rewritten by the next group
         }
-        __syncthreads();   // the slots are rewritten at the next r1
     }
 }
 
@@ -1284,6 +1301,7 @@ template <typename T, int KM>
 int launch_rows_2d(nufft_plan p, const PassArgs<T> &a0, cudaStream_t s) {
     PassArgs<T> a = a0;
     a.S = p->S2;
+    a.G = p->G2d;   // y-ranks per group
     Beta<T, KM> bx, by;
     for (int r = 0; r < KM; ++r)
         for (int q = 0; q < KM; ++q) {
@@ -1310,6 +1328,10 @@ PassArgs<T> base_args(nufft_plan p);
     extern template int launch_rows<T, KM>(nufft_plan, const PassArgs<T> &, bool, cudaStream_t);
 #define NUFFT_DECLARE_COLS(T) \
     extern template int launch_cols<T>(nufft_plan, const PassArgs<T> &, bool, cudaStream_t);
+#define NUFFT_DECLARE_2D_T(T, KM) \
+    extern template int launch_rows_2d<T, KM>(nufft_plan, const PassArgs<T> &, cudaStream_t);
+#define NUFFT_DECLARE_COLS_2D_T(T) \
+    extern template int launch_cols_2d<T>(nufft_plan, const PassArgs<T> &, cudaStream_t);
 // batched launchers: FP32 only
 #define NUFFT_DECLARE_MANY(KM)                                                                         \
     extern template int launch_rows_many<float, KM>(nufft_plan, const PassArgs<float> *,              \

@@ -491,20 +491,27 @@ int plan_device_2d(nufft_plan p, const double *x, const double *y, cudaStream_t 
     const int km = std::max(p->K, p->K2);
     p->kmax = std::min(KMAX_ALL, ((km + 3) / 4) * 4);
 
-    // geometry: pass 1 from the 1D rules; the row pass holds two row buffers, K2 slots
-    // and two mbarriers, with teams for K2 row FFTs per r1
+    // geometry: pass 1 from the 1D rules; the row pass holds two row buffers, G2d slots
+    // (all K2 y-ranks when they fit, else groups of G2d) and two mbarriers, with teams
+    // for G2d row FFTs per group
     if (int rc = plan_geometry<T>(p)) return rc;
     p->B2 = 1;
     p->NB = p->L2;
     {
         const int E1 = std::min(EmaxT<T, PK_ROW_FWD>::v, p->L1), TT1 = p->L1 / E1;
+        auto bytes = [&](int G) {
+            return ((size_t)2 * p->L1 + (size_t)G * p->S2) * 2 * sizeof(T) + 2 * sizeof(uint64_t);
+        };
+        int G = p->K2;
+        while (G > 1 && bytes(G) > SMEM_BUDGET) --G;
+        if (bytes(G) > SMEM_BUDGET) return NUFFT_EUNSUPPORTED;
+        p->G2d = G;
         const int maxt = std::max(1, 256 / TT1);
-        const int rounds = (p->K2 + maxt - 1) / maxt;
-        int nt = (p->K2 + rounds - 1) / rounds;
+        const int rounds = (G + maxt - 1) / maxt;
+        int nt = (G + rounds - 1) / rounds;
         if (nt * TT1 < 64) nt = std::min(maxt, std::max(nt, (64 + TT1 - 1) / TT1));
         p->nt2 = std::max(1, nt);
-        p->smem2 = ((size_t)2 * p->L1 + (size_t)p->K2 * p->S2) * 2 * sizeof(T) + 2 * sizeof(uint64_t);
-        if (p->smem2 > SMEM_BUDGET) return NUFFT_EUNSUPPORTED;
+        p->smem2 = bytes(G);
     }
 
     int rc = sort_samples<T>(p, s);
@@ -551,7 +558,6 @@ extern "C" int nufft2d_plan(nufft_plan *out, int64_t m, int64_t n, int64_t M, co
     if (prec != NUFFT_F32 && prec != NUFFT_F64) return NUFFT_EINVAL;
     if (M > 0 && (!x_dev || !y_dev)) return NUFFT_EINVAL;
     if (flags & ~NUFFT_PLAN_TIMING) return NUFFT_EINVAL;
-    if (prec != NUFFT_F32) return NUFFT_EUNSUPPORTED;   // the 2D kernels are FP32
     if (m > 2048 || n > 2048) return NUFFT_EUNSUPPORTED;
     int64_t Lx = 32, Ly = 32;
     while (Lx < m) Lx <<= 1;
@@ -567,7 +573,8 @@ extern "C" int nufft2d_plan(nufft_plan *out, int64_t m, int64_t n, int64_t M, co
     if (flags & NUFFT_PLAN_TIMING)
         for (cudaEvent_t &e : p->ev)
             if (cudaEventCreate(&e) != cudaSuccess) { (void)cudaGetLastError(); free_plan(p); return NUFFT_ECUDA; }
-    const int rc = plan_device_2d<float>(p, x_dev, y_dev, (cudaStream_t)stream);
+    const int rc = prec == NUFFT_F32 ? plan_device_2d<float>(p, x_dev, y_dev, (cudaStream_t)stream)
+                                     : plan_device_2d<double>(p, x_dev, y_dev, (cudaStream_t)stream);
     if (rc != NUFFT_OK) { free_plan(p); return rc; }
     *out = p;
     return NUFFT_OK;

@@ -108,11 +108,39 @@ def test_2d_full_size_sampled_rows(api):
     assert _rel2(f[rows], fd) <= 1e-5
 
 
-def test_2d_rejects_fp64_and_unsupported_calls(api):
-    from paper_1701_04492_gb300._lib import NufftError
+@pytest.mark.parametrize("m,n,M,eps", [(64, 64, 5000, 1e-9), (100, 40, 3000, 1e-12), (48, 300, 2000, 1e-14),
+                                       (256, 1024, 1 << 16, 1e-6)])
+def test_2d_fp64_matches_oracle(api, m, n, M, eps):
+    """FP64 (the paper's precision): against the FP64 oracle to rounding and against the
+    direct 2D sum within eps(1 + eps/4) ||C||_1.  At n = 1024 the ten y-ranks' FP64 slots do
+    not all fit in shared memory, so the row pass transforms and gathers them in groups."""
+    x, y = wl.samples_2d_uniform(M, m + 3 * n)
+    r = np.random.default_rng(m * n + 1)
+    C = (r.standard_normal((m, n)) + 1j * r.standard_normal((m, n))) / np.sqrt(2)
+    p = api.Plan2D(m, n, x, y, eps, precision="f64")
+    P = lowrank.plan2d(m, n, x, y, eps, p.Lx, p.Ly)
+    assert (p.Kx, p.Ky) == (P.px.K, P.py.K)
+    f = p.forward(torch.tensor(C, device="cuda")).cpu().numpy()
+    assert _rel2(f, lowrank.nufft2_2d(P, C)) <= 1e-12
+    rows = np.arange(0, M, max(1, M // 40))
+    fd = direct.nudft2_2d(x[rows], y[rows], C)
+    assert np.max(np.abs(f[rows] - fd)) <= (eps * (1 + eps / 4) + 1e-13) * np.sum(np.abs(C))
+
+
+def test_2d_fp32_longest_rows_in_groups(api):
+    """n = 2048 in FP32: the ten y-ranks' slots exceed shared memory, so the row pass
+    works in groups; the result still matches the oracle."""
+    m, n, M = 64, 2048, 20000
+    x, y = wl.samples_2d_uniform(M, 98)
+    C = _coeffs(m, n, 99)
+    p = api.Plan2D(m, n, x, y, 1e-6)
+    P = lowrank.plan2d(m, n, x, y, 1e-6, p.Lx, p.Ly)
+    f = p.forward(torch.tensor(C, device="cuda")).cpu().numpy()
+    assert _rel2(f, lowrank.nufft2_2d(P, C.astype(np.complex128))) <= 1e-5
+
+
+def test_2d_unsupported_calls(api):
     x, y = wl.samples_2d_uniform(100, 97)
-    with pytest.raises(NufftError):
-        api.Plan2D(64, 64, x, y, 1e-6, precision="f64")
     p = api.Plan2D(64, 64, x, y, 1e-6)
     lib = __import__("paper_1701_04492_gb300._lib", fromlist=["load"]).load()
     g = torch.zeros(100, dtype=torch.complex64, device="cuda")
