@@ -107,6 +107,25 @@ enum nufft_status {
 int nufft2_plan(nufft_plan *out, int64_t N, int64_t M, const double *x_dev, double eps,
                 int prec, int64_t L, unsigned flags, void *stream);
 
+/* The autotuner's table (NUFFT_PLAN_AUTOTUNE) across processes.  The choices the
+ * tuner has made in this process -- (device, N, M rounded up to a power of two, eps,
+ * prec, K) -> (L, four-step split, pass-1 tile) -- can be written to a text file and
+ * read back in a later process, whose NUFFT_PLAN_AUTOTUNE plans then take the stored
+ * layouts without timing candidates.  A table is only meaningful on the GPU type that
+ * wrote it.  No GPU call is made.
+ *   nufft_tune_save   writes every entry to `path` (replacing the file).
+ *   nufft_tune_load   merges the entries of a file written by nufft_tune_save (an
+ *                     entry for a key already present replaces it).  A file that is
+ *                     not such a table, or holds an invalid entry (a grid that is not a
+ *                     power of two in range, eps outside (0, 1), ...), merges nothing.
+ *   nufft_tune_clear  empties the table.
+ * entries (may be NULL): the number of entries written, read or present before the
+ * clear.  Returns NUFFT_OK, or NUFFT_EINVAL for a NULL path, a file that cannot be
+ * opened or written, or a malformed table. */
+int nufft_tune_save(const char *path, int64_t *entries);
+int nufft_tune_load(const char *path, int64_t *entries);
+int nufft_tune_clear(int64_t *entries);
+
 /* Plan facts.  Any output pointer may be NULL.  K = rank, gamma = max |d_j|,
  * L = grid size, work_bytes = device memory the plan owns. */
 int nufft2_plan_info(nufft_plan p, int *K, double *gamma, int64_t *L, int64_t *work_bytes);

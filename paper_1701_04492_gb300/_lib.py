@@ -38,6 +38,9 @@ SIGNATURES = {
     "nufft2_exec_dx": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp]),
     "nufft2_exec_deriv": (_i32, [_vp, _vp, _vp, _vp, _vp]),
     "nufft2_grad_x": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp]),
+    "nufft_tune_save": (_i32, [ctypes.c_char_p, ctypes.POINTER(_i64)]),
+    "nufft_tune_load": (_i32, [ctypes.c_char_p, ctypes.POINTER(_i64)]),
+    "nufft_tune_clear": (_i32, [ctypes.POINTER(_i64)]),
     "nufft2_exec_batch": (_i32, [_vp, _i64, _vp, _i64, _vp, _i64, _vp]),
     "nufft1_exec_batch": (_i32, [_vp, _i64, _vp, _i64, _vp, _i64, _vp]),
     "nufft2_exec_deriv_batch": (_i32, [_vp, _i64, _vp, _i64, _vp, _vp, _i64, _vp]),

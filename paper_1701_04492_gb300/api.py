@@ -289,6 +289,28 @@ class Plan:
         return f
 
 
+def tune_save(path):
+    """Write the autotuner's choices of this process to ``path``; returns the entry count."""
+    n = ctypes.c_int64()
+    check(_lib.load().nufft_tune_save(str(path).encode(), ctypes.byref(n)), "nufft_tune_save")
+    return n.value
+
+
+def tune_load(path):
+    """Merge a table written by :func:`tune_save`; later autotuned plans reuse it.
+    Returns the number of entries read."""
+    n = ctypes.c_int64()
+    check(_lib.load().nufft_tune_load(str(path).encode(), ctypes.byref(n)), "nufft_tune_load")
+    return n.value
+
+
+def tune_clear():
+    """Empty the autotuner's table; returns the number of entries it held."""
+    n = ctypes.c_int64()
+    check(_lib.load().nufft_tune_clear(ctypes.byref(n)), "nufft_tune_clear")
+    return n.value
+
+
 class _Nufft2(torch.autograd.Function):
     """f = A(x) c with a hand-written backward: dL/dc = A^H g, dL/dx = Re(conj(g) f').
 

@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdio>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -742,8 +743,85 @@ int plan_autotune(nufft_plan *out, int64_t N, int64_t M, const double *x_dev, do
     return NUFFT_OK;
 }
 
+// The tuner's table as text: a header line, then one entry per line,
+//   device N Mb eps prec K -> L long_cols c1_shift
+// with eps printed to 17 significant digits, so that it reads back to the same double.
+constexpr const char *TUNE_HEADER = "nufft-tune-table 1";
+
+bool tune_entry_ok(const TuneKey &k, const Layout &l) {
+    const bool pow2_L = l.L > 0 && (l.L & (l.L - 1)) == 0;
+    const bool pow2_M = k.Mb > 0 && (k.Mb & (k.Mb - 1)) == 0;
+    return k.device >= 0 && k.N >= 1 && pow2_M && k.eps > 0.0 && k.eps < 1.0 && (k.prec == 0 || k.prec == 1) &&
+           k.K >= 1 && k.K <= KMAX_ALL && pow2_L && l.L >= k.N && l.L >= ((int64_t)1 << LOG2_L_MIN) &&
+           l.L <= ((int64_t)1 << LOG2_L_MAX) && (l.c1_shift == 0 || l.c1_shift == 1);
+}
+
 }  // namespace
 }  // namespace nufft
+
+extern "C" int nufft_tune_save(const char *path, int64_t *entries) {
+    using namespace nufft;
+    if (!path) return NUFFT_EINVAL;
+    std::map<TuneKey, Layout> snap;
+    {
+        std::lock_guard<std::mutex> lk(tune_mu);
+        snap = tune_cache;
+    }
+    FILE *f = std::fopen(path, "w");
+    if (!f) return NUFFT_EINVAL;
+    bool ok = std::fprintf(f, "%s\n", TUNE_HEADER) > 0;
+    for (const auto &e : snap) {
+        const TuneKey &k = e.first;
+        const Layout &l = e.second;
+        ok = ok && std::fprintf(f, "%d %lld %lld %.17g %d %d -> %lld %d %d\n", k.device, (long long)k.N,
+                                (long long)k.Mb, k.eps, k.prec, k.K, (long long)l.L, l.long_cols ? 1 : 0,
+                                l.c1_shift) > 0;
+    }
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) return NUFFT_EINVAL;
+    if (entries) *entries = (int64_t)snap.size();
+    return NUFFT_OK;
+}
+
+extern "C" int nufft_tune_load(const char *path, int64_t *entries) {
+    using namespace nufft;
+    if (!path) return NUFFT_EINVAL;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return NUFFT_EINVAL;
+    char line[512];
+    bool ok = std::fgets(line, sizeof line, f) != nullptr && std::strncmp(line, TUNE_HEADER, std::strlen(TUNE_HEADER)) == 0;
+    std::vector<std::pair<TuneKey, Layout>> got;
+    while (ok && std::fgets(line, sizeof line, f)) {
+        if (line[0] == '\n' || line[0] == '\0') continue;
+        TuneKey k{};
+        Layout l;
+        long long N = 0, Mb = 0, L = 0;
+        int lc = 0;
+        char arrow[4] = {0};
+        const int n = std::sscanf(line, "%d %lld %lld %lf %d %d %3s %lld %d %d", &k.device, &N, &Mb, &k.eps, &k.prec,
+                                  &k.K, arrow, &L, &lc, &l.c1_shift);
+        k.N = N;
+        k.Mb = Mb;
+        l.L = L;
+        l.long_cols = lc == 1;
+        ok = n == 10 && std::strcmp(arrow, "->") == 0 && (lc == 0 || lc == 1) && tune_entry_ok(k, l);
+        if (ok) got.emplace_back(k, l);
+    }
+    std::fclose(f);
+    if (!ok) return NUFFT_EINVAL;   // nothing merged from a malformed table
+    std::lock_guard<std::mutex> lk(tune_mu);
+    for (const auto &e : got) tune_cache[e.first] = e.second;
+    if (entries) *entries = (int64_t)got.size();
+    return NUFFT_OK;
+}
+
+extern "C" int nufft_tune_clear(int64_t *entries) {
+    using namespace nufft;
+    std::lock_guard<std::mutex> lk(tune_mu);
+    if (entries) *entries = (int64_t)tune_cache.size();
+    tune_cache.clear();
+    return NUFFT_OK;
+}
 
 extern "C" int nufft2_plan(nufft_plan *out, int64_t N, int64_t M, const double *x_dev, double eps,
                            int prec, int64_t L, unsigned flags, void *stream) {

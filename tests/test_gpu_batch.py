@@ -221,6 +221,38 @@ def test_autotuned_plan_matches_oracle(api, N, eps):
     assert p2.L == p.L
 
 
+def test_tune_table_carries_choices_to_a_cleared_process_table(api, tmp_path):
+    """The tuner's choices written by nufft_tune_save and read back after a clear make
+    a new autotuned plan take the stored layout; a hand-written choice (here: the
+    oversampled grid) is taken as stored, without timing."""
+    N, eps = 5000, 1e-7
+    x = wl.samples_uniform(N, 53)
+    p = api.Plan(N, x, eps, "f32", autotune=True)
+    path = tmp_path / "tune.txt"
+    assert api.tune_save(path) >= 1
+    api.tune_clear()
+    assert api.tune_load(path) >= 1
+    assert api.Plan(N, wl.samples_uniform(N, 54), eps, "f32", autotune=True).L == p.L
+    # a hand-written entry forcing the grid 2 L0 for another shape
+    N2, M2 = 3000, 3000
+    x2 = wl.samples_uniform(M2, 55)
+    K0 = api.Plan(N2, x2, eps, "f32").K               # the rank on the default grid is the key
+    Mb = 1
+    while Mb < M2:
+        Mb *= 2
+    dev = torch.cuda.current_device()
+    forced = tmp_path / "forced.txt"
+    forced.write_text("nufft-tune-table 1\n%d %d %d %.17g 0 %d -> 8192 0 0\n" % (dev, N2, Mb, eps, K0))
+    assert api.tune_load(forced) == 1
+    q = api.Plan(N2, x2, eps, "f32", autotune=True)
+    assert q.L == 8192
+    c = wl.coeffs_cn(N2, 56).astype(np.complex64)
+    f = q.forward(torch.tensor(c, device="cuda")).cpu().numpy()
+    P = lowrank.plan(N2, x2, eps, 8192)
+    assert _rel2(f, lowrank.nufft2(P, c.astype(np.complex128))) <= TOL_REL["f32"]
+    api.tune_clear()
+
+
 def test_batch_autotuned_matches_oracle(api):
     """The batch tuner may move a class to the grid 2 L0 or the other split; every
     problem still computes its transform (low-rank oracle on the grid it got)."""
