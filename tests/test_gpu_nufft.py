@@ -193,7 +193,10 @@ def test_full_size_against_oracle(api, prec, kind):
     f = plan.forward(_dev(c, _cdt(prec))).cpu().numpy()
     P = lowrank.plan(N, x, 1e-9, plan.L)
     assert _rel2(f, lowrank.nufft2(P, c)) <= TOL_REL[prec]
-    rows = np.random.default_rng(10).choice(N, 256, replace=False)
+    # a seeded subset of rows against the direct sum: 4096 at the benchmark's own
+    # configuration (FP32, perturbed grid), 256 elsewhere
+    nrows = 4096 if (prec, kind) == ("f32", "perturbed") else 256
+    rows = np.random.default_rng(10).choice(N, nrows, replace=False)
     fd = direct.nudft2(x[rows], c)
     tol = (1e-9 + 1e-13) if prec == "f64" else 5e-6
     assert np.max(np.abs(f[rows] - fd)) <= tol * np.sum(np.abs(c))
