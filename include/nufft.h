@@ -107,6 +107,21 @@ enum nufft_status {
 int nufft2_plan(nufft_plan *out, int64_t N, int64_t M, const double *x_dev, double eps,
                 int prec, int64_t L, unsigned flags, void *stream);
 
+/* The planner's rank rule, on the host (no GPU call): the smallest K whose
+ * dropped terms of eq. (2.6), summed with the weights of the primes (the
+ * triangle-inequality bound in the proof of Lemma A.1), are <= eps; capped at Table
+ * 2.1's double-precision row; K = 1 for gamma = 0 (section 2.1.2).  gamma is the
+ * largest |delta_j| of eq. (2.9), in [0, 1/2].  NUFFT_EINVAL for eps outside (0, 1),
+ * gamma outside [0, 1/2] (or NaN), or K NULL. */
+int nufft_rank(double eps, double gamma, int *K);
+
+/* The coefficients of eq. (2.6) (Lemma A.1, eq. (A.1)), on the host: alpha[p*K + r]
+ * for 0 <= p, r < K, with a_pr = i^r alpha_pr,
+ *     alpha_pr = 4 J_{(p+r)/2}(-gamma pi / 2) J_{(r-p)/2}(-gamma pi / 2)   (p - r even),
+ * 0 otherwise; J_n by its power series.  alpha: K*K doubles, caller-owned.
+ * NUFFT_EINVAL for K outside 1..64, gamma outside [0, 1/2], or alpha NULL. */
+int nufft_lowrank_coeffs(int K, double gamma, double *alpha);
+
 /* The autotuner's table (NUFFT_PLAN_AUTOTUNE) across processes.  The choices the
  * tuner has made in this process -- (device, N, M rounded up to a power of two, eps,
  * prec, K) -> (L, four-step split, pass-1 tile) -- can be written to a text file and

@@ -38,6 +38,8 @@ SIGNATURES = {
     "nufft2_exec_dx": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp]),
     "nufft2_exec_deriv": (_i32, [_vp, _vp, _vp, _vp, _vp]),
     "nufft2_grad_x": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp]),
+    "nufft_rank": (_i32, [_dbl, _dbl, ctypes.POINTER(_i32)]),
+    "nufft_lowrank_coeffs": (_i32, [_i32, _dbl, ctypes.POINTER(_dbl)]),
     "nufft_tune_save": (_i32, [ctypes.c_char_p, ctypes.POINTER(_i64)]),
     "nufft_tune_load": (_i32, [ctypes.c_char_p, ctypes.POINTER(_i64)]),
     "nufft_tune_clear": (_i32, [ctypes.POINTER(_i64)]),

@@ -289,6 +289,13 @@ class Plan:
         return f
 
 
+def rank(eps, gamma):
+    """The planner's rank for accuracy eps and perturbation gamma = max |delta_j| (host)."""
+    K = ctypes.c_int()
+    check(_lib.load().nufft_rank(float(eps), float(gamma), ctypes.byref(K)), "nufft_rank")
+    return K.value
+
+
 def tune_save(path):
     """Write the autotuner's choices of this process to ``path``; returns the entry count."""
     n = ctypes.c_int64()

@@ -110,3 +110,17 @@ void twiddle(int64_t n, int64_t m, double *c, double *s) {
 }
 
 }  // namespace nufft
+
+// ---- host-only entry points (no GPU call) -----------------------------------------
+
+extern "C" int nufft_rank(double eps, double gamma, int *K) {
+    if (!K || !(eps > 0.0 && eps < 1.0) || !(gamma >= 0.0 && gamma <= 0.5)) return NUFFT_EINVAL;
+    *K = nufft::choose_rank(eps, gamma);
+    return NUFFT_OK;
+}
+
+extern "C" int nufft_lowrank_coeffs(int K, double gamma, double *alpha) {
+    if (!alpha || K < 1 || K > 64 || !(gamma >= 0.0 && gamma <= 0.5)) return NUFFT_EINVAL;
+    nufft::chebyshev_alpha(K, gamma, alpha);
+    return NUFFT_OK;
+}
