@@ -16,7 +16,8 @@ from . import workloads  # noqa: F401
 
 def __getattr__(name):
     # the torch binding is imported on first use, so `workloads` stays light
-    if name in ("Plan", "nufft2", "NufftError", "api"):
+    if name in ("Plan", "Plan2D", "Batch", "nufft2", "NufftError", "api", "rank", "tune_save", "tune_load",
+                "tune_clear"):
         import importlib
         api = importlib.import_module(__name__ + ".api")
         return api if name == "api" else getattr(api, name)
