@@ -50,7 +50,7 @@ enum nufft_status {
     NUFFT_EINVAL = -1,        /* bad argument: size, eps, null pointer, non-finite x */
     NUFFT_ENOMEM = -2,        /* device or host allocation failed */
     NUFFT_ECUDA = -3,         /* a CUDA call failed (no device, launch error, ...) */
-    NUFFT_EUNSUPPORTED = -4,  /* size beyond what this build handles */
+    NUFFT_EUNSUPPORTED = -4,  /* a size or mode beyond the library's limits */
     NUFFT_ESTATE = -5,        /* call needs a plan option that was not set */
     NUFFT_ETIMEOUT = -6,      /* a bounded device-side wait gave up (see nufft2_check) */
     NUFFT_ECHECK = -7         /* an index check failed (builds with NUFFT_CHECK; see nufft2_check) */
