@@ -57,3 +57,36 @@ def test_argument_errors_without_gpu(lib):
     assert lib.nufft_destroy(None) == 0
     msgs = [lib.nufft_strerror(code) for code in (0, -1, -2, -3, -4, -5, -6, -7)]
     assert all(msgs) and len(set(msgs)) == len(msgs)       # every status has its own message
+
+
+def test_argument_errors_of_the_other_entry_families(lib):
+    """The 2D plan, the batch plan, the inverse and the no-allocation forward reject bad
+    arguments before any device work (so this runs without a GPU)."""
+    h = ctypes.c_void_p()
+    p2 = lib.nufft2d_plan
+    assert p2(None, 64, 64, 0, None, None, 1e-6, 0, 0, None) == -1                    # out NULL
+    assert p2(ctypes.byref(h), 0, 64, 0, None, None, 1e-6, 0, 0, None) == -1          # m < 1
+    assert p2(ctypes.byref(h), 64, 0, 0, None, None, 1e-6, 0, 0, None) == -1          # n < 1
+    assert p2(ctypes.byref(h), 64, 64, -1, None, None, 1e-6, 0, 0, None) == -1        # M < 0
+    assert p2(ctypes.byref(h), 64, 64, 0, None, None, 0.0, 0, 0, None) == -1          # eps
+    assert p2(ctypes.byref(h), 64, 64, 0, None, None, 1e-6, 2, 0, None) == -1         # precision
+    assert p2(ctypes.byref(h), 64, 64, 5, None, None, 1e-6, 0, 0, None) == -1         # x, y NULL
+    assert p2(ctypes.byref(h), 64, 64, 0, None, None, 1e-6, 0, 4, None) == -1         # flag
+    assert p2(ctypes.byref(h), 4096, 64, 0, None, None, 1e-6, 0, 0, None) == -4       # m > 2048
+    assert h.value is None
+    b = ctypes.c_void_p()
+    n = (ctypes.c_int64 * 2)(1024, 2048)
+    m = (ctypes.c_int64 * 2)(10, 20)
+    e = (ctypes.c_double * 2)(1e-6, 1e-9)
+    pm = lib.nufft2_plan_many
+    assert pm(None, 2, n, m, None, None, e, 0, 0, None) == -1                          # out NULL
+    assert pm(ctypes.byref(b), 0, n, m, None, None, e, 0, 0, None) == -1               # count < 1
+    assert pm(ctypes.byref(b), 2, None, m, None, None, e, 0, 0, None) == -1            # N NULL
+    assert pm(ctypes.byref(b), 2, n, m, None, None, e, 0, 0, None) == -1               # x NULL, M > 0
+    assert pm(ctypes.byref(b), 2, n, m, None, None, e, 3, 0, None) == -1               # precision
+    assert pm(ctypes.byref(b), 2, n, m, None, None, e, 0, 1, None) == -1               # flag
+    assert b.value is None
+    it, rr = ctypes.c_int(), ctypes.c_double()
+    assert lib.nufft2_inverse(None, None, None, 1e-9, 10, ctypes.byref(it), ctypes.byref(rr), None) == -1
+    assert lib.nufft2_exec_noalloc(0, 4, None, 1e-6, None, None, None) == -1          # N < 1
+    assert lib.nufft2_exec_noalloc(1 << 20, 4, None, 1e-6, None, None, None) in (-1, -4)
