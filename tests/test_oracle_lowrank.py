@@ -57,6 +57,47 @@ def test_rank_within_eq_2_7(eps, gamma):
     assert lowrank.choose_K(eps, gamma) <= lowrank.lambert_w_rank(eps, gamma)
 
 
+def _eq_2_7_root(eps, gamma):
+    """The u > 5 gamma with u log(u / (5 gamma)) = log(140 / eps), by bisection.
+
+    With z = log(140/eps) / (5 gamma) and u = 5 gamma e^{W(z)}: W(z) = log(u / (5 gamma))
+    and W e^W = z give u log(u / (5 gamma)) = log(140 / eps), i.e. 140 (5 gamma / u)^u = eps,
+    the bound in the proof of Lemma A.1 solved for the rank.  No Lambert W is evaluated,
+    so this pins the oracle's use of W (its branch, its argument) from outside."""
+    lo, hi = 5.0 * gamma, 1e4
+    target = math.log(140.0 / eps)
+    for _ in range(300):
+        mid = 0.5 * (lo + hi)
+        if mid * math.log(mid / (5.0 * gamma)) > target:
+            hi = mid
+        else:
+            lo = mid
+    return hi
+
+
+@pytest.mark.parametrize("eps", [1e-2, 1e-4, 1e-9, 1e-12, 1e-14, 2.2e-16])
+@pytest.mark.parametrize("gamma", [1 / 64, 1 / 32, 1 / 8, 0.25, 0.3, 0.5])
+def test_eq_2_7_against_its_defining_equation(eps, gamma):
+    """lambert_w_rank is eq. (2.7): max{3, ceil(u)} for the root u of the bound it inverts."""
+    u = _eq_2_7_root(eps, gamma)
+    assert lowrank.lambert_w_rank(eps, gamma) == max(3, math.ceil(u))
+    # the root does satisfy 140 (5 gamma / u)^u = eps
+    assert math.isclose(140.0 * (5.0 * gamma / u) ** u, eps, rel_tol=1e-9)
+
+
+def test_eq_2_7_hand_values():
+    """Eq. (2.7) evaluated by hand at gamma = 1/2: for eps = 1e-9, log(140/eps) = 25.665;
+    u = 14.564 solves u log(u / 2.5) = 25.665 (14.564 x 1.7623 = 25.666), so K = 15.  The
+    same at eps = 1e-4 (u = 10.12: 10.12 x 1.3983 = 14.152 = log(1.4e6)) gives K = 11, and the
+    floor of 3 applies where u < 3 (eps = 1e-2, gamma = 1/64: u = 2.70)."""
+    assert lowrank.lambert_w_rank(1e-9, 0.5) == 15
+    assert lowrank.lambert_w_rank(1e-4, 0.5) == 11
+    assert lowrank.lambert_w_rank(1e-2, 1 / 64) == 3
+    # a plausible slip, log in place of W, gives another rank at the metric workload
+    z = math.log(140.0 / 1e-9) / 2.5
+    assert max(3, math.ceil(2.5 * math.exp(math.log(z)))) != 15
+
+
 def test_rank_at_the_metric_workload():
     # gamma -> 1/2, eps = 1e-9: K = 12, and 11 does not suffice.
     assert lowrank.choose_K(1e-9, 0.5) == 12
