@@ -7,6 +7,9 @@
  *   nudft2h  c_k = sum_j g_j exp(+2 pi i x_j k)          the adjoint A^H g
  *   nudft2d  f_j = sum_k (-2 pi i k) c_k exp(-2 pi i x_j k)   (d f_j / d x_j)
  *   nudft2_2d f_j = sum_{k1<m,k2<n} C[k1][k2] exp(-2 pi i (k1 x_j + k2 y_j))  (eq. (4.1))
+ *   nudft2h_at     c_k for a list of frequencies k: the adjoint sum at chosen outputs
+ *   nudft2h_2d_at  C[k1][k2] = sum_j g_j exp(+2 pi i (k1 x_j + k2 y_j)) for a list of
+ *                  (k1, k2): the adjoint of eq. (4.1) at chosen outputs
  *
  * The phase x_j k is reduced modulo 1 exactly: with Q = 2^32, x (mod 1) =
  * (s + r) / Q where s = floor(Q x) is an integer and r in [0,1) is exact (Q is a
@@ -132,5 +135,50 @@ void nudft2_2d(int64_t m, int64_t n, int64_t M, const double *x, const double *y
         }
         f[2 * j] = re.s + re.c;
         f[2 * j + 1] = im.s + im.c;
+    }
+}
+
+void nudft2h_at(int64_t nk, const int64_t *ks, int64_t M, const double *x, const double *g, double *c) {
+    #pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t q = 0; q < nk; ++q) {
+        const int64_t k = ks[q];
+        acc_t re = {0, 0}, im = {0, 0};
+        for (int64_t j = 0; j < M; ++j) {
+            uint64_t s; double r;
+            split_x(x[j], &s, &r);
+            double th = TWO_PI * frac_xk(s, r, k);
+            double cs = cos(th), sn = sin(th);          /* exp(+i th) */
+            double gr = g[2 * j], gi = g[2 * j + 1];
+            acc_add(&re, gr * cs);
+            acc_add(&re, -gi * sn);
+            acc_add(&im, gr * sn);
+            acc_add(&im, gi * cs);
+        }
+        c[2 * q] = re.s + re.c;
+        c[2 * q + 1] = im.s + im.c;
+    }
+}
+
+void nudft2h_2d_at(int64_t nk, const int64_t *k1s, const int64_t *k2s, int64_t M, const double *x,
+                   const double *y, const double *g, double *C) {
+    #pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t q = 0; q < nk; ++q) {
+        const int64_t k1 = k1s[q], k2 = k2s[q];
+        acc_t re = {0, 0}, im = {0, 0};
+        for (int64_t j = 0; j < M; ++j) {
+            uint64_t sx, sy; double rx, ry;
+            split_x(x[j], &sx, &rx);
+            split_x(y[j], &sy, &ry);
+            double th = frac_xk(sx, rx, k1) + frac_xk(sy, ry, k2);
+            th = TWO_PI * (th - floor(th));
+            double cs = cos(th), sn = sin(th);          /* exp(+i th) */
+            double gr = g[2 * j], gi = g[2 * j + 1];
+            acc_add(&re, gr * cs);
+            acc_add(&re, -gi * sn);
+            acc_add(&im, gr * sn);
+            acc_add(&im, gi * cs);
+        }
+        C[2 * q] = re.s + re.c;
+        C[2 * q + 1] = im.s + im.c;
     }
 }

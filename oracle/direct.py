@@ -45,6 +45,10 @@ def _load():
             getattr(lib, name).restype = None
         lib.nudft2_2d.argtypes = [i64, i64, i64, p, p, p, p]
         lib.nudft2_2d.restype = None
+        lib.nudft2h_at.argtypes = [i64, p, i64, p, p, p]
+        lib.nudft2h_at.restype = None
+        lib.nudft2h_2d_at.argtypes = [i64, p, p, i64, p, p, p, p]
+        lib.nudft2h_2d_at.restype = None
         _lib = lib
     return _lib
 
@@ -73,6 +77,16 @@ def nudft2_adjoint(x, g, N):
     return c
 
 
+def nudft2_adjoint_at(x, g, ks):
+    """c_k = sum_j g_j exp(+2 pi i x_j k) at the listed frequencies ks (the adjoint of
+    eq. (1.2) at chosen outputs, for sizes where all N outputs would take too long)."""
+    x, g = _f64(x), _c128(g)
+    ks = np.ascontiguousarray(ks, dtype=np.int64)
+    c = np.empty(ks.size, dtype=np.complex128)
+    _load().nudft2h_at(ks.size, ks.ctypes.data, x.size, x.ctypes.data, g.ctypes.data, c.ctypes.data)
+    return c
+
+
 def nudft2_deriv(x, c):
     """f'_j = sum_k (-2 pi i k) c_k exp(-2 pi i x_j k) = d f_j / d x_j."""
     x, c = _f64(x), _c128(c)
@@ -88,3 +102,19 @@ def nudft2_2d(x, y, C):
     f = np.empty(x.size, dtype=np.complex128)
     _load().nudft2_2d(m, n, x.size, x.ctypes.data, y.ctypes.data, C.ctypes.data, f.ctypes.data)
     return f
+
+
+def nudft2_2d_adjoint(x, y, g, m, n, k1s=None, k2s=None):
+    """C[k1, k2] = sum_j g_j exp(+2 pi i (k1 x_j + k2 y_j)): the conjugate transpose of
+    nudft2_2d (eq. (4.1)).  With k1s, k2s (equal-length index lists) only those entries
+    are formed and returned as a vector; otherwise the whole m x n matrix."""
+    x, y, g = _f64(x), _f64(y), _c128(g)
+    full = k1s is None
+    if full:
+        k1s, k2s = np.meshgrid(np.arange(m), np.arange(n), indexing="ij")
+    k1s = np.ascontiguousarray(np.ravel(k1s), dtype=np.int64)
+    k2s = np.ascontiguousarray(np.ravel(k2s), dtype=np.int64)
+    out = np.empty(k1s.size, dtype=np.complex128)
+    _load().nudft2h_2d_at(k1s.size, k1s.ctypes.data, k2s.ctypes.data, x.size, x.ctypes.data, y.ctypes.data,
+                          g.ctypes.data, out.ctypes.data)
+    return out.reshape(int(m), int(n)) if full else out

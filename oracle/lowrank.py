@@ -291,6 +291,26 @@ def nufft2_2d(P, C):
     return f
 
 
+def nufft2_2d_adjoint(P, g):
+    """C = A^H g for the A of nufft2_2d: every step of eq. (4.4) conjugated and reversed.
+
+    For each (r1, r2): Z[tau_x, tau_y] = sum_{j: (t^x_j, t^y_j) = (tau_x, tau_y)}
+    conj(u^x_r1(j) u^y_r2(j)) g_j, then the conjugate 2D DFT (F2^H z = Lx Ly ifft2(z)),
+    cut to the m x n frequencies and scaled by v^x_r1(k1) v^y_r2(k2) (real); the terms
+    are summed.  Section 3.1 gives the 1D transpose; this is its 2D, conjugated form.
+    """
+    g = np.asarray(g, dtype=np.complex128)
+    px, py = P.px, P.py
+    C = np.zeros((P.m, P.n), dtype=np.complex128)
+    for r1 in range(px.K):
+        for r2 in range(py.K):
+            Z = np.zeros((px.L, py.L), dtype=np.complex128)
+            np.add.at(Z, (px.t, py.t), np.conj(px.U[:, r1] * py.U[:, r2]) * g)
+            Y = np.fft.ifft2(Z) * (px.L * py.L)
+            C += px.V[:, r1][:, None] * Y[:P.m, :P.n] * py.V[:, r2][None, :]
+    return C
+
+
 # ---------------------------------------------------------------------------
 # Inverse NUFFT-II (section 3.3): CG on the normal equations
 # ---------------------------------------------------------------------------

@@ -374,6 +374,75 @@ def test_2d_planted_phase_sign_breaks_the_bound(monkeypatch):
     assert np.max(np.abs(f - direct.nudft2_2d(x, y, C))) > 1e-3 * np.sum(np.abs(C))
 
 
+@pytest.mark.parametrize("m,n", [(16, 24), (40, 8)])
+@pytest.mark.parametrize("eps", [1e-4, 1e-12])
+def test_2d_adjoint_within_bound_of_direct_sum(m, n, eps):
+    """The 2D adjoint against the direct conjugate sum of eq. (4.1): each entry of A^H - A_K^H
+    is the conjugate of an entry of A - A_K, so |dC|_max <= (eps (1 + eps/4) + rounding) ||g||_1."""
+    M = 300
+    x, y = wl.samples_2d_uniform(M, 170 + m)
+    g = wl.cotangent_cn(M, 171 + n)
+    P = lowrank.plan2d(m, n, x, y, eps)
+    C = lowrank.nufft2_2d_adjoint(P, g)
+    Cd = direct.nudft2_2d_adjoint(x, y, g, m, n)
+    assert np.max(np.abs(C - Cd)) <= (eps * (1 + eps / 4) + 1e-13) * np.sum(np.abs(g))
+
+
+@pytest.mark.parametrize("Lx,Ly", [(None, None), (64, 32)])
+def test_2d_adjoint_identity(Lx, Ly):
+    """<A C, g> = <C, A^H g> for the oracle's own forward and adjoint (the same factors)."""
+    m, n, M = 24, 20, 400
+    x, y = wl.samples_2d_uniform(M, 172)
+    C = wl.coeffs_cn(m * n, 173).reshape(m, n)
+    g = wl.cotangent_cn(M, 174)
+    P = lowrank.plan2d(m, n, x, y, 1e-9, Lx, Ly)
+    f = lowrank.nufft2_2d(P, C)
+    ah = lowrank.nufft2_2d_adjoint(P, g)
+    assert abs(np.vdot(g, f) - np.vdot(ah, C)) <= 1e-13 * np.linalg.norm(f) * np.linalg.norm(g)
+
+
+def test_2d_adjoint_single_column_is_the_1d_adjoint():
+    """n = 1: C[:, 0] = sum_j g_j exp(+2 pi i k1 x_j), the 1D adjoint sum in x."""
+    m, M = 64, 150
+    x, y = wl.samples_2d_uniform(M, 175)
+    g = wl.cotangent_cn(M, 176)
+    P = lowrank.plan2d(m, 1, x, y, 1e-10)
+    C = lowrank.nufft2_2d_adjoint(P, g)
+    assert C.shape == (m, 1)
+    assert np.max(np.abs(C[:, 0] - direct.nudft2_adjoint(x, g, m))) <= 1.1e-10 * np.sum(np.abs(g))
+
+
+@pytest.mark.parametrize("what", ["phase_sign", "no_conj"])
+def test_2d_adjoint_planted_mistakes_break_the_bound(monkeypatch, what):
+    """A planted phase sign, or factors used without their conjugate, fail the direct pin."""
+    m, n, M = 16, 16, 100
+    x, y = wl.samples_2d_uniform(M, 177)
+    g = wl.cotangent_cn(M, 178)
+    if what == "phase_sign":
+        monkeypatch.setattr(lowrank, "phase", lambda d: np.exp(1j * np.pi * np.asarray(d)))
+    else:
+        monkeypatch.setattr(lowrank.np, "conj", lambda v: np.asarray(v))
+    P = lowrank.plan2d(m, n, x, y, 1e-9)
+    C = lowrank.nufft2_2d_adjoint(P, g)
+    monkeypatch.undo()
+    assert np.max(np.abs(C - direct.nudft2_2d_adjoint(x, y, g, m, n))) > 1e-3 * np.sum(np.abs(g))
+
+
+def test_direct_adjoint_at_chosen_outputs_is_the_full_sum():
+    """The subset forms of the direct adjoint sums return the matching entries of the full ones."""
+    M, N, m, n = 200, 96, 12, 10
+    x, y = wl.samples_2d_uniform(M, 179)
+    g = wl.cotangent_cn(M, 180)
+    ks = np.array([0, 1, 50, 95])
+    assert np.array_equal(direct.nudft2_adjoint_at(x, g, ks), direct.nudft2_adjoint(x, g, N)[ks])
+    Cf = direct.nudft2_2d_adjoint(x, y, g, m, n)
+    k1, k2 = np.array([0, 11, 3]), np.array([9, 0, 4])
+    assert np.array_equal(direct.nudft2_2d_adjoint(x, y, g, m, n, k1, k2), Cf[k1, k2])
+    # and the full 2D adjoint is the conjugate transpose of the dense 2D matrix
+    A = np.exp(-2j * np.pi * (np.outer(x, np.repeat(np.arange(m), n)) + np.outer(y, np.tile(np.arange(n), m))))
+    assert np.max(np.abs(Cf.ravel() - A.conj().T @ g)) <= 1e-12 * np.sum(np.abs(g))
+
+
 # ---- inverse NUFFT-II (section 3.3) -------------------------------------------------
 
 def test_toeplitz_product_is_the_dense_normal_matrix():
