@@ -39,8 +39,9 @@ EPS = 1e-9
 SEED = 2024
 FLUSH_BYTES = 512 << 20
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP32 ALU peak: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2070 MHz (maximum SM clock)
-SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+# the nominal FP32 rate (context only): SMs x 128 FP32 lanes x 2 flops (FMA) x the maximum
+# SM clock; the roofline's denominator is the rate measured by nufft_fp32_fma_peak
+FP32_LANES = 128
 
 
 def _dist():
@@ -290,13 +291,17 @@ def run_ours(args):
         flops["pass1_deriv"] = 5.0 * (K + 1) * L * np.log2(L2) + 2.0 * (K + 1) * N
         flops["pass2_deriv"] = 5.0 * (K + 1) * L * np.log2(L1) + 8.0 * (2 * K + 1) * M
         dom = max(("pass1_deriv", "pass2_deriv", "passA", "passB"), key=lambda k: kavg[k])
-        peak_tf = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        peak = measure_fp32_peak(dev)
+        peak_tf = peak["tflops"]
         ach = flops[dom] / (kavg[dom] * 1e-3) / 1e12
         traffic = committed_traffic(dom)
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s",
                 "frac": ach / peak_tf, "traffic": traffic,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
-                "flops_per_launch": flops[dom]}
+                "peak_source": "measured (of measured): " + peak["how"],
+                "peak_measurement": peak,
+                "frac_of_nominal": ach / peak["nominal_tflops"],
+                "flops_per_launch": flops[dom],
+                "alu_frac_per_kernel": {k: flops[k] / (kavg[k] * 1e-3) / 1e12 / peak_tf for k in kavg}}
         hbm = json.load(open(PEAKS_PATH))["hbm_gbs"] if os.path.exists(PEAKS_PATH) else 6800.0
         if traffic is not None:
             # the DRAM bytes ncu counted for one launch (cold L2) over its measured time
@@ -308,6 +313,7 @@ def run_ours(args):
             "bytes_per_point": 24, "fwd_GBps": 24.0 * M / fwd_s / 1e9,
             "frac_of_measured_hbm": 24.0 * M / fwd_s / 1e9 / hbm, "hbm_peak_GBps": hbm}
         del tplan
+        extra["peak_tflops_fp32"] = peak_tf
 
         # end to end through the API with host buffers: H2D c, g; fwd + bwd; D2H f, gc, gx
         ch = torch.tensor(c_np).pin_memory()
@@ -338,7 +344,7 @@ def run_ours(args):
         line.update(extra)
         if not args.no_batch:
             line["batch_c5"] = batch_c5(api, dev, timed, args.steps)
-            line["nufft2d_c3"] = bench_2d(api, dev, timed, args.steps)
+            line["nufft2d_c3"] = bench_2d(api, dev, timed, args.steps, peak_tf)
             line["inverse"] = bench_inverse(api, dev)
             line["worst_grid_e3"] = worst_grid_sweep(api, dev, timed, args.steps)
             line["autograd_c4"] = bench_autograd_c4(api, dev, timed, args.steps)
@@ -362,6 +368,38 @@ def job_throughput(local_ms, ws, units_per_rank, device):
         dist.all_reduce(tot, op=dist.ReduceOp.MAX)
     total_ms = float(tot.item())
     return total_ms, ws * units_per_rank / (total_ms * 1e-3) / 1e9
+
+
+def measure_fp32_peak(dev, seconds=2.0):
+    """The FP32 FMA rate of this GPU, measured: nufft_fp32_fma_peak (two 1024-thread CTAs
+    per SM, 16 independent FMA chains per thread) launched back to back for about
+    `seconds`, each launch timed by CUDA events; the median launch gives TFLOP/s.  The SM
+    clock is sampled meanwhile, so the figure comes with the clock it was measured at."""
+    import ctypes
+    import torch
+    from paper_1701_04492_gb300 import _lib
+    lib = _lib.load()
+    stream = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+    ms, fl = ctypes.c_float(), ctypes.c_double()
+    _lib.check(lib.nufft_fp32_fma_peak(1000, 2, stream, ctypes.byref(ms), ctypes.byref(fl)), "fma peak")
+    iters = max(1000, int(1000 * 0.2 / max(ms.value * 1e-3, 1e-6)))   # about 0.2 s per launch
+    props = torch.cuda.get_device_properties(dev)
+    uuid = "GPU-" + str(props.uuid)
+    rates = []
+    with ClockSampler(uuid) as clk:
+        clk.wait_first(lambda: lib.nufft_fp32_fma_peak(1000, 2, stream, ctypes.byref(ms), ctypes.byref(fl)))
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < seconds or len(rates) < 3:
+            _lib.check(lib.nufft_fp32_fma_peak(iters, 2, stream, ctypes.byref(ms), ctypes.byref(fl)), "fma peak")
+            rates.append(fl.value / (ms.value * 1e-3) / 1e12)
+    c = clk.summary()
+    sms = props.multi_processor_count
+    nominal = sms * FP32_LANES * 2 * (c["sm_max_mhz"] or 2070.0) * 1e6 / 1e12
+    return {"tflops": float(np.median(rates)), "launches": len(rates), "ms_per_launch": float(ms.value),
+            "sm_mhz_median": c["sm_mhz"], "sm_max_mhz": c["sm_max_mhz"], "clock_reasons": c["reasons"],
+            "sms": sms, "nominal_tflops": nominal,
+            "how": "nufft_fp32_fma_peak: %d SMs x 2 CTAs x 1024 threads x 16 FMA chains, %d launches of "
+                   "%.0f ms, median, CUDA events" % (sms, len(rates), ms.value)}
 
 
 def batch_c5(api, dev, timed, steps):
@@ -408,7 +446,7 @@ def batch_c5(api, dev, timed, steps):
     return out
 
 
-def bench_2d(api, dev, timed, steps):
+def bench_2d(api, dev, timed, steps, peak_tf=None):
     """The 2D workload of section 4: m = n = 1024, M = 2^20 uniform samples in [0,1)^2,
     eps = 1e-6 (K_x = K_y = 10 at eps/2), C[k1][k2] ~ CN(0,1)/(1 + k1^2 + k2^2)^(1/2)
     complex64; forward Gpts/s with per-pass device times and algorithmic flops."""
@@ -434,7 +472,8 @@ def bench_2d(api, dev, timed, steps):
     L = Lx * Ly
     fl_cols = 5.0 * Kx * L * np.log2(Lx) + 2.0 * Kx * m * n
     fl_rows = 5.0 * Kx * Ky * L * np.log2(Ly) + 8.0 * Kx * Ky * M
-    peak_tf = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    if peak_tf is None:
+        peak_tf = measure_fp32_peak(dev)["tflops"]
     return {"workload": "2D NUFFT-II m=n=1024, M=2^20 uniform (x,y), eps=1e-6, C~CN(0,1)/sqrt(1+k1^2+k2^2) complex64",
             "Kx": Kx, "Ky": Ky, "fwd_gpts": M * len(ms) / (sum(ms) * 1e-3) / 1e9, "fwd_ms": float(np.mean(ms)),
             "plan_s": plan_s, "kernel_ms": {"cols": k1, "rows": k2},
@@ -516,32 +555,88 @@ def bench_autograd_c4(api, dev, timed, steps):
             "gpu_launches_per_step": 5}   # batched forward+f' (2), batched adjoint (2), dL/dx summed (1)
 
 
+def _oracle_worker(L, seconds, steps, warmup, ready, start, out):
+    """One process of the CPU baseline: plan the workload with the oracle (untimed), run
+    `warmup` steps, report ready, wait for the common start, then run fwd+bwd steps of the
+    oracle as it stands -- exactly `steps` of them, or (steps = 0) as many as fit in
+    `seconds` -- and report (steps done, seconds taken)."""
+    sys.path.insert(0, ROOT)
+    from oracle import lowrank
+    N, x, c_np, g_np = _workload()
+    c, g = c_np.astype(np.complex128), g_np.astype(np.complex128)
+    P = lowrank.plan(N, x, EPS, L)
+
+    def step():
+        f = lowrank.nufft2(P, c)
+        lowrank.nufft2_adjoint(P, f)
+        lowrank.nufft2_dx(P, c, g)
+    for _ in range(warmup):
+        step()
+    ready.put(P.K)
+    start.wait()
+    t0 = time.perf_counter()
+    n = 0
+    while (n < steps) if steps > 0 else (n < 1 or time.perf_counter() - t0 < seconds):
+        step()
+        n += 1
+    out.put((n, time.perf_counter() - t0))
+
+
+def oracle_pool(L, seconds=10.0, steps=0, warmup=0, procs=None):
+    """The oracle on every host core: `procs` (default: all cores) spawned processes, each
+    running the whole workload's fwd+bwd steps single-threaded (BLAS and OpenMP limited to
+    one thread each), started together.  Throughput = all the points they processed over
+    the slowest one's time.  Spawned, not forked, so the GPU context of this process is
+    not inherited."""
+    import multiprocessing as mp
+    procs = procs or os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    ready, out, start = ctx.Queue(), ctx.Queue(), ctx.Event()
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        ps = [ctx.Process(target=_oracle_worker, args=(L, seconds, steps, warmup, ready, start, out))
+              for _ in range(procs)]
+        for p in ps:
+            p.start()
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    K = [ready.get(timeout=900) for _ in ps][0]
+    start.set()
+    res = [out.get(timeout=1800) for _ in ps]
+    for p in ps:
+        p.join(timeout=60)
+    n_tot = sum(n for n, _ in res)
+    wall = max(dt for _, dt in res)
+    return {"steps_total": n_tot, "wall_s": wall, "procs": procs, "K": K,
+            "gpts": (1 << N_LOG2) * n_tot / wall / 1e9, "steps_per_proc": [n for n, _ in res]}
+
+
 def cpu_baseline(plan, c_np, g_np, x, f_gpu):
-    """The oracle as it stands, one FP64 fwd+bwd step at a time on this host, for
-    about 10-20 s; also the GPU result's error against it."""
+    """The oracle as it stands on all of this host's cores, for about 10 s (see
+    oracle_pool); also the GPU result's error against the oracle."""
     from oracle import lowrank
     N = c_np.size
     c = c_np.astype(np.complex128)
-    g = g_np.astype(np.complex128)
     P = lowrank.plan(N, x, EPS, plan.L)
-    f_cpu = None
-    t0 = time.perf_counter()
-    n = 0
-    while True:
-        f_cpu = lowrank.nufft2(P, c)
-        lowrank.nufft2_adjoint(P, f_cpu)
-        lowrank.nufft2_dx(P, c, g)
-        n += 1
-        if time.perf_counter() - t0 > 10.0 or n >= 3:
-            break
-    dt = time.perf_counter() - t0
+    f_cpu = lowrank.nufft2(P, c)
     fg = f_gpu.cpu().numpy().astype(np.complex128)
     err2 = float(np.linalg.norm(fg - f_cpu) / np.linalg.norm(f_cpu))
     errinf = float(np.max(np.abs(fg - f_cpu)) / np.sum(np.abs(c)))
-    return {"value": x.size * n / dt / 1e9, "unit": "Gpts/s", "cores": 1, "kind": "oracle",
-            "sample": "%d full fwd+bwd step(s) of the same workload (N=M=2^20, K=%d) in numpy FP64 "
-                      "(single-threaded FFT), plan excluded" % (n, P.K),
-            "gpu_f32_fwd_rel2_err_vs_oracle": err2, "gpu_f32_fwd_inf_err_over_c1": errinf}
+    pool = oracle_pool(plan.L, seconds=10.0)
+    return {"value": pool["gpts"], "unit": "Gpts/s", "cores": pool["procs"], "nproc": os.cpu_count(),
+            "kind": "oracle",
+            "sample": "%d processes (one per host core), each running full fwd+bwd steps of the same workload "
+                      "(N=M=2^20, K=%d) with the numpy FP64 oracle, single-threaded, for about 10 s: %d steps in "
+                      "%.1f s, plan excluded" % (pool["procs"], P.K, pool["steps_total"], pool["wall_s"]),
+            "gpu_f32_fwd_rel2_err_vs_oracle": err2, "gpu_f32_fwd_inf_err_over_c1": errinf,
+            "eps_note": "the FP32 path's error is set by FP32 rounding: its infinity-norm error over ||c||_1 "
+                        "is the number above, next to eps = 1e-9"}
 
 
 # ---------------------------------------------------------------------------------
@@ -549,34 +644,28 @@ def cpu_baseline(plan, c_np, g_np, x, f_gpu):
 # ---------------------------------------------------------------------------------
 
 def run_reference(args):
+    """The reference arm: the oracle as it stands on all host cores.  One step = every
+    process runs one full fwd+bwd step of the workload (so a step processes procs x M
+    points); `steps` timed steps after `warmup` untimed ones, the slowest process's time."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
     from oracle import lowrank
-    N, x, c_np, g_np = _workload()
-    c = c_np.astype(np.complex128)
-    g = g_np.astype(np.complex128)
-    P = lowrank.plan(N, x, EPS, None if N >= 1024 else 1024)
-
-    def step():
-        f = lowrank.nufft2(P, c)
-        lowrank.nufft2_adjoint(P, f)
-        lowrank.nufft2_dx(P, c, g)
-
-    for _ in range(args.warmup):
-        step()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step()
-    dt = time.perf_counter() - t0
-    v = x.size * args.steps / dt / 1e9
+    N, x, _, _ = _workload()
+    gamma = float(np.max(np.abs(lowrank.round_to_grid(x, N)[2])))
+    pool = oracle_pool(N, steps=args.steps, warmup=args.warmup, procs=args.cpu_procs)
+    v = pool["gpts"]
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Gpts/s", "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": pool["wall_s"] / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": workload_config(N, x.size, P.K, P.gamma, P.L, ws),
-            "cpu_baseline": {"value": v, "unit": "Gpts/s", "cores": 1, "kind": "oracle",
-                             "sample": "full fwd+bwd steps of the workload in numpy FP64, plan excluded"},
+            "config": workload_config(N, x.size, pool["K"], gamma, N, ws),
+            "cpu_baseline": {"value": v, "unit": "Gpts/s", "cores": pool["procs"], "nproc": os.cpu_count(),
+                             "kind": "oracle",
+                             "sample": "%d processes (one per host core), each running full fwd+bwd steps of the "
+                                       "workload with the numpy FP64 oracle, single-threaded; a step is one such "
+                                       "step in every process (%d x M points), plan excluded"
+                                       % (pool["procs"], pool["procs"])},
             "e2e": {"value": v, "unit": "Gpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -588,6 +677,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-procs", type=int, default=None,
+                    help="processes of the oracle in the CPU baseline and the reference arm (default: all cores)")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-problem batch measurement")
     ap.add_argument("--only", choices=["step", "fwd", "adj", "dx", "batch"], default=None,
                     help="profiling mode: run only this operation warmup+steps times, untimed "

@@ -254,20 +254,23 @@ int nufft_kernel_times(nufft_plan p, float *ms_out, int cap, int *count);
 /* The forward transform without a plan and without any device allocation, for
  * callers that cannot call cudaMalloc (code running inside another allocator's
  * callbacks, plug-ins whose host forbids device allocation, latency-critical
- * paths).  The paper has no counterpart: it is a packaging of eq. (2.11) (FP32
- * exec, the same rank rule and factors as nufft2_plan + nufft2_exec) that keeps
- * every intermediate in one fixed device array compiled into the library
- * (about 17 MiB, held by each GPU that loads the library until exit).
+ * paths).  The paper has no counterpart.  It computes what nufft2_plan (FP32) +
+ * nufft2_exec compute, with the same rank rule and factors, and keeps every
+ * intermediate in one fixed device array compiled into the library (about 17 MiB,
+ * held by each GPU that loads the library until exit).
  *   N, M   1 <= N <= 65536, 0 <= M <= 65536; larger sizes return
  *          NUFFT_EUNSUPPORTED (they do not fit the fixed array).
  *   x_dev  M doubles (device), finite, as for nufft2_plan.
  *   eps    working accuracy, 0 < eps < 1.
  *   c_dev  N complex64 (device).   f_dev  M complex64 (device, written).
- * The first call on a device looks up that array's device address; make it before
- * any stream capture.  Every call uses the same array, so calls whose GPU work
- * overlaps (other streams, other threads) race; serialise them.  Synchronises
- * `stream` once (to read gamma).  Errors: NUFFT_EINVAL, NUFFT_EUNSUPPORTED,
- * NUFFT_ECUDA. */
+ * The first call on a device looks up that array's device address.  Every call uses
+ * the same array, so calls whose GPU work overlaps (other streams, other threads)
+ * race; serialise them.  Synchronises `stream` twice (to read gamma, and at the end to
+ * read the device error word), so it cannot be called inside a stream capture or
+ * recorded into a CUDA graph.  Errors: NUFFT_EINVAL, NUFFT_EUNSUPPORTED, NUFFT_ECUDA;
+ * NUFFT_ETIMEOUT when a bounded device-side wait gave up and NUFFT_ECHECK when an index
+ * check failed (libnufft_check.so), as nufft2_check reports them for a plan: f is then
+ * invalid. */
 int nufft2_exec_noalloc(int64_t N, int64_t M, const double *x_dev, double eps, const void *c_dev,
                         void *f_dev, void *stream);
 
@@ -429,6 +432,16 @@ int nufft_test_wait_timeout(void *stream);
  * recorded and skipped instead of made), whether an index check failed:
  * NUFFT_ECHECK; else NUFFT_OK.  Clears the condition. */
 int nufft2_check(nufft_plan p, void *stream);
+
+/* ---- Measurement ----------------------------------------------------------------
+ * No counterpart in the paper.  The exec kernels are bound by the plain FP32 pipes (FFT
+ * butterflies, factor recurrences), so their roofline is reported against the FP32 FMA
+ * rate of the device, measured by this kernel: blocks_per_sm (1 or 2) CTAs of 1024
+ * threads per SM, each thread running 16 independent FMA chains for 8 * iters steps.
+ * Writes the kernel's device time (CUDA events on `stream`) to *ms_out and the flops it
+ * did (2 per FMA) to *flop_out; synchronises `stream`.  iters >= 1.  Errors:
+ * NUFFT_EINVAL, NUFFT_ECUDA. */
+int nufft_fp32_fma_peak(int64_t iters, int blocks_per_sm, void *stream, float *ms_out, double *flop_out);
 
 /* Human-readable name of a status code. */
 const char *nufft_strerror(int code);

@@ -54,6 +54,7 @@ SIGNATURES = {
     "nufft2_check": (_i32, [_vp, _vp]),
     "nufft2_exec_noalloc": (_i32, [_i64, _i64, _vp, _dbl, _vp, _vp, _vp]),
     "nufft_strerror": (ctypes.c_char_p, [_i32]),
+    "nufft_fp32_fma_peak": (_i32, [_i64, _i32, _vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_dbl)]),
     "nufft_test_fail_alloc": (_i32, [_i32]),
     "nufft_test_wait_timeout": (_i32, [_vp]),
     "nufft2_inverse": (_i32, [_vp, _vp, _vp, _dbl, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_dbl), _vp]),

@@ -76,6 +76,9 @@ class Plan:
         check(rc, "nufft2_plan")
         self._h = h
         self.eps = float(eps)
+        # the samples the plan was built on: nufft2(..., plan=...) checks that it is given these
+        self._x = x
+        self._x_seen = set()
         K, g, Lo, wb = ctypes.c_int(), ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
         check(lib.nufft2_plan_info(h, ctypes.byref(K), ctypes.byref(g), ctypes.byref(Lo), ctypes.byref(wb)),
               "nufft2_plan_info")
@@ -362,13 +365,31 @@ class _Nufft2(torch.autograd.Function):
         return gc, gx, None
 
 
+def _check_plan_samples(plan, x):
+    """Raise ValueError unless x holds the samples `plan` was built on.  A stale plan would
+    give wrong values and gradients silently.  A tensor already found equal is remembered
+    by (storage address, version counter), so a training loop that passes the same x pays
+    for one comparison (a device sync) and not one per step."""
+    if x.numel() != plan.M:
+        raise ValueError("x has %d samples, the plan was built on %d" % (x.numel(), plan.M))
+    key = (x.data_ptr(), x._version, str(x.device))
+    if key in plan._x_seen:
+        return
+    xs = x.detach().to(device=plan.device, dtype=torch.float64).reshape(-1)
+    if not torch.equal(xs, plan._x):
+        raise ValueError("the plan was built on other samples than x: build a new plan for these x")
+    plan._x_seen.add(key)
+
+
 def nufft2(c, x, eps=1e-9, plan=None, L=0):
     """Differentiable NUFFT-II: f_j = sum_k c_k exp(-2 pi i x_j k) for c of shape (N,)
     or (B, N) (complex64 -> FP32 exec, complex128 -> FP64 exec) and samples x (float64).
-    Gradients flow to c and x.  Pass a prebuilt ``plan`` to reuse it (it must have
-    been built on the same x)."""
+    Gradients flow to c and x.  Pass a prebuilt ``plan`` to reuse it; it must have been
+    built on the same x (checked: ValueError otherwise)."""
     if plan is None:
         plan = Plan(c.shape[-1], x.detach(), eps, precision=c.dtype, L=L, device=c.device)
+    else:
+        _check_plan_samples(plan, x)
     return _Nufft2.apply(c, x, plan)
 
 

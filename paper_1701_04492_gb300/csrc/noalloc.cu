@@ -10,8 +10,9 @@
 //
 // The host never dereferences g_scratch: on the first call on each device, with
 // that device current, cudaGetSymbolAddress gives its device address, which is
-// cached per device and passed to the kernels.  That first call should come before
-// any stream capture.  Every call reuses the same array (it keeps the previous
+// cached per device and passed to the kernels.  Every call synchronises its stream
+// (to read gamma, and at the end to read the error word), so no call can be made
+// inside a stream capture.  Every call reuses the same array (it keeps the previous
 // call's contents; the words that must start at zero are cleared on each call),
 // so calls whose work overlaps on the GPU race with each other.
 #include <cuda_runtime.h>
@@ -295,5 +296,12 @@ extern "C" int nufft2_exec_noalloc(int64_t N, int64_t M, const double *x_dev, do
         case 12: rc = gather_launch<12>(X, t, d, M, pl.L, pl.K, a.inv_gamma, pl.beta, (float2 *)f_dev, s); break;
         default: rc = gather_launch<16>(X, t, d, M, pl.L, pl.K, a.inv_gamma, pl.beta, (float2 *)f_dev, s); break;
     }
-    return rc;
+    if (rc) return rc;
+    // the passes' bounded waits and (NUFFT_CHECK builds) index checks report into the
+    // error word; the caller has no plan to ask, so it is read here, once the work is done
+    int h = 0;
+    NUFFT_CUDA_TRY(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    NUFFT_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h) return (h & ERR_TIMEOUT) ? NUFFT_ETIMEOUT : NUFFT_ECHECK;
+    return NUFFT_OK;
 }

@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <type_traits>
 
 #include "async_copy.cuh"
@@ -1128,16 +1129,19 @@ int dispatch_P_many(int P, F &&f) {
     }
 }
 
-// Opt a kernel into more than 48 KB of dynamic shared memory, once per device.
+// Opt a kernel into more than 48 KB of dynamic shared memory, once per device.  The
+// flags are atomics: two threads that plan at once may both set the attribute (the same
+// value, harmless), but neither reads a torn flag.
+using SmemFlags = std::atomic<int>[64];
 template <typename K>
-inline int set_smem(K kern, size_t bytes, int device, int *done) {
-    if (bytes > 48 * 1024 && device >= 0 && device < 64 && !done[device]) {
+inline int set_smem(K kern, size_t bytes, int device, std::atomic<int> *done) {
+    if (bytes > 48 * 1024 && device >= 0 && device < 64 && !done[device].load(std::memory_order_acquire)) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(SMEM_BUDGET + 16 * 1024)) != cudaSuccess) {
             (void)cudaGetLastError();
             return NUFFT_ECUDA;
         }
-        done[device] = 1;
+        done[device].store(1, std::memory_order_release);
     }
     return NUFFT_OK;
 }
@@ -1181,7 +1185,7 @@ int launch_cols(nufft_plan p, const PassArgs<T> &a0, bool adjoint, cudaStream_t 
         cols_fields<T>(p, a, adjoint);
         const size_t smem = adjoint ? p->smemB : p->smem1;
         const dim3 block(a.C * TT);
-        static int done_b[64] = {}, done_1[64] = {};
+        static SmemFlags done_b{}, done_1{};
         if (adjoint) {
             auto kern = k_passB<T, P>;
             if (int rc = set_smem(kern, smem, p->device, done_b)) return rc;
@@ -1214,7 +1218,7 @@ int launch_rows(nufft_plan p, const PassArgs<T> &a0, bool adjoint, cudaStream_t 
         const int nt = adjoint ? p->ntA : (a.nranks > p->K ? p->nt2d : p->nt2);
         const size_t smem2 = p->smem2;
         const dim3 block(nt * TT);
-        static int done_a[64] = {}, done_2[64] = {};
+        static SmemFlags done_a{}, done_2{};
         if (adjoint) {
             auto kern = k_passA<T, P, KM>;
             if (int rc = set_smem(kern, p->smemA, p->device, done_a)) return rc;
@@ -1241,7 +1245,7 @@ int launch_cols_many(nufft_plan rep, const PassArgs<T> *args, int nprob, int ny,
         const int C = adjoint ? rep->CB : rep->C1;
         const size_t smem = adjoint ? rep->smemB : rep->smem1;
         const dim3 grid(rep->L1 / C, ny, nprob), block(C * TT);
-        static int done_b[64] = {}, done_1[64] = {};
+        static SmemFlags done_b{}, done_1{};
         if (adjoint) {
             auto kern = k_passB_many<T, P>;
             if (int rc = set_smem(kern, smem, rep->device, done_b)) return rc;
@@ -1264,7 +1268,7 @@ int launch_rows_many(nufft_plan rep, const PassArgs<T> *args, const Beta<T, KM> 
         const int nt = adjoint ? rep->ntA : rep->nt2;
         const size_t smem = adjoint ? rep->smemA : rep->smem2;
         const dim3 grid(rep->NB, 1, nprob), block(nt * TT);
-        static int done_a[64] = {}, done_2[64] = {};
+        static SmemFlags done_a{}, done_2{};
         if (adjoint) {
             auto kern = k_passA_many<T, P, KM>;
             if (int rc = set_smem(kern, smem, rep->device, done_a)) return rc;
@@ -1287,7 +1291,7 @@ int launch_cols_2d(nufft_plan p, const PassArgs<T> &a0, cudaStream_t s) {
     return dispatch_P(p->L2, [&](auto PC) -> int {
         constexpr int P = decltype(PC)::value;
         constexpr int TT = P / e_of<T, P, PK_COL_FWD>();
-        static int done[64] = {};
+        static SmemFlags done{};
         auto kern = k_pass1_2d<T, P>;
         if (int r = set_smem(kern, p->smem1, p->device, done)) return r;
         kern<<<dim3(p->L1 / a.C, p->K), dim3(a.C * TT), p->smem1, s>>>(a);
@@ -1311,7 +1315,7 @@ int launch_rows_2d(nufft_plan p, const PassArgs<T> &a0, cudaStream_t s) {
     return dispatch_P(p->L1, [&](auto PC) -> int {
         constexpr int P = decltype(PC)::value;
         constexpr int TT = P / e_of<T, P, PK_ROW_FWD>();
-        static int done[64] = {};
+        static SmemFlags done{};
         auto kern = k_pass2d<T, P, KM>;
         if (int r = set_smem(kern, p->smem2, p->device, done)) return r;
         kern<<<dim3(p->L2), dim3(p->nt2 * TT), p->smem2, s>>>(a, bx, by);

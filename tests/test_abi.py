@@ -55,6 +55,10 @@ def test_argument_errors_without_gpu(lib):
     assert lib.nufft2_exec_batch(None, 1, None, 1, None, 1, None) == -1
     assert lib.nufft2_plan_info(None, None, None, None, None) == -1
     assert lib.nufft_destroy(None) == 0
+    ms, fl = ctypes.c_float(), ctypes.c_double()
+    assert lib.nufft_fp32_fma_peak(0, 1, None, ctypes.byref(ms), ctypes.byref(fl)) == -1      # iters < 1
+    assert lib.nufft_fp32_fma_peak(10, 3, None, ctypes.byref(ms), ctypes.byref(fl)) == -1     # blocks per SM
+    assert lib.nufft_fp32_fma_peak(10, 1, None, None, ctypes.byref(fl)) == -1
     msgs = [lib.nufft_strerror(code) for code in (0, -1, -2, -3, -4, -5, -6, -7)]
     assert all(msgs) and len(set(msgs)) == len(msgs)       # every status has its own message
 

@@ -13,6 +13,7 @@ torch = pytest.importorskip("torch")
 
 from oracle import direct, lowrank  # noqa: E402
 from paper_1701_04492_gb300 import workloads as wl  # noqa: E402
+from parity import assert_close  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -45,7 +46,7 @@ def test_2d_matches_oracle(api, m, n, M, eps):
     assert p.gamma_x == P.px.gamma and p.gamma_y == P.py.gamma
     f = p.forward(torch.tensor(C, device="cuda")).cpu().numpy()
     fo = lowrank.nufft2_2d(P, C.astype(np.complex128))
-    assert _rel2(f, fo) <= 1e-5
+    assert_close(f, fo, "f32", what="2d")
     rows = np.arange(0, M, max(1, M // 50))
     fd = direct.nudft2_2d(x[rows], y[rows], C.astype(np.complex128))
     bound = max(eps * (1 + eps / 4), 5e-6) * np.sum(np.abs(C))
@@ -78,6 +79,7 @@ def test_2d_on_grid_is_the_2d_fft(api):
     f = p.forward(torch.tensor(C, device="cuda")).cpu().numpy()
     ref = np.fft.fft2(C.astype(np.complex128))[s, t]
     assert _rel2(f, ref) <= 1e-6
+    assert_close(f, ref, "f32", what="on-grid 2D FFT")
 
 
 def test_2d_deterministic_and_empty(api):
@@ -121,7 +123,7 @@ def test_2d_fp64_matches_oracle(api, m, n, M, eps):
     P = lowrank.plan2d(m, n, x, y, eps, p.Lx, p.Ly)
     assert (p.Kx, p.Ky) == (P.px.K, P.py.K)
     f = p.forward(torch.tensor(C, device="cuda")).cpu().numpy()
-    assert _rel2(f, lowrank.nufft2_2d(P, C)) <= 1e-12
+    assert_close(f, lowrank.nufft2_2d(P, C), "f64", scale=10, what="2d f64")
     rows = np.arange(0, M, max(1, M // 40))
     fd = direct.nudft2_2d(x[rows], y[rows], C)
     assert np.max(np.abs(f[rows] - fd)) <= (eps * (1 + eps / 4) + 1e-13) * np.sum(np.abs(C))
@@ -136,7 +138,7 @@ def test_2d_fp32_longest_rows_in_groups(api):
     p = api.Plan2D(m, n, x, y, 1e-6)
     P = lowrank.plan2d(m, n, x, y, 1e-6, p.Lx, p.Ly)
     f = p.forward(torch.tensor(C, device="cuda")).cpu().numpy()
-    assert _rel2(f, lowrank.nufft2_2d(P, C.astype(np.complex128))) <= 1e-5
+    assert_close(f, lowrank.nufft2_2d(P, C.astype(np.complex128)), "f32", what="2d groups")
 
 
 def test_2d_unsupported_calls(api):

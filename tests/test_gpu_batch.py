@@ -15,6 +15,7 @@ torch = pytest.importorskip("torch")
 
 from oracle import direct, lowrank  # noqa: E402
 from paper_1701_04492_gb300 import workloads as wl  # noqa: E402
+from parity import assert_close  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -66,7 +67,7 @@ def test_batch_forward_matches_single_plans_and_oracle(api, prec):
         assert np.array_equal(f[m0:m1], fi), i        # the same arithmetic, bit for bit
         P = lowrank.plan(N[i], xs[i], eps[i], int(b.L[i]))
         fo = lowrank.nufft2(P, c[n0:n1])
-        assert _rel2(f[m0:m1], fo) <= TOL_REL[prec], i
+        assert_close(f[m0:m1], fo, prec, what=str(i))
         rows = np.arange(0, m1 - m0, max(1, (m1 - m0) // 16))
         fd = direct.nudft2(xs[i][rows], c[n0:n1])
         bound = max(eps[i], 5e-6 if prec == "f32" else 1e-13) * np.sum(np.abs(c[n0:n1]))
@@ -94,7 +95,7 @@ def test_batch_adjoint_matches_single_plans_and_oracle(api, prec):
             assert _rel2(cc[n0:n1], ci) <= 1e-6, i
         P = lowrank.plan(N[i], xs[i], eps[i], int(b.L[i]))
         co = lowrank.nufft2_adjoint(P, g[m0:m1].astype(np.complex128))
-        assert _rel2(cc[n0:n1], co) <= TOL_REL[prec], i
+        assert_close(cc[n0:n1], co, prec, what=str(i))
 
 
 def test_batch_each_and_per_problem_match_batched(api):
@@ -196,11 +197,11 @@ def test_long_columns_split_matches_oracle(api, N, prec):
     f = p.forward(c_dev).cpu().numpy()
     P = lowrank.plan(N, x, 1e-9, L)
     fo = lowrank.nufft2(P, c.astype(np.complex128))
-    assert _rel2(f, fo) <= TOL_REL[prec]
+    assert_close(f, fo, prec, what="oracle")
     assert _rel2(f, q.forward(c_dev).cpu().numpy()) <= TOL_REL[prec]
     g = wl.cotangent_cn(N, 42).astype(NPC[prec])
     ca = p.adjoint(torch.tensor(g, device="cuda")).cpu().numpy()
-    assert _rel2(ca, lowrank.nufft2_adjoint(P, g.astype(np.complex128))) <= TOL_REL[prec]
+    assert_close(ca, lowrank.nufft2_adjoint(P, g.astype(np.complex128)), prec, what="oracle")
 
 
 @pytest.mark.parametrize("N,eps", [(1500, 1e-12), (5000, 1e-7), (40000, 1e-4), (1 << 16, 1e-9)])
@@ -215,7 +216,7 @@ def test_autotuned_plan_matches_oracle(api, N, eps):
     f = p.forward(torch.tensor(c, device="cuda")).cpu().numpy()
     P = lowrank.plan(N, x, eps, p.L)
     assert P.K == p.K
-    assert _rel2(f, lowrank.nufft2(P, c.astype(np.complex128))) <= TOL_REL["f32"]
+    assert_close(f, lowrank.nufft2(P, c.astype(np.complex128)), "f32", what="oracle")
     # the cached choice: a second plan of the same shape takes the same layout
     p2 = api.Plan(N, wl.samples_uniform(N, 52), eps, "f32", autotune=True)
     assert p2.L == p.L
@@ -249,7 +250,7 @@ def test_tune_table_carries_choices_to_a_cleared_process_table(api, tmp_path):
     c = wl.coeffs_cn(N2, 56).astype(np.complex64)
     f = q.forward(torch.tensor(c, device="cuda")).cpu().numpy()
     P = lowrank.plan(N2, x2, eps, 8192)
-    assert _rel2(f, lowrank.nufft2(P, c.astype(np.complex128))) <= TOL_REL["f32"]
+    assert_close(f, lowrank.nufft2(P, c.astype(np.complex128)), "f32", what="oracle")
     api.tune_clear()
 
 
@@ -271,8 +272,8 @@ def test_batch_autotuned_matches_oracle(api):
             continue
         P = lowrank.plan(N[i], xs[i], eps[i], int(b.L[i]))
         assert P.K == b.K[i]
-        assert _rel2(f[m0:m1], lowrank.nufft2(P, c[n0:n1])) <= TOL_REL["f32"], i
-        assert _rel2(cc[n0:n1], lowrank.nufft2_adjoint(P, g[m0:m1].astype(np.complex128))) <= TOL_REL["f32"], i
+        assert_close(f[m0:m1], lowrank.nufft2(P, c[n0:n1]), "f32", what=str(i))
+        assert_close(cc[n0:n1], lowrank.nufft2_adjoint(P, g[m0:m1].astype(np.complex128)), "f32", what=str(i))
 
 
 @pytest.mark.parametrize("N,long_cols", [(2048, False), (3000, True), (1 << 15, False), (1 << 17, True)])
@@ -289,7 +290,7 @@ def test_half_tile_matches_oracle(api, N, long_cols):
     c = wl.coeffs_cn(N, 44).astype(np.complex64)
     f = p.forward(torch.tensor(c, device="cuda")).cpu().numpy()
     P = lowrank.plan(N, x, 1e-9, L)
-    assert _rel2(f, lowrank.nufft2(P, c.astype(np.complex128))) <= TOL_REL["f32"]
+    assert_close(f, lowrank.nufft2(P, c.astype(np.complex128)), "f32", what="oracle")
     g = wl.cotangent_cn(N, 45).astype(np.complex64)
     ca = p.adjoint(torch.tensor(g, device="cuda")).cpu().numpy()
-    assert _rel2(ca, lowrank.nufft2_adjoint(P, g.astype(np.complex128))) <= TOL_REL["f32"]
+    assert_close(ca, lowrank.nufft2_adjoint(P, g.astype(np.complex128)), "f32", what="oracle")

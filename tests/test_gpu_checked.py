@@ -92,6 +92,20 @@ def _child():
     c, it, rr = p.inverse(f, tol=1e-12)
     assert rr <= 1e-12 and it > 1
     p.check()
+    # the forward without a plan or device allocation: its return code carries the checks
+    import ctypes
+    lib = _lib.load()
+    for N, M in [(2048, 3001), (1000, 777)]:
+        x = wl.samples_uniform(M, 95)
+        c = wl.coeffs_cn(N, 96).astype(np.complex64)
+        xd = torch.tensor(x, dtype=torch.float64, device=dev)
+        cd = torch.tensor(c, device=dev)
+        f = torch.empty(M, dtype=torch.complex64, device=dev)
+        rc = lib.nufft2_exec_noalloc(N, M, ctypes.c_void_p(xd.data_ptr()), 1e-9, ctypes.c_void_p(cd.data_ptr()),
+                                     ctypes.c_void_p(f.data_ptr()), api._stream(0))
+        assert rc == 0, _lib.STATUS.get(rc, rc)
+        P = lowrank.plan(N, x, 1e-9, api.Plan(N, x, 1e-9, "f32").L)
+        assert _rel2(f.cpu().numpy(), lowrank.nufft2(P, c.astype(np.complex128))) <= 1e-5
     print("CHECKED-OK")
 
 

@@ -29,14 +29,19 @@ def test_rejects_sizes_beyond_the_fixed_array():
 
 
 @pytest.mark.gpu
+# odd log2 L (2048, 32768) splits the grid into rows and columns of different lengths,
+# with their own stage tables; "equispaced" is x_j = j/N, gamma = 0 and K = 1
 @pytest.mark.parametrize("N,M,kind,eps", [(4096, 5000, "uniform", 1e-9), (65536, 65536, "perturbed", 1e-6),
-                                          (1000, 777, "uniform", 1e-12), (3, 9, "uniform", 1e-4)])
+                                          (1000, 777, "uniform", 1e-12), (3, 9, "uniform", 1e-4),
+                                          (2048, 3001, "uniform", 1e-9), (32768, 40000, "perturbed", 1e-12),
+                                          (4096, 4096, "equispaced", 1e-9)])
 def test_matches_planned_path_twice(N, M, kind, eps):
     torch = pytest.importorskip("torch")
     from oracle import lowrank
     from paper_1701_04492_gb300.api import Plan
     lib = _lib.load()
-    x = wl.samples_uniform(M, 77) if kind == "uniform" else wl.samples_perturbed(M, 77, 0.5)
+    x = {"uniform": lambda: wl.samples_uniform(M, 77), "perturbed": lambda: wl.samples_perturbed(M, 77, 0.5),
+         "equispaced": lambda: wl.samples_equispaced(N)}[kind]()
     c = wl.coeffs_cn(N, 77).astype(np.complex64)
     xd = torch.tensor(x, dtype=torch.float64, device="cuda")
     cd = torch.tensor(c, device="cuda")
@@ -53,3 +58,6 @@ def test_matches_planned_path_twice(N, M, kind, eps):
     P = lowrank.plan(N, x, eps, plan.L)
     fo = lowrank.nufft2(P, c.astype(np.complex128))
     assert np.linalg.norm(got - fo) <= TOL_F32 * np.linalg.norm(fo)
+    if kind == "equispaced":
+        assert P.K == 1 and plan.K == 1
+        assert np.linalg.norm(got - np.fft.fft(c.astype(np.complex128))) <= TOL_F32 * np.linalg.norm(fo)
