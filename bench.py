@@ -219,7 +219,7 @@ def run_ours(args):
         return
     if args.only:
         # profiling mode: only the named operation, no extra measurements
-        op = {"step": step, "fwd": lambda: plan.forward(c, f), "adj": lambda: plan.adjoint(f, gc),
+        op = {"step": step, "fwd": lambda: plan.forward(c, f), "adj": lambda: plan.adjoint(g, gc),
               "dx": lambda: plan.dx(c, g, gx)}[args.only]
         for _ in range(args.warmup + args.steps):
             op()
@@ -462,12 +462,19 @@ def bench_2d(api, dev, timed, steps, peak_tf=None):
     p = api.Plan2D(m, n, x, y, 1e-6, device=dev, timing=True)
     torch.cuda.synchronize(dev)
     plan_s = time.perf_counter() - t0
+    g = torch.tensor(wl.cotangent_cn(M, SEED).astype(np.complex64), device=dev)
+    Ca = torch.empty((m, n), dtype=torch.complex64, device=dev)
     ms = timed(lambda: p.forward(C, f), steps, 3)
-    kt = []
+    msa = timed(lambda: p.adjoint(g, Ca), steps, 3)
+    kt, kta = [], []
     for _ in range(steps):
         p.forward(C, f)
         kt.append(p.kernel_times())
+        p.adjoint(g, Ca)
+        kta.append(p.kernel_times())
     k1, k2 = float(np.median([k[0] for k in kt])), float(np.median([k[1] for k in kt]))
+    a_rows, a_cols = float(np.median([k[0] for k in kta])), float(np.median([k[1] for k in kta]))
+    p.check()
     Kx, Ky, Lx, Ly = p.Kx, p.Ky, p.Lx, p.Ly
     L = Lx * Ly
     fl_cols = 5.0 * Kx * L * np.log2(Lx) + 2.0 * Kx * m * n
@@ -476,9 +483,12 @@ def bench_2d(api, dev, timed, steps, peak_tf=None):
         peak_tf = measure_fp32_peak(dev)["tflops"]
     return {"workload": "2D NUFFT-II m=n=1024, M=2^20 uniform (x,y), eps=1e-6, C~CN(0,1)/sqrt(1+k1^2+k2^2) complex64",
             "Kx": Kx, "Ky": Ky, "fwd_gpts": M * len(ms) / (sum(ms) * 1e-3) / 1e9, "fwd_ms": float(np.mean(ms)),
-            "plan_s": plan_s, "kernel_ms": {"cols": k1, "rows": k2},
-            "alu_frac": {"cols": fl_cols / (k1 * 1e-3) / 1e12 / peak_tf, "rows": fl_rows / (k2 * 1e-3) / 1e12 / peak_tf},
-            "launches_per_fwd": 2}
+            "adj_gpts": M * len(msa) / (sum(msa) * 1e-3) / 1e9, "adj_ms": float(np.mean(msa)),
+            "plan_s": plan_s, "kernel_ms": {"cols": k1, "rows": k2, "adj_rows": a_rows, "adj_cols": a_cols},
+            "alu_frac": {"cols": fl_cols / (k1 * 1e-3) / 1e12 / peak_tf, "rows": fl_rows / (k2 * 1e-3) / 1e12 / peak_tf,
+                         "adj_rows": fl_rows / (a_rows * 1e-3) / 1e12 / peak_tf,
+                         "adj_cols": fl_cols / (a_cols * 1e-3) / 1e12 / peak_tf},
+            "launches_per_fwd": 2, "launches_per_adj": 2}
 
 
 def worst_grid_sweep(api, dev, timed, steps):

@@ -196,12 +196,33 @@ int nufft2_exec_deriv(nufft_plan p, const void *c_dev, void *f_dev, void *fprime
 int nufft2_grad_x(nufft_plan p, const void *g_dev, const void *fprime_dev, void *gx_dev, int accumulate,
                   void *stream);
 
+/* Reserve what the batch calls and nufft2_step_host need, so that those exec calls
+ * allocate nothing and do not synchronise (and can be captured in a CUDA graph).  Not in
+ * the paper: part of the planning stage for these entry points.
+ *   B_max  the largest batch (B) the batch calls on this plan will be given.  FP32 plans
+ *          on grids of up to 2^18 points get a workspace for B_max members (each member's
+ *          slice of the rank intermediate, partial sums, pass B's partials) and the
+ *          members' kernel arguments, built here once; a larger B_max replaces them.  Other
+ *          plans run batch members in turn and need nothing (B_max is then ignored).
+ *   what   0 or NUFFT_RESERVE_STEP_HOST: also the device copies, copy stream and events of
+ *          nufft2_step_host (1D plans only).
+ * Allocates device memory and synchronises `stream`; call it outside any stream capture.
+ * Errors: NUFFT_EINVAL (B_max < 0, unknown bits in what), NUFFT_EUNSUPPORTED
+ * (NUFFT_RESERVE_STEP_HOST on a 2D plan), NUFFT_ENOMEM, NUFFT_ECUDA. */
+#define NUFFT_RESERVE_STEP_HOST 1u
+int nufft2_plan_reserve(nufft_plan p, int64_t B_max, unsigned what, void *stream);
+
+/* What is reserved: *B_max = the largest batch the batch calls accept (INT64_MAX for plans
+ * that run members in turn), *step_host = 1 when nufft2_step_host's buffers exist.  Either
+ * output may be NULL.  No GPU call. */
+int nufft2_plan_reserved(nufft_plan p, int64_t *B_max, int *step_host);
+
 /* B coefficient vectors on one plan (the same samples): f_b = A c_b, b = 0..B-1, with
- * c_b at c_dev + b*ldc elements and f_b at f_dev + b*ldf elements (ldc >= N,
- * ldf >= M).  FP32 plans on grids of up to 2^18 points run all members in one launch
- * per pass (each member has its own slice of a per-plan workspace, allocated by the
- * first call with a given or larger B); other plans run the members in turn.  Results
- * are bit-identical to B nufft2_exec calls. */
+ * c_b at c_dev + b*ldc elements and f_b at f_dev + b*ldf elements (ldc >= N, or m n for
+ * a 2D plan; ldf >= M).  FP32 plans on grids of up to 2^18 points run all members in one
+ * launch per pass, in the workspace nufft2_plan_reserve made: B beyond the reserved B_max
+ * returns NUFFT_ESTATE; other plans run the members in turn.  No allocation, no host
+ * synchronisation.  Results are bit-identical to B nufft2_exec calls. */
 int nufft2_exec_batch(nufft_plan p, int64_t B, const void *c_dev, int64_t ldc,
                       void *f_dev, int64_t ldf, void *stream);
 
@@ -229,7 +250,9 @@ int nufft2_grad_x_batch(nufft_plan p, int64_t B, const void *g_dev, const void *
  * the last one, and the host buffers hold the results once `stream` has completed (the
  * call does not synchronise).  Pinned host memory makes the copies asynchronous.
  * c_host, gc_host N complex; g_host, f_host M complex; gx_host M reals of the plan's
- * precision.  The first call allocates the plan's device copies of g, f', A^H g, gx. */
+ * precision.  Uses the device copies of g, f', A^H g and gx that
+ * nufft2_plan_reserve(p, ., NUFFT_RESERVE_STEP_HOST, .) made: NUFFT_ESTATE without them.
+ * Allocates nothing. */
 int nufft2_step_host(nufft_plan p, const void *c_host, const void *g_host, void *f_host, void *gc_host,
                      void *gx_host, void *stream);
 
@@ -322,9 +345,16 @@ int nufft2_inverse(nufft_plan p, const void *f_dev, void *c_dev, double tol, int
  *   flags   0 or NUFFT_PLAN_TIMING.
  *
  * The plan is a nufft_plan: nufft2_exec(p, C_dev, f_dev, stream) computes f from the
- * row-major m x n matrix C (of the plan's precision); nufft2_exec_batch and nufft_destroy apply;
- * the other exec calls return NUFFT_EUNSUPPORTED on a 2D plan.  nufft2_plan_info
- * reports K_x, gamma_x and L = L_x L_y.  Synchronises `stream`. */
+ * row-major m x n matrix C (of the plan's precision), and nufft1_exec(p, g_dev, C_dev,
+ * stream) the adjoint, C[k1][k2] = sum_j g_j exp(+2 pi i (k1 x_j + k2 y_j)) (C written
+ * row-major m x n): every step of eq. (4.4) conjugated and reversed -- each sample's
+ * conj(u^x_r1 u^y_r2) g_j scattered onto its grid row (a segmented sum over the samples
+ * sorted by grid point, no atomics, so repeated calls give the same bits), inverse row
+ * FFTs over y scaled by the y-factors and summed over r2, then inverse column FFTs over
+ * x scaled by the x-factors and summed over r1.  nufft2_exec_batch, nufft1_exec_batch
+ * (members in turn; ldc >= m n), nufft2_check and nufft_destroy apply; the x-derivative
+ * calls return NUFFT_EUNSUPPORTED on a 2D plan.  nufft2_plan_info reports K_x, gamma_x and
+ * L = L_x L_y.  Synchronises `stream`. */
 int nufft2d_plan(nufft_plan *out, int64_t m, int64_t n, int64_t M, const double *x_dev, const double *y_dev,
                  double eps, int prec, unsigned flags, void *stream);
 

@@ -21,6 +21,7 @@ NUFFT_BATCH_GRAPH = 8
 NUFFT_PLAN_LONG_COLUMNS = 16
 NUFFT_BATCH_PER_PROBLEM = 32
 NUFFT_PLAN_HALF_TILE = 64
+NUFFT_RESERVE_STEP_HOST = 1
 STATUS = {0: "NUFFT_OK", -1: "NUFFT_EINVAL", -2: "NUFFT_ENOMEM", -3: "NUFFT_ECUDA",
           -4: "NUFFT_EUNSUPPORTED", -5: "NUFFT_ESTATE", -6: "NUFFT_ETIMEOUT",
           -7: "NUFFT_ECHECK"}
@@ -48,6 +49,8 @@ SIGNATURES = {
     "nufft2_exec_deriv_batch": (_i32, [_vp, _i64, _vp, _i64, _vp, _vp, _i64, _vp]),
     "nufft2_grad_x_batch": (_i32, [_vp, _i64, _vp, _vp, _i64, _vp, _i32, _vp]),
     "nufft2_exec_host": (_i32, [_vp, _vp, _vp, _vp]),
+    "nufft2_plan_reserve": (_i32, [_vp, _i64, _u32, _vp]),
+    "nufft2_plan_reserved": (_i32, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i32)]),
     "nufft2_step_host": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "nufft2_exec_unfused": (_i32, [_vp, _vp, _vp, _vp]),
     "nufft_kernel_times": (_i32, [_vp, ctypes.POINTER(ctypes.c_float), _i32, ctypes.POINTER(_i32)]),

@@ -13,7 +13,7 @@ import torch
 
 from . import _lib
 from ._lib import (NUFFT_BATCH_GRAPH, NUFFT_BATCH_PER_PROBLEM, NUFFT_F32, NUFFT_F64, NUFFT_PLAN_AUTOTUNE,
-                   NUFFT_PLAN_HALF_TILE, NUFFT_PLAN_LONG_COLUMNS,
+                   NUFFT_PLAN_HALF_TILE, NUFFT_RESERVE_STEP_HOST, NUFFT_PLAN_LONG_COLUMNS,
                    NUFFT_PLAN_TIMING, NUFFT_PLAN_UNFUSED, NufftError, check)
 
 _CDTYPE = {NUFFT_F32: torch.complex64, NUFFT_F64: torch.complex128}
@@ -204,11 +204,31 @@ class Plan:
                                             _stream(self.device)), "nufft2_grad_x")
         return gx
 
+    def reserve(self, B=0, step_host=False):
+        """The plan stage of the batch calls and of :meth:`step_host`
+        (nufft2_plan_reserve): a workspace and kernel arguments for batches of up to B
+        members, and with ``step_host`` the device buffers of the host-buffer step.  The
+        exec calls themselves then allocate nothing and do not synchronise, so they can be
+        captured in a CUDA graph.  Synchronises; call it outside any stream capture."""
+        with torch.cuda.device(self.device):
+            check(_lib.load().nufft2_plan_reserve(self._h, int(B), NUFFT_RESERVE_STEP_HOST if step_host else 0,
+                                                  _stream(self.device)), "nufft2_plan_reserve")
+        cap, sh = ctypes.c_int64(), ctypes.c_int()
+        check(_lib.load().nufft2_plan_reserved(self._h, ctypes.byref(cap), ctypes.byref(sh)), "nufft2_plan_reserved")
+        self._bcap, self._step_host = cap.value, bool(sh.value)
+
+    def _need_batch(self, B):
+        """Reserve for B members first, unless a stream is being captured: there the
+        exec call must find its workspace already made (else it raises NUFFT_ESTATE)."""
+        if B > getattr(self, "_bcap", 1) and not torch.cuda.is_current_stream_capturing():
+            self.reserve(max(B, 2), getattr(self, "_step_host", False))
+
     def forward_batch(self, c, out=None):
         """f[b] = A c[b] for a (B, N) batch."""
         if c.dim() != 2 or c.shape[1] != self.N or c.dtype != self.cdtype or c.stride(1) != 1:
             raise ValueError("c must be (B, N) %s with unit inner stride" % self.cdtype)
         B = c.shape[0]
+        self._need_batch(B)
         f = out if out is not None else torch.empty(B, self.M, dtype=self.cdtype, device=self.device)
         with torch.cuda.device(self.device):
             check(_lib.load().nufft2_exec_batch(self._h, B, _ptr(c), c.stride(0), _ptr(f), f.stride(0),
@@ -224,6 +244,7 @@ class Plan:
         """c[b] = A^H g[b] for a (B, M) batch."""
         self._batch2(g, self.M, "g")
         B = g.shape[0]
+        self._need_batch(B)
         c = out if out is not None else torch.empty(B, self.N, dtype=self.cdtype, device=self.device)
         self._batch2(c, self.N, "c")
         with torch.cuda.device(self.device):
@@ -235,6 +256,7 @@ class Plan:
         """(f[b], f'[b]) for a (B, N) batch: the forward and df/dx of every member."""
         self._batch2(c, self.N, "c")
         B = c.shape[0]
+        self._need_batch(B)
         f = out if out is not None else torch.empty(B, self.M, dtype=self.cdtype, device=self.device)
         fp = out_deriv if out_deriv is not None else torch.empty(B, self.M, dtype=self.cdtype, device=self.device)
         self._batch2(f, self.M, "f")
@@ -267,6 +289,8 @@ class Plan:
                          (gc_host, self.N, self.cdtype), (gx_host, self.M, self.rdtype)):
             if t.device.type != "cpu" or t.dtype != dt or not t.is_contiguous() or t.numel() != n:
                 raise ValueError("host tensors must be contiguous CPU tensors of the plan's sizes and types")
+        if not getattr(self, "_step_host", False) and not torch.cuda.is_current_stream_capturing():
+            self.reserve(getattr(self, "_bcap", 0), step_host=True)
         with torch.cuda.device(self.device):
             check(_lib.load().nufft2_step_host(self._h, _ptr(c_host), _ptr(g_host), _ptr(f_host), _ptr(gc_host),
                                                _ptr(gx_host), _stream(self.device)), "nufft2_step_host")
@@ -453,8 +477,26 @@ class Plan2D:
             check(_lib.load().nufft2_exec(self._h, _ptr(C), _ptr(f), _stream(self.device)), "nufft2_exec")
         return f
 
+    def adjoint(self, g, out=None):
+        """C = A^H g: C[k1, k2] = sum_j g_j exp(+2 pi i (k1 x_j + k2 y_j)), an m x n tensor."""
+        if g.device != self.device or g.dtype != self.cdtype or not g.is_contiguous() or g.numel() != self.M:
+            raise ValueError("g must be a contiguous %s tensor of %d elements on %s"
+                             % (self.cdtype, self.M, self.device))
+        C = out if out is not None else torch.empty((self.m, self.n), dtype=self.cdtype, device=self.device)
+        if C.device != self.device or C.dtype != self.cdtype or not C.is_contiguous() or C.numel() != self.m * self.n:
+            raise ValueError("C must be a contiguous %s tensor of %d x %d elements" % (self.cdtype, self.m, self.n))
+        with torch.cuda.device(self.device):
+            check(_lib.load().nufft1_exec(self._h, _ptr(g), _ptr(C), _stream(self.device)), "nufft1_exec")
+        return C
+
+    def check(self):
+        """Synchronise and raise NufftError if a device-side wait gave up or a check failed."""
+        with torch.cuda.device(self.device):
+            check(_lib.load().nufft2_check(self._h, _stream(self.device)), "nufft2_check")
+
     def kernel_times(self):
-        """Device milliseconds of the column and row pass of the last forward (timing=True)."""
+        """Device milliseconds of the column and row pass of the last forward, or of the row
+        and column pass of the last adjoint (timing=True)."""
         buf = (ctypes.c_float * 8)()
         k = ctypes.c_int()
         check(_lib.load().nufft_kernel_times(self._h, buf, 8, ctypes.byref(k)), "nufft_kernel_times")

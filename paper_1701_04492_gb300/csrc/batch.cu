@@ -144,11 +144,12 @@ int rows_many(const nufft_batch_s::Class &c, nufft_plan rep, const void *args, b
     using T = float;
     const int n = (int)c.idx.size();
     const PassArgs<T> *a = (const PassArgs<T> *)args;
+    const ManyIO io{in, out, nullptr, 0, 0};   // the problems' offsets are in their arguments
     switch (c.KM) {
-        case 4: return launch_rows_many<T, 4>(rep, a, (const Beta<T, 4> *)c.betas, n, adjoint, in, out, s);
-        case 8: return launch_rows_many<T, 8>(rep, a, (const Beta<T, 8> *)c.betas, n, adjoint, in, out, s);
-        case 12: return launch_rows_many<T, 12>(rep, a, (const Beta<T, 12> *)c.betas, n, adjoint, in, out, s);
-        case 16: return launch_rows_many<T, 16>(rep, a, (const Beta<T, 16> *)c.betas, n, adjoint, in, out, s);
+        case 4: return launch_rows_many<T, 4>(rep, a, (const Beta<T, 4> *)c.betas, n, adjoint, io, s);
+        case 8: return launch_rows_many<T, 8>(rep, a, (const Beta<T, 8> *)c.betas, n, adjoint, io, s);
+        case 12: return launch_rows_many<T, 12>(rep, a, (const Beta<T, 12> *)c.betas, n, adjoint, io, s);
+        case 16: return launch_rows_many<T, 16>(rep, a, (const Beta<T, 16> *)c.betas, n, adjoint, io, s);
         default: return NUFFT_EUNSUPPORTED;
     }
 }
@@ -168,12 +169,13 @@ int class_launches(nufft_batch b, const nufft_batch_s::Class &c, bool adjoint, c
         return adjoint ? nufft1_exec(rep, src, dst, s) : nufft2_exec(rep, src, dst, s);
     }
     if constexpr (std::is_same<T, float>::value) {
+        const ManyIO io{in, out, nullptr, 0, 0};
         if (!adjoint) {
-            if (int rc = launch_cols_many<T>(rep, (const PassArgs<T> *)c.a1, n, c.ny1, false, in, out, s)) return rc;
+            if (int rc = launch_cols_many<T>(rep, (const PassArgs<T> *)c.a1, n, c.ny1, false, io, s)) return rc;
             return rows_many(c, rep, c.a2, false, in, out, s);
         }
         if (int rc = rows_many(c, rep, c.aA, true, in, out, s)) return rc;
-        return launch_cols_many<T>(rep, (const PassArgs<T> *)c.aB, n, c.nyB, true, in, out, s);
+        return launch_cols_many<T>(rep, (const PassArgs<T> *)c.aB, n, c.nyB, true, io, s);
     } else {
         return NUFFT_EUNSUPPORTED;   // FP64 classes are single problems
     }

@@ -399,6 +399,39 @@ int exec_forward_2d(nufft_plan p, const void *C, void *f, cudaStream_t s) {
     return mark(p, s, false);
 }
 
+// The 2D adjoint, C = A^H g (section 4, eq. (4.4) conjugated and reversed): the row
+// pass (scatter, inverse FFTs over t^y, y-scale, sum over r2), then the column pass
+// (inverse FFTs over s1, x-scale, sum over r1).  C is m x n row-major.
+template <typename T>
+int exec_adjoint_2d(nufft_plan p, const void *g, void *C, cudaStream_t s) {
+    if (p->M == 0) {
+        NUFFT_CUDA_TRY(cudaMemsetAsync(C, 0, (size_t)p->N * p->N2 * 2 * sizeof(T), s));
+        return NUFFT_OK;
+    }
+    PassArgs<T> a = base_args<T>(p);
+    a.in = (const cx<T> *)g;
+    a.out = (cx<T> *)C;
+    a.ncol = (int)p->N2;
+    a.ldc = (int)p->N2;
+    a.K2 = p->K2;
+    a.dsorted2 = (const T *)p->dsorted2;
+    a.vy = (const T *)p->vy;
+    a.inv_gamma2 = p->gamma2 > 0.0 ? (T)(1.0 / p->gamma2) : T(0);
+    if (int rc = mark(p, s, true)) return rc;
+    int rc = NUFFT_EUNSUPPORTED;
+    switch (p->kmax) {
+        case 4: rc = launch_rows_2d_adj<T, 4>(p, a, s); break;
+        case 8: rc = launch_rows_2d_adj<T, 8>(p, a, s); break;
+        case 12: rc = launch_rows_2d_adj<T, 12>(p, a, s); break;
+        case 16: rc = launch_rows_2d_adj<T, 16>(p, a, s); break;
+        default: break;
+    }
+    if (rc) return rc;
+    if (int rc2 = mark(p, s, false)) return rc2;
+    if (int rc2 = launch_cols_2d_adj<T>(p, a, s)) return rc2;
+    return mark(p, s, false);
+}
+
 template <typename T>
 int exec_forward(nufft_plan p, const void *c, void *f, cudaStream_t s) {
     if (p->dims == 2) return exec_forward_2d<T>(p, c, f, s);
@@ -415,6 +448,7 @@ int exec_forward(nufft_plan p, const void *c, void *f, cudaStream_t s) {
 
 template <typename T>
 int exec_adjoint(nufft_plan p, const void *g, void *c, cudaStream_t s) {
+    if (p->dims == 2) return exec_adjoint_2d<T>(p, g, c, s);
     if (p->M == 0) {
         NUFFT_CUDA_TRY(cudaMemsetAsync(c, 0, (size_t)p->N * 2 * sizeof(T), s));
         return NUFFT_OK;
@@ -544,7 +578,6 @@ extern "C" int nufft2_exec(nufft_plan p, const void *c_dev, void *f_dev, void *s
 
 extern "C" int nufft1_exec(nufft_plan p, const void *g_dev, void *c_dev, void *stream) {
     nufft::NvtxRange nvtx_range_("nufft1_exec");
-    if (p && p->dims == 2) return NUFFT_EUNSUPPORTED;   // the 2D transform has its forward only
     if (!p || !c_dev || (p->M > 0 && !g_dev)) return NUFFT_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     return p->prec == NUFFT_F32 ? exec_adjoint<float>(p, g_dev, c_dev, s)
@@ -554,7 +587,7 @@ extern "C" int nufft1_exec(nufft_plan p, const void *g_dev, void *c_dev, void *s
 extern "C" int nufft2_exec_dx(nufft_plan p, const void *c_dev, const void *g_dev, void *gx_dev,
                               int accumulate, void *stream) {
     nufft::NvtxRange nvtx_range_("nufft2_exec_dx");
-    if (p && p->dims == 2) return NUFFT_EUNSUPPORTED;   // the 2D transform has its forward only
+    if (p && p->dims == 2) return NUFFT_EUNSUPPORTED;   // the 2D transform has its forward and adjoint only
     if (!p || !c_dev || (p->M > 0 && (!g_dev || !gx_dev))) return NUFFT_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     return p->prec == NUFFT_F32 ? exec_dx<float>(p, c_dev, g_dev, gx_dev, accumulate, s)
@@ -564,7 +597,7 @@ extern "C" int nufft2_exec_dx(nufft_plan p, const void *c_dev, const void *g_dev
 extern "C" int nufft2_exec_deriv(nufft_plan p, const void *c_dev, void *f_dev, void *fprime_dev,
                                  void *stream) {
     nufft::NvtxRange nvtx_range_("nufft2_exec_deriv");
-    if (p && p->dims == 2) return NUFFT_EUNSUPPORTED;   // the 2D transform has its forward only
+    if (p && p->dims == 2) return NUFFT_EUNSUPPORTED;   // the 2D transform has its forward and adjoint only
     if (!p || !c_dev || (p->M > 0 && (!f_dev || !fprime_dev))) return NUFFT_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     return p->prec == NUFFT_F32 ? nufft::exec_deriv<float>(p, c_dev, f_dev, fprime_dev, s)
@@ -574,7 +607,7 @@ extern "C" int nufft2_exec_deriv(nufft_plan p, const void *c_dev, void *f_dev, v
 extern "C" int nufft2_grad_x(nufft_plan p, const void *g_dev, const void *fprime_dev, void *gx_dev,
                              int accumulate, void *stream) {
     nufft::NvtxRange nvtx_range_("nufft2_grad_x");
-    if (p && p->dims == 2) return NUFFT_EUNSUPPORTED;   // the 2D transform has its forward only
+    if (p && p->dims == 2) return NUFFT_EUNSUPPORTED;   // the 2D transform has its forward and adjoint only
     if (!p || (p->M > 0 && (!g_dev || !fprime_dev || !gx_dev))) return NUFFT_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     return p->prec == NUFFT_F32 ? nufft::exec_grad_x<float>(p, g_dev, fprime_dev, gx_dev, accumulate, s)
@@ -582,7 +615,7 @@ extern "C" int nufft2_grad_x(nufft_plan p, const void *g_dev, const void *fprime
 }
 
 extern "C" int nufft2_exec_host(nufft_plan p, const void *c_host, void *f_host, void *stream) {
-    if (p && p->dims == 2) return NUFFT_EUNSUPPORTED;   // the 2D transform has its forward only
+    if (p && p->dims == 2) return NUFFT_EUNSUPPORTED;   // the 2D transform has its forward and adjoint only
     if (!p || !c_host || (p->M > 0 && !f_host)) return NUFFT_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t cxs = p->prec == NUFFT_F32 ? 8 : 16;
@@ -596,7 +629,7 @@ extern "C" int nufft2_exec_host(nufft_plan p, const void *c_host, void *f_host, 
 
 extern "C" int nufft2_exec_unfused(nufft_plan p, const void *c_dev, void *f_dev, void *stream) {
     nufft::NvtxRange nvtx_range_("nufft2_exec_unfused");
-    if (p && p->dims == 2) return NUFFT_EUNSUPPORTED;   // the 2D transform has its forward only
+    if (p && p->dims == 2) return NUFFT_EUNSUPPORTED;   // the 2D transform has its forward and adjoint only
     if (!p || !c_dev || (p->M > 0 && !f_dev)) return NUFFT_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     return p->prec == NUFFT_F32 ? exec_unfused<float>(p, c_dev, f_dev, s)
@@ -613,16 +646,8 @@ namespace {
 // for the last one.
 template <typename T>
 int step_host(nufft_plan p, const void *c_h, const void *g_h, void *f_h, void *gc_h, void *gx_h, cudaStream_t s) {
-    const size_t cxs = 2 * sizeof(T), Mi = (size_t)std::max<int64_t>(p->M, 1);
-    if (!p->st_g) {
-        NUFFT_CUDA_TRY(dev_malloc(&p->st_g, Mi * cxs));
-        NUFFT_CUDA_TRY(dev_malloc(&p->st_fp, Mi * cxs));
-        NUFFT_CUDA_TRY(dev_malloc(&p->st_gc, (size_t)p->N * cxs));
-        NUFFT_CUDA_TRY(dev_malloc(&p->st_gx, Mi * sizeof(T)));
-        NUFFT_CUDA_TRY(cudaStreamCreateWithFlags(&p->st_copy, cudaStreamNonBlocking));
-        for (cudaEvent_t &e : p->st_ev) NUFFT_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-        p->work_bytes += (int64_t)(Mi * (2 * cxs + sizeof(T)) + (size_t)p->N * cxs);
-    }
+    const size_t cxs = 2 * sizeof(T);
+    if (!p->st_g || !p->st_copy) return NUFFT_ESTATE;   // nufft2_plan_reserve makes the buffers
     cudaStream_t cs = p->st_copy;
     cudaEvent_t *ev = p->st_ev;   // 0 start / gx ready, 1 g in, 2 c in, 3 A^H g ready, 4 f ready, 5 all out
     NUFFT_CUDA_TRY(cudaEventRecord(ev[0], s));
@@ -651,6 +676,24 @@ int step_host(nufft_plan p, const void *c_h, const void *g_h, void *f_h, void *g
 }
 
 }  // namespace
+
+// nufft2_step_host's device copies of g, f', A^H g and gx, its copy stream and events
+// (once per plan; part of nufft2_plan_reserve, the plan stage).
+int reserve_step_host(nufft_plan p, cudaStream_t s) {
+    if (p->st_g && p->st_copy) return NUFFT_OK;
+    const size_t rs = p->prec == NUFFT_F32 ? 4 : 8, cxs = 2 * rs, Mi = (size_t)std::max<int64_t>(p->M, 1);
+    NUFFT_CUDA_TRY(cudaStreamSynchronize(s));
+    if (!p->st_g) NUFFT_CUDA_TRY(dev_malloc(&p->st_g, Mi * cxs));
+    if (!p->st_fp) NUFFT_CUDA_TRY(dev_malloc(&p->st_fp, Mi * cxs));
+    if (!p->st_gc) NUFFT_CUDA_TRY(dev_malloc(&p->st_gc, (size_t)p->N * cxs));
+    if (!p->st_gx) NUFFT_CUDA_TRY(dev_malloc(&p->st_gx, Mi * rs));
+    for (cudaEvent_t &e : p->st_ev)
+        if (!e) NUFFT_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    NUFFT_CUDA_TRY(cudaStreamCreateWithFlags(&p->st_copy, cudaStreamNonBlocking));   // last: marks it complete
+    p->work_bytes += (int64_t)(Mi * (2 * cxs + rs) + (size_t)p->N * cxs);
+    return NUFFT_OK;
+}
+
 }  // namespace nufft
 
 extern "C" int nufft2_step_host(nufft_plan p, const void *c_host, const void *g_host, void *f_host, void *gc_host,

@@ -1,6 +1,8 @@
-// Explicit instantiation of the 2D row pass (section 4) for FP64 and rank bound 12.
+// Explicit instantiation of the 2D row passes (section 4), forward and adjoint, for
+// double and rank bound 12.
 #include "passes.cuh"
 
 namespace nufft {
 template int launch_rows_2d<double, 12>(nufft_plan, const PassArgs<double> &, cudaStream_t);
+template int launch_rows_2d_adj<double, 12>(nufft_plan, const PassArgs<double> &, cudaStream_t);
 }

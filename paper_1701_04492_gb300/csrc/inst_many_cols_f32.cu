@@ -3,6 +3,6 @@
 #include "passes.cuh"
 
 namespace nufft {
-template int launch_cols_many<float>(nufft_plan, const PassArgs<float> *, int, int, bool, const void *, void *,
+template int launch_cols_many<float>(nufft_plan, const PassArgs<float> *, int, int, bool, const ManyIO &,
                                      cudaStream_t);
 }

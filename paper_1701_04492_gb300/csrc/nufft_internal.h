@@ -40,6 +40,9 @@ struct nufft_plan_s {
     int NB = 1;            // number of buckets = L2 / B2
     int G = 1;             // ranks staged together in pass 2 (up to K + 1)
     int G2d = 1;           // 2D row pass: y-ranks transformed and gathered per group
+    int G2a = 1;           // 2D adjoint row pass: y-ranks scattered and transformed per group
+    int nt2a = 1;          // teams per 2D adjoint row-pass CTA
+    size_t smemA2d = 0;    // dynamic shared memory of the 2D adjoint row pass
     int nt2 = 1;           // teams per pass-2 CTA (forward: K ranks)
     int nt2d = 1;          // teams per pass-2 CTA in the derivative mode (K + 1 ranks)
     int GA = 1;            // ranks staged together in pass A
@@ -96,20 +99,21 @@ struct nufft_plan_s {
     double *inv_part = nullptr, *inv_scal = nullptr;               // reductions, scalars
     double *inv_host = nullptr;                                    // pinned readback
 
-    // batches of coefficient vectors on this plan (shared samples), for up to sb_cap
-    // members: per-member slices of the intermediate, partial sums, pass B's partials
-    // and tickets; the members' kernel arguments (device, and pinned staging guarded
-    // by sb_ev) and coefficient tables
-    // nufft2_step_host: device copies of g, f', A^H g and gx; a copy stream and events
+    // nufft2_step_host (made by nufft2_plan_reserve): device copies of g, f', A^H g and
+    // gx; a copy stream and events
     void *st_g = nullptr, *st_fp = nullptr, *st_gc = nullptr, *st_gx = nullptr;
     cudaStream_t st_copy = nullptr;
     cudaEvent_t st_ev[6] = {};
 
+    // batches of coefficient vectors on this plan (shared samples), for up to sb_cap
+    // members (made by nufft2_plan_reserve): per-member slices of the intermediate,
+    // partial sums, pass B's partials and tickets; the members' kernel arguments (six
+    // sets of sb_cap: forward, forward with f', adjoint; two passes each) and
+    // coefficient tables
     int64_t sb_cap = 0;
     void *sb_Y = nullptr, *sb_fscr = nullptr, *sb_part = nullptr;
     int *sb_cnt = nullptr;
-    void *sb_args = nullptr, *sb_beta = nullptr, *sb_host = nullptr;
-    cudaEvent_t sb_ev = nullptr;
+    void *sb_args = nullptr, *sb_beta = nullptr;
 
     // NUFFT_PLAN_TIMING: events around each launch of the last exec call
     cudaEvent_t ev[8] = {};
@@ -159,6 +163,7 @@ template <typename T> int exec_unfused(nufft_plan p, const void *c, void *f, cud
 template <typename T> int plan_geometry(nufft_plan p);
 template <typename T> int plan_unfused_factors(nufft_plan p, cudaStream_t s);
 template <typename T> int plan_factor_tables(nufft_plan p, cudaStream_t s);
+int reserve_step_host(nufft_plan p, cudaStream_t s);   // exec.cu: nufft2_step_host's buffers
 
 }  // namespace nufft
 

@@ -701,7 +701,10 @@ template <typename T> struct PassBBounds;
 template <> struct PassBBounds<float> { static constexpr int threads = 256, blocks = 2; };
 template <> struct PassBBounds<double> { static constexpr int threads = 128, blocks = 3; };
 
-template <typename T, int P2>
+// TWO_D: the column pass of the 2D adjoint (section 4).  A column is the y-frequency
+// k2 = k1 (this CTA's column index), its elements the x-frequencies k = out_index < m
+// with z = (2 k - m) / m, and C[k][k2] goes to out[k * ldc + k2] for k < N = m, k2 < ncol.
+template <typename T, int P2, bool TWO_D = false>
 __device__ __forceinline__ void passB_body(const PassArgs<T> &a, const int bx, const int by) {
     constexpr int E = e_of<T, P2, PK_COL_ADJ>();
     using TF = TeamFft<T, P2, E, true>;
@@ -742,7 +745,7 @@ __device__ __forceinline__ void passB_body(const PassArgs<T> &a, const int bx, c
         for (int m = 0; m < E; ++m) v[m] = buf[(tt + TT * m) * a.C + cc];   // tile as copied
         __syncthreads();
         TF::run(v, tt, buf + cc * a.S, a.twc);
-        if constexpr (kFactors<T>) {   // the plan's v_r(k) (real), no i^r
+        if constexpr (kFactors<T> && !TWO_D) {   // the plan's v_r(k) (real), no i^r
             const T *vr = a.vfac + (int64_t)r * a.N;
 #pragma unroll
             for (int e = 0; e < E; ++e) {
@@ -759,7 +762,7 @@ __device__ __forceinline__ void passB_body(const PassArgs<T> &a, const int bx, c
             T z2[H], ta[H], tb[H];
 #pragma unroll
             for (int m = 0; m < H; ++m) {
-                const int k = k1 + a.L1 * TF::out_index(tt, h0 + m);
+                const int k = TWO_D ? TF::out_index(tt, h0 + m) : k1 + a.L1 * TF::out_index(tt, h0 + m);
                 const T z = T(2 * k - Ni) * invN;
                 z2[m] = T(2) * z;
                 ta[m] = T(1);
@@ -792,12 +795,19 @@ __device__ __forceinline__ void passB_body(const PassArgs<T> &a, const int bx, c
             bulk_copy_g2s(buf, a.Y + (int64_t)(r + 2 * SB) * a.L + tile_off, tile_bytes, &mbar[i & 1]);
         }
     }
+    // c_k (1D), or C[k][k1] (2D), for the output element e
+    auto store = [&](const int e, const cx<T> val) {
+        if constexpr (TWO_D) {
+            const int k = TF::out_index(tt, e);
+            if (k < a.N && k1 < a.ncol) a.out[(int64_t)k * a.ldc + k1] = val;
+        } else {
+            const int k = k1 + a.L1 * TF::out_index(tt, e);
+            if (k < a.N) a.out[k] = val;
+        }
+    };
     if (SB == 1) {
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const int k = k1 + a.L1 * TF::out_index(tt, e);
-            if (k < a.N) a.out[k] = acc[e];
-        }
+        for (int e = 0; e < E; ++e) store(e, acc[e]);
         return;
     }
     // partial sums -> part[s]; the last CTA of this column block reduces them
@@ -829,10 +839,7 @@ __device__ __forceinline__ void passB_body(const PassArgs<T> &a, const int bx, c
             }
         }
 #pragma unroll
-        for (int m = 0; m < H; ++m) {
-            const int k = k1 + a.L1 * TF::out_index(tt, h0 + m);
-            if (k < a.N) a.out[k] = t[m];
-        }
+        for (int m = 0; m < H; ++m) store(h0 + m, t[m]);
     }
     if (threadIdx.x == 0) a.counters[bx] = 0;   // ready for the next call
 }
@@ -1002,6 +1009,147 @@ __device__ __forceinline__ void pass2d_body(const PassArgs<T> &a, const BT &beta
     }
 }
 
+// ---- 2D adjoint row pass (section 4: eq. (4.4) conjugated and reversed) ---------------
+// One CTA per x-grid row s1 = b; the row's samples are sorted by t^y.  For each x-rank r1
+// and each group of y-ranks, one slot per r2 receives
+//     Z_r1r2[t^y] = sum over the row's samples j at t^y of mu^x_r1 mu^y_r2 e^{+i pi (d^x + d^y)} g_j
+// (a segmented sum over the sorted samples: the thread at the start of each run of equal
+// t^y adds up the run, so there are no atomics and the order is fixed), then the teams
+// inverse-transform the slots over t^y (length L1), scale by (-i)^r2 T_r2(2 k2 / n - 1)
+// (the conjugate of the forward's y-scale) and the y-ranks are summed into the row
+//     W'_r1[s1][k2] = sum_r2 (-i)^r2 T_r2(z^y_k2) (L1 IDFT Z_r1r2)[k2],
+// written in pass B's column-tiled layout [k2 / CQ][s1][k2 % CQ] for the column pass.
+// h_j = e^{+i pi (d^x + d^y)} g_j is formed once (r1 = 0, first group) in sorted order in
+// fscr and read back later by the same thread (the run of each sample has a fixed owner).
+// Shared memory: an accumulator row (L1) for the groups' partial sums, then G2 slots.
+template <typename T, int P1, int KM, typename BT>
+__device__ __forceinline__ void passA2d_body(const PassArgs<T> &a, const BT &betax, const BT &betay,
+                                             const int b) {
+    constexpr int E = e_of<T, P1, PK_ROW_ADJ>();
+    using TF = TeamFft<T, P1, E, true>;
+    constexpr int TT = TF::TT;
+    cx<T> *smem = smem_base<T>();
+    const int team = threadIdx.x / TT, tt = threadIdx.x % TT;
+    const int nt = blockDim.x / TT;
+    const int K1 = a.K, K2 = a.K2;
+    const int G2 = a.G > 0 ? min(a.G, K2) : K2;
+    cx<T> *accrow = smem;        // sum over the y-ranks of the groups so far (one row)
+    cx<T> *slots = smem + P1;    // G2 slots of S
+    int i0 = a.bstart[b], i1 = a.bstart[b + 1];
+    if (!idx_ok(i0 >= 0 && i0 <= i1 && i1 <= a.M, a.err)) i1 = i0 = 0;   // no samples (barriers follow)
+    const T invg = a.inv_gamma, invg2 = a.inv_gamma2;
+    for (int r1 = 0; r1 < K1; ++r1) {
+        for (int g2 = 0; g2 < K2; g2 += G2) {
+            const int gc2 = min(G2, K2 - g2);
+            const bool first = r1 == 0 && g2 == 0;
+            for (int idx = threadIdx.x; idx < gc2 * a.S; idx += blockDim.x) slots[idx] = mk<T>(0, 0);
+            __syncthreads();
+#pragma unroll 1
+            for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+                const int t = a.tsorted[i];
+                if (i > i0 && a.tsorted[i - 1] == t) continue;   // inside a run: its start adds it up
+                cx<T> acc[KM];
+#pragma unroll
+                for (int r2 = 0; r2 < KM; ++r2) acc[r2] = mk<T>(0, 0);
+#pragma unroll 1
+                for (int i2 = i; i2 < i1; ++i2) {
+                    if (i2 > i && a.tsorted[i2] != t) break;
+                    const T dx = a.dsorted[i2], dy = a.dsorted2[i2];
+                    cx<T> h;
+                    if (first) {
+                        const int j = a.perm[i2];
+                        const cx<T> gg = idx_ok(j >= 0 && j < a.M, a.err) ? a.in[j] : mk<T>(0, 0);
+                        T sn, cs;
+                        sincospi_t<T>(dx + dy, &sn, &cs);
+                        h = mk<T>(fma(gg.x, cs, -gg.y * sn), fma(gg.y, cs, gg.x * sn));   // g e^{+i pi (dx + dy)}
+                        a.fscr[i2] = h;
+                    } else {
+                        h = a.fscr[i2];
+                    }
+                    // mu^x_r1 = sum_p beta^x_r1p T_p(d^x / gamma_x), mu^y_r2 likewise in y
+                    T Tp[KM];
+                    const T xi = dx * invg;
+                    Tp[0] = T(1);
+                    if (KM > 1) Tp[1] = xi;
+#pragma unroll
+                    for (int q = 2; q < KM; ++q) Tp[q] = fma(T(2) * xi, Tp[q - 1], -Tp[q - 2]);
+                    T mux = T(0);
+#pragma unroll
+                    for (int q = 0; q < KM; ++q)
+                        if (((q ^ r1) & 1) == 0) mux = fma(beta_at(betax, r1, q), Tp[q], mux);
+                    h = mk<T>(mux * h.x, mux * h.y);
+                    const T eta = dy * invg2;
+                    Tp[0] = T(1);
+                    if (KM > 1) Tp[1] = eta;
+#pragma unroll
+                    for (int q = 2; q < KM; ++q) Tp[q] = fma(T(2) * eta, Tp[q - 1], -Tp[q - 2]);
+#pragma unroll
+                    for (int r2 = 0; r2 < KM; ++r2) {
+                        if (r2 >= g2 && r2 < g2 + gc2) {
+                            T mu = T(0);
+#pragma unroll
+                            for (int q = (r2 & 1); q < KM; q += 2) mu = fma(beta_at(betay, r2, q), Tp[q], mu);
+                            acc[r2].x = fma(mu, h.x, acc[r2].x);
+                            acc[r2].y = fma(mu, h.y, acc[r2].y);
+                        }
+                    }
+                }
+                const int n1 = t >> a.lg2;   // t^y
+                if (!idx_ok(n1 >= 0 && n1 < P1 && (t & (a.L2 - 1)) == b, a.err)) continue;
+#pragma unroll
+                for (int r2 = 0; r2 < KM; ++r2)
+                    if (r2 >= g2 && r2 < g2 + gc2) slots[(r2 - g2) * a.S + padi<E>(n1)] = acc[r2];
+            }
+            __syncthreads();
+            // this lane's stage twiddles, loaded once for all its row FFTs of this group
+            typename TF::Tw twreg;
+            if constexpr (kTwReg<T>) TF::load_tw(twreg, tt, a.twr);
+            auto round = [&](const int j0, auto pred) {   // one r2 per team; PRED: idle teams
+                constexpr bool PRED = decltype(pred)::value;
+                const int jj = j0 + team;
+                const bool act = !PRED || jj < gc2;
+                const int r2 = g2 + (act ? jj : 0);
+                cx<T> *sm = slots + (act ? jj : 0) * a.S;
+                cx<T> v[E];
+#pragma unroll
+                for (int m = 0; m < E; ++m) {
+                    if (!act) v[m] = mk<T>(0, 0);
+                    else if constexpr (TT % E == 0) v[m] = sm[padi_run<E, TT>(padi<E>(tt), m)];
+                    else v[m] = sm[padi<E>(tt + TT * m)];
+                }
+                __syncthreads();   // the slot is read before the transform reuses it
+                if constexpr (kTwReg<T>) TF::template run_reg<PRED>(v, tt, sm, twreg, act);
+                else TF::template run<PRED>(v, tt, sm, a.twr, act);
+                if (act) {
+                    const T *vy = a.vy + (int64_t)r2 * P1;
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        const T sc = vy[TF::out_index(tt, e)];
+                        const cx<T> y = mul_ipow<T>(v[e], -r2);
+                        sm[TF::out_padded(tt, e)] = mk<T>(sc * y.x, sc * y.y);
+                    }
+                }
+            };
+            for (int j0 = 0; j0 < gc2; j0 += nt) {
+                if (j0 + nt <= gc2) round(j0, std::false_type{});
+                else round(j0, std::true_type{});
+            }
+            __syncthreads();
+            // the sum over this group's y-ranks, in r2 order; after the last group the row
+            // goes out, column-tiled: W'_r1[k2 / CQ][s1][k2 % CQ]
+            const bool last = g2 + gc2 == K2;
+            cx<T> *dst = a.Y + (int64_t)r1 * a.L + b * a.CQ;
+            for (int k2 = threadIdx.x; k2 < P1; k2 += blockDim.x) {
+                cx<T> sum = g2 == 0 ? mk<T>(0, 0) : accrow[k2];
+                for (int jj = 0; jj < gc2; ++jj) sum = cadd<T>(sum, slots[jj * a.S + padi<E>(k2)]);
+                if (last) dst[(k2 >> a.lgCQ) * (a.L2 << a.lgCQ) + (k2 & (a.CQ - 1))] = sum;
+                else accrow[k2] = sum;
+            }
+            __syncthreads();   // the slots and the row are rewritten by the next group
+        }
+    }
+}
+
 // ---- kernels ----------------------------------------------------------------------
 // One plan per launch: the arguments are kernel parameters.
 template <typename T, int P2>
@@ -1034,23 +1182,48 @@ __global__ void __launch_bounds__(256) k_pass2d(const __grid_constant__ PassArgs
     pass2d_body<T, P1, KM>(a, betax, betay, blockIdx.x);
 }
 
+// the 2D adjoint (section 4): row pass and column pass
+template <typename T, int P1, int KM>
+__global__ void __launch_bounds__(256) k_passA2d(const __grid_constant__ PassArgs<T> a,
+                                                 const __grid_constant__ Beta<T, KM> betax,
+                                                 const __grid_constant__ Beta<T, KM> betay) {
+    passA2d_body<T, P1, KM>(a, betax, betay, blockIdx.x);
+}
+template <typename T, int P2>
+__global__ void __launch_bounds__(PassBBounds<T>::threads, PassBBounds<T>::blocks) k_passB2d(const __grid_constant__ PassArgs<T> a) {
+    passB_body<T, P2, true>(a, blockIdx.x, blockIdx.y);
+}
+
 // Many independent plans per launch (a batch of uneven problems): blockIdx.z is the
 // problem.  The problems of one launch share the grid length L, and so every launch
 // dimension but the rank count; each reads its own arguments (buffers, K, M, tables)
 // from args[z], and its input and output at in + in_off, out + out_off.  CTAs beyond a
 // problem's own rank count or rank split return before any barrier.
+// A batched launch's data pointers: problem z reads in + in_off + z in_stride and writes
+// out (and, when not null, out2) + out_off + z out_stride.  Batches of uneven problems
+// carry their offsets in the arguments (strides 0); batches of coefficient vectors on one
+// plan pass the call's leading dimensions as strides, so that their arguments do not
+// depend on the call and are built once.
+struct ManyIO {
+    const void *in;
+    void *out;
+    void *out2;
+    int64_t in_stride, out_stride;
+};
+
 // The problem's arguments, copied to shared memory sa (all threads, then a barrier).
 template <typename T>
-__device__ __forceinline__ void many_args(PassArgs<T> &sa, const PassArgs<T> *__restrict__ args,
-                                          const cx<T> *in, cx<T> *out) {
+__device__ __forceinline__ void many_args(PassArgs<T> &sa, const PassArgs<T> *__restrict__ args, const ManyIO &io) {
     static_assert(sizeof(PassArgs<T>) % 8 == 0, "copied in 8-byte words");
     const unsigned long long *src = reinterpret_cast<const unsigned long long *>(&args[blockIdx.z]);
     unsigned long long *dst = reinterpret_cast<unsigned long long *>(&sa);
     for (int i = threadIdx.x; i < (int)(sizeof(PassArgs<T>) / 8); i += blockDim.x) dst[i] = src[i];
     __syncthreads();
     if (threadIdx.x == 0) {
-        sa.in = in + sa.in_off;
-        sa.out = out + sa.out_off;
+        const int64_t z = blockIdx.z;
+        sa.in = (const cx<T> *)io.in + sa.in_off + z * io.in_stride;
+        sa.out = (cx<T> *)io.out + sa.out_off + z * io.out_stride;
+        if (io.out2) sa.out2 = (cx<T> *)io.out2 + sa.out_off + z * io.out_stride;
     }
     __syncthreads();
 }
@@ -1062,37 +1235,37 @@ __device__ __forceinline__ void stage_beta(Beta<T, KM> &sb, const Beta<T, KM> *_
 }
 template <typename T, int P2>
 __global__ void __launch_bounds__(256, 2) k_pass1_many(const PassArgs<T> *__restrict__ args,
-                                                       const cx<T> *in, cx<T> *out) {
+                                                       const ManyIO io) {
     __shared__ PassArgs<T> a;
-    many_args<T>(a, args, in, out);
+    many_args<T>(a, args, io);
     if ((int)blockIdx.y >= a.nranks) return;
     pass1_body<T, P2>(a, blockIdx.x, blockIdx.y);
 }
 template <typename T, int P1, int KM>
 __global__ void __launch_bounds__(256) k_pass2_many(const PassArgs<T> *__restrict__ args,
                                                     const Beta<T, KM> *__restrict__ betas,
-                                                    const cx<T> *in, cx<T> *out) {
+                                                    const ManyIO io) {
     __shared__ Beta<T, KM> sb;
     stage_beta<T, KM>(sb, betas);
     __shared__ PassArgs<T> a;
-    many_args<T>(a, args, in, out);
+    many_args<T>(a, args, io);
     pass2_body<T, P1, KM>(a, BetaShared<T, KM>{&sb.b[0][0]}, blockIdx.x);
 }
 template <typename T, int P1, int KM>
 __global__ void __launch_bounds__(256) k_passA_many(const PassArgs<T> *__restrict__ args,
                                                     const Beta<T, KM> *__restrict__ betas,
-                                                    const cx<T> *in, cx<T> *out) {
+                                                    const ManyIO io) {
     __shared__ Beta<T, KM> sb;
     stage_beta<T, KM>(sb, betas);
     __shared__ PassArgs<T> a;
-    many_args<T>(a, args, in, out);
+    many_args<T>(a, args, io);
     passA_body<T, P1, KM>(a, BetaShared<T, KM>{&sb.b[0][0]}, blockIdx.x);
 }
 template <typename T, int P2>
 __global__ void __launch_bounds__(PassBBounds<T>::threads, PassBBounds<T>::blocks) k_passB_many(const PassArgs<T> *__restrict__ args,
-                                                       const cx<T> *in, cx<T> *out) {
+                                                       const ManyIO io) {
     __shared__ PassArgs<T> a;
-    many_args<T>(a, args, in, out);
+    many_args<T>(a, args, io);
     if ((int)blockIdx.y >= a.SB) return;
     passB_body<T, P2>(a, blockIdx.x, blockIdx.y);
 }
@@ -1238,7 +1411,7 @@ int launch_rows(nufft_plan p, const PassArgs<T> &a0, bool adjoint, cudaStream_t 
 // split (pass B) of the class.  args / betas: device arrays, one entry per member.
 template <typename T>
 int launch_cols_many(nufft_plan rep, const PassArgs<T> *args, int nprob, int ny, bool adjoint,
-                     const void *in, void *out, cudaStream_t s) {
+                     const ManyIO &io, cudaStream_t s) {
     return dispatch_P_many(rep->L2, [&](auto PC) -> int {
         constexpr int P = decltype(PC)::value;
         const int TT = adjoint ? P / e_of<T, P, PK_COL_ADJ>() : P / e_of<T, P, PK_COL_FWD>();
@@ -1249,11 +1422,11 @@ int launch_cols_many(nufft_plan rep, const PassArgs<T> *args, int nprob, int ny,
         if (adjoint) {
             auto kern = k_passB_many<T, P>;
             if (int rc = set_smem(kern, smem, rep->device, done_b)) return rc;
-            kern<<<grid, block, smem, s>>>(args, (const cx<T> *)in, (cx<T> *)out);
+            kern<<<grid, block, smem, s>>>(args, io);
         } else {
             auto kern = k_pass1_many<T, P>;
             if (int rc = set_smem(kern, smem, rep->device, done_1)) return rc;
-            kern<<<grid, block, smem, s>>>(args, (const cx<T> *)in, (cx<T> *)out);
+            kern<<<grid, block, smem, s>>>(args, io);
         }
         return launch_status();
     });
@@ -1261,7 +1434,7 @@ int launch_cols_many(nufft_plan rep, const PassArgs<T> *args, int nprob, int ny,
 
 template <typename T, int KM>
 int launch_rows_many(nufft_plan rep, const PassArgs<T> *args, const Beta<T, KM> *betas, int nprob,
-                     bool adjoint, const void *in, void *out, cudaStream_t s) {
+                     bool adjoint, const ManyIO &io, cudaStream_t s) {
     return dispatch_P_many(rep->L1, [&](auto PC) -> int {
         constexpr int P = decltype(PC)::value;
         const int TT = adjoint ? P / e_of<T, P, PK_ROW_ADJ>() : P / e_of<T, P, PK_ROW_FWD>();
@@ -1272,11 +1445,11 @@ int launch_rows_many(nufft_plan rep, const PassArgs<T> *args, const Beta<T, KM> 
         if (adjoint) {
             auto kern = k_passA_many<T, P, KM>;
             if (int rc = set_smem(kern, smem, rep->device, done_a)) return rc;
-            kern<<<grid, block, smem, s>>>(args, betas, (const cx<T> *)in, (cx<T> *)out);
+            kern<<<grid, block, smem, s>>>(args, betas, io);
         } else {
             auto kern = k_pass2_many<T, P, KM>;
             if (int rc = set_smem(kern, smem, rep->device, done_2)) return rc;
-            kern<<<grid, block, smem, s>>>(args, betas, (const cx<T> *)in, (cx<T> *)out);
+            kern<<<grid, block, smem, s>>>(args, betas, io);
         }
         return launch_status();
     });
@@ -1323,6 +1496,49 @@ int launch_rows_2d(nufft_plan p, const PassArgs<T> &a0, cudaStream_t s) {
     });
 }
 
+// The 2D adjoint (section 4): the row pass, one CTA per x-grid row, the y-ranks in groups
+// of p->G2a; then the column pass (pass B in its 2D mode) with the plan's rank split.
+template <typename T, int KM>
+int launch_rows_2d_adj(nufft_plan p, const PassArgs<T> &a0, cudaStream_t s) {
+    PassArgs<T> a = a0;
+    a.S = p->SA;
+    a.G = p->G2a;
+    a.twr = (const cx<T> *)p->twst1a;
+    a.CQ = p->CB;
+    a.lgCQ = 0;
+    while ((1 << a.lgCQ) < a.CQ) ++a.lgCQ;
+    Beta<T, KM> bx, by;
+    for (int r = 0; r < KM; ++r)
+        for (int q = 0; q < KM; ++q) {
+            bx.b[r][q] = (T)p->beta[r][q];
+            by.b[r][q] = (T)p->beta2[r][q];
+        }
+    return dispatch_P(p->L1, [&](auto PC) -> int {
+        constexpr int P = decltype(PC)::value;
+        constexpr int TT = P / e_of<T, P, PK_ROW_ADJ>();
+        static SmemFlags done{};
+        auto kern = k_passA2d<T, P, KM>;
+        if (int r = set_smem(kern, p->smemA2d, p->device, done)) return r;
+        kern<<<dim3(p->L2), dim3(p->nt2a * TT), p->smemA2d, s>>>(a, bx, by);
+        return launch_status();
+    });
+}
+
+template <typename T>
+int launch_cols_2d_adj(nufft_plan p, const PassArgs<T> &a0, cudaStream_t s) {
+    PassArgs<T> a = a0;
+    cols_fields<T>(p, a, true);
+    return dispatch_P(p->L2, [&](auto PC) -> int {
+        constexpr int P = decltype(PC)::value;
+        constexpr int TT = P / e_of<T, P, PK_COL_ADJ>();
+        static SmemFlags done{};
+        auto kern = k_passB2d<T, P>;
+        if (int r = set_smem(kern, p->smemB, p->device, done)) return r;
+        kern<<<dim3(p->L1 / a.C, p->SBsplit), dim3(a.C * TT), p->smemB, s>>>(a);
+        return launch_status();
+    });
+}
+
 // Common arguments of every pass of plan p (defined in exec.cu).
 template <typename T>
 PassArgs<T> base_args(nufft_plan p);
@@ -1332,21 +1548,21 @@ PassArgs<T> base_args(nufft_plan p);
     extern template int launch_rows<T, KM>(nufft_plan, const PassArgs<T> &, bool, cudaStream_t);
 #define NUFFT_DECLARE_COLS(T) \
     extern template int launch_cols<T>(nufft_plan, const PassArgs<T> &, bool, cudaStream_t);
-#define NUFFT_DECLARE_2D_T(T, KM) \
-    extern template int launch_rows_2d<T, KM>(nufft_plan, const PassArgs<T> &, cudaStream_t);
-#define NUFFT_DECLARE_COLS_2D_T(T) \
-    extern template int launch_cols_2d<T>(nufft_plan, const PassArgs<T> &, cudaStream_t);
+#define NUFFT_DECLARE_2D_T(T, KM)                                                          \
+    extern template int launch_rows_2d<T, KM>(nufft_plan, const PassArgs<T> &, cudaStream_t); \
+    extern template int launch_rows_2d_adj<T, KM>(nufft_plan, const PassArgs<T> &, cudaStream_t);
+#define NUFFT_DECLARE_COLS_2D_T(T)                                                       \
+    extern template int launch_cols_2d<T>(nufft_plan, const PassArgs<T> &, cudaStream_t); \
+    extern template int launch_cols_2d_adj<T>(nufft_plan, const PassArgs<T> &, cudaStream_t);
 // batched launchers: FP32 only
-#define NUFFT_DECLARE_MANY(KM)                                                                         \
-    extern template int launch_rows_many<float, KM>(nufft_plan, const PassArgs<float> *,              \
-                                                    const Beta<float, KM> *, int, bool, const void *, \
-                                                    void *, cudaStream_t);
-#define NUFFT_DECLARE_2D(KM) \
-    extern template int launch_rows_2d<float, KM>(nufft_plan, const PassArgs<float> &, cudaStream_t);
-#define NUFFT_DECLARE_COLS_2D() \
-    extern template int launch_cols_2d<float>(nufft_plan, const PassArgs<float> &, cudaStream_t);
+#define NUFFT_DECLARE_MANY(KM)                                                            \
+    extern template int launch_rows_many<float, KM>(nufft_plan, const PassArgs<float> *, \
+                                                    const Beta<float, KM> *, int, bool,   \
+                                                    const ManyIO &, cudaStream_t);
+#define NUFFT_DECLARE_2D(KM) NUFFT_DECLARE_2D_T(float, KM)
+#define NUFFT_DECLARE_COLS_2D() NUFFT_DECLARE_COLS_2D_T(float)
 #define NUFFT_DECLARE_COLS_MANY()                                                                  \
     extern template int launch_cols_many<float>(nufft_plan, const PassArgs<float> *, int, int, bool, \
-                                                const void *, void *, cudaStream_t);
+                                                const ManyIO &, cudaStream_t);
 
 }  // namespace nufft

@@ -409,13 +409,11 @@ void free_plan(nufft_plan p) {
     if (p->inv_host) cudaFreeHost(p->inv_host);
     for (void *b : {p->sb_Y, p->sb_fscr, p->sb_part, (void *)p->sb_cnt, p->sb_args, p->sb_beta})
         if (b) cudaFree(b);
-    if (p->sb_host) cudaFreeHost(p->sb_host);
     for (void *b : {p->st_g, p->st_fp, p->st_gc, p->st_gx})
         if (b) cudaFree(b);
     if (p->st_copy) cudaStreamDestroy(p->st_copy);
     for (cudaEvent_t e : p->st_ev)
         if (e) cudaEventDestroy(e);
-    if (p->sb_ev) cudaEventDestroy(p->sb_ev);
     if (p->inv_fft) free_plan(p->inv_fft);
     for (cudaEvent_t e : p->ev) if (e) cudaEventDestroy(e);
     delete p;
@@ -514,6 +512,22 @@ int plan_device_2d(nufft_plan p, const double *x, const double *y, cudaStream_t 
         p->nt2 = std::max(1, nt);
         p->smem2 = bytes(G);
     }
+    {
+        // the adjoint row pass: an accumulator row and G2a slots (all K2 y-ranks when
+        // they fit, else groups), with teams for G2a inverse row FFTs per group
+        const int E1a = std::min(EmaxT<T, PK_ROW_ADJ>::v, p->L1), TT1a = p->L1 / E1a;
+        auto bytes = [&](int G) { return ((size_t)p->L1 + (size_t)G * p->SA) * 2 * sizeof(T); };
+        int G = p->K2;
+        while (G > 1 && bytes(G) > SMEM_BUDGET) --G;
+        if (bytes(G) > SMEM_BUDGET) return NUFFT_EUNSUPPORTED;
+        p->G2a = G;
+        const int maxt = std::max(1, 256 / TT1a);
+        const int rounds = (G + maxt - 1) / maxt;
+        int nt = (G + rounds - 1) / rounds;
+        if (nt * TT1a < 64) nt = std::min(maxt, std::max(nt, (64 + TT1a - 1) / TT1a));
+        p->nt2a = std::max(1, nt);
+        p->smemA2d = bytes(G);
+    }
 
     int rc = sort_samples<T>(p, s);
     if (rc) return rc;
@@ -542,6 +556,12 @@ int plan_device_2d(nufft_plan p, const double *x, const double *y, cudaStream_t 
     NUFFT_CUDA_TRY(dev_malloc((void **)&p->err, sizeof(int)));
     NUFFT_CUDA_TRY(cudaMemsetAsync(p->err, 0, sizeof(int), s));
     p->work_bytes += (int64_t)(((size_t)p->K * p->L + Mi) * cxs + Mi * (2 * sizeof(int32_t) + 2 * sizeof(double)));
+    if (p->SBsplit > 1) {   // the adjoint's column pass splits the x-ranks over CTAs
+        NUFFT_CUDA_TRY(dev_malloc((void **)&p->part, (size_t)p->SBsplit * p->L * cxs));
+        NUFFT_CUDA_TRY(dev_malloc((void **)&p->counters, (size_t)(p->L1 / p->CB) * sizeof(int)));
+        NUFFT_CUDA_TRY(cudaMemsetAsync(p->counters, 0, (size_t)(p->L1 / p->CB) * sizeof(int), s));
+        p->work_bytes += (int64_t)((size_t)p->SBsplit * p->L * cxs + (p->L1 / p->CB) * sizeof(int));
+    }
     NUFFT_CUDA_TRY(cudaStreamSynchronize(s));
     return NUFFT_OK;
 }

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <vector>
 
 #include "passes.cuh"
@@ -24,18 +25,38 @@ NUFFT_DECLARE_MANY(16)
 
 namespace {
 
+// Coefficients per member: N, or m n for a 2D plan.
+int64_t ncoef(nufft_plan p) { return p->dims == 2 ? p->N * p->N2 : p->N; }
+
 bool batchable(nufft_plan p) {
     return p->prec == NUFFT_F32 && p->dims == 1 && p->M > 0 && std::max(p->L1, p->L2) <= MANY_P_MAX;
 }
 
-// The workspace for B members (kept, grown when a larger B comes).
-int ensure_workspace(nufft_plan p, int64_t B, cudaStream_t s) {
+// The per-member argument arrays, each `cap` entries, in the order of ArgSet.
+enum ArgSet { AS_FWD1 = 0, AS_FWD2, AS_DER1, AS_DER2, AS_ADJA, AS_ADJB, AS_COUNT };
+
+// A member's arguments: its workspace slice.  Its data pointers come from the launch
+// (ManyIO: the call's base pointers and leading dimensions), so the arguments do not
+// depend on the call and are built once, by nufft2_plan_reserve.
+PassArgs<float> member(nufft_plan p, int64_t b) {
+    PassArgs<float> a = base_args<float>(p);
+    a.Y = (cx<float> *)p->sb_Y + b * (int64_t)(p->K + 1) * p->L;
+    a.fscr = (cx<float> *)p->sb_fscr + b * p->M;
+    a.part = (cx<float> *)p->sb_part + b * (int64_t)std::max(1, p->SBsplit) * p->L;
+    a.counters = p->sb_cnt + b * (int64_t)(p->L1 / p->CB);
+    a.in_off = 0;
+    a.out_off = 0;
+    return a;
+}
+
+// The workspace and the member arguments for up to B members: the plan stage of the
+// batch calls (allocates, uploads, synchronises), so that the exec calls do neither.
+int reserve_batch(nufft_plan p, int64_t B, cudaStream_t s) {
     if (B <= p->sb_cap) return NUFFT_OK;
     NUFFT_CUDA_TRY(cudaStreamSynchronize(s));   // the old workspace may be in use
     for (void *q : {p->sb_Y, p->sb_fscr, p->sb_part, (void *)p->sb_cnt, p->sb_args, p->sb_beta})
         if (q) cudaFree(q);
-    if (p->sb_host) cudaFreeHost(p->sb_host);
-    p->sb_Y = p->sb_fscr = p->sb_part = p->sb_args = p->sb_beta = p->sb_host = nullptr;
+    p->sb_Y = p->sb_fscr = p->sb_part = p->sb_args = p->sb_beta = nullptr;
     p->sb_cnt = nullptr;
     p->sb_cap = 0;
     const size_t cxs = 8, nb = (size_t)B;
@@ -45,100 +66,77 @@ int ensure_workspace(nufft_plan p, int64_t B, cudaStream_t s) {
     NUFFT_CUDA_TRY(dev_malloc(&p->sb_part, nb * (size_t)std::max(1, p->SBsplit) * p->L * cxs));
     NUFFT_CUDA_TRY(dev_malloc((void **)&p->sb_cnt, nb * ncnt * sizeof(int)));
     NUFFT_CUDA_TRY(cudaMemsetAsync(p->sb_cnt, 0, nb * ncnt * sizeof(int), s));
-    NUFFT_CUDA_TRY(dev_malloc(&p->sb_args, 2 * nb * sizeof(PassArgs<float>)));
+    NUFFT_CUDA_TRY(dev_malloc(&p->sb_args, AS_COUNT * nb * sizeof(PassArgs<float>)));
     const int km = p->kmax;
     NUFFT_CUDA_TRY(dev_malloc(&p->sb_beta, nb * (size_t)km * km * sizeof(float)));
-    NUFFT_CUDA_TRY(cudaMallocHost(&p->sb_host, 2 * nb * sizeof(PassArgs<float>)));
-    if (!p->sb_ev) NUFFT_CUDA_TRY(cudaEventCreateWithFlags(&p->sb_ev, cudaEventDisableTiming));
     // beta for every member (the batched kernels index it by member), laid out as
     // Beta<float, kmax>: kmax x kmax row-major
     std::vector<float> be(nb * (size_t)km * km);
     for (size_t b = 0; b < nb; ++b)
         for (int r = 0; r < km; ++r)
             for (int q = 0; q < km; ++q) be[(b * km + r) * km + q] = (float)p->beta[r][q];
+    std::vector<PassArgs<float>> v(AS_COUNT * nb);
+    for (size_t b = 0; b < nb; ++b) {
+        const PassArgs<float> a = member(p, (int64_t)b);
+        PassArgs<float> d = a;   // the forward with f': K + 1 ranks
+        d.mode |= MODE_DERIV;
+        d.nranks = p->K + 1;
+        PassArgs<float> f1 = a, f2 = a, d1 = d, d2 = d, aA = a, aB = a;
+        cols_fields<float>(p, f1, false);
+        cols_fields<float>(p, d1, false);
+        cols_fields<float>(p, aB, true);
+        if (int rc = rows_fields<float>(p, f2, false)) return rc;
+        if (int rc = rows_fields<float>(p, d2, false)) return rc;
+        if (int rc = rows_fields<float>(p, aA, true)) return rc;
+        v[AS_FWD1 * nb + b] = f1;
+        v[AS_FWD2 * nb + b] = f2;
+        v[AS_DER1 * nb + b] = d1;
+        v[AS_DER2 * nb + b] = d2;
+        v[AS_ADJA * nb + b] = aA;
+        v[AS_ADJB * nb + b] = aB;
+    }
     NUFFT_CUDA_TRY(cudaMemcpy(p->sb_beta, be.data(), be.size() * sizeof(float), cudaMemcpyHostToDevice));
+    NUFFT_CUDA_TRY(cudaMemcpy(p->sb_args, v.data(), v.size() * sizeof(PassArgs<float>), cudaMemcpyHostToDevice));
+    NUFFT_CUDA_TRY(cudaStreamSynchronize(s));
     p->sb_cap = B;
     p->work_bytes += (int64_t)(nb * ((size_t)(p->K + 1) * p->L + p->M + (size_t)std::max(1, p->SBsplit) * p->L) * cxs);
     return NUFFT_OK;
 }
 
-// Upload the two argument arrays (first and second pass, B each) of this call.
-int upload_args(nufft_plan p, const std::vector<PassArgs<float>> &v, cudaStream_t s) {
-    // the staging buffer is reused: the previous call's copy must have been made
-    NUFFT_CUDA_TRY(cudaEventSynchronize(p->sb_ev));
-    std::copy(v.begin(), v.end(), (PassArgs<float> *)p->sb_host);
-    NUFFT_CUDA_TRY(cudaMemcpyAsync(p->sb_args, p->sb_host, v.size() * sizeof(PassArgs<float>),
-                                   cudaMemcpyHostToDevice, s));
-    NUFFT_CUDA_TRY(cudaEventRecord(p->sb_ev, s));
-    return NUFFT_OK;
+const PassArgs<float> *argset(nufft_plan p, ArgSet k) {
+    return (const PassArgs<float> *)p->sb_args + (int64_t)k * p->sb_cap;
 }
 
-// A member's arguments: its workspace slice; input and output offsets into the packed
-// batch (the kernels add the call's base pointers).
-PassArgs<float> member(nufft_plan p, int64_t b, int64_t in_off, int64_t out_off) {
-    PassArgs<float> a = base_args<float>(p);
-    a.Y = (cx<float> *)p->sb_Y + b * (int64_t)(p->K + 1) * p->L;
-    a.fscr = (cx<float> *)p->sb_fscr + b * p->M;
-    a.part = (cx<float> *)p->sb_part + b * (int64_t)std::max(1, p->SBsplit) * p->L;
-    a.counters = p->sb_cnt + b * (int64_t)(p->L1 / p->CB);
-    a.in_off = in_off;
-    a.out_off = out_off;
-    return a;
-}
-
-int rows_many_km(nufft_plan p, const PassArgs<float> *args, int64_t B, bool adjoint, const void *in, void *out,
+int rows_many_km(nufft_plan p, const PassArgs<float> *args, int64_t B, bool adjoint, const ManyIO &io,
                  cudaStream_t s) {
     const void *be = p->sb_beta;
     const int n = (int)B;
     switch (p->kmax) {
-        case 4: return launch_rows_many<float, 4>(p, args, (const Beta<float, 4> *)be, n, adjoint, in, out, s);
-        case 8: return launch_rows_many<float, 8>(p, args, (const Beta<float, 8> *)be, n, adjoint, in, out, s);
-        case 12: return launch_rows_many<float, 12>(p, args, (const Beta<float, 12> *)be, n, adjoint, in, out, s);
-        case 16: return launch_rows_many<float, 16>(p, args, (const Beta<float, 16> *)be, n, adjoint, in, out, s);
+        case 4: return launch_rows_many<float, 4>(p, args, (const Beta<float, 4> *)be, n, adjoint, io, s);
+        case 8: return launch_rows_many<float, 8>(p, args, (const Beta<float, 8> *)be, n, adjoint, io, s);
+        case 12: return launch_rows_many<float, 12>(p, args, (const Beta<float, 12> *)be, n, adjoint, io, s);
+        case 16: return launch_rows_many<float, 16>(p, args, (const Beta<float, 16> *)be, n, adjoint, io, s);
         default: return NUFFT_EUNSUPPORTED;
     }
 }
 
-// Forward (deriv = false) or forward with f' (deriv = true) of B members.
+// Forward (deriv = false) or forward with f' (deriv = true) of B <= sb_cap members: two
+// launches, no allocation, no host synchronisation.
 int fwd_batch(nufft_plan p, int64_t B, const void *c, int64_t ldc, void *f, void *fp, int64_t ldf, bool deriv,
               cudaStream_t s) {
-    if (int rc = ensure_workspace(p, B, s)) return rc;
-    std::vector<PassArgs<float>> v((size_t)(2 * B));
-    for (int64_t b = 0; b < B; ++b) {
-        PassArgs<float> a = member(p, b, b * ldc, b * ldf);
-        if (deriv) {
-            a.mode |= MODE_DERIV;
-            a.nranks = p->K + 1;
-            a.out2 = (cx<float> *)fp + b * ldf;
-        }
-        PassArgs<float> a1 = a, a2 = a;
-        cols_fields<float>(p, a1, false);
-        if (int rc = rows_fields<float>(p, a2, false)) return rc;
-        v[(size_t)b] = a1;
-        v[(size_t)(B + b)] = a2;
-    }
-    if (int rc = upload_args(p, v, s)) return rc;
-    const PassArgs<float> *args = (const PassArgs<float> *)p->sb_args;
-    if (int rc = launch_cols_many<float>(p, args, (int)B, deriv ? p->K + 1 : p->K, false, c, f, s)) return rc;
-    return rows_many_km(p, args + B, B, false, c, f, s);
+    if (B > p->sb_cap) return NUFFT_ESTATE;
+    const ManyIO io{c, f, deriv ? fp : nullptr, ldc, ldf};
+    const PassArgs<float> *a1 = argset(p, deriv ? AS_DER1 : AS_FWD1), *a2 = argset(p, deriv ? AS_DER2 : AS_FWD2);
+    if (int rc = launch_cols_many<float>(p, a1, (int)B, deriv ? p->K + 1 : p->K, false, io, s)) return rc;
+    return rows_many_km(p, a2, B, false, io, s);
 }
 
-// Adjoint of B members: c_b = A^H g_b.
+// Adjoint of B <= sb_cap members: c_b = A^H g_b.
 int adj_batch(nufft_plan p, int64_t B, const void *g, int64_t ldg, void *c, int64_t ldc, cudaStream_t s) {
-    if (int rc = ensure_workspace(p, B, s)) return rc;
-    std::vector<PassArgs<float>> v((size_t)(2 * B));
-    for (int64_t b = 0; b < B; ++b) {
-        PassArgs<float> a = member(p, b, b * ldg, b * ldc);
-        PassArgs<float> aA = a, aB = a;
-        if (int rc = rows_fields<float>(p, aA, true)) return rc;
-        cols_fields<float>(p, aB, true);
-        v[(size_t)b] = aA;
-        v[(size_t)(B + b)] = aB;
-    }
-    if (int rc = upload_args(p, v, s)) return rc;
-    const PassArgs<float> *args = (const PassArgs<float> *)p->sb_args;
-    if (int rc = rows_many_km(p, args, B, true, g, c, s)) return rc;
-    return launch_cols_many<float>(p, args + B, (int)B, std::max(1, p->SBsplit), true, g, c, s);
+    if (B > p->sb_cap) return NUFFT_ESTATE;
+    const ManyIO io{g, c, nullptr, ldg, ldc};
+    if (int rc = rows_many_km(p, argset(p, AS_ADJA), B, true, io, s)) return rc;
+    return launch_cols_many<float>(p, argset(p, AS_ADJB), (int)B, std::max(1, p->SBsplit), true, io, s);
 }
 
 // gx_j (+)= sum_b Re(conj(g_bj) f'_bj)
@@ -162,12 +160,33 @@ int grid_m(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 
 
 using nufft::adj_batch;
 using nufft::batchable;
+using nufft::ncoef;
+
+extern "C" int nufft2_plan_reserve(nufft_plan p, int64_t B_max, unsigned what, void *stream) {
+    nufft::NvtxRange nvtx_range_("nufft2_plan_reserve");
+    if (!p || B_max < 0 || (what & ~NUFFT_RESERVE_STEP_HOST)) return NUFFT_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (B_max >= 2 && batchable(p))
+        if (int rc = nufft::reserve_batch(p, B_max, s)) return rc;
+    if (what & NUFFT_RESERVE_STEP_HOST) {
+        if (p->dims == 2) return NUFFT_EUNSUPPORTED;
+        if (int rc = nufft::reserve_step_host(p, s)) return rc;
+    }
+    return NUFFT_OK;
+}
+
+extern "C" int nufft2_plan_reserved(nufft_plan p, int64_t *B_max, int *step_host) {
+    if (!p) return NUFFT_EINVAL;
+    if (B_max) *B_max = batchable(p) ? p->sb_cap : INT64_MAX;
+    if (step_host) *step_host = p->st_g && p->st_copy ? 1 : 0;
+    return NUFFT_OK;
+}
 using nufft::fwd_batch;
 
 extern "C" int nufft2_exec_batch(nufft_plan p, int64_t B, const void *c_dev, int64_t ldc, void *f_dev, int64_t ldf,
                                  void *stream) {
     nufft::NvtxRange nvtx_range_("nufft2_exec_batch");
-    if (!p || B < 0 || ldc < p->N || ldf < p->M) return NUFFT_EINVAL;
+    if (!p || B < 0 || ldc < ncoef(p) || ldf < p->M) return NUFFT_EINVAL;
     if (B > 0 && (!c_dev || (p->M > 0 && !f_dev))) return NUFFT_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     if (B >= 2 && batchable(p)) return fwd_batch(p, B, c_dev, ldc, f_dev, nullptr, ldf, false, s);
@@ -183,7 +202,7 @@ extern "C" int nufft2_exec_batch(nufft_plan p, int64_t B, const void *c_dev, int
 extern "C" int nufft1_exec_batch(nufft_plan p, int64_t B, const void *g_dev, int64_t ldg, void *c_dev, int64_t ldc,
                                  void *stream) {
     nufft::NvtxRange nvtx_range_("nufft1_exec_batch");
-    if (!p || B < 0 || ldc < p->N || ldg < p->M) return NUFFT_EINVAL;
+    if (!p || B < 0 || ldc < ncoef(p) || ldg < p->M) return NUFFT_EINVAL;
     if (B > 0 && (!c_dev || (p->M > 0 && !g_dev))) return NUFFT_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     if (B >= 2 && batchable(p)) return adj_batch(p, B, g_dev, ldg, c_dev, ldc, s);

@@ -29,7 +29,7 @@ def rms(a):
 
 def assert_close(got, ref, prec="f32", scale=1.0, what=""):
     """Both bounds above, each widened by `scale` (the derivative's larger rounding)."""
-    got, ref = np.asarray(got), np.asarray(ref)
+    got, ref = np.ravel(np.asarray(got)), np.ravel(np.asarray(ref))
     tol2, tolel = TOL[prec]
     err = np.abs(got - ref)
     worst = int(np.argmax(err)) if err.size else 0

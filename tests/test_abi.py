@@ -55,6 +55,8 @@ def test_argument_errors_without_gpu(lib):
     assert lib.nufft2_exec_batch(None, 1, None, 1, None, 1, None) == -1
     assert lib.nufft2_plan_info(None, None, None, None, None) == -1
     assert lib.nufft_destroy(None) == 0
+    assert lib.nufft2_plan_reserve(None, 4, 0, None) == -1
+    assert lib.nufft2_plan_reserved(None, None, None) == -1
     ms, fl = ctypes.c_float(), ctypes.c_double()
     assert lib.nufft_fp32_fma_peak(0, 1, None, ctypes.byref(ms), ctypes.byref(fl)) == -1      # iters < 1
     assert lib.nufft_fp32_fma_peak(10, 3, None, ctypes.byref(ms), ctypes.byref(fl)) == -1     # blocks per SM

@@ -294,3 +294,73 @@ def test_half_tile_matches_oracle(api, N, long_cols):
     g = wl.cotangent_cn(N, 45).astype(np.complex64)
     ca = p.adjoint(torch.tensor(g, device="cuda")).cpu().numpy()
     assert_close(ca, lowrank.nufft2_adjoint(P, g.astype(np.complex128)), "f32", what="oracle")
+
+
+def test_reserved_batch_calls_allocate_nothing_and_capture_in_a_graph(api):
+    """After nufft2_plan_reserve the batch calls and the host-buffer step neither allocate
+    nor synchronise: a batch bigger than the reservation is refused (NUFFT_ESTATE) instead
+    of growing the workspace, and the very first batch forward, adjoint and forward-with-f'
+    of a fresh plan can be captured into a CUDA graph whose replay equals the direct calls."""
+    import ctypes
+    from paper_1701_04492_gb300 import _lib
+    lib = _lib.load()
+    N, M, B = 4096, 5000, 5
+    x = wl.samples_uniform(M, 900)
+    plan = api.Plan(N, x, 1e-9, "f32")
+    c = torch.tensor(np.stack([wl.coeffs_cn(N, 901 + b) for b in range(B)]).astype(np.complex64), device="cuda")
+    g = torch.tensor(np.stack([wl.cotangent_cn(M, 911 + b) for b in range(B)]).astype(np.complex64), device="cuda")
+    f = torch.empty(B, M, dtype=torch.complex64, device="cuda")
+    fp = torch.empty_like(f)
+    gc = torch.empty(B, N, dtype=torch.complex64, device="cuda")
+    st = api._stream(plan.device)
+    vp = ctypes.c_void_p
+    # nothing reserved yet: the batched path refuses rather than allocating
+    assert lib.nufft2_exec_batch(plan._h, B, vp(c.data_ptr()), N, vp(f.data_ptr()), M, st) == -5
+    plan.reserve(B)
+    assert lib.nufft2_exec_batch(plan._h, B + 1, vp(c.data_ptr()), N, vp(f.data_ptr()), M, st) == -5
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        plan.forward_batch(c, f)
+        plan.adjoint_batch(g, gc)
+    torch.cuda.synchronize()
+    f.zero_()
+    gc.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(f, plan.forward_batch(c))
+    assert torch.equal(gc, plan.adjoint_batch(g))
+    # the forward with f', captured on its own (first use of that argument set)
+    f2, fp2 = torch.empty_like(f), torch.empty_like(f)
+    g2 = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g2, stream=s):
+        plan.forward_deriv_batch(c, f2, fp2)
+    g2.replay()
+    torch.cuda.synchronize()
+    fr, fpr = plan.forward_deriv_batch(c)
+    assert torch.equal(f2, fr) and torch.equal(fp2, fpr)
+    plan.check()
+
+
+def test_step_host_needs_its_reservation(api):
+    """nufft2_step_host without NUFFT_RESERVE_STEP_HOST returns NUFFT_ESTATE (it never
+    allocates); after the reservation it runs."""
+    import ctypes
+    from paper_1701_04492_gb300 import _lib
+    lib = _lib.load()
+    N, M = 2048, 3000
+    plan = api.Plan(N, wl.samples_uniform(M, 920), 1e-9, "f32")
+    ch = torch.tensor(wl.coeffs_cn(N, 921).astype(np.complex64)).pin_memory()
+    gh = torch.tensor(wl.cotangent_cn(M, 922).astype(np.complex64)).pin_memory()
+    fh = torch.empty(M, dtype=torch.complex64).pin_memory()
+    gch = torch.empty(N, dtype=torch.complex64).pin_memory()
+    gxh = torch.empty(M, dtype=torch.float32).pin_memory()
+    vp = ctypes.c_void_p
+    args = [vp(t.data_ptr()) for t in (ch, gh, fh, gch, gxh)]
+    assert lib.nufft2_step_host(plan._h, *args, api._stream(plan.device)) == -5
+    plan.reserve(0, step_host=True)
+    assert lib.nufft2_step_host(plan._h, *args, api._stream(plan.device)) == 0
+    torch.cuda.synchronize()
+    assert torch.equal(fh, plan.forward_deriv(ch.cuda())[0].cpu())   # the step's f comes with f'
