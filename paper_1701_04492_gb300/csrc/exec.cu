@@ -20,8 +20,13 @@ NUFFT_DECLARE_ROWS(double, 4)
 NUFFT_DECLARE_ROWS(double, 8)
 NUFFT_DECLARE_ROWS(double, 12)
 NUFFT_DECLARE_ROWS(double, 16)
+NUFFT_DECLARE_ROWS(dfloat, 4)
+NUFFT_DECLARE_ROWS(dfloat, 8)
+NUFFT_DECLARE_ROWS(dfloat, 12)
+NUFFT_DECLARE_ROWS(dfloat, 16)
 NUFFT_DECLARE_COLS(float)
 NUFFT_DECLARE_COLS(double)
+NUFFT_DECLARE_COLS(dfloat)
 NUFFT_DECLARE_COLS_2D()
 NUFFT_DECLARE_2D(4)
 NUFFT_DECLARE_2D(8)
@@ -139,16 +144,16 @@ PassArgs<T> base_args(nufft_plan p) {
     a.perm = p->perm;
     a.bstart = p->bstart;
     a.dsorted = (const T *)p->dsorted;
-    a.twc = (const cx<T> *)p->twst2;
-    a.twr = (const cx<T> *)p->twst1;
-    a.twhi = (const cx<T> *)p->twhi;
+    a.twc = tab<T>(p->twst2, p->twst2_dw);
+    a.twr = tab<T>(p->twst1, p->twst1_dw);
+    a.twhi = tab<T>(p->twhi, p->twhi_dw);
     a.part = (cx<T> *)p->part;
     a.counters = p->counters;
     a.err = p->err;
     a.vfac = (const T *)p->Vfac;
     a.ufac = (const cx<T> *)p->Ufac;
     a.mode = p->Ufac ? MODE_FACTORS : 0;
-    a.twlo = (const cx<T> *)p->twlo;
+    a.twlo = tab<T>(p->twlo, p->twlo_dw);
     a.N = p->N;
     a.M = p->M;
     a.L = p->L;
@@ -167,6 +172,7 @@ PassArgs<T> base_args(nufft_plan p) {
 
 template PassArgs<float> base_args<float>(nufft_plan);
 template PassArgs<double> base_args<double>(nufft_plan);
+template PassArgs<dfloat> base_args<dfloat>(nufft_plan);
 
 namespace {
 
@@ -295,7 +301,7 @@ __global__ void k_fac_V(int64_t N, int K, int trivial, T *__restrict__ V) {
 }
 
 template <typename T>
-__global__ void k_fac_U(const T *__restrict__ dsorted, int64_t M, int K, double inv_gamma, int trivial,
+__global__ void k_fac_U(const io_r<T> *__restrict__ dsorted, int64_t M, int K, double inv_gamma, int trivial,
                         const Beta<double, KMAX_ALL> aw, cx<T> *__restrict__ U) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -312,7 +318,7 @@ __global__ void k_fac_U(const T *__restrict__ dsorted, int64_t M, int K, double 
             double sum = 0.0;
             for (int q = 0; q < K; ++q) sum += aw.b[r][q] * Tp[q];
             const cx<double> u = mul_ipow<double>(mk<double>(cs * sum, -sn * sum), r);
-            U[i * K + r] = mk<T>((T)u.x, (T)u.y);
+            U[i * K + r] = mk<T>(T(u.x), T(u.y));
         }
     }
 }
@@ -332,14 +338,14 @@ int plan_factor_tables(nufft_plan p, cudaStream_t s) {
     const int trivial = p->gamma == 0.0;
     const double inv_gamma = trivial ? 0.0 : 1.0 / p->gamma;
     if (p->M > 0)
-        k_fac_U<T><<<grid1d(p->M), 256, 0, s>>>((const T *)p->dsorted, p->M, p->K, inv_gamma, trivial, aw,
+        k_fac_U<T><<<grid1d(p->M), 256, 0, s>>>((const io_r<T> *)p->dsorted, p->M, p->K, inv_gamma, trivial, aw,
                                                 (cx<T> *)p->Ufac);
     k_fac_V<T><<<grid1d(p->N), 256, 0, s>>>(p->N, p->K, trivial, (T *)p->Vfac);
     NUFFT_CUDA_TRY(cudaGetLastError());
     return NUFFT_OK;
 }
 
-template int plan_factor_tables<double>(nufft_plan, cudaStream_t);
+template int plan_factor_tables<dfloat>(nufft_plan, cudaStream_t);
 
 namespace {
 }  // namespace
@@ -436,13 +442,14 @@ template <typename T>
 int exec_forward(nufft_plan p, const void *c, void *f, cudaStream_t s) {
     if (p->dims == 2) return exec_forward_2d<T>(p, c, f, s);
     if (p->M == 0) return NUFFT_OK;
-    PassArgs<T> a = base_args<T>(p);
-    a.in = (const cx<T> *)c;
-    a.out = (cx<T> *)f;
+    using A = Arith<T>;
+    PassArgs<A> a = base_args<A>(p);
+    a.in = (const io_c<A> *)c;
+    a.out = (io_c<A> *)f;
     if (int rc = mark(p, s, true)) return rc;
-    if (int rc = launch_cols<T>(p, a, false, s)) return rc;
+    if (int rc = launch_cols<A>(p, a, false, s)) return rc;
     if (int rc = mark(p, s, false)) return rc;
-    if (int rc = run_rows<T>(p, a, false, s)) return rc;
+    if (int rc = run_rows<A>(p, a, false, s)) return rc;
     return mark(p, s, false);
 }
 
@@ -453,25 +460,27 @@ int exec_adjoint(nufft_plan p, const void *g, void *c, cudaStream_t s) {
         NUFFT_CUDA_TRY(cudaMemsetAsync(c, 0, (size_t)p->N * 2 * sizeof(T), s));
         return NUFFT_OK;
     }
-    PassArgs<T> a = base_args<T>(p);
-    a.in = (const cx<T> *)g;
-    a.out = (cx<T> *)c;
+    using A = Arith<T>;
+    PassArgs<A> a = base_args<A>(p);
+    a.in = (const io_c<A> *)g;
+    a.out = (io_c<A> *)c;
     if (int rc = mark(p, s, true)) return rc;
-    if (int rc = run_rows<T>(p, a, true, s)) return rc;
+    if (int rc = run_rows<A>(p, a, true, s)) return rc;
     if (int rc = mark(p, s, false)) return rc;
-    if (int rc = launch_cols<T>(p, a, true, s)) return rc;
+    if (int rc = launch_cols<A>(p, a, true, s)) return rc;
     return mark(p, s, false);
 }
 
 template <typename T>
 int exec_dx(nufft_plan p, const void *c, const void *g, void *gx, int acc, cudaStream_t s) {
     if (p->M == 0) return NUFFT_OK;
-    PassArgs<T> a = base_args<T>(p);
-    a.in = (const cx<T> *)c;
-    a.g = (const cx<T> *)g;
-    a.gx = (T *)gx;
+    using A = Arith<T>;
+    PassArgs<A> a = base_args<A>(p);
+    a.in = (const io_c<A> *)c;
+    a.g = (const io_c<A> *)g;
+    a.gx = (io_r<A> *)gx;
     a.accumulate = acc;
-    if (!kFactors<T> && p->G >= p->K + 1) {
+    if (!kFactors<A> && p->G >= p->K + 1) {
         a.mode |= MODE_DERIV | MODE_GX;
         a.nranks = p->K + 1;
         a.out = nullptr;
@@ -480,9 +489,9 @@ int exec_dx(nufft_plan p, const void *c, const void *g, void *gx, int acc, cudaS
         a.mode |= MODE_PRESCALE | MODE_GX;
     }
     if (int rc = mark(p, s, true)) return rc;
-    if (int rc = launch_cols<T>(p, a, false, s)) return rc;
+    if (int rc = launch_cols<A>(p, a, false, s)) return rc;
     if (int rc = mark(p, s, false)) return rc;
-    if (int rc = run_rows<T>(p, a, false, s)) return rc;
+    if (int rc = run_rows<A>(p, a, false, s)) return rc;
     return mark(p, s, false);
 }
 
@@ -490,27 +499,28 @@ int exec_dx(nufft_plan p, const void *c, const void *g, void *gx, int acc, cudaS
 template <typename T>
 int exec_deriv(nufft_plan p, const void *c, void *f, void *fprime, cudaStream_t s) {
     if (p->M == 0) return NUFFT_OK;
-    if (!kFactors<T> && p->G >= p->K + 1) {
-        PassArgs<T> a = base_args<T>(p);
-        a.in = (const cx<T> *)c;
-        a.out = (cx<T> *)f;
-        a.out2 = (cx<T> *)fprime;
+    using A = Arith<T>;
+    if (!kFactors<A> && p->G >= p->K + 1) {
+        PassArgs<A> a = base_args<A>(p);
+        a.in = (const io_c<A> *)c;
+        a.out = (io_c<A> *)f;
+        a.out2 = (io_c<A> *)fprime;
         a.mode |= MODE_DERIV;
         a.nranks = p->K + 1;
         if (int rc = mark(p, s, true)) return rc;
-        if (int rc = launch_cols<T>(p, a, false, s)) return rc;
+        if (int rc = launch_cols<A>(p, a, false, s)) return rc;
         if (int rc = mark(p, s, false)) return rc;
-        if (int rc = run_rows<T>(p, a, false, s)) return rc;
+        if (int rc = run_rows<A>(p, a, false, s)) return rc;
         return mark(p, s, false);
     }
     // otherwise: the forward, then A((-2 pi i k) o c)
     if (int rc = exec_forward<T>(p, c, f, s)) return rc;
-    PassArgs<T> a = base_args<T>(p);
-    a.in = (const cx<T> *)c;
-    a.out = (cx<T> *)fprime;
+    PassArgs<A> a = base_args<A>(p);
+    a.in = (const io_c<A> *)c;
+    a.out = (io_c<A> *)fprime;
     a.mode |= MODE_PRESCALE;
-    if (int rc = launch_cols<T>(p, a, false, s)) return rc;
-    return run_rows<T>(p, a, false, s);
+    if (int rc = launch_cols<A>(p, a, false, s)) return rc;
+    return run_rows<A>(p, a, false, s);
 }
 
 // gx_j (+)= Re(conj(g_j) f'_j)

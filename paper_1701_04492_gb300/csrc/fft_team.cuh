@@ -21,12 +21,49 @@
 
 #include <utility>
 
+#include "dfloat.cuh"
+
 namespace nufft {
+
+// A complex double-word value: 16 bytes, so that it moves as one vector access.
+struct __align__(16) cdf {
+    dfloat x, y;
+};
 
 template <typename T> struct CxT;
 template <> struct CxT<float> { using type = float2; };
 template <> struct CxT<double> { using type = double2; };
+template <> struct CxT<dfloat> { using type = cdf; };
 template <typename T> using cx = typename CxT<T>::type;
+
+// The types the caller's arrays hold for an element type T: complex64 / float for FP32,
+// complex128 / double for FP64 and for the double-word kernels (which convert on load
+// and on store).
+template <typename T> struct IoT { using c = cx<T>; using r = T; };
+template <> struct IoT<dfloat> { using c = double2; using r = double; };
+template <typename T> using io_c = typename IoT<T>::c;
+template <typename T> using io_r = typename IoT<T>::r;
+
+// Read-only loads of complex values (16-byte double-word values as one vector load).
+__device__ __forceinline__ float2 ldg_cx(const float2 *p) { return __ldg(p); }
+__device__ __forceinline__ double2 ldg_cx(const double2 *p) { return __ldg(p); }
+__device__ __forceinline__ cdf ldg_cx(const cdf *p) {
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+    cdf r;
+    r.x = dfloat(v.x, v.y);
+    r.y = dfloat(v.z, v.w);
+    return r;
+}
+// Loads that bypass L1 (partial sums written by other CTAs of the same launch).
+__device__ __forceinline__ float2 ldcg_cx(const float2 *p) { return __ldcg(p); }
+__device__ __forceinline__ double2 ldcg_cx(const double2 *p) { return __ldcg(p); }
+__device__ __forceinline__ cdf ldcg_cx(const cdf *p) {
+    const float4 v = __ldcg(reinterpret_cast<const float4 *>(p));
+    cdf r;
+    r.x = dfloat(v.x, v.y);
+    r.y = dfloat(v.z, v.w);
+    return r;
+}
 
 template <typename T> __device__ __forceinline__ cx<T> mk(T a, T b) { cx<T> r; r.x = a; r.y = b; return r; }
 template <typename T> __device__ __forceinline__ cx<T> cadd(cx<T> a, cx<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
@@ -166,6 +203,9 @@ template <> struct EmaxBase<float> {
 template <> struct EmaxBase<double> {
     __host__ __device__ static constexpr int of(int) { return 16; }
 };
+template <> struct EmaxBase<dfloat> {
+    __host__ __device__ static constexpr int of(int) { return 16; }
+};
 template <typename T, int KIND> struct EmaxT { static constexpr int v = EmaxBase<T>::of(KIND); };
 template <typename T, int P, int KIND> __host__ __device__ constexpr int e_of() {
     return P < EmaxT<T, KIND>::v ? P : EmaxT<T, KIND>::v;
@@ -209,7 +249,7 @@ struct TeamFft {
                 const int j = v & (NS - 1);
 #pragma unroll
                 for (int i = 1; i < R; ++i) {
-                    const cx<T> w = __ldg(&tw[OFF + (i - 1) * NS + j]);
+                    const cx<T> w = ldg_cx(&tw[OFF + (i - 1) * NS + j]);
                     s[i] = INV ? cmulc<T>(s[i], w) : cmul<T>(s[i], w);
                 }
             }
@@ -233,7 +273,7 @@ struct TeamFft {
             for (int b = 0; b < E / R1; ++b) {
                 const int j = (tt + TT * b) & (R0 - 1);
 #pragma unroll
-                for (int i = 1; i < R1; ++i) t.w[b * (R1 - 1) + i - 1] = __ldg(&tw[TW_OFF1 + (i - 1) * R0 + j]);
+                for (int i = 1; i < R1; ++i) t.w[b * (R1 - 1) + i - 1] = ldg_cx(&tw[TW_OFF1 + (i - 1) * R0 + j]);
             }
         }
         if constexpr (R2 > 1) {
@@ -242,7 +282,7 @@ struct TeamFft {
             for (int b = 0; b < E / R2; ++b) {
                 const int j = (tt + TT * b) & (NS - 1);
 #pragma unroll
-                for (int i = 1; i < R2; ++i) t.w[NW1 + b * (R2 - 1) + i - 1] = __ldg(&tw[TW_OFF2 + (i - 1) * NS + j]);
+                for (int i = 1; i < R2; ++i) t.w[NW1 + b * (R2 - 1) + i - 1] = ldg_cx(&tw[TW_OFF2 + (i - 1) * NS + j]);
             }
         }
     }

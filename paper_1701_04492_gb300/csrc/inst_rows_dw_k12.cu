@@ -1,0 +1,5 @@
+// Explicit instantiation of the row passes for the double-word kernels (the fused FP64
+// exec), rank bound 12.
+#define NUFFT_INST_T dfloat
+#define NUFFT_INST_KM 12
+#include "inst_rows.inc"

@@ -26,6 +26,8 @@ NUFFT_DECLARE_COLS(float)
 NUFFT_DECLARE_COLS(double)
 NUFFT_DECLARE_ROWS(float, 4)
 NUFFT_DECLARE_ROWS(double, 4)
+NUFFT_DECLARE_ROWS(dfloat, 4)
+NUFFT_DECLARE_COLS(dfloat)
 
 namespace {
 
@@ -163,17 +165,19 @@ int grid1(int64_t n) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(RED_BLOCKS, (n + RED_THREADS - 1) / RED_THREADS));
 }
 
-// FFT_P of `in` (its first n_valid entries, zeros beyond) in natural order into `out`.
+// FFT_P of `in` (its first n_valid entries, zeros beyond) in natural order into `out`,
+// in the plan's fused-exec arithmetic (FP32, or double-word for FP64 plans).
 template <typename T>
 int fft_natural(nufft_plan fp, const void *in, int64_t n_valid, void *out, cudaStream_t s) {
-    PassArgs<T> a = base_args<T>(fp);
-    a.in = (const cx<T> *)in;
-    a.out = (cx<T> *)out;
+    using A = Arith<T>;
+    PassArgs<A> a = base_args<A>(fp);
+    a.in = (const io_c<A> *)in;
+    a.out = (io_c<A> *)out;
     a.N = n_valid;
     a.nranks = 1;
-    if (int rc = launch_cols<T>(fp, a, false, s)) return rc;
+    if (int rc = launch_cols<A>(fp, a, false, s)) return rc;
     a.mode |= MODE_PLAIN_OUT;
-    return launch_rows<T, 4>(fp, a, false, s);
+    return launch_rows<A, 4>(fp, a, false, s);
 }
 
 // Free the solver state (after a failed build, so that the next call starts afresh).

@@ -69,6 +69,10 @@ struct nufft_plan_s {
     void *twst1 = nullptr, *twst2 = nullptr;   // stage twiddle tables: pass 2 (L1), pass 1 (L2)
     void *twst1a = nullptr, *twst2b = nullptr; // and pass A (L1), pass B (L2): each pass's own E
     void *twhi = nullptr, *twlo = nullptr;     // four-step twiddle, two levels
+    // FP64 plans: the same four stage tables and four-step levels in double-word form,
+    // for the double-word kernels of the fused FP64 exec
+    void *twst1_dw = nullptr, *twst1a_dw = nullptr, *twst2_dw = nullptr, *twst2b_dw = nullptr;
+    void *twhi_dw = nullptr, *twlo_dw = nullptr;
     void *Y = nullptr;         // (K + 1) * L complex: intermediate between the passes
     void *fscr = nullptr;      // M complex: partial sums when G < K
     void *cstage = nullptr, *fstage = nullptr;   // exec_host staging
@@ -76,8 +80,8 @@ struct nufft_plan_s {
     void *part = nullptr;      // pass B partial sums, SBsplit x L complex
     int *counters = nullptr;   // pass B tickets, one per column block
     int *err = nullptr;        // device error word: bounded waits that timed out
-    void *Ufac = nullptr;      // FP64 plans: u_r in sorted order, M x K complex
-    void *Vfac = nullptr;      // FP64 plans: v_r, K x N real
+    void *Ufac = nullptr;      // FP64 plans: u_r in sorted order, M x K complex (double-word)
+    void *Vfac = nullptr;      // FP64 plans: v_r, K x N real (double-word)
     int64_t work_bytes = 0;
 
     // the 2D transform: the y direction (x uses N, K, gamma, beta, t_j, d_j, dsorted)

@@ -41,23 +41,60 @@ enum PassMode : int {
                           // recomputing them (the FP64 plans: FP64 arithmetic is scarce)
 };
 
-// The fused kernels of FP64 plans read the plan's materialised factors (MODE_FACTORS);
-// those of FP32 plans recompute them.  Fixed per element type, so the FP32 kernels
-// carry no code for it.
-template <typename T> constexpr bool kFactors = std::is_same<T, double>::value;
+// The fused kernels of FP64 plans (double-word arithmetic, or native FP64) read the
+// plan's materialised factors (MODE_FACTORS); those of FP32 plans recompute them.  Fixed
+// per element type, so the FP32 kernels carry no code for it.
+template <typename T> constexpr bool kFactors = std::is_same<T, double>::value || std::is_same<T, dfloat>::value;
+
+// The arithmetic of a 1D plan's fused exec: FP32 plans compute in FP32; FP64 plans in
+// double-word FP32 pairs (dfloat.cuh: about 48 bits, from the FP32 pipes), since GB300's
+// FP64 pipe is a small fraction of its FP32 one.  Their arrays stay complex128.
+template <typename T> using Arith = typename std::conditional<std::is_same<T, double>::value, dfloat, T>::type;
 
 // The row passes keep each lane's stage twiddles in registers across its row FFTs
 // (FP32; in FP64 they would take twice the registers).
 template <typename T> constexpr bool kTwReg = std::is_same<T, float>::value;
 
 
+// The caller's arrays hold io_c<T> / io_r<T> (complex64 / float, or complex128 / double);
+// to_cx and from_cx convert an element on load and on store (the identity except for the
+// double-word kernels, whose caller's arrays are complex128).
+template <typename T> __device__ __forceinline__ cx<T> to_cx(const io_c<T> &v) {
+    if constexpr (std::is_same<T, dfloat>::value) {
+        cx<T> r;
+        r.x = dfloat(v.x);
+        r.y = dfloat(v.y);
+        return r;
+    } else {
+        return v;
+    }
+}
+template <typename T> __device__ __forceinline__ io_c<T> from_cx(const cx<T> &v) {
+    if constexpr (std::is_same<T, dfloat>::value) {
+        return make_double2(v.x.to_double(), v.y.to_double());
+    } else {
+        return v;
+    }
+}
+
+template <typename T> struct PassArgs;
+// gx_j = re, or gx_j += re
+template <typename T>
+__device__ __forceinline__ void store_gx(const PassArgs<T> &a, int j, T re) {
+    if constexpr (std::is_same<T, dfloat>::value) {
+        a.gx[j] = a.accumulate ? a.gx[j] + re.to_double() : re.to_double();
+    } else {
+        a.gx[j] = a.accumulate ? a.gx[j] + re : re;
+    }
+}
+
 template <typename T>
 struct PassArgs {
-    const cx<T> *in;      // pass 1: c (or W);  pass A: g
+    const io_c<T> *in;    // pass 1: c (or W);  pass A: g
     cx<T> *Y;             // intermediate, K x L2 x L1
-    cx<T> *out;           // pass 2: f (or X);  pass B: c
-    const cx<T> *g;       // dx cotangent
-    T *gx;                // dx output
+    io_c<T> *out;         // pass 2: f (or X);  pass B: c
+    const io_c<T> *g;     // dx cotangent
+    io_r<T> *gx;          // dx output
     cx<T> *fscr;          // partial sums over rank groups (sorted order)
     cx<T> *part;          // pass B: per-split partial sums, SB x L
     int *counters;        // pass B: per-column-block tickets (zero between calls)
@@ -73,7 +110,7 @@ struct PassArgs {
     int mbar_off;         // pass 2: byte offset of the slot mbarriers in shared memory
     int CQ, lgCQ;         // pass A/B: columns of pass B's tiles (the adjoint intermediate's tiling)
     int nranks;           // ranks transformed: K, or K + 1 for MODE_DERIV
-    cx<T> *out2;          // MODE_DERIV: f' output (may be null)
+    io_c<T> *out2;        // MODE_DERIV: f' output (may be null)
     T piN;                // pi N
     int *err;             // device error word (bounded waits that timed out)
     const T *vfac;        // MODE_FACTORS: V[r][k] = v_r(k) of eq. (2.6), K x N
@@ -112,8 +149,8 @@ __device__ __forceinline__ void sincospi_t<double>(double x, double *s, double *
 // w_L^m for 0 <= m < L from the two-level table (two roundings, ~1.5 ulp).
 template <typename T>
 __device__ __forceinline__ cx<T> twiddle_L(const PassArgs<T> &a, int m) {
-    const cx<T> hi = __ldg(&a.twhi[m >> 12]);
-    const cx<T> lo = __ldg(&a.twlo[m & 4095]);
+    const cx<T> hi = ldg_cx(&a.twhi[m >> 12]);
+    const cx<T> lo = ldg_cx(&a.twlo[m & 4095]);
     return cmul<T>(hi, lo);
 }
 
@@ -182,19 +219,19 @@ __device__ __forceinline__ void pass1_body(const PassArgs<T> &a, const int bx, c
     if constexpr (TWO_D) {
         // element e = tt + TT m of column k1: C[e][k1]
         const bool col_ok = k1 < a.ncol;
-        const cx<T> *cb = a.in + (int64_t)tt * a.ldc + k1;
+        const io_c<T> *cb = a.in + (int64_t)tt * a.ldc + k1;
         const int64_t estride = (int64_t)TT * a.ldc;
 #pragma unroll
         for (int m = 0; m < E; ++m)
-            v[m] = (col_ok && tt + TT * m < a.N) ? cb[m * estride] : mk<T>(0, 0);
+            v[m] = (col_ok && tt + TT * m < a.N) ? to_cx<T>(cb[m * estride]) : mk<T>(0, 0);
     } else if (a.mode & MODE_PLAIN_IN) {
-        const cx<T> *W = a.in + (int64_t)r * a.L + k1 + a.L1 * tt;
+        const io_c<T> *W = a.in + (int64_t)r * a.L + k1 + a.L1 * tt;
 #pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = W[m * (a.L1 * TT)];
+        for (int m = 0; m < E; ++m) v[m] = to_cx<T>(W[m * (a.L1 * TT)]);
     } else {
-        const cx<T> *cb = a.in + k0;
+        const io_c<T> *cb = a.in + k0;
 #pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = k0 + m * kstride < a.N ? cb[m * kstride] : mk<T>(0, 0);
+        for (int m = 0; m < E; ++m) v[m] = k0 + m * kstride < a.N ? to_cx<T>(cb[m * kstride]) : mk<T>(0, 0);
     }
     if (!(a.mode & MODE_PLAIN_IN)) {
         if constexpr (kFactors<T> && !TWO_D) {
@@ -348,87 +385,113 @@ __device__ __forceinline__ void pass2_body(const PassArgs<T> &a, const BT &beta,
                 const int n1 = rest % a.L1;
                 const int rl = rest / a.L1;
                 a.out[(int64_t)(g0 + rl) * a.L + (int64_t)a.L2 * n1 + b * a.B2 + row] =
-                    smem[(rl * a.B2 + row) * a.S + padi<E>(n1)];
+                    from_cx<T>(smem[(rl * a.B2 + row) * a.S + padi<E>(n1)]);
             }
         } else if ((a.mode & MODE_DERIV) && !kFactors<T>) {
+          if constexpr (!kFactors<T>) {
             // f and f' = df/dx from the K + 1 staged ranks (one group).  With
             // k = N (z + 1)/2 and z T_r = (T_{r+1} + T_{r-1})/2, the rank-r term of
             // A_K((-2 pi i k) o c) is -pi i N (X_r - i X_{r+1}/2 + i X_{r-1}/2) (r >= 1;
             // X_0 - i X_1 for r = 0), so f'_j = -pi i N e^{-i pi d} sum_{s<=K} rho_s X_s[t_j]
             // with rho_s = mu_s + i (mu_{s+1}/2 - mu_{s-1}/2 [s >= 2] - mu_0 [s = 1]).
-            // software-pipelined: the next sample's t, d and j are loaded while this
-            // one is formed
-            int tn = 0, jn = 0;
-            T dn = T(0);
-            if (i0 + (int)threadIdx.x < i1) {
-                tn = a.tsorted[i0 + threadIdx.x];
-                dn = a.dsorted[i0 + threadIdx.x];
-                jn = a.perm[i0 + threadIdx.x];
-            }
+            // Two samples per iteration (sorted positions i and i + blockDim), formed side
+            // by side so that their dependency chains (the Chebyshev recurrence, the phase)
+            // interleave; software-pipelined: the next pair's t, d and j are loaded while
+            // this pair is formed.  A missing second sample repeats the first and is not stored.
+            const int nb = blockDim.x;
+            int tn[2] = {0, 0}, jn[2] = {0, 0};
+            T dn[2] = {T(0), T(0)};
+            auto fetch2 = [&](const int i) {
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int iu = min(i + u * nb, i1 - 1);
+                    tn[u] = a.tsorted[iu];
+                    dn[u] = a.dsorted[iu];
+                    jn[u] = a.perm[iu];
+                }
+            };
+            if (i0 + (int)threadIdx.x < i1) fetch2(i0 + threadIdx.x);
 #pragma unroll 1
-            for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-                const int t = tn, j = jn;
-                const T d = dn;
-                if (i + (int)blockDim.x < i1) {
-                    tn = a.tsorted[i + blockDim.x];
-                    dn = a.dsorted[i + blockDim.x];
-                    jn = a.perm[i + blockDim.x];
+            for (int i = i0 + threadIdx.x; i < i1; i += 2 * nb) {
+                int tq[2], jq[2];
+                T dq[2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    tq[u] = tn[u];
+                    jq[u] = jn[u];
+                    dq[u] = dn[u];
                 }
-                const int row = (t & L2m) - b * a.B2;
-                const int n1 = t >> a.lg2;
-                if (!idx_ok(row >= 0 && row < a.B2 && n1 >= 0 && n1 < a.L1, a.err)) continue;
-                const T xi = d * a.inv_gamma;
-                T Tp[KM];
-                Tp[0] = T(1);
-                if (KM > 1) Tp[1] = xi;
+                if (i + 2 * nb < i1) fetch2(i + 2 * nb);
+                cx<T> fo[2], fpo[2];
+                int rowq[2], n1q[2];
 #pragma unroll
-                for (int q = 2; q < KM; ++q) Tp[q] = fma(T(2) * xi, Tp[q - 1], -Tp[q - 2]);
-                T mu[KM];
+                for (int u = 0; u < 2; ++u) {
+                    rowq[u] = (tq[u] & L2m) - b * a.B2;
+                    n1q[u] = tq[u] >> a.lg2;
+                    const bool ok = idx_ok(rowq[u] >= 0 && rowq[u] < a.B2 && n1q[u] >= 0 && n1q[u] < a.L1, a.err);
+                    if (!ok) rowq[u] = n1q[u] = 0;   // (checked builds) read a valid slot, store nothing
+                    const T d = dq[u];
+                    const T xi = d * a.inv_gamma;
+                    T Tp[KM];
+                    Tp[0] = T(1);
+                    if (KM > 1) Tp[1] = xi;
 #pragma unroll
-                for (int r = 0; r < KM; ++r) {
-                    T m = T(0);
+                    for (int q = 2; q < KM; ++q) Tp[q] = fma(T(2) * xi, Tp[q - 1], -Tp[q - 2]);
+                    T mu[KM];
 #pragma unroll
-                    for (int q = (r & 1); q < KM; q += 2) m = fma(beta_at(beta, r, q), Tp[q], m);
-                    mu[r] = m;   // zero for r >= K (beta is zero-padded)
+                    for (int r = 0; r < KM; ++r) {
+                        T m = T(0);
+#pragma unroll
+                        for (int q = (r & 1); q < KM; q += 2) m = fma(beta_at(beta, r, q), Tp[q], m);
+                        mu[r] = m;   // zero for r >= K (beta is zero-padded)
+                    }
+                    // plain sums here: compensating these four products per rank cost 20 % of
+                    // the derivative pass (70 -> 84 us at 2^20)
+                    cx<T> S = mk<T>(0, 0), Sp = mk<T>(0, 0);
+#pragma unroll
+                    for (int sidx = 0; sidx <= KM; ++sidx) {
+                        if (sidx < a.nranks) {
+                            const cx<T> x = smem[(sidx * a.B2 + rowq[u]) * a.S + padi<E>(n1q[u])];
+                            const T ms = sidx < KM ? mu[sidx] : T(0);
+                            T ri = sidx + 1 < KM ? T(0.5) * mu[sidx + 1] : T(0);
+                            if (sidx == 1) ri -= mu[0];
+                            if (sidx >= 2 && sidx - 1 < KM) ri -= T(0.5) * mu[sidx - 1];
+                            S.x = fma(ms, x.x, S.x);
+                            S.y = fma(ms, x.y, S.y);
+                            Sp.x = fma(ms, x.x, fma(-ri, x.y, Sp.x));
+                            Sp.y = fma(ms, x.y, fma(ri, x.x, Sp.y));
+                        }
+                    }
+                    T sn, cs;
+                    sincospi_t<T>(d, &sn, &cs);
+                    fo[u] = mk<T>(fma(S.x, cs, S.y * sn), fma(S.y, cs, -S.x * sn));
+                    const cx<T> ph = mk<T>(fma(Sp.x, cs, Sp.y * sn), fma(Sp.y, cs, -Sp.x * sn));
+                    fpo[u] = mk<T>(a.piN * ph.y, -a.piN * ph.x);   // -i pi N (phase Sp)
+                    if (!ok) jq[u] = -1;
                 }
-                // plain sums here: compensating these four products per rank cost 20 % of
-                // the derivative pass (70 -> 84 us at 2^20)
-                cx<T> S = mk<T>(0, 0), Sp = mk<T>(0, 0);
 #pragma unroll
-                for (int sidx = 0; sidx <= KM; ++sidx) {
-                    if (sidx < a.nranks) {
-                        const cx<T> x = smem[(sidx * a.B2 + row) * a.S + padi<E>(n1)];
-                        const T ms = sidx < KM ? mu[sidx] : T(0);
-                        T ri = sidx + 1 < KM ? T(0.5) * mu[sidx + 1] : T(0);
-                        if (sidx == 1) ri -= mu[0];
-                        if (sidx >= 2 && sidx - 1 < KM) ri -= T(0.5) * mu[sidx - 1];
-                        S.x = fma(ms, x.x, S.x);
-                        S.y = fma(ms, x.y, S.y);
-                        Sp.x = fma(ms, x.x, fma(-ri, x.y, Sp.x));
-                        Sp.y = fma(ms, x.y, fma(ri, x.x, Sp.y));
+                for (int u = 0; u < 2; ++u) {
+                    const int j = jq[u];
+                    if (u == 1 && i + nb >= i1) break;   // no second sample
+                    if (!idx_ok(j >= 0 && j < a.M, a.err)) continue;
+                    if (a.out) a.out[j] = from_cx<T>(fo[u]);
+                    if (a.out2) a.out2[j] = from_cx<T>(fpo[u]);
+                    if (a.mode & MODE_GX) {
+                        const cx<T> gg = to_cx<T>(a.g[j]);
+                        const T re = fma(gg.x, fpo[u].x, gg.y * fpo[u].y);
+                        store_gx<T>(a, j, re);
                     }
                 }
-                T sn, cs;
-                sincospi_t<T>(d, &sn, &cs);
-                const cx<T> f = mk<T>(fma(S.x, cs, S.y * sn), fma(S.y, cs, -S.x * sn));
-                const cx<T> ph = mk<T>(fma(Sp.x, cs, Sp.y * sn), fma(Sp.y, cs, -Sp.x * sn));
-                const cx<T> fp = mk<T>(a.piN * ph.y, -a.piN * ph.x);   // -i pi N (phase Sp)
-                if (!idx_ok(j >= 0 && j < a.M, a.err)) continue;
-                if (a.out) a.out[j] = f;
-                if (a.out2) a.out2[j] = fp;
-                if (a.mode & MODE_GX) {
-                    const cx<T> gg = a.g[j];
-                    const T re = fma(gg.x, fp.x, gg.y * fp.y);
-                    a.gx[j] = a.accumulate ? a.gx[j] + re : re;
-                }
             }
+          }
         } else {
-            // software-pipelined as the derivative mode's loop
+            // software-pipelined as the derivative mode's loop (d only where the factors
+            // are recomputed)
             int tn = 0, jn = 0;
             T dn = T(0);
             if (i0 + (int)threadIdx.x < i1) {
                 tn = a.tsorted[i0 + threadIdx.x];
-                dn = a.dsorted[i0 + threadIdx.x];
+                if constexpr (!kFactors<T>) dn = a.dsorted[i0 + threadIdx.x];
                 jn = a.perm[i0 + threadIdx.x];
             }
 #pragma unroll 1
@@ -437,7 +500,7 @@ __device__ __forceinline__ void pass2_body(const PassArgs<T> &a, const BT &beta,
                 const T d = dn;
                 if (i + (int)blockDim.x < i1) {
                     tn = a.tsorted[i + blockDim.x];
-                    dn = a.dsorted[i + blockDim.x];
+                    if constexpr (!kFactors<T>) dn = a.dsorted[i + blockDim.x];
                     jn = a.perm[i + blockDim.x];
                 }
                 const int row = (t & L2m) - b * a.B2;
@@ -446,7 +509,7 @@ __device__ __forceinline__ void pass2_body(const PassArgs<T> &a, const BT &beta,
                 cx<T> acc = g0 == 0 ? mk<T>(0, 0) : a.fscr[i];
                 cx<T> comp = mk<T>(0, 0);   // the rank-sum's compensation
                 constexpr bool fac = kFactors<T>;
-                if (fac) {
+                if constexpr (fac) {
                     // f_j = sum_r u_r(j) X_r[t_j] with the plan's U (phase included)
                     const cx<T> *ui = a.ufac + (int64_t)i * a.K;
                     for (int r = g0; r < g0 + gc; ++r) {
@@ -474,24 +537,26 @@ __device__ __forceinline__ void pass2_body(const PassArgs<T> &a, const BT &beta,
                         }
                     }
                 }
-                acc.x += comp.x;
-                acc.y += comp.y;
+                if constexpr (!fac) {
+                    acc.x += comp.x;
+                    acc.y += comp.y;
+                }
                 if (g0 + gc < a.nranks) {
                     a.fscr[i] = acc;
                 } else {
                     cx<T> val = acc;
-                    if (!fac) {
+                    if constexpr (!fac) {
                         T sn, cs;
                         sincospi_t<T>(d, &sn, &cs);
                         val = mk<T>(fma(acc.x, cs, acc.y * sn), fma(acc.y, cs, -acc.x * sn));
                     }
                     if (!idx_ok(j >= 0 && j < a.M, a.err)) continue;
                     if (a.mode & MODE_GX) {
-                        const cx<T> gg = a.g[j];
+                        const cx<T> gg = to_cx<T>(a.g[j]);
                         const T re = fma(gg.x, val.x, gg.y * val.y);
-                        a.gx[j] = a.accumulate ? a.gx[j] + re : re;
+                        store_gx<T>(a, j, re);
                     } else {
-                        a.out[j] = val;
+                        a.out[j] = from_cx<T>(val);
                     }
                 }
             }
@@ -515,6 +580,7 @@ __device__ __forceinline__ void passA_body(const PassArgs<T> &a, const BT &beta,
     if (!idx_ok(i0 >= 0 && i0 <= i1 && i1 <= a.M, a.err)) i1 = i0 = 0;   // no samples (barriers follow)
     const int L2m = a.L2 - 1;
     const int Gs = a.G > 0 ? a.G : 1;   // never a zero stride
+    __shared__ int rounds_max;          // the chunk's longest run of equal grid points, less one
     for (int g0 = 0; g0 < a.K; g0 += Gs) {
         const int gc = min(Gs, a.K - g0);
         const int njobs = gc * a.B2;
@@ -534,7 +600,7 @@ __device__ __forceinline__ void passA_body(const PassArgs<T> &a, const BT &beta,
                 const int i = threadIdx.x + u * blockDim.x;
                 if (i < n) {
                     pt[u] = a.tsorted[c0 + i];
-                    pd[u] = a.dsorted[c0 + i];
+                    if constexpr (!kFactors<T>) pd[u] = a.dsorted[c0 + i];
                     pj[u] = a.perm[c0 + i];
                 }
             }
@@ -555,9 +621,9 @@ __device__ __forceinline__ void passA_body(const PassArgs<T> &a, const BT &beta,
                     const int i = threadIdx.x + u * blockDim.x;
                     if (i < n) {
                         st_t[i] = pt[u];
-                        st_d[i] = pd[u];
+                        if constexpr (!kFactors<T>) st_d[i] = pd[u];
                         const int j = pj[u];
-                        st_g[i] = idx_ok(j >= 0 && j < a.M, a.err) ? a.in[j] : mk<T>(0, 0);
+                        st_g[i] = idx_ok(j >= 0 && j < a.M, a.err) ? to_cx<T>(a.in[j]) : mk<T>(0, 0);
                     }
                 }
                 if (c0 + chunk < i1) fetch(c0 + chunk);
@@ -565,71 +631,82 @@ __device__ __forceinline__ void passA_body(const PassArgs<T> &a, const BT &beta,
 #pragma unroll 4
                 for (int i = threadIdx.x; i < n; i += blockDim.x) {
                     st_t[i] = a.tsorted[c0 + i];
-                    st_d[i] = a.dsorted[c0 + i];
+                    if constexpr (!kFactors<T>) st_d[i] = a.dsorted[c0 + i];
                     const int j = a.perm[c0 + i];
-                    st_g[i] = idx_ok(j >= 0 && j < a.M, a.err) ? a.in[j] : mk<T>(0, 0);
+                    st_g[i] = idx_ok(j >= 0 && j < a.M, a.err) ? to_cx<T>(a.in[j]) : mk<T>(0, 0);
                 }
             }
-            __syncthreads();
-            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            // The chunk's samples are added into the slots sample-parallel, in rounds: round q
+            // adds the q-th sample (within this chunk) of every run of equal grid points, so
+            // each slot receives its samples one after another in sorted order -- the same
+            // operations in the same order as one thread summing the run, and no two threads
+            // of a round touch the same slot.  A run continued from the previous chunk adds to
+            // what that chunk left in the slot.  (One round when every grid point holds at most
+            // one sample of the chunk, as on a perturbed equispaced grid.)
+            auto run_pos = [&](const int i) {
                 const int t = st_t[i];
-                if (c0 + i > i0 && (i > 0 ? st_t[i - 1] : a.tsorted[c0 - 1]) == t) continue;
-                cx<T> acc[KM];
-#pragma unroll
-                for (int r = 0; r < KM; ++r) acc[r] = mk<T>(0, 0);
-                // every sample of this grid point, possibly running into the next chunk
-                for (int i2 = i; c0 + i2 < i1; ++i2) {
-                    T d;
-                    cx<T> gg;
-                    if (i2 < n) {
-                        if (st_t[i2] != t) break;
-                        d = st_d[i2];
-                        gg = st_g[i2];
-                    } else {
-                        if (a.tsorted[c0 + i2] != t) break;
-                        d = a.dsorted[c0 + i2];
-                        const int j = a.perm[c0 + i2];
-                        gg = idx_ok(j >= 0 && j < a.M, a.err) ? a.in[j] : mk<T>(0, 0);
-                    }
+                int q = 0;
+                while (q < i && st_t[i - q - 1] == t) ++q;
+                return q;
+            };
+            if (threadIdx.x == 0) rounds_max = 0;
+            __syncthreads();
+            {
+                int qm = 0;
+                for (int i = threadIdx.x; i < n; i += blockDim.x) qm = max(qm, run_pos(i));
+                if (qm > 0) atomicMax(&rounds_max, qm);
+            }
+            __syncthreads();
+            const int nrounds = rounds_max + 1;
+            for (int qr = 0; qr < nrounds; ++qr) {
+#pragma unroll 1
+                for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                    if (nrounds > 1 && run_pos(i) != qr) continue;
+                    const int t = st_t[i];
+                    const int row = (t & L2m) - b * a.B2;
+                    const int n1 = t >> a.lg2;
+                    if (!idx_ok(row >= 0 && row < a.B2 && n1 >= 0 && n1 < a.L1, a.err)) continue;
+                    cx<T> *slot = smem + row * a.S + padi<E>(n1);   // rank r at + (r - g0) B2 S
+                    const cx<T> gg = st_g[i];
                     if constexpr (kFactors<T>) {
                         // Z_r += conj(u_r(j)) g_j with the plan's U
-                        const cx<T> *ui = a.ufac + (int64_t)(c0 + i2) * a.K;
+                        const cx<T> *ui = a.ufac + (int64_t)(c0 + i) * a.K;
 #pragma unroll
                         for (int r = 0; r < KM; ++r) {
                             if (r >= g0 && r < g0 + gc) {
                                 const cx<T> u = ui[r];
-                                acc[r].x = fma(u.x, gg.x, fma(u.y, gg.y, acc[r].x));
-                                acc[r].y = fma(u.x, gg.y, fma(-u.y, gg.x, acc[r].y));
+                                cx<T> z = slot[(r - g0) * a.B2 * a.S];
+                                z.x = fma(u.x, gg.x, fma(u.y, gg.y, z.x));
+                                z.y = fma(u.x, gg.y, fma(-u.y, gg.x, z.y));
+                                slot[(r - g0) * a.B2 * a.S] = z;
                             }
                         }
-                        continue;
-                    }
-                    const T xi = d * a.inv_gamma;
-                    T Tp[KM];
-                    Tp[0] = T(1);
-                    if (KM > 1) Tp[1] = xi;
+                    } else {
+                        const T d = st_d[i];
+                        const T xi = d * a.inv_gamma;
+                        T Tp[KM];
+                        Tp[0] = T(1);
+                        if (KM > 1) Tp[1] = xi;
 #pragma unroll
-                    for (int q = 2; q < KM; ++q) Tp[q] = fma(T(2) * xi, Tp[q - 1], -Tp[q - 2]);
-                    T sn, cs;
-                    sincospi_t<T>(d, &sn, &cs);
-                    const cx<T> h = mk<T>(fma(gg.x, cs, -gg.y * sn), fma(gg.y, cs, gg.x * sn));  // g e^{+i pi d}
+                        for (int q = 2; q < KM; ++q) Tp[q] = fma(T(2) * xi, Tp[q - 1], -Tp[q - 2]);
+                        T sn, cs;
+                        sincospi_t<T>(d, &sn, &cs);
+                        const cx<T> h = mk<T>(fma(gg.x, cs, -gg.y * sn), fma(gg.y, cs, gg.x * sn));  // g e^{+i pi d}
 #pragma unroll
-                    for (int r = 0; r < KM; ++r) {
-                        if (r >= g0 && r < g0 + gc) {
-                            T mu = T(0);
+                        for (int r = 0; r < KM; ++r) {
+                            if (r >= g0 && r < g0 + gc) {
+                                T mu = T(0);
 #pragma unroll
-                            for (int q = (r & 1); q < KM; q += 2) mu = fma(beta_at(beta, r, q), Tp[q], mu);
-                            acc[r].x = fma(mu, h.x, acc[r].x);
-                            acc[r].y = fma(mu, h.y, acc[r].y);
+                                for (int q = (r & 1); q < KM; q += 2) mu = fma(beta_at(beta, r, q), Tp[q], mu);
+                                cx<T> z = slot[(r - g0) * a.B2 * a.S];
+                                z.x = fma(mu, h.x, z.x);
+                                z.y = fma(mu, h.y, z.y);
+                                slot[(r - g0) * a.B2 * a.S] = z;
+                            }
                         }
                     }
                 }
-                const int row = (t & L2m) - b * a.B2;
-                const int n1 = t >> a.lg2;
-                if (!idx_ok(row >= 0 && row < a.B2 && n1 >= 0 && n1 < a.L1, a.err)) continue;
-#pragma unroll
-                for (int r = 0; r < KM; ++r)
-                    if (r >= g0 && r < g0 + gc) smem[((r - g0) * a.B2 + row) * a.S + padi<E>(n1)] = acc[r];
+                if (qr + 1 < nrounds) __syncthreads();   // the next round adds to these slots
             }
         }
         __syncthreads();
@@ -700,6 +777,7 @@ __device__ __forceinline__ void passA_body(const PassArgs<T> &a, const BT &beta,
 template <typename T> struct PassBBounds;
 template <> struct PassBBounds<float> { static constexpr int threads = 256, blocks = 2; };
 template <> struct PassBBounds<double> { static constexpr int threads = 128, blocks = 3; };
+template <> struct PassBBounds<dfloat> { static constexpr int threads = 128, blocks = 3; };
 
 // TWO_D: the column pass of the 2D adjoint (section 4).  A column is the y-frequency
 // k2 = k1 (this CTA's column index), its elements the x-frequencies k = out_index < m
@@ -715,7 +793,6 @@ __device__ __forceinline__ void passB_body(const PassArgs<T> &a, const int bx, c
     const int k1 = bx * a.C + cc;
     const int s = by, SB = a.SB;
     const int Ni = (int)a.N;   // N < 2^23: 32-bit conversions (64-bit ones run on the FP64 pipe)
-    const T invN = T(1) / T(Ni);
     const int bufsz = a.C * a.S;                        // elements per buffer
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + 2 * bufsz);
     __shared__ int cta_failed;
@@ -756,6 +833,7 @@ __device__ __forceinline__ void passB_body(const PassArgs<T> &a, const int bx, c
             }
         } else {
         // (-i)^r T_r(z_k) v, the recurrence run element-innermost in chunks of H
+        const T invN = T(1) / T(Ni);
         constexpr int H = E < 8 ? E : 8;
 #pragma unroll
         for (int h0 = 0; h0 < E; h0 += H) {
@@ -799,10 +877,10 @@ __device__ __forceinline__ void passB_body(const PassArgs<T> &a, const int bx, c
     auto store = [&](const int e, const cx<T> val) {
         if constexpr (TWO_D) {
             const int k = TF::out_index(tt, e);
-            if (k < a.N && k1 < a.ncol) a.out[(int64_t)k * a.ldc + k1] = val;
+            if (k < a.N && k1 < a.ncol) a.out[(int64_t)k * a.ldc + k1] = from_cx<T>(val);
         } else {
             const int k = k1 + a.L1 * TF::out_index(tt, e);
-            if (k < a.N) a.out[k] = val;
+            if (k < a.N) a.out[k] = from_cx<T>(val);
         }
     };
     if (SB == 1) {
@@ -833,7 +911,7 @@ __device__ __forceinline__ void passB_body(const PassArgs<T> &a, const int bx, c
 #pragma unroll
             for (int m = 0; m < H; ++m) {
                 const int k = k1 + a.L1 * TF::out_index(tt, h0 + m);
-                const cx<T> pv = s2 == s ? acc[h0 + m] : __ldcg(&a.part[(int64_t)s2 * a.L + k]);
+                const cx<T> pv = s2 == s ? acc[h0 + m] : ldcg_cx(&a.part[(int64_t)s2 * a.L + k]);
                 t[m].x += pv.x;
                 t[m].y += pv.y;
             }
@@ -998,7 +1076,7 @@ __device__ __forceinline__ void pass2d_body(const PassArgs<T> &a, const BT &beta
                         sincospi_t<T>(dx + dy, &sn, &cs);
                         const int j = a.perm[i];
                         if (idx_ok(j >= 0 && j < a.M, a.err))
-                            a.out[j] = mk<T>(fma(acc.x, cs, acc.y * sn), fma(acc.y, cs, -acc.x * sn));
+                            a.out[j] = from_cx<T>(mk<T>(fma(acc.x, cs, acc.y * sn), fma(acc.y, cs, -acc.x * sn)));
                     }
                 }
             };
@@ -1058,7 +1136,7 @@ __device__ __forceinline__ void passA2d_body(const PassArgs<T> &a, const BT &bet
                     cx<T> h;
                     if (first) {
                         const int j = a.perm[i2];
-                        const cx<T> gg = idx_ok(j >= 0 && j < a.M, a.err) ? a.in[j] : mk<T>(0, 0);
+                        const cx<T> gg = idx_ok(j >= 0 && j < a.M, a.err) ? to_cx<T>(a.in[j]) : mk<T>(0, 0);
                         T sn, cs;
                         sincospi_t<T>(dx + dy, &sn, &cs);
                         h = mk<T>(fma(gg.x, cs, -gg.y * sn), fma(gg.y, cs, gg.x * sn));   // g e^{+i pi (dx + dy)}
@@ -1221,9 +1299,9 @@ __device__ __forceinline__ void many_args(PassArgs<T> &sa, const PassArgs<T> *__
     __syncthreads();
     if (threadIdx.x == 0) {
         const int64_t z = blockIdx.z;
-        sa.in = (const cx<T> *)io.in + sa.in_off + z * io.in_stride;
-        sa.out = (cx<T> *)io.out + sa.out_off + z * io.out_stride;
-        if (io.out2) sa.out2 = (cx<T> *)io.out2 + sa.out_off + z * io.out_stride;
+        sa.in = (const io_c<T> *)io.in + sa.in_off + z * io.in_stride;
+        sa.out = (io_c<T> *)io.out + sa.out_off + z * io.out_stride;
+        if (io.out2) sa.out2 = (io_c<T> *)io.out2 + sa.out_off + z * io.out_stride;
     }
     __syncthreads();
 }
@@ -1324,6 +1402,13 @@ inline int launch_status() {
     return e == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;
 }
 
+// A plan table for the kernels of element type T: the double-word kernels read the
+// double-word copy an FP64 plan keeps beside the native one.
+template <typename T>
+inline const cx<T> *tab(const void *native, const void *dw) {
+    return (const cx<T> *)(std::is_same<T, dfloat>::value ? dw : native);
+}
+
 // The fields a column-pass launch adds to base_args (single and batched launches).
 template <typename T>
 void cols_fields(nufft_plan p, PassArgs<T> &a, bool adjoint) {
@@ -1332,14 +1417,14 @@ void cols_fields(nufft_plan p, PassArgs<T> &a, bool adjoint) {
     while ((1 << a.lgC) < a.C) ++a.lgC;
     a.S = adjoint ? p->SB : p->S1;
     a.SB = p->SBsplit;
-    a.twc = (const cx<T> *)(adjoint ? p->twst2b : p->twst2);   // each pass's own stage layout
+    a.twc = adjoint ? tab<T>(p->twst2b, p->twst2b_dw) : tab<T>(p->twst2, p->twst2_dw);   // each pass's own layout
 }
 
 // The fields a row-pass launch adds to base_args (single and batched launches).
 template <typename T>
 int rows_fields(nufft_plan p, PassArgs<T> &a, bool adjoint) {
     a.S = adjoint ? p->SA : p->S2;
-    a.twr = (const cx<T> *)(adjoint ? p->twst1a : p->twst1);   // each pass's own stage layout
+    a.twr = adjoint ? tab<T>(p->twst1a, p->twst1a_dw) : tab<T>(p->twst1, p->twst1_dw);   // each pass's own layout
     a.chunk = p->chunkA;
     a.mbar_off = (int)p->mbar_off2;
     a.G = adjoint ? p->GA : p->G;

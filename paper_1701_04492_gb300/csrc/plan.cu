@@ -16,6 +16,7 @@
 #include <mutex>
 #include <new>
 #include <tuple>
+#include <type_traits>
 #include <vector>
 
 #include "async_copy.cuh"
@@ -252,9 +253,20 @@ int build_tables(nufft_plan p, cudaStream_t s) {
     re.assign(nlo, 0.0); im.assign(nlo, 0.0);
     for (int64_t m = 0; m < nlo; ++m) twiddle(p->L, m, &re[m], &im[m]);
     if ((rc = upload_table<T>(&p->twlo, re, im, s, &p->work_bytes))) return rc;
+    std::vector<double> rel = re, iml = im;
     re.assign(nhi, 0.0); im.assign(nhi, 0.0);
     for (int64_t m = 0; m < nhi; ++m) twiddle(p->L, m * TW_BASE, &re[m], &im[m]);
-    return upload_table<T>(&p->twhi, re, im, s, &p->work_bytes);
+    if ((rc = upload_table<T>(&p->twhi, re, im, s, &p->work_bytes))) return rc;
+    if constexpr (std::is_same<T, double>::value) {
+        // the double-word copies for the fused FP64 exec (same entries, rounded to hi + lo)
+        if ((rc = stage_table<dfloat>(p->L1, EmaxT<dfloat, PK_ROW_FWD>::v, &p->twst1_dw, s, &p->work_bytes))) return rc;
+        if ((rc = stage_table<dfloat>(p->L1, EmaxT<dfloat, PK_ROW_ADJ>::v, &p->twst1a_dw, s, &p->work_bytes))) return rc;
+        if ((rc = stage_table<dfloat>(p->L2, EmaxT<dfloat, PK_COL_FWD>::v, &p->twst2_dw, s, &p->work_bytes))) return rc;
+        if ((rc = stage_table<dfloat>(p->L2, EmaxT<dfloat, PK_COL_ADJ>::v, &p->twst2b_dw, s, &p->work_bytes))) return rc;
+        if ((rc = upload_table<dfloat>(&p->twlo_dw, rel, iml, s, &p->work_bytes))) return rc;
+        if ((rc = upload_table<dfloat>(&p->twhi_dw, re, im, s, &p->work_bytes))) return rc;
+    }
+    return NUFFT_OK;
 }
 
 // Bucket the samples: a stable LSD radix sort by (bucket, n1, row) of the grid index
@@ -393,7 +405,7 @@ int plan_device(nufft_plan p, const double *x, cudaStream_t s) {
     // FP64 plans read materialised factors in the fused kernels: on this GPU FP64
     // arithmetic is scarce and bandwidth is not
     if (p->prec == NUFFT_F64) {
-        if ((rc = plan_factor_tables<double>(p, s))) return rc;
+        if ((rc = plan_factor_tables<dfloat>(p, s))) return rc;
     }
     NUFFT_CUDA_TRY(cudaStreamSynchronize(s));
     return NUFFT_OK;
@@ -401,6 +413,8 @@ int plan_device(nufft_plan p, const double *x, cudaStream_t s) {
 
 void free_plan(nufft_plan p) {
     if (!p) return;
+    for (void *b : {p->twst1_dw, p->twst1a_dw, p->twst2_dw, p->twst2b_dw, p->twhi_dw, p->twlo_dw})
+        if (b) cudaFree(b);
     void *bufs[] = {p->tsorted, p->perm, p->bstart, p->t_j, p->dsorted, p->d_j, p->twst1,
                     p->twst2, p->twst1a, p->twst2b, p->twhi, p->twlo, p->Y, p->fscr, p->cstage, p->fstage, p->U, p->V, p->Xg,
                     p->part, p->counters, p->err, p->Ufac, p->Vfac, p->t2_j, p->d2_j, p->dsorted2, p->vy,
