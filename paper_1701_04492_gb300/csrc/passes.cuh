@@ -394,93 +394,70 @@ __device__ __forceinline__ void pass2_body(const PassArgs<T> &a, const BT &beta,
             // A_K((-2 pi i k) o c) is -pi i N (X_r - i X_{r+1}/2 + i X_{r-1}/2) (r >= 1;
             // X_0 - i X_1 for r = 0), so f'_j = -pi i N e^{-i pi d} sum_{s<=K} rho_s X_s[t_j]
             // with rho_s = mu_s + i (mu_{s+1}/2 - mu_{s-1}/2 [s >= 2] - mu_0 [s = 1]).
-            // Two samples per iteration (sorted positions i and i + blockDim), formed side
-            // by side so that their dependency chains (the Chebyshev recurrence, the phase)
-            // interleave; software-pipelined: the next pair's t, d and j are loaded while
-            // this pair is formed.  A missing second sample repeats the first and is not stored.
-            const int nb = blockDim.x;
-            int tn[2] = {0, 0}, jn[2] = {0, 0};
-            T dn[2] = {T(0), T(0)};
-            auto fetch2 = [&](const int i) {
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    const int iu = min(i + u * nb, i1 - 1);
-                    tn[u] = a.tsorted[iu];
-                    dn[u] = a.dsorted[iu];
-                    jn[u] = a.perm[iu];
-                }
-            };
-            if (i0 + (int)threadIdx.x < i1) fetch2(i0 + threadIdx.x);
+            // software-pipelined: the next sample's t, d and j are loaded while this
+            // one is formed
+            int tn = 0, jn = 0;
+            T dn = T(0);
+            if (i0 + (int)threadIdx.x < i1) {
+                tn = a.tsorted[i0 + threadIdx.x];
+                dn = a.dsorted[i0 + threadIdx.x];
+                jn = a.perm[i0 + threadIdx.x];
+            }
 #pragma unroll 1
-            for (int i = i0 + threadIdx.x; i < i1; i += 2 * nb) {
-                int tq[2], jq[2];
-                T dq[2];
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    tq[u] = tn[u];
-                    jq[u] = jn[u];
-                    dq[u] = dn[u];
+            for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+                const int t = tn, j = jn;
+                const T d = dn;
+                if (i + (int)blockDim.x < i1) {
+                    tn = a.tsorted[i + blockDim.x];
+                    dn = a.dsorted[i + blockDim.x];
+                    jn = a.perm[i + blockDim.x];
                 }
-                if (i + 2 * nb < i1) fetch2(i + 2 * nb);
-                cx<T> fo[2], fpo[2];
-                int rowq[2], n1q[2];
+                const int row = (t & L2m) - b * a.B2;
+                const int n1 = t >> a.lg2;
+                if (!idx_ok(row >= 0 && row < a.B2 && n1 >= 0 && n1 < a.L1, a.err)) continue;
+                const T xi = d * a.inv_gamma;
+                T Tp[KM];
+                Tp[0] = T(1);
+                if (KM > 1) Tp[1] = xi;
 #pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    rowq[u] = (tq[u] & L2m) - b * a.B2;
-                    n1q[u] = tq[u] >> a.lg2;
-                    const bool ok = idx_ok(rowq[u] >= 0 && rowq[u] < a.B2 && n1q[u] >= 0 && n1q[u] < a.L1, a.err);
-                    if (!ok) rowq[u] = n1q[u] = 0;   // (checked builds) read a valid slot, store nothing
-                    const T d = dq[u];
-                    const T xi = d * a.inv_gamma;
-                    T Tp[KM];
-                    Tp[0] = T(1);
-                    if (KM > 1) Tp[1] = xi;
+                for (int q = 2; q < KM; ++q) Tp[q] = fma(T(2) * xi, Tp[q - 1], -Tp[q - 2]);
+                T mu[KM];
 #pragma unroll
-                    for (int q = 2; q < KM; ++q) Tp[q] = fma(T(2) * xi, Tp[q - 1], -Tp[q - 2]);
-                    T mu[KM];
+                for (int r = 0; r < KM; ++r) {
+                    T m = T(0);
 #pragma unroll
-                    for (int r = 0; r < KM; ++r) {
-                        T m = T(0);
-#pragma unroll
-                        for (int q = (r & 1); q < KM; q += 2) m = fma(beta_at(beta, r, q), Tp[q], m);
-                        mu[r] = m;   // zero for r >= K (beta is zero-padded)
-                    }
-                    // plain sums here: compensating these four products per rank cost 20 % of
-                    // the derivative pass (70 -> 84 us at 2^20)
-                    cx<T> S = mk<T>(0, 0), Sp = mk<T>(0, 0);
-#pragma unroll
-                    for (int sidx = 0; sidx <= KM; ++sidx) {
-                        if (sidx < a.nranks) {
-                            const cx<T> x = smem[(sidx * a.B2 + rowq[u]) * a.S + padi<E>(n1q[u])];
-                            const T ms = sidx < KM ? mu[sidx] : T(0);
-                            T ri = sidx + 1 < KM ? T(0.5) * mu[sidx + 1] : T(0);
-                            if (sidx == 1) ri -= mu[0];
-                            if (sidx >= 2 && sidx - 1 < KM) ri -= T(0.5) * mu[sidx - 1];
-                            S.x = fma(ms, x.x, S.x);
-                            S.y = fma(ms, x.y, S.y);
-                            Sp.x = fma(ms, x.x, fma(-ri, x.y, Sp.x));
-                            Sp.y = fma(ms, x.y, fma(ri, x.x, Sp.y));
-                        }
-                    }
-                    T sn, cs;
-                    sincospi_t<T>(d, &sn, &cs);
-                    fo[u] = mk<T>(fma(S.x, cs, S.y * sn), fma(S.y, cs, -S.x * sn));
-                    const cx<T> ph = mk<T>(fma(Sp.x, cs, Sp.y * sn), fma(Sp.y, cs, -Sp.x * sn));
-                    fpo[u] = mk<T>(a.piN * ph.y, -a.piN * ph.x);   // -i pi N (phase Sp)
-                    if (!ok) jq[u] = -1;
+                    for (int q = (r & 1); q < KM; q += 2) m = fma(beta_at(beta, r, q), Tp[q], m);
+                    mu[r] = m;   // zero for r >= K (beta is zero-padded)
                 }
+                // plain sums here: compensating these four products per rank cost 20 % of
+                // the derivative pass (70 -> 84 us at 2^20)
+                cx<T> S = mk<T>(0, 0), Sp = mk<T>(0, 0);
 #pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    const int j = jq[u];
-                    if (u == 1 && i + nb >= i1) break;   // no second sample
-                    if (!idx_ok(j >= 0 && j < a.M, a.err)) continue;
-                    if (a.out) a.out[j] = from_cx<T>(fo[u]);
-                    if (a.out2) a.out2[j] = from_cx<T>(fpo[u]);
-                    if (a.mode & MODE_GX) {
-                        const cx<T> gg = to_cx<T>(a.g[j]);
-                        const T re = fma(gg.x, fpo[u].x, gg.y * fpo[u].y);
-                        store_gx<T>(a, j, re);
+                for (int sidx = 0; sidx <= KM; ++sidx) {
+                    if (sidx < a.nranks) {
+                        const cx<T> x = smem[(sidx * a.B2 + row) * a.S + padi<E>(n1)];
+                        const T ms = sidx < KM ? mu[sidx] : T(0);
+                        T ri = sidx + 1 < KM ? T(0.5) * mu[sidx + 1] : T(0);
+                        if (sidx == 1) ri -= mu[0];
+                        if (sidx >= 2 && sidx - 1 < KM) ri -= T(0.5) * mu[sidx - 1];
+                        S.x = fma(ms, x.x, S.x);
+                        S.y = fma(ms, x.y, S.y);
+                        Sp.x = fma(ms, x.x, fma(-ri, x.y, Sp.x));
+                        Sp.y = fma(ms, x.y, fma(ri, x.x, Sp.y));
                     }
+                }
+                T sn, cs;
+                sincospi_t<T>(d, &sn, &cs);
+                const cx<T> f = mk<T>(fma(S.x, cs, S.y * sn), fma(S.y, cs, -S.x * sn));
+                const cx<T> ph = mk<T>(fma(Sp.x, cs, Sp.y * sn), fma(Sp.y, cs, -Sp.x * sn));
+                const cx<T> fp = mk<T>(a.piN * ph.y, -a.piN * ph.x);   // -i pi N (phase Sp)
+                if (!idx_ok(j >= 0 && j < a.M, a.err)) continue;
+                if (a.out) a.out[j] = from_cx<T>(f);
+                if (a.out2) a.out2[j] = from_cx<T>(fp);
+                if (a.mode & MODE_GX) {
+                    const cx<T> gg = to_cx<T>(a.g[j]);
+                    const T re = fma(gg.x, fp.x, gg.y * fp.y);
+                    store_gx<T>(a, j, re);
                 }
             }
           }
