@@ -432,7 +432,10 @@ def batch_c5(api, dev, timed, steps):
                 ("batched", {}, False),
                 ("batched_graph", {"graph": True}, False),
                 ("batched_autotuned", {"autotune": True}, False),
-                ("batched_graph_autotuned", {"graph": True, "autotune": True}, False)]
+                ("batched_graph_autotuned", {"graph": True, "autotune": True}, False),
+                ("persistent", {"persistent": True}, False),
+                ("persistent_graph", {"persistent": True, "graph": True}, False),
+                ("persistent_graph_autotuned", {"persistent": True, "graph": True, "autotune": True}, False)]
     for name, kw, each in variants:
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
@@ -449,7 +452,7 @@ def batch_c5(api, dev, timed, steps):
         out[name] = {"fwd": tot * len(ms_f) / (sum(ms_f) * 1e-3) / 1e9,
                      "fwd_bwd": tot * len(ms_fb) / (sum(ms_fb) * 1e-3) / 1e9,
                      "fwd_ms": float(np.mean(ms_f)), "plan_s": plan_s,
-                     "launches_per_fwd": 2 * (b.count if each else b.classes),
+                     "launches_per_fwd": 2 * b.count if each else b.launches_per_direction,
                      "grid_doubled": int(sum(int(L) > max(1024, 1 << (n - 1).bit_length()) for L, n in zip(b.L, Ns)))}
         b.close()
     return out

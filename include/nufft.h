@@ -388,6 +388,16 @@ typedef struct nufft_batch_s *nufft_batch;
                                   graph (each class a parallel branch); later calls
                                   with those pointers replay it.  Other pointers run
                                   the launches directly. */
+#define NUFFT_BATCH_PERSISTENT 128u /* nufft2_plan_many: run every batched class of a
+                                  direction in ONE launch of a persistent kernel: about as
+                                  many 256-thread CTAs as fit on the GPU take the classes'
+                                  blocks (first passes of every problem, then second passes)
+                                  from one queue by an atomic ticket; a second-pass block
+                                  waits (bounded by time; a timeout is reported by
+                                  nufft_batch_check) until its problem's first pass is done.
+                                  Results equal the class launches' bit for bit.  Combines
+                                  with NUFFT_BATCH_GRAPH (the graph then holds that one
+                                  launch).  Calls on one batch must not overlap. */
 #define NUFFT_BATCH_PER_PROBLEM 32u /* nufft2_plan_many: run every problem with its
                                   own plan's launches (with NUFFT_BATCH_GRAPH, one
                                   parallel graph branch per problem) instead of
@@ -402,8 +412,8 @@ typedef struct nufft_batch_s *nufft_batch;
  *   L_host    count grid sizes as nufft2_plan's L, or NULL (all 0: the default grid).
  *   x_dev     sum M_i doubles on the device, packed; read during the call only.
  *   prec      NUFFT_F32 or NUFFT_F64 for every problem.
- *   flags     NUFFT_BATCH_GRAPH, NUFFT_BATCH_PER_PROBLEM, NUFFT_PLAN_AUTOTUNE (applied
- *             to each problem's plan).
+ *   flags     NUFFT_BATCH_GRAPH, NUFFT_BATCH_PER_PROBLEM, NUFFT_BATCH_PERSISTENT,
+ *             NUFFT_PLAN_AUTOTUNE (applied to each problem's plan).
  *
  * Synchronises `stream` once per problem (each plan reads its gamma).  Errors: those
  * of nufft2_plan for any problem (the batch is then not created), NUFFT_EINVAL. */
@@ -417,8 +427,14 @@ int nufft2_plan_many(nufft_batch *out, int64_t count, const int64_t *N_host, con
 int nufft_batch_info(nufft_batch b, int64_t *classes, int64_t *total_N, int64_t *total_M, int *K_host,
                      int64_t *L_host);
 
+/* Kernel launches per direction of nufft2_exec_many / nufft1_exec_many: two per class, or
+ * with NUFFT_BATCH_PERSISTENT one for all batched classes (plus two per problem that runs
+ * its own plan's launches).  No GPU call.  NUFFT_EINVAL for NULL arguments. */
+int nufft_batch_launches(nufft_batch b, int64_t *per_direction);
+
 /* Forward transform of every problem: f_i = A_i c_i (packed c: sum N_i, f: sum M_i
- * complex values on the device).  Two launches per class. */
+ * complex values on the device).  Two launches per class (one for all of them with
+ * NUFFT_BATCH_PERSISTENT). */
 int nufft2_exec_many(nufft_batch b, const void *c_dev, void *f_dev, void *stream);
 
 /* Adjoint of every problem: c_i = A_i^H g_i (packed g: sum M_i, c: sum N_i). */

@@ -21,6 +21,7 @@ NUFFT_BATCH_GRAPH = 8
 NUFFT_PLAN_LONG_COLUMNS = 16
 NUFFT_BATCH_PER_PROBLEM = 32
 NUFFT_PLAN_HALF_TILE = 64
+NUFFT_BATCH_PERSISTENT = 128
 NUFFT_RESERVE_STEP_HOST = 1
 STATUS = {0: "NUFFT_OK", -1: "NUFFT_EINVAL", -2: "NUFFT_ENOMEM", -3: "NUFFT_ECUDA",
           -4: "NUFFT_EUNSUPPORTED", -5: "NUFFT_ESTATE", -6: "NUFFT_ETIMEOUT",
@@ -70,6 +71,7 @@ SIGNATURES = {
     "nufft1_exec_many": (_i32, [_vp, _vp, _vp, _vp]),
     "nufft2_exec_each": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "nufft_batch_check": (_i32, [_vp, _vp]),
+    "nufft_batch_launches": (_i32, [_vp, ctypes.POINTER(_i64)]),
     "nufft_batch_destroy": (_i32, [_vp]),
 }
 

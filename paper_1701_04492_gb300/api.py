@@ -12,7 +12,8 @@ import ctypes
 import torch
 
 from . import _lib
-from ._lib import (NUFFT_BATCH_GRAPH, NUFFT_BATCH_PER_PROBLEM, NUFFT_F32, NUFFT_F64, NUFFT_PLAN_AUTOTUNE,
+from ._lib import (NUFFT_BATCH_GRAPH, NUFFT_BATCH_PER_PROBLEM, NUFFT_BATCH_PERSISTENT, NUFFT_F32, NUFFT_F64,
+                   NUFFT_PLAN_AUTOTUNE,
                    NUFFT_PLAN_HALF_TILE, NUFFT_RESERVE_STEP_HOST, NUFFT_PLAN_LONG_COLUMNS,
                    NUFFT_PLAN_TIMING, NUFFT_PLAN_UNFUSED, NufftError, check)
 
@@ -514,12 +515,13 @@ class Batch:
 
     graph : replay a CUDA graph of the launches when called again with the same tensors
     per_problem : each problem runs its own plan's launches (no batched launches)
+    persistent : every batched class of a direction in one persistent launch
     autotune : tune each problem's grid and split (see :class:`Plan`)
     L : optional per-problem grid sizes (0 = default)
     """
 
     def __init__(self, Ns, xs, eps, precision="f32", graph=False, autotune=False, L=None, device=None,
-                 per_problem=False):
+                 per_problem=False, persistent=False):
         import numpy as np
         lib = _lib.load()
         device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
@@ -538,7 +540,7 @@ class Batch:
         xp = torch.cat(xs) if self.count else torch.empty(0, dtype=torch.float64, device=device)
         Lv = np.zeros(self.count, dtype=np.int64) if L is None else np.asarray(L, dtype=np.int64)
         flags = ((NUFFT_BATCH_GRAPH if graph else 0) | (NUFFT_PLAN_AUTOTUNE if autotune else 0)
-                 | (NUFFT_BATCH_PER_PROBLEM if per_problem else 0))
+                 | (NUFFT_BATCH_PER_PROBLEM if per_problem else 0) | (NUFFT_BATCH_PERSISTENT if persistent else 0))
         h = ctypes.c_void_p()
         with torch.cuda.device(device):
             rc = lib.nufft2_plan_many(ctypes.byref(h), self.count, self.N.ctypes.data, self.M.ctypes.data,
@@ -553,6 +555,9 @@ class Batch:
                                    Lo.ctypes.data), "nufft_batch_info")
         self.classes, self.total_N, self.total_M = ncls.value, tn.value, tm.value
         self.K, self.L = K, Lo
+        nl = ctypes.c_int64()
+        check(lib.nufft_batch_launches(h, ctypes.byref(nl)), "nufft_batch_launches")
+        self.launches_per_direction = nl.value
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -22,6 +22,7 @@
 
 #include "fill.cuh"
 #include "passes.cuh"
+#include "persist.cuh"
 #include "nvtx_range.h"
 
 namespace nufft {
@@ -59,6 +60,13 @@ struct nufft_batch_s {
     void *lastout[2] = {nullptr, nullptr};
     cudaStream_t cap = nullptr;
     cudaEvent_t fork = nullptr;
+    // NUFFT_BATCH_PERSISTENT: every batched class of a direction in one persistent launch
+    // ([0] forward, [1] adjoint): its device state, grid and shared memory
+    bool persist = false;
+    nufft::PState pst[2] = {};
+    int pgrid[2] = {0, 0};
+    size_t psmem[2] = {0, 0};
+    std::vector<void *> pbufs;   // device allocations of the persistent state
 };
 
 namespace nufft {
@@ -76,6 +84,8 @@ void free_batch(nufft_batch b) {
         if (g) cudaGraphExecDestroy(g);
     if (b->cap) cudaStreamDestroy(b->cap);
     if (b->fork) cudaEventDestroy(b->fork);
+    for (void *q : b->pbufs)
+        if (q) cudaFree(q);
     for (nufft_plan p : b->plans)
         if (p) nufft_destroy(p);
     delete b;
@@ -181,11 +191,20 @@ int class_launches(nufft_batch b, const nufft_batch_s::Class &c, bool adjoint, c
     }
 }
 
+// The persistent launch of one direction (every batched class), if the batch has one.
+int persistent_launch(nufft_batch b, bool adjoint, const void *in, void *out, cudaStream_t s) {
+    const int dir = adjoint ? 1 : 0;
+    if (!b->persist || b->pst[dir].n_items == 0) return NUFFT_OK;
+    return launch_persistent(dir, b->pst[dir], b->pgrid[dir], b->psmem[dir], ManyIO{in, out, nullptr, 0, 0}, s);
+}
+
 template <typename T>
 int launch_all(nufft_batch b, bool adjoint, const void *in, void *out, cudaStream_t s) {
-    for (const auto &c : b->cls)
+    for (const auto &c : b->cls) {
+        if (b->persist && !c.single) continue;   // in the persistent launch
         if (int rc = class_launches<T>(b, c, adjoint, in, out, s)) return rc;
-    return NUFFT_OK;
+    }
+    return persistent_launch(b, adjoint, in, out, s);
 }
 
 // Capture every class as a parallel branch of one graph (fork from b->cap, join back).
@@ -200,12 +219,14 @@ int capture(nufft_batch b, int dir, const void *in, void *out) {
     if (cudaEventRecord(b->fork, b->cap) != cudaSuccess) rc = NUFFT_ECUDA;
     for (auto &c : b->cls) {
         if (rc) break;
+        if (b->persist && !c.single) continue;   // in the persistent launch, below
         if (cudaStreamWaitEvent(c.st, b->fork, 0) != cudaSuccess) { rc = NUFFT_ECUDA; break; }
         rc = class_launches<T>(b, c, dir == 1, in, out, c.st);
         if (!rc && (cudaEventRecord(c.done, c.st) != cudaSuccess ||
                     cudaStreamWaitEvent(b->cap, c.done, 0) != cudaSuccess))
             rc = NUFFT_ECUDA;
     }
+    if (!rc) rc = persistent_launch(b, dir == 1, in, out, b->cap);
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(b->cap, &g);
     if (!rc && e != cudaSuccess) rc = NUFFT_ECUDA;
@@ -246,6 +267,170 @@ using nufft::free_batch;
 
 namespace nufft {
 namespace {
+
+// The persistent kernel's CTAs (128 registers, 256 threads) fit two per SM only with at most
+// this much shared memory each; its dynamic shared memory is the largest any item needs, so
+// the row passes' rank groups are re-chosen to stay within it.
+constexpr size_t PERSIST_SMEM_CAP = 110 * 1024;
+
+// Pass A's arguments and shared memory in a CTA of 256 threads (the persistent kernel):
+// 256 / TT teams, each with its four-step table, and the largest rank group that fits.
+PassArgs<float> passA_persistent(nufft_plan p, size_t *smem) {
+    PassArgs<float> a = base_args<float>(p);
+    (void)rows_fields<float>(p, a, true);
+    const int E = std::min<int>(EmaxT<float, PK_ROW_ADJ>::v, p->L1), TT = p->L1 / E, nt = 256 / TT;
+    const size_t staging = (size_t)p->chunkA * (sizeof(int32_t) + sizeof(float)) + (size_t)p->chunkA * 8;
+    auto bytes = [&](int G) { return ((size_t)G * p->B2 * p->SA + (size_t)nt * E) * 8 + staging; };
+    int G = p->GA;
+    while (G > 1 && bytes(G) > PERSIST_SMEM_CAP) --G;
+    a.G = G;
+    *smem = bytes(G);
+    return a;
+}
+
+// Pass 2's arguments with its rank group re-chosen to stay within PERSIST_SMEM_CAP (its
+// slots, then one mbarrier per slot); a group smaller than K keeps partial sums in fscr.
+PassArgs<float> pass2_persistent(nufft_plan p, size_t *smem) {
+    PassArgs<float> a = base_args<float>(p);
+    (void)rows_fields<float>(p, a, false);
+    auto body = [&](int G) { return ((size_t)G * p->B2 * p->S2 * 8 + 15) / 16 * 16; };
+    auto bytes = [&](int G) { return body(G) + (size_t)G * p->B2 * sizeof(uint64_t); };
+    int G = std::min(p->G, p->K);   // the plain forward stages K ranks
+    while (G > 1 && bytes(G) > PERSIST_SMEM_CAP) --G;
+    a.G = G;
+    a.mbar_off = (int)body(G);
+    *smem = bytes(G);
+    return a;
+}
+
+template <typename D, typename V>
+int upload_persist(nufft_batch b, D **dst, const std::vector<V> &h) {
+    void *q = nullptr;
+    NUFFT_CUDA_TRY(dev_malloc(&q, std::max<size_t>(1, h.size()) * sizeof(V)));
+    b->pbufs.push_back(q);
+    if (!h.empty()) NUFFT_CUDA_TRY(cudaMemcpy(q, h.data(), h.size() * sizeof(V), cudaMemcpyHostToDevice));
+    *dst = (D *)q;
+    return NUFFT_OK;
+}
+
+// The persistent launches' state (NUFFT_BATCH_PERSISTENT): per direction, the class table
+// (the class launches' argument arrays; pass A's rebuilt for 256-thread CTAs), the work
+// items -- every first-pass block of every problem, largest problems first, then every
+// second-pass block in the same order -- the first-pass counts each problem's second pass
+// waits for, the coefficients as 16 x 16 tables, the counters, and the grid (the CTAs
+// that fit on the device at once).
+int build_persistent(nufft_batch b) {
+    const int nprob = (int)b->plans.size();
+    std::vector<Beta<float, 16>> be((size_t)nprob);
+    for (int i = 0; i < nprob; ++i)
+        for (int r = 0; r < 16; ++r)
+            for (int q = 0; q < 16; ++q) be[i].b[r][q] = (float)b->plans[i]->beta[r][q];
+    const Beta<float, 16> *dbe = nullptr;
+    if (int rc = upload_persist(b, &dbe, be)) return rc;
+    int *done = nullptr, *ctl = nullptr;
+    if (int rc = upload_persist(b, &done, std::vector<int>((size_t)nprob, 0))) return rc;
+    if (int rc = upload_persist(b, &ctl, std::vector<int>(4, 0))) return rc;
+    int dev = 0, sms = 0;
+    NUFFT_CUDA_TRY(cudaGetDevice(&dev));
+    NUFFT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    // problems of batched classes, largest grid first (they take longest)
+    std::vector<std::pair<int, int>> order;   // (class, member)
+    for (int c = 0; c < (int)b->cls.size(); ++c)
+        if (!b->cls[c].single)
+            for (int m = 0; m < (int)b->cls[c].idx.size(); ++m) order.push_back({c, m});
+    std::stable_sort(order.begin(), order.end(), [&](const std::pair<int, int> &u, const std::pair<int, int> &v) {
+        return b->cls[u.first].L > b->cls[v.first].L;
+    });
+    for (int dir = 0; dir < 2; ++dir) {
+        std::vector<PClass> pc(b->cls.size());
+        std::vector<PItem> first, second;
+        std::vector<int> need((size_t)nprob, 0);
+        size_t smem = 0;
+        for (int c = 0; c < (int)b->cls.size(); ++c) {
+            auto &cl = b->cls[c];
+            if (cl.single) continue;
+            nufft_plan r = b->plans[cl.rep];
+            pc[c].P_rows = r->L1;
+            pc[c].P_cols = r->L2;
+            if (dir == 0) {
+                std::vector<PassArgs<float>> v2;
+                for (int i : cl.idx) {
+                    size_t sm = 0;
+                    PassArgs<float> a = pass2_persistent(b->plans[i], &sm);
+                    a.in_off = b->offN[i];
+                    a.out_off = b->offM[i];
+                    v2.push_back(a);
+                    smem = std::max(smem, sm);
+                }
+                const PassArgs<float> *d2 = nullptr;
+                if (int rc = upload_persist(b, &d2, v2)) return rc;
+                pc[c].args[0] = (const PassArgs<float> *)cl.a1;
+                pc[c].args[1] = d2;
+                smem = std::max(smem, r->smem1);
+            } else {
+                std::vector<PassArgs<float>> vA;
+                for (int i : cl.idx) {
+                    size_t sm = 0;
+                    PassArgs<float> a = passA_persistent(b->plans[i], &sm);
+                    a.in_off = b->offM[i];
+                    a.out_off = b->offN[i];
+                    vA.push_back(a);
+                    smem = std::max(smem, sm);
+                }
+                const PassArgs<float> *dA = nullptr;
+                if (int rc = upload_persist(b, &dA, vA)) return rc;
+                pc[c].args[0] = dA;
+                pc[c].args[1] = (const PassArgs<float> *)cl.aB;
+                smem = std::max(smem, r->smemB);
+            }
+        }
+        // a row of nbx blocks in items of up to `per` consecutive blocks: problems with many
+        // blocks take several per item, so that the per-item work (the ticket, the arguments,
+        // the barriers) is a small part of it
+        auto add_row = [&](std::vector<PItem> &v, int kind, const std::pair<int, int> &cm, int i, int nbx, int by) {
+            const int per = nbx >= 256 ? 4 : nbx >= 64 ? 2 : 1;
+            for (int bx = 0; bx < nbx; bx += per)
+                v.push_back(PItem{kind, cm.first, cm.second, i, bx, by, std::min(per, nbx - bx)});
+        };
+        for (const auto &cm : order) {
+            const auto &cl = b->cls[cm.first];
+            const int i = cl.idx[cm.second];
+            nufft_plan p = b->plans[i];
+            if (p->M == 0 && dir == 0) continue;   // nothing to transform (its f is empty)
+            if (dir == 0) {
+                const int nbx = p->L1 / p->C1;
+                for (int by = 0; by < p->K; ++by) add_row(first, 0, cm, i, nbx, by);
+                need[i] = nbx * p->K;
+                add_row(second, 1, cm, i, p->NB, 0);
+            } else {
+                add_row(first, 0, cm, i, p->NB, 0);
+                need[i] = p->NB;
+                for (int by = 0; by < cl.nyB; ++by) add_row(second, 1, cm, i, p->L1 / p->CB, by);
+            }
+        }
+        first.insert(first.end(), second.begin(), second.end());
+        PState &st = b->pst[dir];
+        if (int rc = upload_persist(b, &st.items, first)) return rc;
+        const PClass *dpc = nullptr;
+        if (int rc = upload_persist(b, &dpc, pc)) return rc;
+        const int *dneed = nullptr;
+        if (int rc = upload_persist(b, &dneed, need)) return rc;
+        st.n_items = (int)first.size();
+        st.classes = dpc;
+        st.betas = dbe;
+        st.done = done;
+        st.need = dneed;
+        st.ctl = ctl + 2 * dir;
+        st.nprob = nprob;
+        b->psmem[dir] = smem;
+        int per_sm = 0;
+        if (int rc = persistent_blocks_per_sm(dir, smem, &per_sm)) return rc;
+        if (per_sm < 1) return NUFFT_EUNSUPPORTED;
+        b->pgrid[dir] = per_sm * sms;
+    }
+    b->persist = true;
+    return NUFFT_OK;
+}
 
 // A batch from per-problem inputs: sample pointers xs[i], layouts lays (or NULL: each
 // problem's default).  flags may hold NUFFT_PLAN_AUTOTUNE for the problems' own plans.
@@ -334,6 +519,12 @@ int plan_many_core(nufft_batch *out, int64_t count, const int64_t *N_host, const
             (void)cudaGetLastError();
             free_batch(b);
             return NUFFT_ECUDA;
+        }
+    }
+    if (flags & NUFFT_BATCH_PERSISTENT) {
+        if (int rc = build_persistent(b)) {
+            free_batch(b);
+            return rc;
         }
     }
     *out = b;
@@ -473,7 +664,8 @@ extern "C" int nufft2_plan_many(nufft_batch *out, int64_t count, const int64_t *
     *out = nullptr;
     if (count < 1 || count > 65535 || !N_host || !M_host || !eps_host) return NUFFT_EINVAL;
     if (prec != NUFFT_F32 && prec != NUFFT_F64) return NUFFT_EINVAL;
-    if (flags & ~(NUFFT_BATCH_GRAPH | NUFFT_BATCH_PER_PROBLEM | NUFFT_PLAN_AUTOTUNE)) return NUFFT_EINVAL;
+    if (flags & ~(NUFFT_BATCH_GRAPH | NUFFT_BATCH_PER_PROBLEM | NUFFT_PLAN_AUTOTUNE | NUFFT_BATCH_PERSISTENT))
+        return NUFFT_EINVAL;
     int64_t totM = 0;
     for (int64_t i = 0; i < count; ++i) {
         if (M_host[i] < 0 || M_host[i] >= ((int64_t)1 << 31)) return NUFFT_EINVAL;
@@ -511,6 +703,15 @@ extern "C" int nufft_batch_info(nufft_batch b, int64_t *classes, int64_t *total_
         if (K_host) K_host[i] = b->plans[i]->K;
         if (L_host) L_host[i] = b->plans[i]->L;
     }
+    return NUFFT_OK;
+}
+
+extern "C" int nufft_batch_launches(nufft_batch b, int64_t *per_direction) {
+    if (!b || !per_direction) return NUFFT_EINVAL;
+    int64_t n = 0;
+    for (const auto &c : b->cls) n += (b->persist && !c.single) ? 0 : 2;
+    if (b->persist) n += 1;
+    *per_direction = n;
     return NUFFT_OK;
 }
 

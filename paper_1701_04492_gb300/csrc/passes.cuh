@@ -208,8 +208,12 @@ __device__ __forceinline__ void pass1_body(const PassArgs<T> &a, const int bx, c
     using TF = TeamFft<T, P2, E, false>;
     constexpr int TT = TF::TT;
     cx<T> *smem = smem_base<T>();
-    const int cc = threadIdx.x & (a.C - 1);
-    const int tt = threadIdx.x >> a.lgC;
+    // the thread's role among the C TT threads the pass needs; in a larger CTA (the
+    // persistent batch kernel) the extra threads shadow a role exactly, writing the same
+    // values to the same places (the leader-only steps stay with thread 0)
+    const int lt = threadIdx.x & (a.C * TT - 1);
+    const int cc = lt & (a.C - 1);
+    const int tt = lt >> a.lgC;
     const int k1 = bx * a.C + cc;
     const int r = by;
     cx<T> *ftab = smem + a.C * a.S;
@@ -765,8 +769,11 @@ __device__ __forceinline__ void passB_body(const PassArgs<T> &a, const int bx, c
     using TF = TeamFft<T, P2, E, true>;
     constexpr int TT = TF::TT;
     cx<T> *smem = smem_base<T>();
-    const int cc = threadIdx.x & (a.C - 1);
-    const int tt = threadIdx.x >> a.lgC;
+    // the thread's role among the C TT threads the pass needs (extra threads of a larger
+    // CTA shadow a role exactly, as in pass 1; the copies and tickets stay with thread 0)
+    const int lt = threadIdx.x & (a.C * TT - 1);
+    const int cc = lt & (a.C - 1);
+    const int tt = lt >> a.lgC;
     const int k1 = bx * a.C + cc;
     const int s = by, SB = a.SB;
     const int Ni = (int)a.N;   // N < 2^23: 32-bit conversions (64-bit ones run on the FP64 pipe)

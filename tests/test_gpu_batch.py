@@ -364,3 +364,43 @@ def test_step_host_needs_its_reservation(api):
     assert lib.nufft2_step_host(plan._h, *args, api._stream(plan.device)) == 0
     torch.cuda.synchronize()
     assert torch.equal(fh, plan.forward_deriv(ch.cuda())[0].cpu())   # the step's f comes with f'
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_persistent_launch_matches_class_launches(api, graph):
+    """NUFFT_BATCH_PERSISTENT: one launch per direction for every batched class (grids from
+    2^10 to 2^15 points, several rank bounds, one empty problem).  The adjoint equals the
+    class launches bit for bit; the forward agrees to FP32 rounding (its rank groups are
+    re-chosen so that two CTAs fit per SM, and a group boundary moves where the compensated
+    rank-sum folds in its correction); repeated calls give the same bits (the kernel resets
+    its own ticket and counters), with and without a CUDA graph; and both agree with the
+    oracle."""
+    N, xs, eps = _problems(40, 31, lo=10, hi=15)
+    ref = api.Batch(N, xs, eps, "f32")
+    per = api.Batch(N, xs, eps, "f32", persistent=True, graph=graph)
+    assert ref.launches_per_direction == 2 * ref.classes and ref.classes > 4
+    assert per.launches_per_direction == 1
+    c_dev, c = _packed("f32", N, 32)
+    g = wl.cotangent_cn(int(ref.total_M), 33).astype(np.complex64)
+    g_dev = torch.tensor(g, device="cuda")
+    f0 = ref.forward(c_dev)
+    a0 = ref.adjoint(g_dev)
+    first = None
+    for _ in range(3):
+        f1 = per.forward(c_dev)
+        a1 = per.adjoint(g_dev)
+        torch.cuda.synchronize()
+        assert _rel2(f1.cpu().numpy(), f0.cpu().numpy()) <= 1e-6
+        assert torch.equal(a1, a0)
+        if first is None:
+            first = f1.clone()
+        assert torch.equal(f1, first)
+    per.check()
+    fh = f1.cpu().numpy()
+    for i in (0, len(N) // 3, len(N) - 1):
+        m0, m1 = per.offM[i], per.offM[i + 1]
+        n0, n1 = per.offN[i], per.offN[i + 1]
+        if m1 == m0:
+            continue
+        P = lowrank.plan(N[i], xs[i], eps[i], int(per.L[i]))
+        assert_close(fh[m0:m1], lowrank.nufft2(P, c[n0:n1]), "f32", what=str(i))

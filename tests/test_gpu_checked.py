@@ -62,8 +62,8 @@ def _child():
     # a batch of uneven problems, graph and direct launches
     Ns, epss = [1500, 3001, 7000, 20000], [1e-6, 1e-9, 1e-4, 1e-6]
     xs = [wl.samples_uniform(n + 17, 70 + i) for i, n in enumerate(Ns)]
-    for graph in (False, True):
-        b = api.Batch(Ns, xs, epss, "f32", graph=graph)
+    for graph, persistent in ((False, False), (True, False), (False, True)):
+        b = api.Batch(Ns, xs, epss, "f32", graph=graph, persistent=persistent)
         cs = [wl.coeffs_cn(n, 80 + i).astype(np.complex64) for i, n in enumerate(Ns)]
         f = b.forward(torch.tensor(np.concatenate(cs), device=dev)).cpu().numpy()
         off = 0
