@@ -148,14 +148,17 @@ def kernel_source_hash():
 
 
 def committed_traffic(kernel):
-    path = os.path.join(ROOT, "profiles", "ncu_traffic_n2e20.md")
+    """DRAM bytes per launch of `kernel` inside a running step (ncu, --cache-control none),
+    from the committed summary, while the kernel sources still hash as they did then."""
+    path = os.path.join(ROOT, "profiles", "ncu_step_kernels_n2e20.md")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
     m = re.search(r"source_hash:\s*(\w+)", txt)
     if not m or m.group(1) != kernel_source_hash():
         return None
-    m = re.search(r"^\|\s*%s\s*\|[^|]*\|\s*([0-9.eE+]+)\s*\|" % re.escape(kernel), txt, re.M)
+    # | kernel | dram read MB | dram write MB | in-step dram bytes per launch | ...
+    m = re.search(r"^\|\s*%s\s*\|[^|]*\|[^|]*\|\s*([0-9]+)\s*\|" % re.escape(kernel), txt, re.M)
     return float(m.group(1)) if m else None
 
 
@@ -312,7 +315,7 @@ def run_ours(args):
                 "alu_frac_per_kernel": {k: flops[k] / (kavg[k] * 1e-3) / 1e12 / peak_tf for k in kavg}}
         hbm = json.load(open(PEAKS_PATH))["hbm_gbs"] if os.path.exists(PEAKS_PATH) else 6800.0
         if traffic is not None:
-            # the DRAM bytes ncu counted for one launch (cold L2) over its measured time
+            # the DRAM bytes ncu counted for one launch inside a step over its measured time
             roof["dram_GBps"] = traffic / (kavg[dom] * 1e-3) / 1e9
             roof["dram_frac_of_measured_hbm"] = roof["dram_GBps"] / hbm
             roof["dram_bytes_per_point"] = traffic / M
