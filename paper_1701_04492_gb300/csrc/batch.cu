@@ -270,7 +270,7 @@ namespace {
 
 // The persistent kernel's CTAs (128 registers, 256 threads) fit two per SM only with at most
 // this much shared memory each; its dynamic shared memory is the largest any item needs, so
-// the row passes' rank groups are re-chosen to stay within it.
+// the row passes' rank groups and pass 1's columns per CTA are re-chosen to stay within it.
 constexpr size_t PERSIST_SMEM_CAP = 110 * 1024;
 
 // Pass A's arguments and shared memory in a CTA of 256 threads (the persistent kernel):
@@ -285,6 +285,23 @@ PassArgs<float> passA_persistent(nufft_plan p, size_t *smem) {
     while (G > 1 && bytes(G) > PERSIST_SMEM_CAP) --G;
     a.G = G;
     *smem = bytes(G);
+    return a;
+}
+
+// Pass 1's arguments with its columns per CTA halved until its slots and four-step table
+// stay within PERSIST_SMEM_CAP (a class launch may take more shared memory, and run one
+// CTA per SM, but the persistent kernel's size is every item's); with fewer columns the
+// extra threads of the 256-thread CTA shadow roles.  The slot stride is kept.
+PassArgs<float> pass1_persistent(nufft_plan p, size_t *smem) {
+    PassArgs<float> a = base_args<float>(p);
+    cols_fields<float>(p, a, false);
+    const size_t E2 = (size_t)std::min<int>(EmaxT<float, PK_COL_FWD>::v, p->L2);
+    auto bytes = [&](int C) { return ((size_t)C * a.S + (size_t)C * E2) * sizeof(float2); };
+    while (a.C > 1 && bytes(a.C) > PERSIST_SMEM_CAP) {
+        a.C /= 2;
+        --a.lgC;
+    }
+    *smem = bytes(a.C);
     return a;
 }
 
@@ -343,6 +360,7 @@ int build_persistent(nufft_batch b) {
     });
     for (int dir = 0; dir < 2; ++dir) {
         std::vector<PClass> pc(b->cls.size());
+        std::vector<int> c1(b->cls.size(), 1);   // pass 1's columns per CTA, per class
         std::vector<PItem> first, second;
         std::vector<int> need((size_t)nprob, 0);
         size_t smem = 0;
@@ -352,21 +370,28 @@ int build_persistent(nufft_batch b) {
             nufft_plan r = b->plans[cl.rep];
             pc[c].P_rows = r->L1;
             pc[c].P_cols = r->L2;
+            pc[c].km = cl.KM <= 8 ? 8 : cl.KM <= 12 ? 12 : 16;
             if (dir == 0) {
-                std::vector<PassArgs<float>> v2;
+                std::vector<PassArgs<float>> v1, v2;
                 for (int i : cl.idx) {
                     size_t sm = 0;
-                    PassArgs<float> a = pass2_persistent(b->plans[i], &sm);
+                    PassArgs<float> a = pass1_persistent(b->plans[i], &sm);
+                    a.in_off = b->offN[i];
+                    a.out_off = b->offM[i];
+                    v1.push_back(a);
+                    smem = std::max(smem, sm);
+                    a = pass2_persistent(b->plans[i], &sm);
                     a.in_off = b->offN[i];
                     a.out_off = b->offM[i];
                     v2.push_back(a);
                     smem = std::max(smem, sm);
                 }
-                const PassArgs<float> *d2 = nullptr;
+                const PassArgs<float> *d1 = nullptr, *d2 = nullptr;
+                if (int rc = upload_persist(b, &d1, v1)) return rc;
                 if (int rc = upload_persist(b, &d2, v2)) return rc;
-                pc[c].args[0] = (const PassArgs<float> *)cl.a1;
+                pc[c].args[0] = d1;
                 pc[c].args[1] = d2;
-                smem = std::max(smem, r->smem1);
+                c1[c] = v1.empty() ? r->C1 : v1[0].C;
             } else {
                 std::vector<PassArgs<float>> vA;
                 for (int i : cl.idx) {
@@ -398,7 +423,7 @@ int build_persistent(nufft_batch b) {
             nufft_plan p = b->plans[i];
             if (p->M == 0 && dir == 0) continue;   // nothing to transform (its f is empty)
             if (dir == 0) {
-                const int nbx = p->L1 / p->C1;
+                const int nbx = p->L1 / c1[cm.first];
                 for (int by = 0; by < p->K; ++by) add_row(first, 0, cm, i, nbx, by);
                 need[i] = nbx * p->K;
                 add_row(second, 1, cm, i, p->NB, 0);

@@ -17,8 +17,9 @@
 // (idle teams only meet the barriers), and the column passes of small grids, which need
 // fewer threads, let the extra threads shadow a role (pass 1 and pass B write the same
 // values to the same places from both).  Items use the class arguments built at plan time
-// (each member's own plan: its buffers, K, tables); coefficient tables are read as
-// 16 x 16 (zero-padded), so one kernel covers every rank bound.
+// (each member's own plan: its buffers, K, tables); the coefficient tables are stored
+// 16 x 16 (zero-padded) and staged per item at the class's rank bound, for which the row
+// passes are compiled (8, 12, 16).
 #pragma once
 
 #include "passes.cuh"
@@ -36,6 +37,7 @@ struct PItem {
 
 struct PClass {
     int P_rows, P_cols;                      // row FFT length (L1), column FFT length (L2)
+    int km;                                  // the row passes' rank bound: 8, 12 or 16
     const PassArgs<float> *args[2];          // per member: first pass, second pass
 };
 

@@ -35,50 +35,58 @@ __device__ __forceinline__ void wait_count(const int *cnt, int need, int *err) {
     }
 }
 
-// Each pass and size is its own (not inlined) function: the kernel is one launch, but the
-// compiler allocates registers per body, as for the class launches.  The body works on a
-// private copy of the item's arguments (sa is in shared memory, and reached through a
-// pointer the compiler could not keep its fields in registers across the body's stores).
-template <int DIR, int P>
-__device__ __noinline__ void run_first(const PassArgs<float> &sa, const BetaShared<float, 16> &bs, const PItem &w) {
+// Each pass, size and rank bound is its own (not inlined) function: the kernel is one
+// launch, but the compiler allocates registers per body, as for the class launches, and a
+// row pass loops over its class's rank bound KM (8, 12 or 16), not over the largest.  The
+// body works on a private copy of the item's arguments (sa is in shared memory, and
+// reached through a pointer the compiler could not keep its fields in registers across
+// the body's stores).
+template <int DIR, int P, int KM>
+__device__ __noinline__ void run_first(const PassArgs<float> &sa, const float *beta, const PItem &w) {
     const PassArgs<float> a = sa;
     if constexpr (DIR == 0) {
-        (void)bs;
+        (void)beta;
         pass1_body<float, P>(a, w.bx, w.by);
     } else {
-        passA_body<float, P, 16>(a, bs, w.bx);
+        passA_body<float, P, KM>(a, BetaShared<float, KM>{beta}, w.bx);
     }
 }
-template <int DIR, int P>
-__device__ __noinline__ void run_second(const PassArgs<float> &sa, const BetaShared<float, 16> &bs, const PItem &w) {
+template <int DIR, int P, int KM>
+__device__ __noinline__ void run_second(const PassArgs<float> &sa, const float *beta, const PItem &w) {
     const PassArgs<float> a = sa;
     if constexpr (DIR == 0) {
-        pass2_body<float, P, 16>(a, bs, w.bx);
+        pass2_body<float, P, KM>(a, BetaShared<float, KM>{beta}, w.bx);
     } else {
-        (void)bs;
+        (void)beta;
         passB_body<float, P>(a, w.bx, w.by);
     }
 }
 
-template <int DIR>
-__device__ __forceinline__ void run_block(const PassArgs<float> &a, const BetaShared<float, 16> &bs, PItem w,
-                                          int P) {
+// the row pass of the item's kind takes the class's rank bound; the column pass none
+template <int DIR, int P>
+__device__ __forceinline__ void run_sized(const PassArgs<float> &a, const float *beta, const PItem &w, int km) {
+    const bool row = (w.kind == 0) == (DIR == 1);
     if (w.kind == 0) {
-        switch (P) {
-            case 32: run_first<DIR, 32>(a, bs, w); break;
-            case 64: run_first<DIR, 64>(a, bs, w); break;
-            case 128: run_first<DIR, 128>(a, bs, w); break;
-            case 256: run_first<DIR, 256>(a, bs, w); break;
-            default: run_first<DIR, 512>(a, bs, w); break;
-        }
+        if (!row) run_first<DIR, P, 16>(a, beta, w);
+        else if (km <= 8) run_first<DIR, P, 8>(a, beta, w);
+        else if (km <= 12) run_first<DIR, P, 12>(a, beta, w);
+        else run_first<DIR, P, 16>(a, beta, w);
     } else {
-        switch (P) {
-            case 32: run_second<DIR, 32>(a, bs, w); break;
-            case 64: run_second<DIR, 64>(a, bs, w); break;
-            case 128: run_second<DIR, 128>(a, bs, w); break;
-            case 256: run_second<DIR, 256>(a, bs, w); break;
-            default: run_second<DIR, 512>(a, bs, w); break;
-        }
+        if (!row) run_second<DIR, P, 16>(a, beta, w);
+        else if (km <= 8) run_second<DIR, P, 8>(a, beta, w);
+        else if (km <= 12) run_second<DIR, P, 12>(a, beta, w);
+        else run_second<DIR, P, 16>(a, beta, w);
+    }
+}
+
+template <int DIR>
+__device__ __forceinline__ void run_block(const PassArgs<float> &a, const float *beta, PItem w, int P, int km) {
+    switch (P) {
+        case 32: run_sized<DIR, 32>(a, beta, w, km); break;
+        case 64: run_sized<DIR, 64>(a, beta, w, km); break;
+        case 128: run_sized<DIR, 128>(a, beta, w, km); break;
+        case 256: run_sized<DIR, 256>(a, beta, w, km); break;
+        default: run_sized<DIR, 512>(a, beta, w, km); break;
     }
 }
 
@@ -97,14 +105,15 @@ __global__ void __launch_bounds__(256, 2) k_persist(const PState st, const ManyI
         if (threadIdx.x == 0) next = atomicAdd(&st.ctl[0], 1);
         const PItem w = st.items[it];
         const PClass c = st.classes[w.cls];
-        // the item's arguments and coefficients, to shared memory
+        // the item's arguments, and its coefficients as a km x km table, to shared memory
+        const int km = c.km;
         {
             const unsigned long long *src =
                 reinterpret_cast<const unsigned long long *>(c.args[w.kind] + w.member);
             unsigned long long *dst = reinterpret_cast<unsigned long long *>(&a);
             for (int i = threadIdx.x; i < (int)(sizeof(PassArgs<float>) / 8); i += blockDim.x) dst[i] = src[i];
             const float *bsrc = &st.betas[w.prob].b[0][0];
-            for (int i = threadIdx.x; i < 16 * 16; i += blockDim.x) (&sb.b[0][0])[i] = bsrc[i];
+            for (int i = threadIdx.x; i < km * km; i += blockDim.x) (&sb.b[0][0])[i] = bsrc[(i / km) * 16 + i % km];
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -117,12 +126,11 @@ __global__ void __launch_bounds__(256, 2) k_persist(const PState st, const ManyI
             }
         }
         __syncthreads();
-        const BetaShared<float, 16> bs{&sb.b[0][0]};
         const int P = w.kind == 0 ? (DIR == 0 ? c.P_cols : c.P_rows) : (DIR == 0 ? c.P_rows : c.P_cols);
         for (int q = 0; q < w.nbx; ++q) {
             PItem wq = w;
             wq.bx = w.bx + q;
-            run_block<DIR>(a, bs, wq, P);
+            run_block<DIR>(a, &sb.b[0][0], wq, P, km);
             // every thread's writes of this block; then the block's mbarriers, quiescent now
             // (every copy was waited for), are invalidated before shared memory is reused
             __threadfence();
