@@ -244,9 +244,9 @@ int nufft2_grad_x_batch(nufft_plan p, int64_t B, const void *g_dev, const void *
 
 /* One training step with HOST buffers: f = A c and f' = df/dx (nufft2_exec_deriv),
  * A^H g (nufft1_exec) and gx_j = Re(conj(g_j) f'_j) (nufft2_grad_x), with c and g
- * copied in and f, A^H g and gx copied out.  The adjoint, which needs only g, runs
- * while c is still arriving; the copies run on a stream of the plan's own, each as soon
- * as its data is ready, overlapping the transforms; `stream` waits for
+ * copied in and f, A^H g and gx copied out.  c is copied in first and the forward runs
+ * while g arrives; f and gx are copied out while the adjoint runs.  The copies run on a
+ * stream of the plan's own, each as soon as its data is ready; `stream` waits for
  * the last one, and the host buffers hold the results once `stream` has completed (the
  * call does not synchronise).  Pinned host memory makes the copies asynchronous.
  * c_host, gc_host N complex; g_host, f_host M complex; gx_host M reals of the plan's

@@ -660,26 +660,29 @@ int step_host(nufft_plan p, const void *c_h, const void *g_h, void *f_h, void *g
     if (!p->st_g || !p->st_copy) return NUFFT_ESTATE;   // nufft2_plan_reserve makes the buffers
     cudaStream_t cs = p->st_copy;
     cudaEvent_t *ev = p->st_ev;   // 0 start / gx ready, 1 g in, 2 c in, 3 A^H g ready, 4 f ready, 5 all out
+    // c goes up first and the forward starts as soon as it is in, while g follows; f and
+    // gx come down while the adjoint runs, so that only the first upload and A^H g's
+    // download stay outside the kernels' time
     NUFFT_CUDA_TRY(cudaEventRecord(ev[0], s));
     NUFFT_CUDA_TRY(cudaStreamWaitEvent(cs, ev[0], 0));
-    if (p->M > 0) NUFFT_CUDA_TRY(cudaMemcpyAsync(p->st_g, g_h, (size_t)p->M * cxs, cudaMemcpyHostToDevice, cs));
-    NUFFT_CUDA_TRY(cudaEventRecord(ev[1], cs));
     NUFFT_CUDA_TRY(cudaMemcpyAsync(p->cstage, c_h, (size_t)p->N * cxs, cudaMemcpyHostToDevice, cs));
     NUFFT_CUDA_TRY(cudaEventRecord(ev[2], cs));
-    NUFFT_CUDA_TRY(cudaStreamWaitEvent(s, ev[1], 0));
-    if (int rc = exec_adjoint<T>(p, p->st_g, p->st_gc, s)) return rc;
-    NUFFT_CUDA_TRY(cudaEventRecord(ev[3], s));
+    if (p->M > 0) NUFFT_CUDA_TRY(cudaMemcpyAsync(p->st_g, g_h, (size_t)p->M * cxs, cudaMemcpyHostToDevice, cs));
+    NUFFT_CUDA_TRY(cudaEventRecord(ev[1], cs));
     NUFFT_CUDA_TRY(cudaStreamWaitEvent(s, ev[2], 0));
     if (int rc = exec_deriv<T>(p, p->cstage, p->fstage, p->st_fp, s)) return rc;
     NUFFT_CUDA_TRY(cudaEventRecord(ev[4], s));
+    NUFFT_CUDA_TRY(cudaStreamWaitEvent(s, ev[1], 0));
     if (int rc = exec_grad_x<T>(p, p->st_g, p->st_fp, p->st_gx, 0, s)) return rc;
     NUFFT_CUDA_TRY(cudaEventRecord(ev[0], s));   // gx ready
-    NUFFT_CUDA_TRY(cudaStreamWaitEvent(cs, ev[3], 0));
-    NUFFT_CUDA_TRY(cudaMemcpyAsync(gc_h, p->st_gc, (size_t)p->N * cxs, cudaMemcpyDeviceToHost, cs));
+    if (int rc = exec_adjoint<T>(p, p->st_g, p->st_gc, s)) return rc;
+    NUFFT_CUDA_TRY(cudaEventRecord(ev[3], s));
     NUFFT_CUDA_TRY(cudaStreamWaitEvent(cs, ev[4], 0));
     if (p->M > 0) NUFFT_CUDA_TRY(cudaMemcpyAsync(f_h, p->fstage, (size_t)p->M * cxs, cudaMemcpyDeviceToHost, cs));
     NUFFT_CUDA_TRY(cudaStreamWaitEvent(cs, ev[0], 0));
     if (p->M > 0) NUFFT_CUDA_TRY(cudaMemcpyAsync(gx_h, p->st_gx, (size_t)p->M * sizeof(T), cudaMemcpyDeviceToHost, cs));
+    NUFFT_CUDA_TRY(cudaStreamWaitEvent(cs, ev[3], 0));
+    NUFFT_CUDA_TRY(cudaMemcpyAsync(gc_h, p->st_gc, (size_t)p->N * cxs, cudaMemcpyDeviceToHost, cs));
     NUFFT_CUDA_TRY(cudaEventRecord(ev[5], cs));
     NUFFT_CUDA_TRY(cudaStreamWaitEvent(s, ev[5], 0));
     return NUFFT_OK;
