@@ -103,11 +103,11 @@ template <typename T, int KM>
 int build_class(nufft_batch b, nufft_batch_s::Class &c) {
     std::vector<PassArgs<T>> v1, v2, vA, vB;
     std::vector<Beta<T, KM>> be;
-    // pass B's rank split for the class: about four CTAs per SM over all its problems,
-    // at most any member's own split (whose partial-sum buffer it uses)
+    // pass B's rank split for the class: about one CTA per SM over all its problems (as
+    // for a single plan), at most any member's own split (whose partial-sum buffer it uses)
     nufft_plan r = b->plans[c.rep];
     const int blocks = (int)(r->L1 / r->CB) * (int)c.idx.size();
-    int sb = (4 * 152 + blocks - 1) / blocks;
+    int sb = (device_sm_count() + blocks - 1) / blocks;
     for (int i : c.idx) sb = std::min(sb, b->plans[i]->SBsplit);
     sb = std::max(1, sb);
     c.nyB = sb;

@@ -125,6 +125,18 @@ struct nufft_plan_s {
 };
 
 namespace nufft {
+// The current device's SM count, for launch-geometry choices at plan time (152 on
+// GB300, which is also the value taken if the query fails: the choices are heuristics).
+inline int device_sm_count() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+        (void)cudaGetLastError();
+        return 152;
+    }
+    return sms;
+}
+
 // Record the next timing event (no-op without NUFFT_PLAN_TIMING).
 inline int mark(nufft_plan p, cudaStream_t s, bool first) {
     if (!(p->flags & NUFFT_PLAN_TIMING)) return NUFFT_OK;
