@@ -83,13 +83,17 @@ int plan_geometry(nufft_plan p) {
     p->smem1 = ((size_t)p->C1 * p->S1 + (size_t)p->C1 * E2) * cxs;   // slots + four-step table
     // two tile buffers (copy landing zone and exchange slots), then two mbarriers
     p->smemB = ((2 * (size_t)p->CB * p->SB * cxs + 15) / 16) * 16 + 2 * sizeof(uint64_t);
-    // rank splits of pass B: about one CTA per SM, at most one rank each.  Every further
-    // split costs a partial sum to write and add; at 2^20 (K = 12) pass B took 45 us with
-    // 256 CTAs (no split), 49 with two splits and 53 with three; at 2^18 20.5 us with 128
-    // CTAs against 28.7 with 640; at 2^22 151.6 us unsplit against 190.5 with two.
+    // rank splits of pass B, at most one rank each.  FP32: about one CTA per SM.  Every
+    // further split costs a partial sum to write and add; at 2^20 (K = 12) pass B took
+    // 45 us with 256 CTAs (no split), 49 with two splits and 53 with three; at 2^18 20.5 us
+    // with 128 CTAs against 28.7 with 640; at 2^22 151.6 us unsplit against 190.5 with two.
+    // The double-word FP64 pass B (128-thread CTAs, three per SM, several times the
+    // arithmetic per element) wants about four per SM: 308 us with two splits at 2^20
+    // against 342 unsplit.
     {
         const int blocks = p->L1 / p->CB, sms = device_sm_count();
-        p->SBsplit = std::max(1, std::min(p->K, (sms + blocks - 1) / blocks));
+        const int target = std::is_same<T, float>::value ? sms : 4 * sms;
+        p->SBsplit = std::max(1, std::min(p->K, (target + blocks - 1) / blocks));
     }
     // row passes: buckets of B2 rows; G ranks staged at once by nt teams
     p->B2 = clamp_pow2(1024 / p->L1, 1, p->L2);
