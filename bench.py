@@ -268,6 +268,18 @@ def run_ours(args):
         extra["fused_fp64_vs_plain_fp64_fwd_speedup"] = extra["fused_fp64_fwd_gpts"] / extra["plain_unfused_fp64_fwd_gpts"]
         extra["fused_fp32_vs_plain_fp64_fwd_speedup_unequal_accuracy"] = \
             extra["fwd_gpts"] / extra["plain_unfused_fp64_fwd_gpts"]
+        # for information: the FFT stage alone of a cuFFT-based plain form (torch.fft on the
+        # K x L rank matrix), a lower bound on that form's time, in both precisions
+        cuf = {}
+        for name, dt in (("fp32", torch.complex64), ("fp64", torch.complex128)):
+            Xr = torch.randn((plan.K, plan.L), dtype=dt, device=dev)   # not constant: the GPU compresses constant data
+            cuf[name + "_K_ffts_ms"] = float(np.median(timed(lambda: torch.fft.fft(Xr, dim=1), args.steps, 3)))
+            del Xr
+        cuf["fused_fp32_fwd_ms"] = extra["fwd_ms"]
+        cuf["fused_fp64_fwd_ms"] = M / (extra["fused_fp64_fwd_gpts"] * 1e9) * 1e3
+        cuf["note"] = ("torch.fft (cuFFT) of K x L complex values, the FFT stage alone of a plain form "
+                       "that calls cuFFT: a lower bound on its time, beside the whole fused forward")
+        extra["cufft_comparator"] = cuf
         plan64.forward_unfused(c64, f64)
         f64_plain = f64.cpu().numpy()
         plan64.forward(c64, f64)

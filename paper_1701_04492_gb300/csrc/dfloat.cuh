@@ -62,6 +62,25 @@ __device__ __forceinline__ dfloat operator*(dfloat a, dfloat b) {
     return r;
 }
 __device__ __forceinline__ dfloat &operator+=(dfloat &a, dfloat b) { return a = a + b; }
+// a1 b1 + a2 b2 with one renormalisation: the two high products summed by TwoSum, their
+// exact errors (FMA), the TwoSum error and the four cross terms gathered in one word, then
+// Fast2Sum.  19 operations against 25 for two products and a sum; the error stays a few
+// u^2 (|a1 b1| + |a2 b2|), the normwise bound the FFTs use.
+__device__ __forceinline__ dfloat dot2(dfloat a1, dfloat b1, dfloat a2, dfloat b2) {
+    const float p1 = __fmul_rn(a1.hi, b1.hi);
+    const float p2 = __fmul_rn(a2.hi, b2.hi);
+    float s, e;
+    two_sum(p1, p2, s, e);
+    float t = __fadd_rn(__fmaf_rn(a1.hi, b1.hi, -p1), __fmaf_rn(a2.hi, b2.hi, -p2));
+    t = __fadd_rn(t, e);
+    t = __fmaf_rn(a1.hi, b1.lo, t);
+    t = __fmaf_rn(a1.lo, b1.hi, t);
+    t = __fmaf_rn(a2.hi, b2.lo, t);
+    t = __fmaf_rn(a2.lo, b2.hi, t);
+    dfloat r;
+    fast_two_sum(s, t, r.hi, r.lo);
+    return r;
+}
 // the generic code calls fma unqualified: keep the float and double ones visible beside this
 using ::fma;
 // a b + c, as the product then the sum (each with its own double-word rounding)

@@ -121,17 +121,21 @@ int plan_geometry(nufft_plan p) {
         };
     };
     const auto teams = teams_of(TT1), teamsA = teams_of(TT1a);
-    auto choose = [&](int Gmax, auto bytes, auto teams, int *Gout, int *ntout) -> bool {
+    auto choose = [&](int Gmax, auto bytes, auto teams, int *Gout, int *ntout, size_t budget) -> bool {
         int G = Gmax;
-        while (G > 1 && bytes(G, teams(G * p->B2)) > SMEM_BUDGET) --G;
+        while (G > 1 && bytes(G, teams(G * p->B2)) > budget) --G;
         *Gout = G;
         *ntout = teams(G * p->B2);
-        return bytes(G, *ntout) <= SMEM_BUDGET;
+        return bytes(G, *ntout) <= budget;
     };
-    // pass 2 stages up to K + 1 ranks (the derivative mode adds rank K, and its gather
-    // needs them all in one group)
+    // pass 2 stages up to K + 1 ranks (the FP32 derivative mode adds rank K, and its
+    // gather needs them all in one group).  FP64 plans (double-word passes, which take
+    // the derivative another way) stage groups that let two CTAs share an SM: at 2^20
+    // (K = 12) pass 2 took 639 us with all 12 ranks (192 KB, one CTA per SM) and 403 us
+    // in two groups of 6, the partial sums kept in the plan's scratch between them.
+    const size_t budget2 = std::is_same<T, float>::value ? SMEM_BUDGET : (size_t)110 * 1024;
     int nt_dummy = 1;
-    if (!choose(p->K + 1, bytes2, teams, &p->G, &nt_dummy)) return NUFFT_EUNSUPPORTED;
+    if (!choose(p->K + 1, bytes2, teams, &p->G, &nt_dummy, budget2)) return NUFFT_EUNSUPPORTED;
     p->nt2 = teams(std::min(p->G, p->K) * p->B2);   // forward: K ranks
     p->nt2d = teams(p->G * p->B2);                  // derivative: K + 1 ranks
     p->mbar_off2 = body2(p->G);
@@ -139,7 +143,9 @@ int plan_geometry(nufft_plan p) {
     // (A smaller group for the plain forward, so that four CTAs fit per SM, was faster,
     // 78 -> 74 us at 2^20, until the row passes kept their stage twiddles in registers: at
     // about 120 registers per thread four CTAs no longer fit.)
-    if (!choose(p->K, bytesA, teamsA, &p->GA, &p->ntA)) return NUFFT_EUNSUPPORTED;
+    // (Pass A keeps the full budget in both precisions: its samples are staged again per
+    // group, and the FP64 pass A measured 1003 us in one group against 1139 in two.)
+    if (!choose(p->K, bytesA, teamsA, &p->GA, &p->ntA, SMEM_BUDGET)) return NUFFT_EUNSUPPORTED;
     p->smemA = bytesA(p->GA, p->ntA);
     if (p->smem1 > SMEM_BUDGET || p->smemB > SMEM_BUDGET) return NUFFT_EUNSUPPORTED;
     return NUFFT_OK;

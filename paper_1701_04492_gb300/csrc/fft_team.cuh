@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
 #include <utility>
 
 #include "dfloat.cuh"
@@ -76,6 +77,19 @@ template <typename T> __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
 template <typename T> __device__ __forceinline__ cx<T> cmulc(cx<T> a, cx<T> b) {
     return mk<T>(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y));
 }
+// the double-word products as one dot2 per component
+template <> __device__ __forceinline__ cdf cmul<dfloat>(cdf a, cdf b) {
+    cdf r;
+    r.x = dot2(a.x, b.x, -a.y, b.y);
+    r.y = dot2(a.x, b.y, a.y, b.x);
+    return r;
+}
+template <> __device__ __forceinline__ cdf cmulc<dfloat>(cdf a, cdf b) {
+    cdf r;
+    r.x = dot2(a.x, b.x, a.y, b.y);
+    r.y = dot2(a.y, b.x, -a.x, b.y);
+    return r;
+}
 // a * i^q  (q mod 4)
 template <typename T> __device__ __forceinline__ cx<T> mul_ipow(cx<T> a, int q) {
     switch (q & 3) {
@@ -116,6 +130,12 @@ __device__ __forceinline__ cx<T> mul_w32(cx<T> a, int m) {
     if (m == 24) return INV ? mk<T>(a.y, -a.x) : mk<T>(-a.y, a.x);
     const T c = (T)cos32(m);
     const T s = (T)(INV ? sin32(m) : -sin32(m));   // exp(i s') with s' = -+ angle
+    if constexpr (std::is_same<T, dfloat>::value) {
+        cdf r;
+        r.x = dot2(c, a.x, -s, a.y);
+        r.y = dot2(c, a.y, s, a.x);
+        return r;
+    }
     if (m == 4 || m == 12 || m == 20 || m == 28) {
         // |c| = |s| = 1/sqrt(2): (c a.x - s a.y, c a.y + s a.x) with shared products
         return mk<T>(c * a.x - s * a.y, c * a.y + s * a.x);
