@@ -81,6 +81,35 @@ __device__ __forceinline__ dfloat dot2(dfloat a1, dfloat b1, dfloat a2, dfloat b
     fast_two_sum(s, t, r.hi, r.lo);
     return r;
 }
+// Lazy forms for the chains of one in-register DFT: each result is an exact (hi, lo) pair
+// but not renormalised (|lo| may grow to a few ulp(hi) over the DFT's log2 R levels, and
+// the rounding of the low words stays a few u^2 of the operands); renorm() restores the
+// invariant at the DFT's end.  Addition: TwoSum of the high words, the low words added to
+// its error (8 operations against 11); dot2_lazy: dot2 without its Fast2Sum (16 against 19).
+__device__ __forceinline__ dfloat add_lazy(dfloat a, dfloat b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    return dfloat(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ dfloat sub_lazy(dfloat a, dfloat b) { return add_lazy(a, dfloat(-b.hi, -b.lo)); }
+__device__ __forceinline__ dfloat dot2_lazy(dfloat a1, dfloat b1, dfloat a2, dfloat b2) {
+    const float p1 = __fmul_rn(a1.hi, b1.hi);
+    const float p2 = __fmul_rn(a2.hi, b2.hi);
+    float s, e;
+    two_sum(p1, p2, s, e);
+    float t = __fadd_rn(__fmaf_rn(a1.hi, b1.hi, -p1), __fmaf_rn(a2.hi, b2.hi, -p2));
+    t = __fadd_rn(t, e);
+    t = __fmaf_rn(a1.hi, b1.lo, t);
+    t = __fmaf_rn(a1.lo, b1.hi, t);
+    t = __fmaf_rn(a2.hi, b2.lo, t);
+    t = __fmaf_rn(a2.lo, b2.hi, t);
+    return dfloat(s, t);
+}
+__device__ __forceinline__ dfloat renorm(dfloat a) {
+    dfloat r;
+    fast_two_sum(a.hi, a.lo, r.hi, r.lo);
+    return r;
+}
 // the generic code calls fma unqualified: keep the float and double ones visible beside this
 using ::fma;
 // a b + c, as the product then the sum (each with its own double-word rounding)

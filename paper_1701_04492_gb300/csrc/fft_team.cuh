@@ -190,6 +190,55 @@ struct Dft {
     }
 };
 
+// The double-word DFT: the same radix-2 decimation in time, with the lazy double-word
+// operations along its chains and one renormalisation of each output.
+template <bool INV>
+__device__ __forceinline__ cdf mul_w32_lazy(cdf a, int m) {
+    m &= 31;
+    if (m == 0) return a;
+    cdf r;
+    if (m == 16) { r.x = -a.x; r.y = -a.y; return r; }
+    if (m == 8) { if (INV) { r.x = -a.y; r.y = a.x; } else { r.x = a.y; r.y = -a.x; } return r; }
+    if (m == 24) { if (INV) { r.x = a.y; r.y = -a.x; } else { r.x = -a.y; r.y = a.x; } return r; }
+    const dfloat c(cos32(m));
+    const dfloat sn(INV ? sin32(m) : -sin32(m));
+    r.x = dot2_lazy(c, a.x, -sn, a.y);
+    r.y = dot2_lazy(c, a.y, sn, a.x);
+    return r;
+}
+template <int R, bool INV>
+struct Dft<R, INV, dfloat> {
+    __device__ __forceinline__ static void run(cdf (&s)[R]) {
+        constexpr int LG = R == 1 ? 0 : R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : R == 16 ? 4 : 5;
+        cdf t[R];
+        static_for<R>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            constexpr int j = bitrev_c(i, LG);
+            t[i] = s[j];
+        });
+#pragma unroll
+        for (int h = 1; h < R; h *= 2) {
+#pragma unroll
+            for (int g = 0; g < R; g += 2 * h) {
+#pragma unroll
+                for (int k = 0; k < h; ++k) {
+                    const cdf a = t[g + k];
+                    const cdf b = mul_w32_lazy<INV>(t[g + k + h], k * (16 / h));
+                    t[g + k].x = add_lazy(a.x, b.x);
+                    t[g + k].y = add_lazy(a.y, b.y);
+                    t[g + k + h].x = sub_lazy(a.x, b.x);
+                    t[g + k + h].y = sub_lazy(a.y, b.y);
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            s[i].x = renorm(t[i].x);
+            s[i].y = renorm(t[i].y);
+        }
+    }
+};
+
 __host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v / 2); }
 
 // Shared-memory index with one pad element per E elements (bank-conflict relief).

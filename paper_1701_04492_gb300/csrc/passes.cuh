@@ -1218,8 +1218,12 @@ template <typename T, int P2>
 __global__ void __launch_bounds__(256, 2) k_pass1(const __grid_constant__ PassArgs<T> a) {
     pass1_body<T, P2>(a, blockIdx.x, blockIdx.y);
 }
+// Two CTAs per SM for the FP64 row pass (its rank groups are sized for that); the FP32
+// one is left to the compiler (it stays below 128 registers).
+template <typename T> struct Pass2MinBlocks { static constexpr int v = 2; };
+template <> struct Pass2MinBlocks<float> { static constexpr int v = 1; };
 template <typename T, int P1, int KM>
-__global__ void __launch_bounds__(256) k_pass2(const __grid_constant__ PassArgs<T> a,
+__global__ void __launch_bounds__(256, Pass2MinBlocks<T>::v) k_pass2(const __grid_constant__ PassArgs<T> a,
                                                const __grid_constant__ Beta<T, KM> beta) {
     pass2_body<T, P1, KM>(a, beta, blockIdx.x);
 }
