@@ -131,9 +131,8 @@ __global__ void __launch_bounds__(256, 2) k_persist(const PState st, const ManyI
             PItem wq = w;
             wq.bx = w.bx + q;
             run_block<DIR>(a, &sb.b[0][0], wq, P, km);
-            // every thread's writes of this block; then the block's mbarriers, quiescent now
-            // (every copy was waited for), are invalidated before shared memory is reused
-            __threadfence();
+            // the block's mbarriers, quiescent now (every copy was waited for), are
+            // invalidated before shared memory is reused
             __syncthreads();
             if (threadIdx.x == 0 && w.kind == 1) {
                 if (DIR == 0) {
@@ -147,6 +146,12 @@ __global__ void __launch_bounds__(256, 2) k_persist(const PState st, const ManyI
                     mbar_inval(&mb[1]);
                 }
             }
+            __syncthreads();
+        }
+        // a first-pass item's writes are made visible GPU-wide by every thread before its
+        // count is published (the second pass reads them); a second-pass item has no reader
+        if (w.kind == 0) {
+            __threadfence();
             __syncthreads();
         }
         if (threadIdx.x == 0) {
