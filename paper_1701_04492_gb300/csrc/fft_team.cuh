@@ -12,8 +12,8 @@
 //   input layout : thread tt holds x[tt + TT m], m = 0..E-1      (strided by TT)
 //   output layout: register e holds X[out_index(tt, e)]
 //
-// Every thread of the CTA must call run() the same number of times (it uses
-// __syncthreads between stages); teams with no work run on a scratch slot.
+// Every thread of the CTA (of the warp, for warp-contained teams) must call run() the same
+// number of times (it synchronises between stages); teams with no work run on a scratch slot.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -280,6 +280,21 @@ template <typename T, int P, int KIND> __host__ __device__ constexpr int e_of() 
     return P < EmaxT<T, KIND>::v ? P : EmaxT<T, KIND>::v;
 }
 
+// The barrier between the stages of a team FFT.  WS: every team is a run of lanes inside
+// one warp (row passes with at most 32 threads per team), so the warp's own barrier orders
+// the team's shared-memory exchange; otherwise the whole CTA synchronises (column passes,
+// whose teams are spread across warps, and teams of more than one warp).
+template <bool WS>
+__device__ __forceinline__ void team_sync() {
+    if constexpr (WS) {
+        // the lanes that exist in this warp (a CTA of, say, 240 threads ends in a half warp)
+        const unsigned n = min(32u, blockDim.x - (threadIdx.x & ~31u));
+        __syncwarp(n == 32u ? 0xffffffffu : (1u << n) - 1u);
+    } else {
+        __syncthreads();
+    }
+}
+
 template <typename T, int P, int E, bool INV>
 struct TeamFft {
     static_assert(P % E == 0, "P must be a multiple of E");
@@ -380,7 +395,7 @@ struct TeamFft {
     // barriers.  Full rounds take PRED = false: stores guarded by a branch cost about a
     // quarter of a row pass's time, since the stage arithmetic can no longer be
     // scheduled around them.
-    template <int R, int NS, int Rn, bool PRED>
+    template <int R, int NS, int Rn, bool PRED, bool WS>
     __device__ __forceinline__ static void exchange(cx<T> (&a)[E], int tt, cx<T>* sm, bool act) {
         static_assert(NS == 1 || NS % E == 0, "later stages follow a radix-E stage");
 #pragma unroll
@@ -403,7 +418,7 @@ struct TeamFft {
                 }
             }
         }
-        __syncthreads();
+        team_sync<WS>();
         constexpr int Vn = P / Rn;
         static_assert(Vn % E == 0, "exchange strides are multiples of E");
 #pragma unroll
@@ -415,7 +430,7 @@ struct TeamFft {
 #pragma unroll
             for (int i = 0; i < Rn; ++i) a[b * Rn + i] = sm[padi_run<E, Vn>(pb, i)];
         }
-        __syncthreads();
+        team_sync<WS>();
     }
 
     // Padded shared index of output e after run() (out_index(tt, e) padded).
@@ -428,29 +443,30 @@ struct TeamFft {
 
     // tw: this length's stage table (TW_SIZE entries, forward exponent).
     // PRED with act = false: an idle team, which only meets the barriers.
-    template <bool PRED = false>
+    // WS: the teams are warp-contained (see team_sync).
+    template <bool PRED = false, bool WS = false>
     __device__ __forceinline__ static void run(cx<T> (&a)[E], int tt, cx<T>* sm,
                                                const cx<T>* __restrict__ tw, bool act = true) {
         stage<R0, 1, 0>(a, tt, tw);
         if constexpr (R1 > 1) {
-            exchange<R0, 1, R1, PRED>(a, tt, sm, act);
+            exchange<R0, 1, R1, PRED, WS>(a, tt, sm, act);
             stage<R1, R0, TW_OFF1>(a, tt, tw);
             if constexpr (R2 > 1) {
-                exchange<R1, R0, R2, PRED>(a, tt, sm, act);
+                exchange<R1, R0, R2, PRED, WS>(a, tt, sm, act);
                 stage<R2, R0 * R1, TW_OFF2>(a, tt, tw);
             }
         }
     }
 
     // run() with the stage twiddles already in registers (load_tw).
-    template <bool PRED = false>
+    template <bool PRED = false, bool WS = false>
     __device__ __forceinline__ static void run_reg(cx<T> (&a)[E], int tt, cx<T>* sm, const Tw& t, bool act = true) {
         stage<R0, 1, 0>(a, tt, nullptr);
         if constexpr (R1 > 1) {
-            exchange<R0, 1, R1, PRED>(a, tt, sm, act);
+            exchange<R0, 1, R1, PRED, WS>(a, tt, sm, act);
             stage_reg<R1, R0, 0>(a, t);
             if constexpr (R2 > 1) {
-                exchange<R1, R0, R2, PRED>(a, tt, sm, act);
+                exchange<R1, R0, R2, PRED, WS>(a, tt, sm, act);
                 stage_reg<R2, R0 * R1, NW1>(a, t);
             }
         }

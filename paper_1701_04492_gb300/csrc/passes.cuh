@@ -324,6 +324,7 @@ __device__ __forceinline__ void pass2_body(const PassArgs<T> &a, const BT &beta,
     constexpr int E = e_of<T, P1, PK_ROW_FWD>();
     using TF = TeamFft<T, P1, E, false>;
     constexpr int TT = TF::TT;
+    constexpr bool WS = TT <= 32;   // each team inside one warp: its FFT syncs the warp only
     cx<T> *smem = smem_base<T>();
     const int nt = blockDim.x / TT;
     const int team = threadIdx.x / TT, tt = threadIdx.x % TT;
@@ -367,9 +368,9 @@ __device__ __forceinline__ void pass2_body(const PassArgs<T> &a, const BT &beta,
             if (act) mbar_wait_bounded(&mbar[job], gi & 1, a.err, &cta_failed);
 #pragma unroll
             for (int m = 0; m < E; ++m) v[m] = act ? sm[tt + TT * m] : mk<T>(0, 0);   // row as copied
-            __syncthreads();   // the row is read before the transform reuses its slot
-            if constexpr (kTwReg<T>) TF::template run_reg<PRED>(v, tt, sm, twreg, act);
-            else TF::template run<PRED>(v, tt, sm, a.twr, act);
+            team_sync<WS>();   // the row is read before the transform reuses its slot
+            if constexpr (kTwReg<T>) TF::template run_reg<PRED, WS>(v, tt, sm, twreg, act);
+            else TF::template run<PRED, WS>(v, tt, sm, a.twr, act);
             if (act) {
 #pragma unroll
                 for (int e = 0; e < E; ++e) sm[TF::out_padded(tt, e)] = v[e];
@@ -553,6 +554,7 @@ __device__ __forceinline__ void passA_body(const PassArgs<T> &a, const BT &beta,
     constexpr int E = e_of<T, P1, PK_ROW_ADJ>();
     using TF = TeamFft<T, P1, E, true>;
     constexpr int TT = TF::TT;
+    constexpr bool WS = TT <= 32;   // each team inside one warp: its FFT rounds sync the warp only
     cx<T> *smem = smem_base<T>();
     const int nt = blockDim.x / TT;
     const int team = threadIdx.x / TT, tt = threadIdx.x % TT;
@@ -720,9 +722,9 @@ __device__ __forceinline__ void passA_body(const PassArgs<T> &a, const BT &beta,
             if (!one_row) fill_fourstep<T, E, TT>(a, n2, tt, ftab, 1);
             // the base twiddle w_L^{n2 tt}, loaded before the transform hides its latency
             const cx<T> base = one_row ? base1 : twiddle_L<T>(a, n2 * tt);
-            __syncthreads();
-            if constexpr (kTwReg<T>) TF::template run_reg<PRED>(v, tt, sm, twreg, act);
-            else TF::template run<PRED>(v, tt, sm, a.twr, act);
+            team_sync<WS>();
+            if constexpr (kTwReg<T>) TF::template run_reg<PRED, WS>(v, tt, sm, twreg, act);
+            else TF::template run<PRED, WS>(v, tt, sm, a.twr, act);
             if (act) {
                 // column-tiled layout for pass B: Y'_r[k1 / CQ][n2][k1 % CQ], so each
                 // CQ-column tile of a rank is one contiguous block
@@ -734,7 +736,7 @@ __device__ __forceinline__ void passA_body(const PassArgs<T> &a, const BT &beta,
                         cmulc<T>(v[e], cmul<T>(base, ftab[TF::out_q(e)]));
                 }
             }
-            __syncthreads();   // the next job may refill ftab
+            team_sync<WS>();   // the next job may refill the team's ftab
         };
         for (int j0 = 0; j0 < njobs; j0 += nt) {
             if (j0 + nt <= njobs) round(j0, std::false_type{});
