@@ -40,3 +40,23 @@ def test_reference_arm_other_ranks_exit_quietly():
                           "--warmup", "3"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
     assert res.returncode == 0, res.stderr[-2000:]
     assert not [ln for ln in res.stdout.splitlines() if ln.startswith("{")]
+
+
+def test_committed_traffic_follows_the_kernel_sources(monkeypatch):
+    """roofline.traffic is read from the committed in-step capture only while the kernel
+    sources hash as they did when it was taken; the figure is the pass's in-step DRAM bytes
+    per launch, a whole number of bytes, and unknown kernels give None."""
+    sys.path.insert(0, ROOT)
+    import bench
+    path = os.path.join(ROOT, "profiles", "ncu_step_kernels_n2e20.md")
+    txt = open(path).read()
+    recorded = txt.split("source_hash:")[1].split()[0]
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: recorded)
+    for k in ("pass1", "pass2", "passA", "passB"):
+        t = bench.committed_traffic(k)
+        assert t is not None and t == int(t) and 1e6 < t < 1e9, (k, t)
+    row = [ln for ln in txt.splitlines() if ln.startswith("| passA |")][0].split("|")
+    assert bench.committed_traffic("passA") == int(row[4])
+    assert bench.committed_traffic("nonexistent") is None
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
+    assert bench.committed_traffic("passA") is None
